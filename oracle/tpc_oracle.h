@@ -1,0 +1,110 @@
+/*
+ * tpc_oracle.h -- CPU oracle of the TPC cellular-automaton + Kalman tracker.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA tracker; both are written
+ * independently from the same written specification of the method.
+ *
+ * Method: cellular-automaton seeding + Kalman-filter track following and
+ * refit of the paper's section "TPC Tracking" (the combinatorial part is
+ * confined to seeding, one hypothesis per track is followed, later steps are
+ * linear), with continuous read-out handled as in section "Tracking" (time
+ * scaled linearly to z with the average drift velocity, primary-track
+ * assumption while seeding, later refit).
+ *
+ * Precision: every decision that produces an integer result (links, start
+ * hits, tracklet hit lists, ownership, merges) is taken in IEEE binary32 with
+ * an explicitly fixed operation order (fmaf where fused), exactly like the
+ * GPU.  The final refit is IEEE binary64.
+ */
+#ifndef TPC_ORACLE_H
+#define TPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    float dy_link, dz_link, s_max_link;   /* seeding windows (cm) and straightness cut (cm^2) */
+    float sigma_y, sigma_z;               /* cluster errors (cm) */
+    float c0_snp, c0_tgl, c0_qpt;         /* prior variances of sin(phi), tan(lambda), q/pT */
+    float win_nsigma, win_min, win_max;   /* following window: clamp(n*sigma, min, max) (cm) */
+    float chi2_cut;                       /* per-update chi2 cut while following (2 dof) */
+    int32_t max_miss;                     /* stop after this many consecutive empty rows */
+    int32_t min_hits;                     /* tracklet needs at least this many hits */
+    int32_t min_owned;                    /* selector: owned hits needed */
+    float edge_margin;                    /* stop following when |y| > x tan(10 deg) + margin */
+    float merge_dz, merge_chi2;           /* merger candidate window (cm) and chi2 (5 dof) cut */
+    int32_t refit_passes;                 /* Kalman refit passes, alternating direction */
+} orc_params;
+
+typedef struct {
+    int32_t n_sectors;      /* 36 (18 per side) or 1 (one 20 degree wedge spanning both z signs) */
+    int32_t n_rows;         /* pad rows */
+    const float *row_x;     /* [n_rows] row plane x (cm) */
+    float z_max;            /* drift length (cm) */
+    int32_t continuous;     /* 1: cluster carries drift time (us), 0: z (cm) */
+} orc_geom;
+
+/* Everything the oracle computes; arrays are malloc'ed by the oracle. */
+typedef struct {
+    int32_t n;
+    float *z;                 /* [n] z after time->z (cm) */
+    int32_t *up_raw, *dn_raw; /* [n] best link pair per hit (cluster index or -1) */
+    int32_t *up, *dn;         /* [n] mutual links after cleaning */
+    uint8_t *is_start;        /* [n] chain start flag */
+    /* tracklets: one per start hit, in ascending start cluster index */
+    int32_t n_tracklets;
+    int32_t *trk_start;       /* [nt] start cluster index */
+    int32_t *trk_nhits;       /* [nt] */
+    int32_t *trk_off;         /* [nt+1] offsets into trk_hits */
+    int32_t *trk_hits;        /* cluster indices, ascending row */
+    uint8_t *trk_kept;        /* [nt] selector verdict */
+    float *trk_top;           /* [nt][21]: x, p[5], c[15] at the outermost fitted hit */
+    float *trk_bot;           /* [nt][21]: x, p[5], c[15] at the innermost hit */
+    /* segments = kept tracklets (ascending start index) */
+    int32_t n_seg;
+    int32_t *seg_trk;         /* [ns] tracklet index */
+    int32_t *seg_next, *seg_prev;  /* [ns] merge links after the mutual-best rule, -1 none */
+    /* merged + refitted tracks, ordered by the start index of their innermost segment */
+    int32_t n_tracks;
+    int32_t *tr_sector;       /* [T] sector of the innermost cluster (frame of the output state) */
+    double *tr_x;             /* [T] */
+    double *tr_p;             /* [T][5] y, z, sin(phi), tan(lambda), q/pT */
+    double *tr_c;             /* [T][15] lower-triangular covariance */
+    double *tr_chi2;          /* [T] */
+    int32_t *tr_ndf;          /* [T] */
+    int32_t *tr_status;       /* [T] 0 ok, 1 refit propagation failed */
+    int32_t *tr_nclus;        /* [T] */
+    int32_t *tr_off;          /* [T+1] */
+    int32_t *tr_clus;         /* cluster indices inner -> outer */
+    int32_t *assign;          /* [n] track index or -1 */
+    float row_qup[256], row_qdn[256], row_w[256];
+} orc_result;
+
+void orc_params_default(orc_params *p);
+int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, int32_t n,
+              const uint8_t *sector, const uint8_t *row, const float *y, const float *zt,
+              orc_result *out);
+void orc_free(orc_result *r);
+
+/* single Kalman steps, exposed for the pins */
+int orc_prop32(float *st21, float x2, float kb);
+int orc_rot32(float *st21, float cs, float sn, float kb);
+int orc_update32(float *st21, float my, float mz, float vy, float vz, float chi2max, float *chi2);
+int orc_prop64(double *st21, double x2, double kb);
+int orc_rot64(double *st21, double cs, double sn, double kb);
+int orc_update64(double *st21, double my, double mz, double vy, double vz, double *chi2);
+/* FP64 multi-pass fit of a cluster list (inner -> outer); st21 in: initial
+ * state in the outermost cluster's frame, out: state at the innermost cluster */
+int orc_fit64(const orc_params *P, const orc_geom *G, double kb, int32_t n,
+              const int32_t *sector, const double *x, const double *y, const double *z,
+              int32_t n_passes, double *st21, double *chi2);
+float orc_merge_chi2(const float *top21, const float *bot21, float cs, float sn, float kb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
