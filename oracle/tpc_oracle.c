@@ -14,6 +14,17 @@
  * readings of a silent paper; this file follows them step by step, in the
  * order seeding -> following -> selection -> merging -> refit.
  *
+ * Pins (tests/test_oracle_*.py): propagation and rotation against exact
+ * helix crossings (forward and backward), Jacobians against finite
+ * differences, the update against the information form, the B = 0 fit
+ * against closed-form least squares, exact recovery of noise-free helices,
+ * pulls and chi2/ndf, the NeighboursFinder against an exhaustive search with
+ * exact binary32 emulation, hand-built link cases, efficiency / clone / fake
+ * rates against generator truth.  The exact decisions of the tracklet
+ * constructor, selector and merger have no worked example in the paper:
+ * beyond those statistical bars and structural invariants their parity is
+ * unpinned.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math (see build.py);
  * x86-64 evaluates float in binary32 (FLT_EVAL_METHOD 0), so every float
  * expression below is one correctly rounded binary32 operation and fmaf() is

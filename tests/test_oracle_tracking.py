@@ -1,0 +1,124 @@
+"""Tracking-level pins of the oracle: efficiency, clone and fake rates against
+generator truth on seeded events, and the structural invariants every output
+must satisfy.  The exact decisions of the tracklet constructor, selector and
+merger have no worked example in the paper; beyond these statistical bars and
+invariants their parity is unpinned (stated in the oracle header)."""
+import numpy as np
+import pytest
+
+import tpcgen
+from helpers import evaluate
+
+
+@pytest.fixture(scope="module")
+def sector_ev():
+    return tpcgen.one_sector(seed=1)
+
+
+@pytest.fixture(scope="module")
+def central_ev():
+    return tpcgen.central_event(seed=2, n_tracks=2000)
+
+
+@pytest.fixture(scope="module")
+def frame_ev():
+    return tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False)
+
+
+def _check_invariants(ev, r):
+    n = ev.n
+    # each cluster in at most one track; assign consistent with the lists
+    used = np.zeros(n, int)
+    for t in range(r.n_tracks):
+        cl = r.track_clusters(t)
+        used[cl] += 1
+        assert (r.assign[cl] == t).all()
+        assert r.tr_ndf[t] == 2 * cl.size - 5
+        assert r.tr_sector[t] == ev.sector[cl[0]]
+        if r.tr_status[t] == 0:
+            assert r.tr_x[t] == pytest.approx(float(ev.row_x[ev.row[cl[0]]]))
+        # inside each sector run rows ascend; consecutive runs are neighbours on one side
+        sec = ev.sector[cl].astype(int)
+        cut = np.where(sec[1:] != sec[:-1])[0] + 1
+        for run in np.split(np.arange(cl.size), cut):
+            assert np.all(np.diff(ev.row[cl[run]].astype(int)) > 0)
+        for a, b in zip(sec[cut - 1], sec[cut]):
+            assert a // 18 == b // 18 and (b - a) % 18 in (1, 17)
+    assert used.max() <= 1
+    assert ((r.assign >= 0) == (used == 1)).all()
+    # tracklets: distinct rows, ascending, all in the start's sector
+    for t in range(r.trk_start.size):
+        h = r.tracklet_hits(t)
+        assert h.size == r.trk_nhits[t]
+        assert np.all(np.diff(ev.row[h].astype(int)) > 0)
+        assert (ev.sector[h] == ev.sector[r.trk_start[t]]).all()
+        assert r.trk_start[t] in h
+    # selector: a kept tracklet owns >= 10 hits and at least half of its hits
+    weight = {}
+    for t in range(r.trk_start.size):
+        if r.trk_nhits[t] >= 10:
+            w = (int(r.trk_nhits[t]), -int(r.trk_start[t]))
+            for c in r.tracklet_hits(t):
+                weight[c] = max(weight.get(c, w), w)
+    for t in range(r.trk_start.size):
+        if r.trk_nhits[t] < 10:
+            assert not r.trk_kept[t]
+            continue
+        w = (int(r.trk_nhits[t]), -int(r.trk_start[t]))
+        own = sum(weight[c] == w for c in r.tracklet_hits(t))
+        assert bool(r.trk_kept[t]) == (own >= 10 and 2 * own >= r.trk_nhits[t])
+    # merge links are mutual
+    for a in range(r.seg_trk.size):
+        if r.seg_next[a] >= 0:
+            assert r.seg_prev[r.seg_next[a]] == a
+    # output order: ascending start index of the innermost segment
+    heads = [r.trk_start[r.seg_trk[a]] for a in range(r.seg_trk.size) if r.seg_prev[a] < 0]
+    assert heads == sorted(heads) and len(heads) == r.n_tracks
+
+
+def test_one_sector_quality(orc, sector_ev):
+    r = orc.track_event(sector_ev)
+    q = evaluate(sector_ev, r.tr_off, r.tr_clus)
+    assert q["findable"] > 80
+    assert q["eff"] >= 0.97 and q["fake"] <= 0.02 and q["clone"] <= 0.02, q
+    _check_invariants(sector_ev, r)
+
+
+def test_central_event_quality(orc, central_ev):
+    r = orc.track_event(central_ev)
+    q = evaluate(central_ev, r.tr_off, r.tr_clus)
+    assert q["findable"] > 1500
+    assert q["eff"] >= 0.97 and q["fake"] <= 0.02 and q["clone"] <= 0.03, q
+    assert (r.tr_status == 0).mean() > 0.99
+    ok = r.tr_status == 0
+    assert 0.9 < np.median(r.tr_chi2[ok] / r.tr_ndf[ok]) < 1.1
+    _check_invariants(central_ev, r)
+
+
+def test_time_frame_quality(orc, frame_ev):
+    """Continuous read-out with overlapping collisions and loopers: z from
+    drift time and the average drift velocity, seeding without knowledge of
+    the collision time (section "Tracking")."""
+    r = orc.track_event(frame_ev)
+    q = evaluate(frame_ev, r.tr_off, r.tr_clus)
+    assert q["findable"] > 1000
+    assert q["eff"] >= 0.97 and q["fake"] <= 0.02 and q["clone"] <= 0.03, q
+    _check_invariants(frame_ev, r)
+
+
+def test_links_independent_of_input_order(orc, sector_ev):
+    """Permuting the input clusters permutes the links and nothing else (ties
+    by index only matter for bitwise-identical clusters, absent here).  Track
+    sets may differ only where the selector breaks a tie between tracklets of
+    equal length by start index."""
+    ev = sector_ev
+    r = orc.track_event(ev)
+    perm = np.random.default_rng(3).permutation(ev.n)
+    inv = np.argsort(perm)
+    r2 = orc.track(ev.sector[perm], ev.row[perm], ev.y[perm], ev.zt[perm], ev.row_x, n_sectors=1)
+    for a, b in ((r2.up, r.up), (r2.dn, r.dn), (r2.up_raw, r.up_raw), (r2.dn_raw, r.dn_raw)):
+        mapped = np.where(a[inv] >= 0, perm[np.maximum(a[inv], 0)], -1)
+        np.testing.assert_array_equal(mapped, b)
+    sets1 = {tuple(sorted(r.track_clusters(t))) for t in range(r.n_tracks)}
+    sets2 = {tuple(sorted(perm[r2.track_clusters(t)])) for t in range(r2.n_tracks)}
+    assert len(sets1 & sets2) >= 0.9 * len(sets1)
