@@ -1,0 +1,166 @@
+/*
+ * tpc_track.h -- C ABI of the B300 TPC tracker (libtpcgpu.so).
+ *
+ * The library reconstructs tracks from TPC clusters on one GPU with the
+ * method of Rohr, Gorbunov, Schmidt, Shahoyan, "GPU-based Online Track
+ * Reconstruction for the ALICE TPC in Run 3 with Continuous Read-Out":
+ *   - section "Tracking", first two bullets: in the seeding phase the drift
+ *     time is scaled linearly to z with the average drift velocity and tracks
+ *     are assumed to come from the origin; a preliminary fit then finds the
+ *     full track and a later fit refines it;
+ *   - section "TPC Tracking": the combinatorial part is confined to a
+ *     cellular-automaton seeding (NeighboursFinder, NeighboursCleaner,
+ *     StartHitsFinder); one hypothesis per track is followed with a Kalman
+ *     filter (TrackletConstructor), overlapping candidates are resolved
+ *     (TrackletSelector), sector pieces are merged across sector boundaries
+ *     and refitted with several fit iterations.
+ *
+ * Conventions (all entry points):
+ *   - Pointers named "device" are CUDA device memory owned by the caller;
+ *     the library never frees them and never allocates device memory.
+ *   - All work is enqueued on the caller's stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).
+ *   - Return value: TPC_OK (0) or a negative TPC_ERR_* code; no exception
+ *     crosses the ABI.  tpc_error_string() names the code.
+ *   - Units: cm, microseconds, Tesla, GeV/c.
+ *   - Numerics: links, start hits, tracklet hit lists, ownership and merge
+ *     decisions are IEEE binary32 with a fixed operation order (bit-exact
+ *     against the CPU oracle); the refit is binary32 (optionally binary64 for
+ *     the final covariance update and chi2).
+ */
+#ifndef TPC_TRACK_H
+#define TPC_TRACK_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPC_OK 0
+#define TPC_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad geometry) */
+#define TPC_ERR_CAPACITY (-2)  /* workspace / output capacity too small; see the *_needed fields */
+#define TPC_ERR_TIMEOUT (-3)   /* a bounded device-side wait gave up */
+#define TPC_ERR_CUDA (-4)      /* a CUDA runtime call failed */
+#define TPC_ERR_DATA (-5)      /* a cluster has sector/row out of range or a non-finite coordinate */
+
+/* Method parameters.  tpc_params_default() fills the values of the reading
+ * used throughout (seeding windows, straightness cut, cluster errors,
+ * priors, following window and cuts, selector and merger cuts). */
+typedef struct {
+    float dy_link, dz_link;      /* NeighboursFinder windows (cm) around y*x_other/x_mid and z */
+    float s_max_link;            /* straightness cut: (chord deviation)^2 < s_max_link (cm^2) */
+    float sigma_y, sigma_z;      /* cluster position errors (cm) */
+    float c0_snp, c0_tgl, c0_qpt;/* prior variances of sin(phi), tan(lambda), q/pT */
+    float win_nsigma, win_min, win_max; /* following window clamp(n*sigma, min, max) (cm) */
+    float chi2_cut;              /* per-update chi2 cut while following (2 dof) */
+    int32_t max_miss;            /* stop following after this many consecutive empty rows */
+    int32_t min_hits;            /* tracklets shorter than this are dropped */
+    int32_t min_owned;           /* selector: owned hits a tracklet needs */
+    float edge_margin;           /* stop following when |y| > x tan(10 deg) + margin (cm) */
+    float merge_dz;              /* merger: |z_B - z_A| window before the chi2 test (cm) */
+    float merge_chi2;            /* merger: chi2 (5 dof) cut */
+    int32_t refit_passes;        /* refit passes, alternating inward / outward (odd: ends inward) */
+    /* acceleration structure and capacities (do not change results) */
+    float z_cell;                /* minimum grid cell length in z (cm); must exceed dz_link, win_max */
+    int32_t max_z_cells;         /* maximum grid cells per pad row */
+    int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
+    int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
+} tpc_params;
+
+/* Detector geometry (host memory). */
+typedef struct {
+    int32_t n_sectors;           /* 36 (sectors 0..17 at z > 0, 18..35 at z < 0) or 1 (one wedge, both z signs) */
+    int32_t n_rows;              /* pad rows, 3..255 */
+    const float *row_x;          /* host [n_rows]: local x of each pad-row plane (cm), increasing */
+    float z_max;                 /* drift length (cm) */
+    int32_t continuous;          /* 0: clusters carry z (cm); 1: drift time (us), z = s (z_max - v_drift t) */
+} tpc_geometry;
+
+/* Input clusters: device SoA, n entries each. */
+typedef struct {
+    int32_t n;
+    const uint8_t *sector;       /* device [n] */
+    const uint8_t *row;          /* device [n] */
+    const float *y;              /* device [n] sector-local y (cm) */
+    const float *zt;             /* device [n] z (cm) or drift time (us) */
+} tpc_clusters;
+
+/* Outputs: device arrays allocated by the caller with the stated capacities.
+ * Tracks are ordered by the input index of the start hit of their innermost
+ * sector piece; each track's state is at its innermost cluster, in the frame
+ * of that cluster's sector (alpha = (sector mod 18) * 20 + 10 degrees). */
+typedef struct {
+    int32_t capacity_tracks;     /* rows available in the per-track arrays */
+    int32_t capacity_clusters;   /* entries available in clus_index */
+    int32_t *sector;             /* [T] sector of the output frame */
+    float *x;                    /* [T] local x of the output state (cm) */
+    float *param;                /* [T][5] y, z, sin(phi), tan(lambda), q/pT */
+    float *cov;                  /* [T][15] lower-triangular covariance, row-major packed */
+    float *chi2;                 /* [T] chi2 of the last refit pass */
+    int32_t *ndf;                /* [T] 2 * nclus - 5 */
+    int32_t *status;             /* [T] 0 ok; 1 refit propagation failed (state at the failure point) */
+    int32_t *nclus;              /* [T] clusters of the track */
+    int32_t *clus_offset;        /* [T+1] offsets into clus_index */
+    int32_t *clus_index;         /* [capacity_clusters] input cluster indices, inner -> outer */
+    int32_t *assign;             /* [n] track index of each input cluster, -1 if unassigned */
+    double *cov64;               /* nullable [T][15]: binary64 covariance when fp64_final */
+    double *chi2_64;             /* nullable [T]: binary64 chi2 when fp64_final */
+    /* nullable intermediate results, indexed by input cluster (parity checks) */
+    float *z;                    /* [n] z after the time -> z conversion */
+    int32_t *link_up_raw, *link_dn_raw;   /* [n] NeighboursFinder best pair (input index or -1) */
+    int32_t *link_up, *link_dn;           /* [n] after NeighboursCleaner */
+    uint8_t *is_start;                    /* [n] StartHitsFinder flag */
+    /* filled on return (host-visible fields of this struct) */
+    int32_t n_tracks;
+    int32_t n_tracklets;
+    int32_t n_segments;
+    int64_t tracklets_needed;    /* on TPC_ERR_CAPACITY */
+    int64_t tracks_needed;
+    int64_t clusters_needed;
+} tpc_tracks;
+
+/* Fill *p with the default parameters.  Returns TPC_OK, or TPC_ERR_ARG for p == NULL. */
+int tpc_params_default(tpc_params *p);
+
+/* Bytes of device workspace tpc_track needs for n_clusters clusters with
+ * these parameters and geometry; written to *bytes.  Errors: TPC_ERR_ARG. */
+int tpc_workspace_size(const tpc_params *p, const tpc_geometry *g, int64_t n_clusters, size_t *bytes);
+
+/* Track one event or continuous read-out frame (sections "Tracking" and
+ * "TPC Tracking").  Inputs: cluster SoA (device), magnetic field bz (T)
+ * along z, average drift velocity v_drift (cm/us, used when
+ * g->continuous).  workspace: device buffer of ws_bytes >= tpc_workspace_size.
+ * The call enqueues the whole chain on `stream`, then waits for it
+ * (one device->host read of the counts) and fills out->n_tracks etc.
+ * Errors: TPC_ERR_ARG (bad arguments), TPC_ERR_DATA (bad cluster),
+ * TPC_ERR_CAPACITY (workspace or outputs too small: *_needed fields set),
+ * TPC_ERR_CUDA.  Output arrays beyond n_tracks are unspecified. */
+int tpc_track(const tpc_params *p, const tpc_geometry *g, float bz, float v_drift,
+              const tpc_clusters *cl, void *workspace, size_t ws_bytes, tpc_tracks *out,
+              void *stream);
+
+/* Export the tracklets of the last tpc_track call that used `workspace`
+ * (TrackletConstructor and TrackletSelector results, for parity checks).
+ * Host outputs, rows in ascending start-hit input index:
+ *   start[nt]  input index of the start hit;  nhits[nt];  kept[nt] (0/1);
+ *   hits[nt * hits_stride]  input indices in ascending row, unused entries -1
+ *                           (hits_stride >= n_rows);
+ *   top[nt * 21], bot[nt * 21]  x, p[5], c[15] right after the outermost
+ *                           fitted hit / at the innermost hit.
+ * capacity = rows available in the host arrays (0 with null arrays: only
+ * query the count); *nt_out receives the tracklet count.  Synchronises `stream`, then reads the workspace with blocking copies.
+ * Errors: TPC_ERR_ARG (null pointer, workspace not written by tpc_track,
+ * hits_stride too small), TPC_ERR_CAPACITY (capacity < tracklet count; *nt_out
+ * is set), TPC_ERR_CUDA. */
+int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_stride, int32_t *start,
+                         int32_t *nhits, uint8_t *kept, int32_t *hits, float *top, float *bot,
+                         int32_t *nt_out, void *stream);
+
+/* Human-readable name of a return code (static string). */
+const char *tpc_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1190 @@
+// tpc_track.cu -- B300 TPC tracker: binning, cellular-automaton seeding,
+// tracklet construction and selection, cross-sector merging, track assembly
+// and the C-ABI entry points (include/tpc_track.h).
+//
+// Compiled with -fmad=false: every binary32 decision (links, start hits,
+// tracklet hits, ownership, merges) follows the fixed operation order of the
+// method's specification and is bit-identical to any IEEE implementation of
+// it.
+#include "tpc_dev.cuh"
+#include "tpc_track.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace tpc;
+
+namespace {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+constexpr int MAX_MERGE_CELLS = 4096;
+constexpr int MAX_CHAIN = 36;
+constexpr int ROWTAB = 4;   // X, q_up, q_dn, w per row
+constexpr uint32_t WS_MAGIC = 0x54504331u;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// workspace layout (byte offsets from the workspace base)
+// ---------------------------------------------------------------------------
+struct Layout {
+    uint32_t magic;
+    int32_t n, ns, nr, np, nzmax, ntcap, mnzmax;
+    int64_t ncells;
+    size_t hdr, frame, rowtab, zlin, cell, slot, cstart, scan, ys, zs, ids, plane;
+    size_t upr, dnr, up, dn, starts;
+    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
+    size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
+    size_t bnext, bprev, snext, sprev, bad, next2, prev2;
+    size_t headmark, tcount, thead, ttail;
+    size_t total;
+};
+
+int64_t scan_aux_elems(int64_t n)
+{
+    int64_t s = 0;
+    while (n > 1) {
+        n = (n + SCAN_TILE - 1) / SCAN_TILE;
+        s += n + 1;
+    }
+    return s + 16;
+}
+
+Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    L.magic = WS_MAGIC;
+    L.n = (int32_t)n;
+    L.ns = g->n_sectors;
+    L.nr = g->n_rows;
+    L.np = L.ns * L.nr;
+    L.nzmax = p->max_z_cells;
+    L.ncells = (int64_t)L.np * L.nzmax;
+    int64_t cap = std::max<int64_t>(4096, (n * (int64_t)p->tracklets_per_1k) / 1000);
+    L.ntcap = (int32_t)std::min<int64_t>(cap, std::max<int64_t>(n, 4096));
+    L.mnzmax = MAX_MERGE_CELLS;
+    const int64_t N = std::max<int64_t>(n, 1);
+    const int64_t T = L.ntcap;
+    const int64_t mcells = (int64_t)L.ns * L.mnzmax;
+    int64_t scan_max = std::max({L.ncells + 1, N + 1, T + 1, mcells + 1});
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1), 256); return r; };
+    L.hdr = take(sizeof(Layout));
+    L.frame = take(sizeof(Frame));
+    L.rowtab = take(sizeof(float) * ROWTAB * 256);
+    L.zlin = take(4 * N);
+    L.cell = take(4 * N);
+    L.slot = take(4 * N);
+    L.cstart = take(4 * (L.ncells + 1));
+    L.scan = take(4 * scan_aux_elems(scan_max));
+    L.ys = take(4 * N);
+    L.zs = take(4 * N);
+    L.ids = take(4 * N);
+    L.plane = take(2 * N);
+    L.upr = take(4 * N);
+    L.dnr = take(4 * N);
+    L.up = take(4 * N);
+    L.dn = take(4 * N);
+    L.starts = take(4 * T);
+    L.t_start = take(4 * T);
+    L.t_id = take(4 * T);
+    L.t_nhits = take(4 * T);
+    L.t_nup = take(4 * T);
+    L.t_hits = take(4 * T * (size_t)L.nr);
+    L.t_top = take(4 * T * NST);
+    L.t_bot = take(4 * T * NST);
+    L.hitw = take(8 * N);
+    L.t_kept = take(T);
+    L.seg = take(4 * T);
+    L.keyb = take(4 * T);
+    L.keyt = take(4 * T);
+    L.slotb = take(4 * T);
+    L.slott = take(4 * T);
+    L.cntb = take(4 * (mcells + 1));
+    L.cntt = take(4 * (mcells + 1));
+    L.byb = take(4 * T);
+    L.byt = take(4 * T);
+    L.bnext = take(4 * T);
+    L.bprev = take(4 * T);
+    L.snext = take(4 * T);
+    L.sprev = take(4 * T);
+    L.bad = take(T);
+    L.next2 = take(4 * T);
+    L.prev2 = take(4 * T);
+    L.headmark = take(4 * (N + 1));
+    L.tcount = take(4 * (T + 1));
+    L.thead = take(4 * T);
+    L.ttail = take(4 * T);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+int grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 16));
+}
+
+// ---------------------------------------------------------------------------
+// generic exclusive scan (in place), total written at a[n]
+// ---------------------------------------------------------------------------
+__global__ void k_scan_tiles(uint32_t* a, int64_t n, uint32_t* sums)
+{
+    __shared__ uint32_t sh[SCAN_BLOCK];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        v[k] = (base + k < n) ? a[base + k] : 0u;
+        s += v[k];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+        uint32_t t = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = sh[threadIdx.x] - s;   // exclusive prefix of this thread
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        if (base + k < n) a[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == SCAN_BLOCK - 1) sums[blockIdx.x] = sh[SCAN_BLOCK - 1];
+}
+
+__global__ void k_scan_add(uint32_t* a, int64_t n, const uint32_t* sums)
+{
+    const uint32_t add = sums[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_BLOCK)
+        if (base + k < n) a[base + k] += add;
+}
+
+// exclusive scan of a[0..n), total stored in a[n]; aux holds the tile sums
+void scan_u32(uint32_t* a, int64_t n, uint32_t* aux, cudaStream_t st)
+{
+    const int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;    // include the total slot
+    // a[n] must be 0 on entry so that the scan of n+1 entries leaves the total there
+    k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+    if (tiles > 1) {
+        scan_u32(aux, tiles - 1, aux + tiles + 1, st);   // aux[tiles-1] becomes the last exclusive offset
+        k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2: time -> z, validation, folded-z extrema; grid histogram / scatter
+// ---------------------------------------------------------------------------
+__global__ void k_init_frame(Frame* f)
+{
+    if (threadIdx.x == 0) {
+        memset(f, 0, sizeof(Frame));
+        f->zmin_key = 0xFFFFFFFFu;
+        f->zmax_key = 0u;
+    }
+}
+
+__global__ void k_prep(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
+                       const float* __restrict__ y, const float* __restrict__ zt, int ns, int nr, int continuous,
+                       float zmax, float vdrift, float* __restrict__ zlin, Frame* f)
+{
+    unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
+    int bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = sector[i], r = row[i];
+        float z = zt[i];
+        if (continuous) {
+            const float zl = zmax - vdrift * z;
+            z = (ns == 36 && s >= 18) ? -zl : zl;
+        }
+        zlin[i] = z;
+        const bool ok = s < ns && r < nr && isfinite(z) && isfinite(y[i]);
+        if (!ok) {
+            bad++;
+            continue;
+        }
+        const float zeta = (ns == 36 && s >= 18) ? -z : z;
+        const unsigned k = fkey(zeta);
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+    }
+    // warp then block reduction
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&f->zmin_key, kmin);
+        atomicMax(&f->zmax_key, kmax);
+        if (bad) {
+            atomicAdd(&f->n_bad, bad);
+            atomicExch(&f->err, TPC_ERR_DATA);
+        }
+    }
+}
+
+__global__ void k_grid_setup(Frame* f, float z_cell, int nzmax, float merge_cell, int mnzmax)
+{
+    if (threadIdx.x != 0) return;
+    float zmin = 0.0f, span = 0.0f;
+    if (f->zmin_key != 0xFFFFFFFFu) {
+        zmin = fkey_inv(f->zmin_key);
+        span = fkey_inv(f->zmax_key) - zmin;
+    }
+    float cs = fmaxf(z_cell, span / (float)(nzmax - 1) * 1.001f);
+    f->zmin = zmin;
+    f->inv_cs = 1.0f / cs;
+    f->nz = min(nzmax, (int)(span / cs) + 1);
+    float mcs = fmaxf(merge_cell, span / (float)(mnzmax - 1) * 1.001f);
+    f->mzmin = zmin;
+    f->minv_cs = 1.0f / mcs;
+    f->mnz = min(mnzmax, (int)(span / mcs) + 1);
+}
+
+__device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
+
+__global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
+                       const float* __restrict__ zlin, int nr, int ns, const Frame* __restrict__ f,
+                       uint32_t* __restrict__ count, uint32_t* __restrict__ cell, uint32_t* __restrict__ slot)
+{
+    if (f->err) return;   // invalid clusters: nothing after validation runs
+    const float zmin = f->zmin, inv = f->inv_cs;
+    const int nz = f->nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = sector[i], r = row[i];
+        const int pl = s * nr + r;
+        const uint32_t c = (uint32_t)pl * (uint32_t)nz + (uint32_t)grid_cell(fold(zlin[i], s, ns), zmin, inv, nz);
+        cell[i] = c;
+        slot[i] = atomicAdd(&count[c], 1u);
+    }
+}
+
+__global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
+                          const float* __restrict__ y, const float* __restrict__ zlin, int nr,
+                          const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
+                          const uint32_t* __restrict__ slot, float* __restrict__ ys, float* __restrict__ zs,
+                          int32_t* __restrict__ ids, uint16_t* __restrict__ plane, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t pos = cstart[cell[i]] + slot[i];
+        ys[pos] = y[i];
+        zs[pos] = zlin[i];
+        ids[pos] = i;
+        plane[pos] = (uint16_t)(sector[i] * nr + row[i]);
+    }
+}
+
+// sorted-index range of cells c-1 .. c+1 of one plane
+struct Range {
+    int b, e;
+};
+__device__ __forceinline__ Range cell_range(const uint32_t* __restrict__ cstart, int plane, int c, int nz)
+{
+    const int lo = max(c - 1, 0), hi = min(c + 1, nz - 1);
+    Range r;
+    r.b = (int)cstart[(int64_t)plane * nz + lo];
+    r.e = (int)cstart[(int64_t)plane * nz + hi + 1];
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// a3: NeighboursFinder (one thread per sorted hit)
+// ---------------------------------------------------------------------------
+constexpr int MAXD = 8;
+
+__global__ void __launch_bounds__(256) k_neighbours(
+    int n, int nr, int ns, const float* __restrict__ rowtab, const float* __restrict__ ys,
+    const float* __restrict__ zs, const int32_t* __restrict__ ids, const uint16_t* __restrict__ plane,
+    const uint32_t* __restrict__ cstart, const Frame* __restrict__ f, float DY, float DZ, float SMAX,
+    int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
+{
+    if (f->err) return;
+    const float zmin = f->zmin, inv = f->inv_cs;
+    const int nz = f->nz;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        const int pl = plane[h];
+        const int s = pl / nr, r = pl - s * nr;
+        int bu = -1, bd = -1, bidu = 0, bidd = 0;
+        float bs = 0.0f;
+        if (r >= 1 && r <= nr - 2) {
+            const float yh = ys[h], zh = zs[h];
+            const float yu_pred = yh * rowtab[r * ROWTAB + 1];
+            const float yd_pred = yh * rowtab[r * ROWTAB + 2];
+            const float w = rowtab[r * ROWTAB + 3];
+            const int c = grid_cell(fold(zh, s, ns), zmin, inv, nz);
+            const Range ru = cell_range(cstart, pl + 1, c, nz);
+            const Range rd = cell_range(cstart, pl - 1, c, nz);
+            // down candidates inside the windows
+            int dl[MAXD];
+            int ndn = 0;
+            bool overflow = false;
+            for (int q = rd.b; q < rd.e; q++) {
+                if (fabsf(ys[q] - yd_pred) <= DY && fabsf(zs[q] - zh) <= DZ) {
+                    if (ndn < MAXD) dl[ndn++] = q;
+                    else overflow = true;
+                }
+            }
+            if (ndn > 0) {
+                for (int u = ru.b; u < ru.e; u++) {
+                    const float yu = ys[u], zu = zs[u];
+                    if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
+                    const int idu = ids[u];
+                    auto consider = [&](int d) {
+                        const float yd = ys[d], zd = zs[d];
+                        const float ey = __fmaf_rn(yu - yd, w, yd) - yh;
+                        const float ez = __fmaf_rn(zu - zd, w, zd) - zh;
+                        const float sc = __fmaf_rn(ey, ey, ez * ez);
+                        if (!(sc < SMAX)) return;
+                        const int idd = ids[d];
+                        if (bu < 0 || sc < bs || (sc == bs && (idu < bidu || (idu == bidu && idd < bidd)))) {
+                            bu = u; bd = d; bs = sc; bidu = idu; bidd = idd;
+                        }
+                    };
+                    if (!overflow) {
+                        for (int k = 0; k < ndn; k++) consider(dl[k]);
+                    } else {
+                        for (int d = rd.b; d < rd.e; d++)
+                            if (fabsf(ys[d] - yd_pred) <= DY && fabsf(zs[d] - zh) <= DZ) consider(d);
+                    }
+                }
+            }
+        }
+        upr[h] = bu;
+        dnr[h] = bd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4 NeighboursCleaner, a5 StartHitsFinder
+// ---------------------------------------------------------------------------
+__global__ void k_clean(int n, const int32_t* __restrict__ upr, const int32_t* __restrict__ dnr,
+                        int32_t* __restrict__ up, int32_t* __restrict__ dn, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        const int u = upr[h], d = dnr[h];
+        up[h] = (u >= 0 && dnr[u] == h) ? u : -1;
+        dn[h] = (d >= 0 && upr[d] == h) ? d : -1;
+    }
+}
+
+__global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* __restrict__ dn,
+                         int32_t* __restrict__ starts, int cap, Frame* f)
+{
+    if (f->err) return;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int h = base + threadIdx.x;
+        bool is = false;
+        if (h < n) {
+            const int u = up[h];
+            is = u >= 0 && dn[h] < 0 && up[u] >= 0;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, is);
+        int pos0 = 0;
+        const int lane = threadIdx.x & 31;
+        if (lane == 0 && mask) pos0 = atomicAdd(&f->n_starts, __popc(mask));
+        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+        if (is) {
+            const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
+            if (pos < cap) starts[pos] = h;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6: TrackletConstructor (one thread per start hit)
+// ---------------------------------------------------------------------------
+struct TrkArgs {
+    const float* rowtab;
+    const float* ys;
+    const float* zs;
+    const int32_t* ids;
+    const uint16_t* plane;
+    const uint32_t* cstart;
+    const int32_t* up;
+    const int32_t* starts;
+    const Frame* f;
+    int nr, ns, cap;
+    float kb, vy, vz, c0s, c0t, c0q, nsig, wmin, wmax, chi2cut, edge;
+    int max_miss;
+    int32_t *t_start, *t_id, *t_nhits, *t_nup, *t_hits;
+    float *t_top, *t_bot;
+};
+
+__device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int s, float yp, float zp, float wy, float wz,
+                                            float zmin, float inv, int nz)
+{
+    const int c = grid_cell(fold(zp, s, A.ns), zmin, inv, nz);
+    const Range rg = cell_range(A.cstart, pl, c, nz);
+    int best = -1, bid = 0;
+    float bd = 0.0f;
+    for (int q = rg.b; q < rg.e; q++) {
+        const float dy = A.ys[q] - yp;
+        const float dz = A.zs[q] - zp;
+        if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
+        const float d2 = __fmaf_rn(dy, dy, dz * dz);
+        const int id = A.ids[q];
+        if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
+            best = q; bd = d2; bid = id;
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ void copy_state(float* d, const float* s)
+{
+#pragma unroll
+    for (int i = 0; i < NST; i++) d[i] = s[i];
+}
+
+__global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
+{
+    if (A.f->err) return;
+    const float zmin = A.f->zmin, inv = A.f->inv_cs;
+    const int nz = A.f->nz;
+    const int nt = min(A.f->n_starts, A.cap);
+    const float INF = __int_as_float(0x7f800000);
+    const int NR = A.nr;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int h1 = A.starts[t];
+        const int pl1 = A.plane[h1];
+        const int s = pl1 / NR, r1 = pl1 - s * NR;
+        const int pbase = s * NR;
+        const int h2 = A.up[h1];
+        float st[NST], keep[NST];
+        const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
+        const float dx12 = x2 - x1;
+        const float y1 = A.ys[h1], z1 = A.zs[h1];
+        const float dy12 = A.ys[h2] - y1, dz12 = A.zs[h2] - z1;
+        const float ty = __fdiv_rn(dy12, dx12);
+        const float sp = __fdiv_rn(ty, __fsqrt_rn(__fmaf_rn(ty, ty, 1.0f)));
+        const float dl12 = __fsqrt_rn(__fmaf_rn(dx12, dx12, dy12 * dy12));
+        const float tl = __fdiv_rn(dz12, dl12);
+#pragma unroll
+        for (int i = 0; i < NST; i++) st[i] = 0.0f;
+        st[0] = x1; st[1] = y1; st[2] = z1; st[3] = sp; st[4] = tl; st[5] = 0.0f;
+        st[6 + 0] = A.vy; st[6 + 2] = A.vz; st[6 + 5] = A.c0s; st[6 + 9] = A.c0t; st[6 + 14] = A.c0q;
+        int32_t* slot = A.t_hits + (int64_t)t * NR;
+        int nu = 0, nd = 0;
+        slot[nu++] = h1;
+        copy_state(keep, st);
+        int rc = r1;
+        bool ok = true;
+        // phase A: fit along the up links
+        for (int hc = h1; A.up[hc] >= 0;) {
+            const int hn = A.up[hc];
+            const int rn = A.plane[hn] - pbase;
+            if (!prop32(st, A.rowtab[rn * ROWTAB], A.kb)) { ok = false; break; }
+            rc = rn;
+            update32(st, A.ys[hn], A.zs[hn], A.vy, A.vz, INF);
+            slot[nu++] = hn;
+            copy_state(keep, st);
+            hc = hn;
+        }
+        // phase B: follow row by row beyond the chain end
+        if (ok) {
+            int miss = 0;
+            for (int r = rc + 1; r < NR; r++) {
+                if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
+                rc = r;
+                if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
+                const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
+                const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
+                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz);
+                if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                    slot[nu++] = c;
+                    copy_state(keep, st);
+                    miss = 0;
+                } else if (++miss >= A.max_miss) {
+                    break;
+                }
+            }
+        }
+        float* top = A.t_top + (int64_t)t * NST;
+#pragma unroll
+        for (int i = 0; i < NST; i++) top[i] = keep[i];
+        // phase C: back down through the fitted rows, then follow below the start
+        if (rc == r1) copy_state(keep, st);
+        {
+            int miss = 0;
+            for (int r = rc - 1; r >= 0; r--) {
+                if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
+                if (r > r1) continue;
+                if (r == r1) { copy_state(keep, st); continue; }
+                if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
+                const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
+                const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
+                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz);
+                if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                    nd++;
+                    slot[NR - nd] = c;
+                    copy_state(keep, st);
+                    miss = 0;
+                } else if (++miss >= A.max_miss) {
+                    break;
+                }
+            }
+        }
+        float* bot = A.t_bot + (int64_t)t * NST;
+#pragma unroll
+        for (int i = 0; i < NST; i++) bot[i] = keep[i];
+        A.t_start[t] = h1;
+        A.t_id[t] = A.ids[h1];
+        A.t_nhits[t] = nu + nd;
+        A.t_nup[t] = nu;
+    }
+}
+
+// k-th hit (ascending row) of tracklet t
+__device__ __forceinline__ int trk_hit(const int32_t* slot, int nr, int nhits, int nup, int k)
+{
+    const int nd = nhits - nup;
+    return k < nd ? slot[nr - nd + k] : slot[k - nd];
+}
+
+// ---------------------------------------------------------------------------
+// a7: TrackletSelector
+// ---------------------------------------------------------------------------
+__global__ void k_sel_weight(const Frame* __restrict__ f, int cap, int nr, int min_hits, const int32_t* __restrict__ t_id,
+                             const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
+                             const int32_t* __restrict__ t_hits, unsigned long long* __restrict__ hitw)
+{
+    const int nt = min(f->n_starts, cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int nh = t_nhits[t];
+        if (nh < min_hits) continue;
+        const unsigned long long w = tracklet_weight(nh, t_id[t]);
+        const int32_t* slot = t_hits + (int64_t)t * nr;
+        const int nup = t_nup[t];
+        for (int k = 0; k < nh; k++) atomicMax(&hitw[trk_hit(slot, nr, nh, nup, k)], w);
+    }
+}
+
+__global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned, const int32_t* __restrict__ t_id,
+                          const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
+                          const int32_t* __restrict__ t_hits, const unsigned long long* __restrict__ hitw,
+                          uint8_t* __restrict__ kept, int32_t* __restrict__ seg)
+{
+    const int nt = min(f->n_starts, cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int nh = t_nhits[t];
+        uint8_t k = 0;
+        if (nh >= min_hits) {
+            const unsigned long long w = tracklet_weight(nh, t_id[t]);
+            const int32_t* slot = t_hits + (int64_t)t * nr;
+            const int nup = t_nup[t];
+            int own = 0;
+            for (int q = 0; q < nh; q++) own += hitw[trk_hit(slot, nr, nh, nup, q)] == w;
+            if (own >= min_owned && 2 * own >= nh) {
+                k = 1;
+                seg[atomicAdd(&f->n_seg, 1)] = t;
+            }
+        }
+        kept[t] = k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: cross-sector merger
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
+{
+    return grid_cell(zeta, f->mzmin, f->minv_cs, f->mnz);
+}
+
+__global__ void k_seg_keys(const Frame* __restrict__ f, int ns, const int32_t* __restrict__ seg,
+                           const uint16_t* __restrict__ plane, const int32_t* __restrict__ t_start, int nr,
+                           const float* __restrict__ t_top, const float* __restrict__ t_bot,
+                           uint32_t* __restrict__ cntb, uint32_t* __restrict__ cntt, uint32_t* __restrict__ keyb,
+                           uint32_t* __restrict__ keyt, uint32_t* __restrict__ slotb, uint32_t* __restrict__ slott)
+{
+    const int nseg = f->n_seg;
+    const int mnz = f->mnz;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        const int t = seg[a];
+        const int s = plane[t_start[t]] / nr;
+        const uint32_t kb = (uint32_t)s * mnz + merge_cell(fold(t_bot[(int64_t)t * NST + 2], s, ns), f);
+        const uint32_t kt = (uint32_t)s * mnz + merge_cell(fold(t_top[(int64_t)t * NST + 2], s, ns), f);
+        keyb[a] = kb;
+        keyt[a] = kt;
+        slotb[a] = atomicAdd(&cntb[kb], 1u);
+        slott[a] = atomicAdd(&cntt[kt], 1u);
+    }
+}
+
+__global__ void k_seg_scatter(const Frame* __restrict__ f, const uint32_t* __restrict__ cntb,
+                              const uint32_t* __restrict__ cntt, const uint32_t* __restrict__ keyb,
+                              const uint32_t* __restrict__ keyt, const uint32_t* __restrict__ slotb,
+                              const uint32_t* __restrict__ slott, int32_t* __restrict__ byb, int32_t* __restrict__ byt)
+{
+    const int nseg = f->n_seg;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        byb[cntb[keyb[a]] + slotb[a]] = a;
+        byt[cntt[keyt[a]] + slott[a]] = a;
+    }
+}
+
+struct MergeArgs {
+    const Frame* f;
+    int ns, nr;
+    float kb, dz, chi2cut;
+    const int32_t* seg;
+    const uint16_t* plane;
+    const int32_t* t_start;
+    const int32_t* t_id;
+    const float* t_top;
+    const float* t_bot;
+    const uint32_t* cntb;   // scanned
+    const uint32_t* cntt;
+    const int32_t* byb;
+    const int32_t* byt;
+    int32_t* bnext;
+    int32_t* bprev;
+};
+
+__device__ __forceinline__ int seg_sector(const MergeArgs& M, int a) { return M.plane[M.t_start[M.seg[a]]] / M.nr; }
+
+// best B (outer piece) for every A: A's outer end against B's inner end
+__global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
+{
+    const int nseg = M.f->n_seg, mnz = M.f->mnz;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        const int ta = M.seg[a];
+        const int sa = seg_sector(M, a);
+        float top[NST];
+#pragma unroll
+        for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
+        const int mc = merge_cell(fold(top[2], sa, M.ns), M.f);
+        int best = -1, bid = 0;
+        float bc = 0.0f;
+        for (int dir = 1; dir >= -1; dir -= 2) {
+            const int sb = neighbour_sector(sa, dir, M.ns);
+            if (sb < 0) continue;
+            const float sn = dir > 0 ? SIN20 : -SIN20;
+            const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
+            const int qb = M.cntb[sb * mnz + lo], qe = M.cntb[sb * mnz + hi + 1];
+            for (int q = qb; q < qe; q++) {
+                const int b = M.byb[q];
+                const int tb = M.seg[b];
+                const float* bot = M.t_bot + (int64_t)tb * NST;
+                if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
+                const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
+                if (!(c2 < M.chi2cut)) continue;
+                const int idb = M.t_id[tb];
+                if (best < 0 || c2 < bc || (c2 == bc && idb < bid)) { best = b; bc = c2; bid = idb; }
+            }
+        }
+        M.bnext[a] = best;
+    }
+}
+
+// best A (inner piece) for every B
+__global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
+{
+    const int nseg = M.f->n_seg, mnz = M.f->mnz;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+        const int tb = M.seg[b];
+        const int sb = seg_sector(M, b);
+        float bot[NST];
+#pragma unroll
+        for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
+        const int mc = merge_cell(fold(bot[2], sb, M.ns), M.f);
+        int best = -1, bid = 0;
+        float bc = 0.0f;
+        for (int d = 1; d >= -1; d -= 2) {
+            const int sa = neighbour_sector(sb, d, M.ns);
+            if (sa < 0) continue;
+            // seen from A, B lies in direction -d
+            const float sn = (-d) > 0 ? SIN20 : -SIN20;
+            const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
+            const int qb = M.cntt[sa * mnz + lo], qe = M.cntt[sa * mnz + hi + 1];
+            for (int q = qb; q < qe; q++) {
+                const int a = M.byt[q];
+                const int ta = M.seg[a];
+                const float* top = M.t_top + (int64_t)ta * NST;
+                if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
+                const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
+                if (!(c2 < M.chi2cut)) continue;
+                const int ida = M.t_id[ta];
+                if (best < 0 || c2 < bc || (c2 == bc && ida < bid)) { best = a; bc = c2; bid = ida; }
+            }
+        }
+        M.bprev[b] = best;
+    }
+}
+
+__global__ void k_merge_link(const Frame* __restrict__ f, const int32_t* __restrict__ bnext,
+                             const int32_t* __restrict__ bprev, int32_t* __restrict__ snext, int32_t* __restrict__ sprev)
+{
+    const int nseg = f->n_seg;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        const int b = bnext[a];
+        if (b >= 0 && bprev[b] == a) {
+            snext[a] = b;
+            sprev[b] = a;
+        }
+    }
+}
+
+__global__ void k_merge_cycles(const Frame* __restrict__ f, const int32_t* __restrict__ sprev, uint8_t* __restrict__ bad)
+{
+    const int nseg = f->n_seg;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        int c = a, steps = 0;
+        while (sprev[c] >= 0 && steps <= MAX_CHAIN) { c = sprev[c]; steps++; }
+        bad[a] = sprev[c] >= 0 ? 1 : 0;
+    }
+}
+
+__global__ void k_merge_fix(const Frame* __restrict__ f, const int32_t* __restrict__ snext,
+                            const int32_t* __restrict__ sprev, const uint8_t* __restrict__ bad,
+                            int32_t* __restrict__ next2, int32_t* __restrict__ prev2, const int32_t* __restrict__ seg,
+                            const int32_t* __restrict__ t_id, uint32_t* __restrict__ headmark)
+{
+    const int nseg = f->n_seg;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        int nx = snext[a], pv = sprev[a];
+        if (bad[a]) { nx = -1; pv = -1; }
+        if (nx >= 0 && bad[nx]) nx = -1;
+        if (pv >= 0 && bad[pv]) pv = -1;
+        next2[a] = nx;
+        prev2[a] = pv;
+        if (pv < 0) headmark[t_id[seg[a]]] = 1u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// track assembly: rank of each chain head, cluster counts, cluster lists
+// ---------------------------------------------------------------------------
+struct AsmArgs {
+    Frame* f;
+    int nr, n, cap_tracks, cap_clus, ntcap;
+    const int32_t* seg;
+    const int32_t* next2;
+    const int32_t* prev2;
+    const int32_t* t_id;
+    const int32_t* t_nhits;
+    const int32_t* t_nup;
+    const int32_t* t_hits;
+    const int32_t* ids;
+    const unsigned long long* hitw;
+    const uint32_t* headmark;   // scanned: rank of each head's start id
+    uint32_t* tcount;           // [ntcap + 1]
+    int32_t* thead;
+    int32_t* ttail;
+    int32_t* clus_offset;
+    int32_t* nclus;
+    int32_t* clus_index;
+    int32_t* assign;
+};
+
+__global__ void k_track_count(AsmArgs A)
+{
+    const int nseg = A.f->n_seg;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+        if (A.prev2[a] >= 0) continue;
+        const int rank = (int)A.headmark[A.t_id[A.seg[a]]];
+        int cnt = 0, tail = a, steps = 0;
+        for (int b = a; b >= 0 && steps <= MAX_CHAIN; b = A.next2[b], steps++) {
+            const int t = A.seg[b];
+            const int nh = A.t_nhits[t], nup = A.t_nup[t];
+            const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
+            const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
+            for (int k = 0; k < nh; k++) cnt += A.hitw[trk_hit(slot, A.nr, nh, nup, k)] == w;
+            tail = b;
+        }
+        A.tcount[rank] = (uint32_t)cnt;
+        A.thead[rank] = a;
+        A.ttail[rank] = A.seg[tail];
+    }
+}
+
+__global__ void k_track_fill(AsmArgs A)
+{
+    const int T = (int)A.headmark[A.n];
+    const uint32_t total = A.tcount[A.ntcap];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.f->n_tracks = T;
+        A.f->n_clus = (int)total;
+        if (T > A.cap_tracks || total > (uint32_t)A.cap_clus) atomicExch(&A.f->err, TPC_ERR_CAPACITY);
+    }
+    if (T > A.cap_tracks || total > (uint32_t)A.cap_clus) return;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const int a = A.thead[r];
+        const uint32_t off = A.tcount[r];
+        const uint32_t end = A.tcount[r + 1];
+        A.clus_offset[r] = (int)off;
+        if (r == T - 1) A.clus_offset[T] = (int)end;
+        A.nclus[r] = (int)(end - off);
+        uint32_t o = off;
+        int steps = 0;
+        for (int b = a; b >= 0 && steps <= MAX_CHAIN; b = A.next2[b], steps++) {
+            const int t = A.seg[b];
+            const int nh = A.t_nhits[t], nup = A.t_nup[t];
+            const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
+            const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
+            for (int k = 0; k < nh; k++) {
+                const int h = trk_hit(slot, A.nr, nh, nup, k);
+                if (A.hitw[h] == w) {
+                    const int id = A.ids[h];
+                    A.clus_index[o++] = id;
+                    A.assign[id] = r;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// intermediate results in input-index space (optional outputs)
+// ---------------------------------------------------------------------------
+__global__ void k_export_links(int n, const int32_t* __restrict__ ids, const int32_t* __restrict__ upr,
+                               const int32_t* __restrict__ dnr, const int32_t* __restrict__ up,
+                               const int32_t* __restrict__ dn, int32_t* o_upr, int32_t* o_dnr, int32_t* o_up,
+                               int32_t* o_dn, uint8_t* o_start, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        const int id = ids[h];
+        const int a = upr[h], b = dnr[h], c = up[h], d = dn[h];
+        if (o_upr) o_upr[id] = a >= 0 ? ids[a] : -1;
+        if (o_dnr) o_dnr[id] = b >= 0 ? ids[b] : -1;
+        if (o_up) o_up[id] = c >= 0 ? ids[c] : -1;
+        if (o_dn) o_dn[id] = d >= 0 ? ids[d] : -1;
+        if (o_start) o_start[id] = (c >= 0 && d < 0 && up[c] >= 0) ? 1 : 0;
+    }
+}
+
+#define CK(x)                                          \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return TPC_ERR_CUDA;    \
+    } while (0)
+
+}  // namespace
+
+// refit launcher (tpc_refit.cu)
+int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const tpc_clusters* cl,
+                     const float* zlin, const float* rowtab, const void* frame, const int32_t* ttail,
+                     const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st);
+
+extern "C" {
+
+int tpc_params_default(tpc_params* p)
+{
+    if (!p) return TPC_ERR_ARG;
+    memset(p, 0, sizeof(*p));
+    p->dy_link = 3.0f;
+    p->dz_link = 3.0f;
+    p->s_max_link = 0.5f;
+    p->sigma_y = 0.1f;
+    p->sigma_z = 0.15f;
+    p->c0_snp = 0.25f;
+    p->c0_tgl = 0.25f;
+    p->c0_qpt = 100.0f;
+    p->win_nsigma = 3.0f;
+    p->win_min = 0.5f;
+    p->win_max = 3.0f;
+    p->chi2_cut = 10.0f;
+    p->max_miss = 8;
+    p->min_hits = 10;
+    p->min_owned = 10;
+    p->edge_margin = 1.0f;
+    p->merge_dz = 10.0f;
+    p->merge_chi2 = 50.0f;
+    p->refit_passes = 3;
+    p->z_cell = 3.5f;
+    p->max_z_cells = 1024;
+    p->tracklets_per_1k = 125;
+    p->fp64_final = 0;
+    return TPC_OK;
+}
+
+static int check_args(const tpc_params* p, const tpc_geometry* g)
+{
+    if (!p || !g || !g->row_x) return TPC_ERR_ARG;
+    if (!(g->n_sectors == 36 || g->n_sectors == 1)) return TPC_ERR_ARG;
+    if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
+    if (g->n_sectors * g->n_rows > 65535) return TPC_ERR_ARG;
+    if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
+    if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
+    for (int r = 0; r + 1 < g->n_rows; r++)
+        if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
+    return TPC_OK;
+}
+
+int tpc_workspace_size(const tpc_params* p, const tpc_geometry* g, int64_t n, size_t* bytes)
+{
+    if (!bytes || n < 0 || n > (int64_t)INT32_MAX / 2) return TPC_ERR_ARG;
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    *bytes = make_layout(p, g, n).total;
+    return TPC_OK;
+}
+
+int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
+              void* ws, size_t ws_bytes, tpc_tracks* out, void* stream)
+{
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    if (!cl || !out || !ws || cl->n < 0) return TPC_ERR_ARG;
+    const int n = cl->n;
+    if (n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->zt)) return TPC_ERR_ARG;
+    if (!out->sector || !out->x || !out->param || !out->cov || !out->chi2 || !out->ndf || !out->status ||
+        !out->nclus || !out->clus_offset || !out->clus_index || !out->assign)
+        return TPC_ERR_ARG;
+    if (out->capacity_tracks < 0 || out->capacity_clusters < 0) return TPC_ERR_ARG;
+    if (p->fp64_final && (!out->cov64 || !out->chi2_64)) return TPC_ERR_ARG;
+    const Layout L = make_layout(p, g, n);
+    if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    out->n_tracks = out->n_tracklets = out->n_segments = 0;
+    out->tracklets_needed = out->tracks_needed = out->clusters_needed = 0;
+
+    Frame* f = at<Frame>(ws, L.frame);
+    float* rowtab = at<float>(ws, L.rowtab);
+    float* zlin = at<float>(ws, L.zlin);
+    uint32_t* cell = at<uint32_t>(ws, L.cell);
+    uint32_t* slot = at<uint32_t>(ws, L.slot);
+    uint32_t* cstart = at<uint32_t>(ws, L.cstart);
+    uint32_t* aux = at<uint32_t>(ws, L.scan);
+    float* ys = at<float>(ws, L.ys);
+    float* zs = at<float>(ws, L.zs);
+    int32_t* ids = at<int32_t>(ws, L.ids);
+    uint16_t* plane = at<uint16_t>(ws, L.plane);
+    int32_t* upr = at<int32_t>(ws, L.upr);
+    int32_t* dnr = at<int32_t>(ws, L.dnr);
+    int32_t* up = at<int32_t>(ws, L.up);
+    int32_t* dn = at<int32_t>(ws, L.dn);
+    int32_t* starts = at<int32_t>(ws, L.starts);
+    unsigned long long* hitw = at<unsigned long long>(ws, L.hitw);
+
+    // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r], (X[r]-X[r-1])/(X[r+1]-X[r-1])
+    float tab[ROWTAB * 256];
+    memset(tab, 0, sizeof(tab));
+    const float* X = g->row_x;
+    for (int r = 0; r < g->n_rows; r++) {
+        volatile float xr = X[r];
+        tab[r * ROWTAB] = xr;
+        if (r >= 1 && r + 1 < g->n_rows) {
+            volatile float a = X[r + 1] / X[r];
+            volatile float b = X[r - 1] / X[r];
+            volatile float num = X[r] - X[r - 1];
+            volatile float den = X[r + 1] - X[r - 1];
+            volatile float w = num / den;
+            tab[r * ROWTAB + 1] = a;
+            tab[r * ROWTAB + 2] = b;
+            tab[r * ROWTAB + 3] = w;
+        }
+    }
+    CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
+    // a copy of the layout at the workspace base lets tpc_export_tracklets find the arrays
+    static_assert(sizeof(Layout) <= 512, "layout header");
+    CK(cudaMemcpyAsync(at<char>(ws, L.hdr), &L, sizeof(Layout), cudaMemcpyHostToDevice, st));
+
+    volatile float vyv = p->sigma_y * p->sigma_y;
+    volatile float vzv = p->sigma_z * p->sigma_z;
+    volatile float kbv = KB_C * bz;
+    const float vy = vyv, vz = vzv, kb = kbv;
+    const int B = 256;
+    const int gN = grid_for(n, B);
+    const int ntcap = L.ntcap;
+
+    k_init_frame<<<1, 32, 0, st>>>(f);
+    if (n > 0)
+        k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
+                                 g->z_max, v_drift, zlin, f);
+    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, L.nzmax, p->merge_dz * 1.1f + 0.5f, L.mnzmax);
+    CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(L.ncells + 1), st));
+    if (n > 0) {
+        k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
+    }
+    scan_u32(cstart, L.ncells, aux, st);
+    if (n > 0) {
+        k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs,
+                                    ids, plane, f);
+        k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f,
+                                       p->dy_link, p->dz_link, p->s_max_link, upr, dnr);
+        k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
+        k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
+    }
+    // tracklets
+    TrkArgs TA;
+    TA.rowtab = rowtab; TA.ys = ys; TA.zs = zs; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
+    TA.starts = starts; TA.f = f; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.cap = ntcap;
+    TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
+    TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
+    TA.edge = p->edge_margin; TA.max_miss = p->max_miss;
+    TA.t_start = at<int32_t>(ws, L.t_start); TA.t_id = at<int32_t>(ws, L.t_id);
+    TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
+    TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
+    const int gT = grid_for(ntcap, 128);
+    if (n > 0) k_tracklets<<<gT, 128, 0, st>>>(TA);
+    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)std::max(n, 1), st));
+    const int gt2 = grid_for(ntcap, B);
+    uint8_t* kept = at<uint8_t>(ws, L.t_kept);
+    int32_t* seg = at<int32_t>(ws, L.seg);
+    if (n > 0) {
+        k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits,
+                                        hitw);
+        k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
+                                     TA.t_hits, hitw, kept, seg);
+    }
+    // merger
+    const int64_t mcells = (int64_t)g->n_sectors * L.mnzmax;
+    uint32_t* cntb = at<uint32_t>(ws, L.cntb);
+    uint32_t* cntt = at<uint32_t>(ws, L.cntt);
+    CK(cudaMemsetAsync(cntb, 0, 4 * (size_t)(mcells + 1), st));
+    CK(cudaMemsetAsync(cntt, 0, 4 * (size_t)(mcells + 1), st));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, st));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
+    uint32_t* headmark = at<uint32_t>(ws, L.headmark);
+    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(std::max(n, 1) + 1), st));
+    if (n > 0) {
+        k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, seg, plane, TA.t_start, g->n_rows, TA.t_top, TA.t_bot, cntb,
+                                      cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
+                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott));
+    }
+    scan_u32(cntb, mcells, aux, st);
+    scan_u32(cntt, mcells, aux, st);
+    MergeArgs M;
+    M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
+    M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
+    M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
+    M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev);
+    if (n > 0) {
+        k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
+                                         at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
+                                         at<int32_t>(ws, L.byt));
+        k_merge_next<<<gT, 128, 0, st>>>(M);
+        k_merge_prev<<<gT, 128, 0, st>>>(M);
+        k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
+        k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
+        k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
+                                       at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
+    }
+    scan_u32(headmark, std::max(n, 1), aux, st);
+    // track assembly
+    uint32_t* tcount = at<uint32_t>(ws, L.tcount);
+    CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), st));
+    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)std::max(n, 1), st));
+    AsmArgs AA;
+    AA.f = f; AA.nr = g->n_rows; AA.n = std::max(n, 1); AA.cap_tracks = out->capacity_tracks;
+    AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
+    AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits; AA.t_nup = TA.t_nup;
+    AA.t_hits = TA.t_hits; AA.ids = ids; AA.hitw = hitw; AA.headmark = headmark; AA.tcount = tcount;
+    AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail); AA.clus_offset = out->clus_offset;
+    AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
+    if (n > 0) k_track_count<<<gt2, B, 0, st>>>(AA);
+    scan_u32(tcount, ntcap, aux, st);
+    k_track_fill<<<gt2, B, 0, st>>>(AA);
+    int rr = tpc_launch_refit(p, g, bz, cl, zlin, rowtab, f, AA.ttail, TA.t_top, out,
+                              std::min(out->capacity_tracks, ntcap), st);
+    if (rr) return rr;
+    // optional intermediate outputs
+    if (out->z && n > 0) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 0 && (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start))
+        k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
+                                         out->link_dn, out->is_start, f);
+    CK(cudaGetLastError());
+    Frame hf;
+    CK(cudaMemcpyAsync(&hf, f, sizeof(Frame), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->n_tracklets = std::min(hf.n_starts, ntcap);
+    out->n_segments = hf.n_seg;
+    out->n_tracks = hf.n_tracks;
+    if (hf.err == TPC_ERR_DATA) return TPC_ERR_DATA;
+    if (hf.n_starts > ntcap) {
+        out->tracklets_needed = hf.n_starts;
+        return TPC_ERR_CAPACITY;
+    }
+    if (hf.err == TPC_ERR_CAPACITY) {
+        out->tracks_needed = hf.n_tracks;
+        out->clusters_needed = hf.n_clus;
+        return TPC_ERR_CAPACITY;
+    }
+    return TPC_OK;
+}
+
+int tpc_export_tracklets(const void* ws, int32_t capacity, int32_t hits_stride, int32_t* start, int32_t* nhits,
+                         uint8_t* kept, int32_t* hits, float* top, float* bot, int32_t* nt_out, void* stream)
+{
+    if (!ws || !nt_out || capacity < 0) return TPC_ERR_ARG;
+    if (capacity > 0 && (!start || !nhits || !kept || !hits || !top || !bot)) return TPC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st));
+    Layout L;
+    CK(cudaMemcpy(&L, ws, sizeof(Layout), cudaMemcpyDeviceToHost));
+    if (L.magic != WS_MAGIC || L.hdr != 0) return TPC_ERR_ARG;
+    if (hits_stride < L.nr) return TPC_ERR_ARG;
+    Frame F;
+    CK(cudaMemcpy(&F, static_cast<const char*>(ws) + L.frame, sizeof(Frame), cudaMemcpyDeviceToHost));
+    const int nt = std::min(F.n_starts, L.ntcap);
+    *nt_out = nt;
+    if (capacity < nt) return TPC_ERR_CAPACITY;
+    const int nr = L.nr;
+    const int n = std::max(L.n, 1);
+    std::vector<int32_t> id(nt), nh(nt), nup(nt), h((size_t)nt * nr), ids(n);
+    std::vector<float> tp((size_t)nt * NST), bt((size_t)nt * NST);
+    std::vector<uint8_t> kp(nt);
+    auto get = [&](void* dst, size_t off, size_t bytes) {
+        return bytes ? cudaMemcpy(dst, static_cast<const char*>(ws) + off, bytes, cudaMemcpyDeviceToHost) : cudaSuccess;
+    };
+    CK(get(id.data(), L.t_id, 4 * (size_t)nt));
+    CK(get(nh.data(), L.t_nhits, 4 * (size_t)nt));
+    CK(get(nup.data(), L.t_nup, 4 * (size_t)nt));
+    CK(get(h.data(), L.t_hits, 4 * (size_t)nt * nr));
+    CK(get(tp.data(), L.t_top, 4 * (size_t)nt * NST));
+    CK(get(bt.data(), L.t_bot, 4 * (size_t)nt * NST));
+    CK(get(kp.data(), L.t_kept, (size_t)nt));
+    CK(get(ids.data(), L.ids, 4 * (size_t)L.n));
+    std::vector<int> order(nt);
+    for (int i = 0; i < nt; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return id[a] < id[b]; });
+    for (int k = 0; k < nt; k++) {
+        const int t = order[k];
+        start[k] = id[t];
+        nhits[k] = nh[t];
+        kept[k] = kp[t];
+        const int nd = nh[t] - nup[t];
+        int32_t* row = hits + (size_t)k * hits_stride;
+        for (int q = 0; q < hits_stride; q++) row[q] = -1;
+        for (int q = 0; q < nh[t]; q++) {
+            const int hs = q < nd ? h[(size_t)t * nr + nr - nd + q] : h[(size_t)t * nr + q - nd];
+            row[q] = ids[hs];
+        }
+        memcpy(top + (size_t)k * NST, &tp[(size_t)t * NST], NST * sizeof(float));
+        memcpy(bot + (size_t)k * NST, &bt[(size_t)t * NST], NST * sizeof(float));
+    }
+    return TPC_OK;
+}
+
+const char* tpc_error_string(int code)
+{
+    switch (code) {
+    case TPC_OK: return "ok";
+    case TPC_ERR_ARG: return "invalid argument";
+    case TPC_ERR_CAPACITY: return "workspace or output capacity too small";
+    case TPC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TPC_ERR_CUDA: return "CUDA runtime error";
+    case TPC_ERR_DATA: return "invalid cluster data (sector/row out of range or non-finite coordinate)";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+"""CPU-side checks of the C ABI library: it builds for sm_103a, loads, and
+exports every function include/tpc_track.h declares; host-only entry points
+validate their arguments (no GPU needed for these)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tpc_track.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpc_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1905_05515_b300 as tpc
+    L = tpc.lib()
+    names = _declared()
+    assert "tpc_track" in names and len(names) >= 5
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+def test_params_and_workspace_size_host_only():
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    p = tpc.tpc_params_default()
+    assert p.dy_link == 3.0 and p.refit_passes == 3
+    g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
+    small = tpc.tpc_workspace_size(p, g, 1000)
+    big = tpc.tpc_workspace_size(p, g, 16_000_000)
+    assert 0 < small < big < 8 * 2**30
+    with pytest.raises(tpc.TpcError):
+        tpc.tpc_workspace_size(p, tpc.abi.make_geometry(np.array([1, 2], np.float32), 36, 250.0, False), 10)
+    with pytest.raises(tpc.TpcError):
+        tpc.tpc_workspace_size(p, tpc.abi.make_geometry(tpcgen.row_x_f32(), 5, 250.0, False), 10)
+    bad = tpc.tpc_params_default(z_cell=2.0)       # cell shorter than the link window
+    with pytest.raises(tpc.TpcError):
+        tpc.tpc_workspace_size(bad, g, 10)
+    assert tpc.tpc_error_string(tpc.TPC_ERR_DATA).startswith("invalid cluster")
+
+
+def test_track_rejects_null_arguments_without_touching_the_gpu():
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    L = tpc.lib()
+    p = tpc.tpc_params_default()
+    g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, False)
+    rc = L.tpc_track(C.byref(p), C.byref(g), 0.5, 2.58, None, None, 0, None, None)
+    assert rc == tpc.TPC_ERR_ARG

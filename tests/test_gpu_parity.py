@@ -1,0 +1,98 @@
+"""Parity of the CUDA tracker (called through the C ABI) with the CPU oracle
+on the same seeded inputs.  Decisions -- z after time->z, raw and cleaned
+links, start hits, tracklet hit lists and end states, selector verdicts,
+merged cluster lists, assignments -- are bit-exact; refitted parameters agree
+within 1e-4 relative (floors 1 cm, 1 cm, 0.01, 0.01, 0.01 GeV^-1 for y, z,
+sin phi, tan lambda, q/pT) and chi2 within 1e-3 relative of the binary64
+oracle fit."""
+import numpy as np
+import pytest
+
+import tpcgen
+from gpu_helpers import compare_decisions, compare_fit, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+PARAM_TOL = 1e-4
+CHI2_TOL = 1e-3
+
+
+def _check(ev, orc, params=None, fit=True):
+    g = run_gpu(ev, params=params)
+    r = orc.track_event(ev)
+    bad = compare_decisions(ev, g, r)
+    assert all(v == 0 for v in bad.values()), bad
+    if fit:
+        f = compare_fit(g, r)
+        assert f["status_mismatch"] <= max(2, r.n_tracks // 1000), f
+        assert f["param_max"].max() < PARAM_TOL, f
+        assert f["chi2_max"] < CHI2_TOL, f
+        assert f["x_max"] < 1e-3, f
+    return g, r
+
+
+def test_one_sector(orc):
+    _check(tpcgen.one_sector(seed=1), orc)
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_one_sector_other_seeds(orc, seed):
+    _check(tpcgen.one_sector(seed=seed, with_truth=False), orc)
+
+
+def test_central_event_small(orc):
+    _check(tpcgen.central_event(seed=2, n_tracks=1500, with_truth=False), orc)
+
+
+def test_central_event_full(orc):
+    """The full 10k-track central event (1.67 M clusters)."""
+    _check(tpcgen.central_event(seed=2, with_truth=False), orc)
+
+
+def test_time_frame_small(orc):
+    _check(tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False), orc)
+
+
+def test_ragged_sizes(orc):
+    """Sizes that are not multiples of any block or tile size."""
+    for n_tracks, seed in ((1, 31), (7, 32), (33, 33), (257, 34)):
+        _check(tpcgen.central_event(seed=seed, n_tracks=n_tracks, with_truth=False), orc)
+
+
+def test_noise_only_and_tiny_inputs(orc):
+    ev = tpcgen.central_event(seed=40, n_tracks=0, with_truth=False)
+    assert ev.n == 0
+    g = run_gpu(ev)
+    assert g["n_tracks"] == 0
+    ev = tpcgen.generate(n_sectors=36, n_tracks=0, noise_frac=0.0, seed=41, with_truth=False)
+    # pure noise: many random clusters, no tracks expected
+    rng = np.random.default_rng(5)
+    n = 5000
+    ev.sector = rng.integers(0, 36, n).astype(np.uint8)
+    ev.row = rng.integers(0, 152, n).astype(np.uint8)
+    ev.y = rng.uniform(-10, 10, n).astype(np.float32)
+    ev.zt = rng.uniform(-250, 250, n).astype(np.float32)
+    _check(ev, orc)
+
+
+def test_fp64_final_refit(orc):
+    """Binary64 covariance (Joseph form) and chi2 in the final pass."""
+    import paper_1905_05515_b300 as tpc
+    ev = tpcgen.central_event(seed=2, n_tracks=1500, with_truth=False)
+    g = run_gpu(ev, params=tpc.tpc_params_default(fp64_final=1))
+    r = orc.track_event(ev)
+    bad = compare_decisions(ev, g, r)
+    assert all(v == 0 for v in bad.values()), bad
+    ok = (g["status"] == 0) & (r.tr_status == 0)
+    ce = np.abs(g["chi2_64"][ok] - r.tr_chi2[ok]) / np.maximum(r.tr_chi2[ok], 1.0)
+    assert ce.max() < CHI2_TOL
+    cov_rel = np.abs(g["cov64"][ok] - r.tr_c[ok]) / np.maximum(np.abs(r.tr_c[ok]), 1e-12)
+    diag = [0, 2, 5, 9, 14]
+    assert np.median(cov_rel[:, diag]) < 1e-4
+
+
+@pytest.mark.slow
+def test_time_frame_full(orc):
+    """The 50-collision continuous read-out frame (16 M clusters), whole-chain
+    parity with the oracle (the oracle takes a few minutes here)."""
+    _check(tpcgen.time_frame(seed=3, with_truth=False), orc)
