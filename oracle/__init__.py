@@ -23,7 +23,8 @@ class OrcParams(C.Structure):
                 ("win_nsigma", C.c_float), ("win_min", C.c_float), ("win_max", C.c_float),
                 ("chi2_cut", C.c_float), ("max_miss", C.c_int32), ("min_hits", C.c_int32),
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float),
-                ("merge_dz", C.c_float), ("merge_chi2", C.c_float), ("refit_passes", C.c_int32)]
+                ("merge_dz", C.c_float), ("merge_chi2", C.c_float), ("refit_passes", C.c_int32),
+                ("refit_inflate", C.c_float)]
 
 
 class OrcGeom(C.Structure):

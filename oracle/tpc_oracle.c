@@ -67,6 +67,7 @@ void orc_params_default(orc_params *p)
     p->edge_margin = 1.0f;
     p->merge_dz = 10.0f; p->merge_chi2 = 50.0f;
     p->refit_passes = 3;
+    p->refit_inflate = 100.0f;
 }
 
 /* ===================================================================== *
@@ -395,9 +396,14 @@ static double sector_alpha64(int s, int n_sectors)
 
 /* Multi-pass refit ("multiple fit iterations", section "TPC Tracking"):
  * pass 1 runs from the outermost cluster inwards, the next pass outwards,
- * and so on; each pass restarts from the previous pass's state with y, z
- * taken from the first measurement and the covariance reset to the prior.
- * Clusters in another sector are reached by rotating the frame. */
+ * and so on.  Each pass restarts from the previous fit's state: y, z from
+ * the first measurement (variance sigma^2, no correlations), sin(phi),
+ * tan(lambda), q/pT with the previous covariance block times refit_inflate
+ * (pass 1 starts from the tracklet's outer-end fit).  A fixed point of the
+ * passes is the least-squares fit; keeping the previous angular covariance,
+ * instead of a wide diagonal prior, keeps the filter well conditioned where
+ * a looper runs nearly parallel to the pad rows.  Clusters in another sector
+ * are reached by rotating the frame. */
 int orc_fit64(const orc_params *P, const orc_geom *G, double kb, int32_t n,
               const int32_t *sector, const double *x, const double *y, const double *z,
               int32_t n_passes, double *st, double *chi2o)
@@ -419,14 +425,18 @@ int orc_fit64(const orc_params *P, const orc_geom *G, double kb, int32_t n,
             }
             if (!orc_prop64(st, x[i], kb)) { *chi2o = chi2; return 0; }
             if (q == 0) {
+                /* restart: position from the first measurement, its
+                 * correlations dropped; angles and curvature keep the
+                 * previous fit's covariance inflated by refit_inflate */
+                double *c = st + 6;
                 st[1] = y[i];
                 st[2] = z[i];
-                memset(st + 6, 0, 15 * sizeof(double));
-                st[6 + 0] = vy;
-                st[6 + 2] = vz;
-                st[6 + 5] = P->c0_snp;
-                st[6 + 9] = P->c0_tgl;
-                st[6 + 14] = P->c0_qpt;
+                c[0] = vy; c[1] = 0; c[2] = vz;
+                for (int a = 2; a < 5; a++) {
+                    c[a * (a + 1) / 2 + 0] = 0;
+                    c[a * (a + 1) / 2 + 1] = 0;
+                    for (int b = 2; b <= a; b++) c[a * (a + 1) / 2 + b] *= (double)P->refit_inflate;
+                }
             } else {
                 double c2;
                 if (!orc_update64(st, y[i], z[i], vy, vz, &c2)) { *chi2o = chi2; return 0; }

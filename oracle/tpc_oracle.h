@@ -38,6 +38,7 @@ typedef struct {
     float edge_margin;                    /* stop following when |y| > x tan(10 deg) + margin */
     float merge_dz, merge_chi2;           /* merger candidate window (cm) and chi2 (5 dof) cut */
     int32_t refit_passes;                 /* Kalman refit passes, alternating direction */
+    float refit_inflate;                  /* factor on the previous angular covariance at each pass start */
 } orc_params;
 
 typedef struct {
