@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Throughput of the B300 TPC tracker on the 50-collision continuous read-out
+frame: TPC clusters/s tracked (CA seeding + Kalman following, selection,
+merging, refit), and ms per 50-collision frame.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one tpc_track call over the whole frame (inputs resident in HBM;
+16 M clusters, 160 MB of cluster SoA, larger than the 126 MB L2).  Under
+torchrun each rank tracks its own frame (different seed): independent
+replicas, no collective on the data path ("weak" scaling).  Rank 0 prints one
+JSON line.  --impl reference times the CPU oracle on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters/s tracked (CA + Kalman fit) on 1 B300; ms per 50-collision frame"
+WORKLOAD = "50-collision continuous read-out frame (36 sectors x 152 rows, Bz 0.5 T, drift times)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak: 148 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# binary32 flops of one step of each decision-path primitive, counted from the
+# operation lists in tpc_dev.cuh (FMA = 2, add/mul/div/sqrt = 1)
+FLOPS_PROP = 181      # prop32: 71 for the state and Jacobian terms + 110 for F C F^T
+FLOPS_UPDATE = 130    # update32: innovation, 2x2 inverse, chi2, gain, state, covariance
+FLOPS_CAND = 5        # one grid candidate in the following window: 2 sub + fused distance
+FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky solve (~250)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--collisions", type=int, default=50)
+    ap.add_argument("--cpu-sample-collisions", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.index), "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            self.p.wait()
+        self.f.flush()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except OSError:
+        return {}
+
+
+def cpu_baseline(n_coll: int, seed: int):
+    """The oracle as it stands, single-threaded, on a bounded frame of the same generator."""
+    import oracle
+    import tpcgen
+    ev = tpcgen.time_frame(seed=seed, n_collisions=n_coll, with_truth=False)
+    t0 = time.perf_counter()
+    cpu0 = time.process_time()
+    r = oracle.track_event(ev)
+    dt = time.perf_counter() - t0
+    cpu = time.process_time() - cpu0
+    return {"value": ev.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_coll}-collision frame of the same generator (seed {seed}), {ev.n} clusters, "
+                      f"{r.n_tracks} tracks, {dt:.1f} s wall / {cpu:.1f} s CPU, single thread"}
+
+
+def run_reference(args, ws, rank, pg):
+    if rank != 0:
+        return
+    import oracle
+    import tpcgen
+    oracle.lib()
+    n_coll = args.cpu_sample_collisions
+    evs = [tpcgen.time_frame(seed=900 + i, n_collisions=n_coll, with_truth=False)
+           for i in range(args.warmup + args.steps)]
+    for ev in evs[:args.warmup]:
+        oracle.track_event(ev)
+    t0 = time.perf_counter()
+    n = 0
+    for ev in evs[args.warmup:]:
+        oracle.track_event(ev)
+        n += ev.n
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + f", bounded to {n_coll} collisions per step for the CPU",
+                       "n_collisions": n_coll, "clusters_per_step": n // args.steps},
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} frames of {n_coll} collisions, single thread"},
+            "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ev = tpcgen.time_frame(seed=3 + rank, n_collisions=args.collisions, with_truth=False)
+    n = ev.n
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(ev, k))).pin_memory()
+            for k in ("sector", "row", "y", "zt")}
+    dv = {k: v.to(dev) for k, v in host.items()}
+    params = tpc.tpc_params_default(profile=1)
+    trk = tpc.Tracker(n, ev.row_x, n_sectors=36, z_max=ev.z_max, continuous=True, params=params, device=dev)
+    args_t = (dv["sector"], dv["row"], dv["y"], dv["zt"])
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        res = trk.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    stage_sum = {k: 0.0 for k in tpc.abi.STAGES}
+    work_sum = {}
+    launches = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = trk.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+            for k, v in res.stage_ms.items():
+                stage_sum[k] += v
+            for k, v in res.work.items():
+                work_sum[k] = work_sum.get(k, 0) + v
+            launches += res.n_launches
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    n_tracks = res.n_tracks
+
+    # ---- end to end through the same API with host buffers
+    T_cap = trk.capacity_tracks
+    outs = {"param": (T_cap, 5), "cov": (T_cap, 15), "chi2": (T_cap,), "ndf": (T_cap,), "nclus": (T_cap,),
+            "clus_offset": (T_cap + 1,)}
+    h_out = {k: torch.empty(sh, dtype=trk.buf[k].dtype).pin_memory() for k, sh in outs.items()}
+    h_clus = torch.empty(trk.capacity_clusters, dtype=torch.int32).pin_memory()
+    h_assign = torch.empty(n, dtype=torch.int32).pin_memory()
+    h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
+    d2h_list = []
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in dv:
+            dv[k].copy_(host[k], non_blocking=True)
+        r = trk.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+        T = r.n_tracks
+        nb = 0
+        for k in outs:
+            m = T + 1 if k == "clus_offset" else T
+            h_out[k][:m].copy_(trk.buf[k][:m], non_blocking=True)
+            nb += m * trk.buf[k][0].numel() * trk.buf[k].element_size()
+        nc = int(r.clus_offset[-1].item()) if T else 0
+        h_clus[:nc].copy_(trk.buf["clus_index"][:nc], non_blocking=True)
+        h_assign.copy_(r.assign, non_blocking=True)
+        nb += 4 * nc + 4 * n + 4
+        torch.cuda.synchronize()
+        d2h_list.append(nb)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    # ---- max over ranks, totals
+    vals = torch.tensor([ms, e2e_s, float(n)], dtype=torch.float64, device=dev)
+    if pg is not None:
+        mx = vals.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        tot = vals.clone()
+        pg.all_reduce(tot, op=pg.ReduceOp.SUM)
+        ms_max, e2e_max, n_total = float(mx[0]), float(mx[1]), float(tot[2])
+    else:
+        ms_max, e2e_max, n_total = ms, e2e_s, float(n)
+    if rank != 0:
+        return
+    value = n_total * args.steps / (ms_max / 1e3)
+    per_step = {k: v / args.steps for k, v in stage_sum.items()}
+    w = {k: v / args.steps for k, v in work_sum.items()}
+    dom = max(per_step, key=per_step.get)
+    roof = roofline(dom, per_step, w, n, peaks())
+    line = {
+        "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_collisions": args.collisions, "clusters": n, "tracks_found": n_tracks,
+                   "collisions_per_s": args.collisions * ws * args.steps / (ms_max / 1e3),
+                   "ms_per_frame": ms_max / args.steps,
+                   "l2": "inputs (10 B/cluster, 160 MB) and workspace exceed the 126 MB L2; no flush",
+                   "replicas": ws},
+        "roofline": roof,
+        "stage_ms": {k: round(v, 4) for k, v in per_step.items()},
+        "work_per_step": w,
+        "e2e": {"value": n_total * args.steps / e2e_max, "unit": "clusters/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(sum(d2h_list) / len(d2h_list))},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_collisions, seed=3)
+    print(json.dumps(line), flush=True)
+
+
+def roofline(stage, per_step, w, n, pk):
+    """Roofline of the dominant stage: algorithmic work of one launch / its
+    event-timed duration."""
+    t = per_step[stage] / 1e3
+    if stage in ("tracklets", "merge", "refit"):
+        if stage == "tracklets":
+            flops = w["trk_prop"] * FLOPS_PROP + w["trk_upd"] * FLOPS_UPDATE + w["trk_cand"] * FLOPS_CAND
+        elif stage == "merge":
+            flops = w["merge_chi2"] * FLOPS_MERGE * 2      # both directions evaluate the chi2
+        else:
+            flops = w["refit_prop"] * (FLOPS_PROP + FLOPS_UPDATE)
+        ach = flops / t / 1e12
+        return {"bound": "alu", "stage": stage, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"}
+    bytes_per = {"prep": 18, "bin": 40, "neighbours": 22, "clean_start": 28}.get(stage, 0)
+    hbm = pk.get("hbm_gbs", 6400.0)
+    ach = bytes_per * n / t / 1e9
+    return {"bound": "hbm", "stage": stage, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "peak_note": "measured" if "hbm_gbs" in pk else "fallback"}
+
+
+def main():
+    args = parse()
+    ws, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank, pg)
+    else:
+        run_ours(args, ws, rank, local, pg)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

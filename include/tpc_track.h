@@ -44,6 +44,18 @@ extern "C" {
 #define TPC_ERR_CUDA (-4)      /* a CUDA runtime call failed */
 #define TPC_ERR_DATA (-5)      /* a cluster has sector/row out of range or a non-finite coordinate */
 
+/* Stages timed with params.profile (indices into tpc_tracks.stage_ms). */
+#define TPC_STAGE_PREP 0        /* time -> z, validation, grid extent */
+#define TPC_STAGE_BIN 1         /* per-row grid binning (histogram, scan, scatter) */
+#define TPC_STAGE_NEIGHBOURS 2  /* NeighboursFinder */
+#define TPC_STAGE_CLEAN_START 3 /* NeighboursCleaner + StartHitsFinder */
+#define TPC_STAGE_TRACKLETS 4   /* TrackletConstructor */
+#define TPC_STAGE_SELECT 5      /* TrackletSelector */
+#define TPC_STAGE_MERGE 6       /* cross-sector merger */
+#define TPC_STAGE_ASSEMBLE 7    /* merged cluster lists and assignments */
+#define TPC_STAGE_REFIT 8       /* Kalman refit */
+#define TPC_N_STAGES 10
+
 /* Method parameters.  tpc_params_default() fills the values of the reading
  * used throughout (seeding windows, straightness cut, cluster errors,
  * priors, following window and cuts, selector and merger cuts). */
@@ -61,11 +73,14 @@ typedef struct {
     float merge_dz;              /* merger: |z_B - z_A| window before the chi2 test (cm) */
     float merge_chi2;            /* merger: chi2 (5 dof) cut */
     int32_t refit_passes;        /* refit passes, alternating inward / outward (odd: ends inward) */
+    float refit_inflate;         /* each pass restarts with the previous sin(phi), tan(lambda), q/pT
+                                    covariance times this factor (y, z from the first measurement) */
     /* acceleration structure and capacities (do not change results) */
     float z_cell;                /* minimum grid cell length in z (cm); must exceed dz_link, win_max */
     int32_t max_z_cells;         /* maximum grid cells per pad row */
     int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
     int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
+    int32_t profile;             /* 1: record CUDA events on the stream at stage boundaries (tpc_tracks.stage_ms) */
 } tpc_params;
 
 /* Detector geometry (host memory). */
@@ -118,6 +133,11 @@ typedef struct {
     int64_t tracklets_needed;    /* on TPC_ERR_CAPACITY */
     int64_t tracks_needed;
     int64_t clusters_needed;
+    int32_t n_launches;          /* kernels this call launched */
+    float stage_ms[TPC_N_STAGES];/* with params.profile: device time of each stage (see TPC_STAGE_*) */
+    int64_t work[5];             /* with params.profile: tracklet propagations, tracklet updates, grid
+                                    candidates examined while following, refit propagations, merger
+                                    chi2 evaluations */
 } tpc_tracks;
 
 /* Fill *p with the default parameters.  Returns TPC_OK, or TPC_ERR_ARG for p == NULL. */

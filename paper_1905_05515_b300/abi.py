@@ -27,8 +27,10 @@ class TpcParams(C.Structure):
                 ("win_nsigma", C.c_float), ("win_min", C.c_float), ("win_max", C.c_float),
                 ("chi2_cut", C.c_float), ("max_miss", C.c_int32), ("min_hits", C.c_int32),
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float), ("merge_dz", C.c_float),
-                ("merge_chi2", C.c_float), ("refit_passes", C.c_int32), ("z_cell", C.c_float),
-                ("max_z_cells", C.c_int32), ("tracklets_per_1k", C.c_int32), ("fp64_final", C.c_int32)]
+                ("merge_chi2", C.c_float), ("refit_passes", C.c_int32), ("refit_inflate", C.c_float),
+                ("z_cell", C.c_float),
+                ("max_z_cells", C.c_int32), ("tracklets_per_1k", C.c_int32), ("fp64_final", C.c_int32),
+                ("profile", C.c_int32)]
 
 
 class TpcGeometry(C.Structure):
@@ -50,7 +52,10 @@ class TpcTracks(C.Structure):
                 ("z", C.c_void_p), ("link_up_raw", C.c_void_p), ("link_dn_raw", C.c_void_p),
                 ("link_up", C.c_void_p), ("link_dn", C.c_void_p), ("is_start", C.c_void_p),
                 ("n_tracks", C.c_int32), ("n_tracklets", C.c_int32), ("n_segments", C.c_int32),
-                ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64)]
+                ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64),
+                ("n_launches", C.c_int32), ("stage_ms", C.c_float * 10), ("work", C.c_int64 * 5)]
+
+STAGES = ("prep", "bin", "neighbours", "clean_start", "tracklets", "select", "merge", "assemble", "refit")
 
 
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_track", "tpc_export_tracklets", "tpc_error_string")

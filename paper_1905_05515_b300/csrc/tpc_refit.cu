@@ -5,8 +5,12 @@
 //
 // One thread per track.  Pass 1 runs from the outermost cluster inwards,
 // pass 2 outwards, pass 3 inwards again; each pass restarts from the previous
-// pass's state with y, z set to the first measurement and the covariance
-// reset to the prior.  Clusters of a neighbouring sector are reached by
+// fit's state with y, z set to the first measurement (variance sigma^2, no
+// correlations) and the sin(phi), tan(lambda), q/pT covariance block of the
+// previous fit multiplied by refit_inflate (pass 1: the tracklet's outer-end
+// fit).  The state parameters are accumulated with compensated binary32
+// sums (a high and a low part), so small curvature increments are not lost
+// against sin(phi) and y.  Clusters of a neighbouring sector are reached by
 // rotating the local frame.  Parameters are binary32; the covariance is
 // binary32, or -- with fp64_final -- binary64 during the final pass with a
 // Joseph-form update and a binary64 chi2 sum.  This is the tolerance path
@@ -61,13 +65,33 @@ __device__ __forceinline__ void asin_ratio(float u, float& A, float& Ap)
     }
 }
 
+// Compensated binary32 accumulation of the state: p[i] + pl[i] carries the
+// parameter with about twice the binary32 precision.  two_sum is Knuth's
+// error-free transformation (s + e == a + b exactly); it has no products, so
+// multiply-add contraction cannot alter it.
+__device__ __forceinline__ void acc(float& hi, float& lo, float d)
+{
+    const float s = hi + d;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (d - bb);
+    hi = s;
+    lo += e;
+}
+__device__ __forceinline__ void renorm(float& hi, float& lo)
+{
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+}
+
 template <typename CT>
-__device__ __forceinline__ bool prop(float& x, float* p, CT* c, float x2, float kb)
+__device__ __forceinline__ bool prop(float& x, float* p, float* pl, CT* c, float x2, float kb)
 {
     const float dx = x2 - x;
     if (dx == 0.0f) return true;
     const float k = kb * p[4];
-    const float s1 = p[2], s2 = s1 + k * dx;
+    const float kdx = k * dx;
+    const float s1 = p[2], s2 = s1 + kdx;
     if (!(fabsf(s1) < SNP_MAX) || !(fabsf(s2) < SNP_MAX)) return false;
     const float c1 = sqrtf((1.0f - s1) * (1.0f + s1)), c2 = sqrtf((1.0f - s2) * (1.0f + s2));
     const float ss = s1 + s2, cc = c1 + c2;
@@ -88,14 +112,16 @@ __device__ __forceinline__ bool prop(float& x, float* p, CT* c, float x2, float 
     const float dS_dk = B * g * dy_dk + 0.5f * dl * dl * Ap;
     transport<CT>(c, (CT)dy_ds, (CT)(dy_dk * kb), (CT)(p[3] * dS_ds), (CT)dS, (CT)(p[3] * dS_dk * kb), (CT)(dx * kb));
     x = x2;
-    p[0] += dy;
-    p[1] += dS * p[3];
-    p[2] = s2;
+    acc(p[0], pl[0], dy);
+    acc(p[1], pl[1], dS * p[3]);
+    acc(p[2], pl[2], kdx);
+#pragma unroll
+    for (int i = 0; i < 3; i++) renorm(p[i], pl[i]);
     return true;
 }
 
 template <typename CT>
-__device__ __forceinline__ bool rot(float& x, float* p, CT* c, float cs, float sn, float kb)
+__device__ __forceinline__ bool rot(float& x, float* p, float* pl, CT* c, float cs, float sn, float kb)
 {
     const float sp = p[2];
     const float cf = sqrtf((1.0f - sp) * (1.0f + sp));
@@ -126,16 +152,22 @@ __device__ __forceinline__ bool rot(float& x, float* p, CT* c, float cs, float s
         if (i >= 4) c[CI(i, 4)] = D[i][4];
     }
     const float xn = x * cs + p[0] * sn;
-    p[0] = -x * sn + p[0] * cs;
+    const float yn = -x * sn + p[0] * cs;
+    pl[0] = pl[0] * cs;
+    pl[2] = pl[2] * (cfn / cf);
     x = xn;
+    p[0] = yn;
     p[2] = spn;
+    renorm(p[0], pl[0]);
+    renorm(p[2], pl[2]);
     return true;
 }
 
 // standard-form update (binary32 covariance)
-__device__ __forceinline__ bool update(float* p, float* c, float my, float mz, float vy, float vz, double& chi2)
+__device__ __forceinline__ bool update(float* p, float* pl, float* c, float my, float mz, float vy, float vz,
+                                       double& chi2)
 {
-    const float r0 = my - p[0], r1 = mz - p[1];
+    const float r0 = (my - p[0]) - pl[0], r1 = (mz - p[1]) - pl[1];
     const float s00 = c[0] + vy, s01 = c[1], s11 = c[2] + vz;
     const float det = s00 * s11 - s01 * s01;
     if (!(det > 0.0f)) return false;
@@ -152,7 +184,10 @@ __device__ __forceinline__ bool update(float* p, float* c, float my, float mz, f
         row1[i] = c1;
     }
 #pragma unroll
-    for (int i = 0; i < 5; i++) p[i] += K0[i] * r0 + K1[i] * r1;
+    for (int i = 0; i < 5; i++) {
+        acc(p[i], pl[i], K0[i] * r0 + K1[i] * r1);
+        renorm(p[i], pl[i]);
+    }
 #pragma unroll
     for (int i = 0; i < 5; i++)
 #pragma unroll
@@ -162,9 +197,10 @@ __device__ __forceinline__ bool update(float* p, float* c, float my, float mz, f
 
 // Joseph-form update with a binary64 covariance and chi2:
 // C+ = (I - K H) C (I - K H)^T + K V K^T
-__device__ __forceinline__ bool update(float* p, double* c, float my, float mz, float vy, float vz, double& chi2)
+__device__ __forceinline__ bool update(float* p, float* pl, double* c, float my, float mz, float vy, float vz,
+                                       double& chi2)
 {
-    const double r0 = (double)my - p[0], r1 = (double)mz - p[1];
+    const double r0 = ((double)my - p[0]) - pl[0], r1 = ((double)mz - p[1]) - pl[1];
     const double s00 = c[0] + vy, s01 = c[1], s11 = c[2] + vz;
     const double det = s00 * s11 - s01 * s01;
     if (!(det > 0.0)) return false;
@@ -181,7 +217,10 @@ __device__ __forceinline__ bool update(float* p, double* c, float my, float mz, 
         K1[i] = C[i][0] * i01 + C[i][1] * i11;
     }
 #pragma unroll
-    for (int i = 0; i < 5; i++) p[i] += (float)(K0[i] * r0 + K1[i] * r1);
+    for (int i = 0; i < 5; i++) {
+        acc(p[i], pl[i], (float)(K0[i] * r0 + K1[i] * r1));
+        renorm(p[i], pl[i]);
+    }
     // A = I - K H (only columns 0, 1 differ from I); M = A C
     double M[5][5];
 #pragma unroll
@@ -209,14 +248,14 @@ struct RefitArgs {
     const float* rowtab;
     const int32_t* ttail;
     const float* t_top;
-    int ns, passes, fp64, max_tracks;
-    float kb, vy, vz, c0s, c0t, c0q;
+    int ns, passes, fp64, max_tracks, prof;
+    float kb, vy, vz, inflate;
     tpc_tracks out;
 };
 
 template <typename CT>
-__device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p, CT* c,
-                         double& chi2)
+__device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p, float* pl,
+                         CT* c, double& chi2, unsigned& nprop, float zref)
 {
     chi2 = 0.0;
     for (int q = 0; q < n; q++) {
@@ -231,22 +270,30 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
             if (da == 20.0f) { cs = COS20; sn = SIN20; }
             else if (da == -20.0f) { cs = COS20; sn = -SIN20; }
             else sincospif(da / 180.0f, &sn, &cs);
-            if (!rot<CT>(x, p, c, cs, sn, R.kb)) return false;
+            if (!rot<CT>(x, p, pl, c, cs, sn, R.kb)) return false;
             sec = s;
         }
-        if (!prop<CT>(x, p, c, R.rowtab[R.row[id] * 4], R.kb)) return false;
-        const float my = R.y[id], mz = R.zlin[id];
+        if (!prop<CT>(x, p, pl, c, R.rowtab[R.row[id] * 4], R.kb)) return false;
+        nprop++;
+        const float my = R.y[id], mz = R.zlin[id] - zref;
         if (q == 0) {
+            // restart: y, z from the measurement; angles and curvature keep the
+            // previous covariance block times refit_inflate
             p[0] = my;
             p[1] = mz;
-#pragma unroll
-            for (int k = 0; k < 15; k++) c[k] = (CT)0;
+            pl[0] = 0.0f;
+            pl[1] = 0.0f;
             c[0] = (CT)R.vy;
+            c[1] = (CT)0;
             c[2] = (CT)R.vz;
-            c[5] = (CT)R.c0s;
-            c[9] = (CT)R.c0t;
-            c[14] = (CT)R.c0q;
-        } else if (!update(p, c, my, mz, R.vy, R.vz, chi2)) {
+#pragma unroll
+            for (int a = 2; a < 5; a++) {
+                c[CI(a, 0)] = (CT)0;
+                c[CI(a, 1)] = (CT)0;
+#pragma unroll
+                for (int b = 2; b <= a; b++) c[CI(a, b)] *= (CT)R.inflate;
+            }
+        } else if (!update(p, pl, c, my, mz, R.vy, R.vz, chi2)) {
             return false;
         }
     }
@@ -255,33 +302,41 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
 
 __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
 {
-    const Frame* f = static_cast<const Frame*>(R.frame);
+    Frame* f = static_cast<Frame*>(const_cast<void*>(R.frame));
     if (f->err) return;
+    unsigned nprop = 0;
     const int T = min(f->n_tracks, R.max_tracks);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
         const int off = R.out.clus_offset[r];
         const int n = R.out.nclus[r];
         const float* ts = R.t_top + (int64_t)R.ttail[r] * NST;
         float x = ts[0];
-        float p[5];
+        float p[5], pl[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         float c[15];
+        // z relative to the first cluster of the track: same-track z values
+        // subtract exactly and the binary32 state keeps small magnitudes
+        const float zref = R.zlin[R.out.clus_index[off]];
 #pragma unroll
         for (int k = 0; k < 5; k++) p[k] = ts[1 + k];
+        p[1] = p[1] - zref;
 #pragma unroll
         for (int k = 0; k < 15; k++) c[k] = ts[6 + k];
         int sec = R.sector[R.out.clus_index[off + n - 1]];
         double chi2 = 0.0;
         bool ok = true;
         const int nfloat = R.fp64 ? R.passes - 1 : R.passes;
-        for (int pass = 0; pass < nfloat && ok; pass++) ok = run_pass<float>(R, off, n, (pass % 2) == 0, sec, x, p, c, chi2);
+        for (int pass = 0; pass < nfloat && ok; pass++) ok = run_pass<float>(R, off, n, (pass % 2) == 0, sec, x, p, pl, c, chi2, nprop, zref);
         double c64[15];
         if (R.fp64 && ok) {
 #pragma unroll
             for (int k = 0; k < 15; k++) c64[k] = c[k];
-            ok = run_pass<double>(R, off, n, ((R.passes - 1) % 2) == 0, sec, x, p, c64, chi2);
+            ok = run_pass<double>(R, off, n, ((R.passes - 1) % 2) == 0, sec, x, p, pl, c64, chi2, nprop, zref);
 #pragma unroll
             for (int k = 0; k < 15; k++) c[k] = (float)c64[k];
         }
+#pragma unroll
+        for (int k = 0; k < 5; k++) p[k] = p[k] + pl[k];
+        p[1] = p[1] + zref;
         R.out.sector[r] = R.sector[R.out.clus_index[off]];
         R.out.x[r] = x;
 #pragma unroll
@@ -297,6 +352,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
             R.out.chi2_64[r] = chi2;
         }
     }
+    if (R.prof) atomicAdd(&f->w_refit_prop, (unsigned long long)nprop);
 }
 
 }  // namespace
@@ -318,18 +374,17 @@ int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const
     R.passes = p->refit_passes;
     R.fp64 = p->fp64_final;
     R.max_tracks = max_tracks;
+    R.prof = p->profile;
     volatile float kb = KB_C * bz;
     volatile float vy = p->sigma_y * p->sigma_y;
     volatile float vz = p->sigma_z * p->sigma_z;
     R.kb = kb;
     R.vy = vy;
     R.vz = vz;
-    R.c0s = p->c0_snp;
-    R.c0t = p->c0_tgl;
-    R.c0q = p->c0_qpt;
+    R.inflate = p->refit_inflate;
     R.out = *out;
     const int64_t want = (max_tracks + 127) / 128;
     const int grid = (int)(want < 1 ? 1 : (want > 148 * 16 ? 148 * 16 : want));
-    if (cl->n > 0) k_refit<<<grid, 128, 0, st>>>(R);
+    k_refit<<<grid, 128, 0, st>>>(R);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }

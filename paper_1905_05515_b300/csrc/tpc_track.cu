@@ -174,16 +174,27 @@ __global__ void k_scan_add(uint32_t* a, int64_t n, const uint32_t* sums)
 }
 
 // exclusive scan of a[0..n), total stored in a[n]; aux holds the tile sums
+int g_launches = 0;   // kernels launched by the current tpc_track call (host thread)
+
 void scan_u32(uint32_t* a, int64_t n, uint32_t* aux, cudaStream_t st)
 {
     const int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;    // include the total slot
-    // a[n] must be 0 on entry so that the scan of n+1 entries leaves the total there
+    // exclusive scan of the n+1 entries a[0..n]: a[n] (zero on entry) receives the total
     k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+    g_launches++;
     if (tiles > 1) {
-        scan_u32(aux, tiles - 1, aux + tiles + 1, st);   // aux[tiles-1] becomes the last exclusive offset
+        scan_u32(aux, tiles - 1, aux + tiles + 1, st);   // exclusive scan of the tile sums
         k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+        g_launches++;
     }
 }
+
+// stage events for params.profile (created once per process, per device)
+struct StageEvents {
+    int device = -1;
+    cudaEvent_t ev[TPC_N_STAGES + 1];
+};
+StageEvents g_events;
 
 // ---------------------------------------------------------------------------
 // a1 + a2: time -> z, validation, folded-z extrema; grid histogram / scatter
@@ -422,15 +433,18 @@ struct TrkArgs {
     int nr, ns, cap;
     float kb, vy, vz, c0s, c0t, c0q, nsig, wmin, wmax, chi2cut, edge;
     int max_miss;
+    int prof;
     int32_t *t_start, *t_id, *t_nhits, *t_nup, *t_hits;
     float *t_top, *t_bot;
+    Frame* fw;
 };
 
 __device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int s, float yp, float zp, float wy, float wz,
-                                            float zmin, float inv, int nz)
+                                            float zmin, float inv, int nz, unsigned& ncand)
 {
     const int c = grid_cell(fold(zp, s, A.ns), zmin, inv, nz);
     const Range rg = cell_range(A.cstart, pl, c, nz);
+    ncand += (unsigned)(rg.e - rg.b);
     int best = -1, bid = 0;
     float bd = 0.0f;
     for (int q = rg.b; q < rg.e; q++) {
@@ -460,6 +474,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
     const int nt = min(A.f->n_starts, A.cap);
     const float INF = __int_as_float(0x7f800000);
     const int NR = A.nr;
+    unsigned nprop = 0, nupd = 0, ncand = 0, nsearch = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const int h1 = A.starts[t];
         const int pl1 = A.plane[h1];
@@ -490,6 +505,8 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             const int hn = A.up[hc];
             const int rn = A.plane[hn] - pbase;
             if (!prop32(st, A.rowtab[rn * ROWTAB], A.kb)) { ok = false; break; }
+            nprop++;
+            nupd++;
             rc = rn;
             update32(st, A.ys[hn], A.zs[hn], A.vy, A.vz, INF);
             slot[nu++] = hn;
@@ -501,12 +518,15 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             int miss = 0;
             for (int r = rc + 1; r < NR; r++) {
                 if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
+                nprop++;
                 rc = r;
                 if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
                 const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
                 const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz);
+                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
+                nsearch++;
                 if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                    nupd++;
                     slot[nu++] = c;
                     copy_state(keep, st);
                     miss = 0;
@@ -524,13 +544,16 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             int miss = 0;
             for (int r = rc - 1; r >= 0; r--) {
                 if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
+                nprop++;
                 if (r > r1) continue;
                 if (r == r1) { copy_state(keep, st); continue; }
                 if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
                 const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
                 const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz);
+                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
+                nsearch++;
                 if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                    nupd++;
                     nd++;
                     slot[NR - nd] = c;
                     copy_state(keep, st);
@@ -547,6 +570,12 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
         A.t_id[t] = A.ids[h1];
         A.t_nhits[t] = nu + nd;
         A.t_nup[t] = nu;
+    }
+    if (A.prof) {
+        atomicAdd(&A.fw->w_prop, (unsigned long long)nprop);
+        atomicAdd(&A.fw->w_upd, (unsigned long long)nupd);
+        atomicAdd(&A.fw->w_cand, (unsigned long long)ncand);
+        (void)nsearch;
     }
 }
 
@@ -655,6 +684,8 @@ struct MergeArgs {
     const int32_t* byt;
     int32_t* bnext;
     int32_t* bprev;
+    int prof;
+    Frame* fw;
 };
 
 __device__ __forceinline__ int seg_sector(const MergeArgs& M, int a) { return M.plane[M.t_start[M.seg[a]]] / M.nr; }
@@ -663,6 +694,7 @@ __device__ __forceinline__ int seg_sector(const MergeArgs& M, int a) { return M.
 __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 {
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
+    unsigned nchi = 0;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
         const int ta = M.seg[a];
         const int sa = seg_sector(M, a);
@@ -684,6 +716,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
                 const float* bot = M.t_bot + (int64_t)tb * NST;
                 if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
                 const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
+                nchi++;
                 if (!(c2 < M.chi2cut)) continue;
                 const int idb = M.t_id[tb];
                 if (best < 0 || c2 < bc || (c2 == bc && idb < bid)) { best = b; bc = c2; bid = idb; }
@@ -691,6 +724,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
         }
         M.bnext[a] = best;
     }
+    if (M.prof) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
 }
 
 // best A (inner piece) for every B
@@ -908,6 +942,7 @@ int tpc_params_default(tpc_params* p)
     p->merge_dz = 10.0f;
     p->merge_chi2 = 50.0f;
     p->refit_passes = 3;
+    p->refit_inflate = 100.0f;
     p->z_cell = 3.5f;
     p->max_z_cells = 1024;
     p->tracklets_per_1k = 125;
@@ -922,6 +957,7 @@ static int check_args(const tpc_params* p, const tpc_geometry* g)
     if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
     if (g->n_sectors * g->n_rows > 65535) return TPC_ERR_ARG;
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
+    if (!(p->refit_inflate >= 1.0f)) return TPC_ERR_ARG;
     if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
@@ -974,6 +1010,15 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     int32_t* starts = at<int32_t>(ws, L.starts);
     unsigned long long* hitw = at<unsigned long long>(ws, L.hitw);
 
+    if (n == 0) {
+        CK(cudaMemsetAsync(out->clus_offset, 0, sizeof(int32_t), st));
+        CK(cudaStreamSynchronize(st));
+        out->n_launches = 0;
+        for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
+        for (int k = 0; k < 5; k++) out->work[k] = 0;
+        return TPC_OK;
+    }
+
     // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r], (X[r]-X[r-1])/(X[r+1]-X[r-1])
     float tab[ROWTAB * 256];
     memset(tab, 0, sizeof(tab));
@@ -1005,47 +1050,68 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     const int gN = grid_for(n, B);
     const int ntcap = L.ntcap;
 
+    // stage events (params.profile): created once per device, recorded on the caller's stream
+    const bool prof = p->profile != 0;
+    if (prof) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (g_events.device != dev) {
+            for (int k = 0; k <= TPC_N_STAGES; k++) CK(cudaEventCreate(&g_events.ev[k]));
+            g_events.device = dev;
+        }
+    }
+    auto mark = [&](int k) -> cudaError_t { return prof ? cudaEventRecord(g_events.ev[k], st) : cudaSuccess; };
+    g_launches = 0;
+
+    CK(mark(0));
     k_init_frame<<<1, 32, 0, st>>>(f);
-    if (n > 0)
-        k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
-                                 g->z_max, v_drift, zlin, f);
+    k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
+                             g->z_max, v_drift, zlin, f);
     k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, L.nzmax, p->merge_dz * 1.1f + 0.5f, L.mnzmax);
+    g_launches += 3;
+    CK(mark(1));
+    // a2: counting sort of the clusters into (sector, row, z-cell) order
     CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(L.ncells + 1), st));
-    if (n > 0) {
-        k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
-    }
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
+    g_launches++;
     scan_u32(cstart, L.ncells, aux, st);
-    if (n > 0) {
-        k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs,
-                                    ids, plane, f);
-        k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f,
-                                       p->dy_link, p->dz_link, p->s_max_link, upr, dnr);
-        k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
-        k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
-    }
-    // tracklets
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs, ids,
+                                plane, f);
+    g_launches++;
+    CK(mark(2));
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f, p->dy_link,
+                                   p->dz_link, p->s_max_link, upr, dnr);
+    g_launches++;
+    CK(mark(3));
+    k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
+    k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
+    g_launches += 2;
+    CK(mark(4));
+    // a6: tracklets
     TrkArgs TA;
     TA.rowtab = rowtab; TA.ys = ys; TA.zs = zs; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
     TA.starts = starts; TA.f = f; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.cap = ntcap;
     TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
     TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
-    TA.edge = p->edge_margin; TA.max_miss = p->max_miss;
+    TA.edge = p->edge_margin; TA.max_miss = p->max_miss; TA.prof = prof ? 1 : 0; TA.fw = f;
     TA.t_start = at<int32_t>(ws, L.t_start); TA.t_id = at<int32_t>(ws, L.t_id);
     TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
     TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
     const int gT = grid_for(ntcap, 128);
-    if (n > 0) k_tracklets<<<gT, 128, 0, st>>>(TA);
-    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)std::max(n, 1), st));
+    k_tracklets<<<gT, 128, 0, st>>>(TA);
+    g_launches++;
+    CK(mark(5));
+    // a7: selector
+    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)n, st));
     const int gt2 = grid_for(ntcap, B);
     uint8_t* kept = at<uint8_t>(ws, L.t_kept);
     int32_t* seg = at<int32_t>(ws, L.seg);
-    if (n > 0) {
-        k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits,
-                                        hitw);
-        k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
-                                     TA.t_hits, hitw, kept, seg);
-    }
-    // merger
+    k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
+    k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
+                                 TA.t_hits, hitw, kept, seg);
+    g_launches += 2;
+    CK(mark(6));
+    // a8: merger
     const int64_t mcells = (int64_t)g->n_sectors * L.mnzmax;
     uint32_t* cntb = at<uint32_t>(ws, L.cntb);
     uint32_t* cntt = at<uint32_t>(ws, L.cntt);
@@ -1054,57 +1120,73 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, st));
     CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
     uint32_t* headmark = at<uint32_t>(ws, L.headmark);
-    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(std::max(n, 1) + 1), st));
-    if (n > 0) {
-        k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, seg, plane, TA.t_start, g->n_rows, TA.t_top, TA.t_bot, cntb,
-                                      cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
-                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott));
-    }
+    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), st));
+    k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, seg, plane, TA.t_start, g->n_rows, TA.t_top, TA.t_bot, cntb, cntt,
+                                  at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt), at<uint32_t>(ws, L.slotb),
+                                  at<uint32_t>(ws, L.slott));
+    g_launches++;
     scan_u32(cntb, mcells, aux, st);
     scan_u32(cntt, mcells, aux, st);
     MergeArgs M;
     M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
     M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
     M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
-    M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev);
-    if (n > 0) {
-        k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
-                                         at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
-                                         at<int32_t>(ws, L.byt));
-        k_merge_next<<<gT, 128, 0, st>>>(M);
-        k_merge_prev<<<gT, 128, 0, st>>>(M);
-        k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
-        k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
-        k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
-                                       at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
-    }
-    scan_u32(headmark, std::max(n, 1), aux, st);
-    // track assembly
+    M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
+    k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
+                                     at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
+                                     at<int32_t>(ws, L.byt));
+    k_merge_next<<<gT, 128, 0, st>>>(M);
+    k_merge_prev<<<gT, 128, 0, st>>>(M);
+    k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
+    k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
+    k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
+                                   at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
+    g_launches += 6;
+    scan_u32(headmark, n, aux, st);
+    CK(mark(7));
+    // merged cluster lists and assignments
     uint32_t* tcount = at<uint32_t>(ws, L.tcount);
     CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), st));
-    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)std::max(n, 1), st));
+    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)n, st));
     AsmArgs AA;
-    AA.f = f; AA.nr = g->n_rows; AA.n = std::max(n, 1); AA.cap_tracks = out->capacity_tracks;
+    AA.f = f; AA.nr = g->n_rows; AA.n = n; AA.cap_tracks = out->capacity_tracks;
     AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
     AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits; AA.t_nup = TA.t_nup;
     AA.t_hits = TA.t_hits; AA.ids = ids; AA.hitw = hitw; AA.headmark = headmark; AA.tcount = tcount;
     AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail); AA.clus_offset = out->clus_offset;
     AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
-    if (n > 0) k_track_count<<<gt2, B, 0, st>>>(AA);
+    k_track_count<<<gt2, B, 0, st>>>(AA);
+    g_launches++;
     scan_u32(tcount, ntcap, aux, st);
     k_track_fill<<<gt2, B, 0, st>>>(AA);
+    g_launches++;
+    CK(mark(8));
+    // a9: refit
     int rr = tpc_launch_refit(p, g, bz, cl, zlin, rowtab, f, AA.ttail, TA.t_top, out,
                               std::min(out->capacity_tracks, ntcap), st);
     if (rr) return rr;
+    g_launches++;
+    CK(mark(9));
     // optional intermediate outputs
-    if (out->z && n > 0) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (n > 0 && (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start))
+    if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
         k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
                                          out->link_dn, out->is_start, f);
+        g_launches++;
+    }
     CK(cudaGetLastError());
     Frame hf;
     CK(cudaMemcpyAsync(&hf, f, sizeof(Frame), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    out->n_launches = g_launches;
+    out->work[0] = (int64_t)hf.w_prop;
+    out->work[1] = (int64_t)hf.w_upd;
+    out->work[2] = (int64_t)hf.w_cand;
+    out->work[3] = (int64_t)hf.w_refit_prop;
+    out->work[4] = (int64_t)hf.w_merge;
+    for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
+    if (prof)
+        for (int k = 0; k < 9; k++) CK(cudaEventElapsedTime(&out->stage_ms[k], g_events.ev[k], g_events.ev[k + 1]));
     out->n_tracklets = std::min(hf.n_starts, ntcap);
     out->n_segments = hf.n_seg;
     out->n_tracks = hf.n_tracks;

@@ -40,6 +40,9 @@ class TrackResult:
     is_start: torch.Tensor | None = None
     n_tracklets: int = 0
     n_segments: int = 0
+    n_launches: int = 0
+    stage_ms: dict | None = None
+    work: dict | None = None
 
 
 class Tracker:
@@ -121,7 +124,10 @@ class Tracker:
                           cov=b["cov"][:T], chi2=b["chi2"][:T], ndf=b["ndf"][:T], status=b["status"][:T],
                           nclus=b["nclus"][:T], clus_offset=b["clus_offset"][:T + 1],
                           clus_index=b["clus_index"], assign=b["assign"][:n],
-                          n_tracklets=out.n_tracklets, n_segments=out.n_segments)
+                          n_tracklets=out.n_tracklets, n_segments=out.n_segments, n_launches=out.n_launches,
+                          stage_ms={k: float(out.stage_ms[i]) for i, k in enumerate(abi.STAGES)},
+                          work=dict(zip(("trk_prop", "trk_upd", "trk_cand", "refit_prop", "merge_chi2"),
+                                        (int(v) for v in out.work))))
         if "cov64" in b:
             res.cov64, res.chi2_64 = b["cov64"][:T], b["chi2_64"][:T]
         if self.debug:
