@@ -177,6 +177,34 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
                          int32_t *nhits, uint8_t *kept, int32_t *hits, float *top, float *bot,
                          int32_t *nt_out, void *stream);
 
+/* Seeding without any allocation: time -> z, per-row grid binning,
+ * NeighboursFinder and NeighboursCleaner for at most
+ * TPC_LINKS_STATIC_MAX_CLUSTERS clusters, with all scratch memory in a fixed
+ * device array inside the library.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory: code running
+ * inside a CUDA graph being captured or replayed, a host thread that must
+ * not block on the allocator while other streams run, or an embedding that
+ * forbids cudaMalloc after start-up.  They still pass their own device inputs
+ * and outputs; nothing else is allocated, by them or by the library.
+ *   - Outputs (device, indexed by input cluster): link_up, link_dn (cleaned
+ *     links, input index or -1), is_start (nullable, 0/1).  They equal the
+ *     link_up / link_dn / is_start outputs of tpc_track on the same input.
+ *   - Limit: n <= TPC_LINKS_STATIC_MAX_CLUSTERS; larger inputs return
+ *     TPC_ERR_CAPACITY without touching the GPU.  n_sectors * n_rows <= 9180.
+ *   - The fixed array holds TPC_LINKS_STATIC_SCRATCH_BYTES on every GPU that
+ *     loads the library, until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind (the
+ *     call clears what must start at zero).  Calls that overlap on the GPU --
+ *     on two streams, or from two host threads -- race on it: serialise them.
+ *   - Enqueues on `stream`, then waits for it (to read the data-error flag).
+ * Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_DATA, TPC_ERR_CUDA. */
+#define TPC_LINKS_STATIC_MAX_CLUSTERS 262144
+#define TPC_LINKS_STATIC_SCRATCH_BYTES 13365760
+int tpc_links_static(const tpc_params *p, const tpc_geometry *g, float v_drift, const tpc_clusters *cl,
+                     int32_t *link_up, int32_t *link_dn, uint8_t *is_start, void *stream);
+
 /* Human-readable name of a return code (static string). */
 const char *tpc_error_string(int code);
 

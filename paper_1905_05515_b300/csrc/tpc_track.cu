@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 using namespace tpc;
@@ -910,6 +911,67 @@ __global__ void k_export_links(int n, const int32_t* __restrict__ ids, const int
         if (e_ != cudaSuccess) return TPC_ERR_CUDA;    \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Scratch for tpc_links_static: a file-scope device array, so that the entry
+// point needs no allocation by its caller or by the library.  Sized for
+// TPC_LINKS_STATIC_MAX_CLUSTERS clusters with a coarser grid (64 z-cells per
+// pad row; coarser cells scan more candidates but give the same links).
+// ---------------------------------------------------------------------------
+constexpr int STATIC_NZ = 64;
+constexpr int STATIC_MAX_PLANES = 36 * 255;
+constexpr int64_t STATIC_NCELLS = (int64_t)STATIC_MAX_PLANES * STATIC_NZ;
+
+struct StaticLayout {
+    size_t frame, rowtab, zlin, cell, slot, cstart, scan, ys, zs, ids, plane, upr, dnr, up, dn, total;
+};
+
+constexpr size_t sa256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr StaticLayout static_layout()
+{
+    const size_t N = TPC_LINKS_STATIC_MAX_CLUSTERS;
+    StaticLayout L{};
+    size_t o = 0;
+    L.frame = o; o += sa256(sizeof(Frame));
+    L.rowtab = o; o += sa256(sizeof(float) * ROWTAB * 256);
+    L.zlin = o; o += sa256(4 * N);
+    L.cell = o; o += sa256(4 * N);
+    L.slot = o; o += sa256(4 * N);
+    L.cstart = o; o += sa256(4 * (STATIC_NCELLS + 1));
+    L.scan = o; o += sa256(4 * (STATIC_NCELLS / SCAN_TILE + 64));
+    L.ys = o; o += sa256(4 * N);
+    L.zs = o; o += sa256(4 * N);
+    L.ids = o; o += sa256(4 * N);
+    L.plane = o; o += sa256(2 * N);
+    L.upr = o; o += sa256(4 * N);
+    L.dnr = o; o += sa256(4 * N);
+    L.up = o; o += sa256(4 * N);
+    L.dn = o; o += sa256(4 * N);
+    L.total = o;
+    return L;
+}
+constexpr StaticLayout SL = static_layout();
+static_assert(SL.total == TPC_LINKS_STATIC_SCRATCH_BYTES, "scratch size stated in tpc_track.h");
+
+static __device__ __align__(256) unsigned char g_links_scratch[TPC_LINKS_STATIC_SCRATCH_BYTES];
+
+// device address of g_links_scratch, looked up once per device
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[128] = {nullptr};
+
+int static_scratch(void** ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return TPC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_links_scratch) != cudaSuccess || !p) return TPC_ERR_CUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *ptr = g_scratch_ptr[dev];
+    return TPC_OK;
+}
+
 }  // namespace
 
 // refit launcher (tpc_refit.cu)
@@ -1254,6 +1316,78 @@ int tpc_export_tracklets(const void* ws, int32_t capacity, int32_t hits_stride, 
         memcpy(bot + (size_t)k * NST, &bt[(size_t)t * NST], NST * sizeof(float));
     }
     return TPC_OK;
+}
+
+int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, const tpc_clusters* cl,
+                     int32_t* link_up, int32_t* link_dn, uint8_t* is_start, void* stream)
+{
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    if (!cl || cl->n < 0 || !link_up || !link_dn) return TPC_ERR_ARG;
+    const int n = cl->n;
+    if (n > TPC_LINKS_STATIC_MAX_CLUSTERS) return TPC_ERR_CAPACITY;
+    if (n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->zt)) return TPC_ERR_ARG;
+    if (g->n_sectors * g->n_rows > STATIC_MAX_PLANES) return TPC_ERR_ARG;
+    if (n == 0) return TPC_OK;
+    void* base = nullptr;
+    rc = static_scratch(&base);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Frame* f = at<Frame>(base, SL.frame);
+    float* rowtab = at<float>(base, SL.rowtab);
+    float* zlin = at<float>(base, SL.zlin);
+    uint32_t* cell = at<uint32_t>(base, SL.cell);
+    uint32_t* slot = at<uint32_t>(base, SL.slot);
+    uint32_t* cstart = at<uint32_t>(base, SL.cstart);
+    uint32_t* aux = at<uint32_t>(base, SL.scan);
+    float* ys = at<float>(base, SL.ys);
+    float* zs = at<float>(base, SL.zs);
+    int32_t* ids = at<int32_t>(base, SL.ids);
+    uint16_t* plane = at<uint16_t>(base, SL.plane);
+    int32_t* upr = at<int32_t>(base, SL.upr);
+    int32_t* dnr = at<int32_t>(base, SL.dnr);
+    int32_t* up = at<int32_t>(base, SL.up);
+    int32_t* dn = at<int32_t>(base, SL.dn);
+    float tab[ROWTAB * 256];
+    memset(tab, 0, sizeof(tab));
+    const float* X = g->row_x;
+    for (int r = 0; r < g->n_rows; r++) {
+        volatile float xr = X[r];
+        tab[r * ROWTAB] = xr;
+        if (r >= 1 && r + 1 < g->n_rows) {
+            volatile float a = X[r + 1] / X[r];
+            volatile float b = X[r - 1] / X[r];
+            volatile float num = X[r] - X[r - 1];
+            volatile float den = X[r + 1] - X[r - 1];
+            volatile float w = num / den;
+            tab[r * ROWTAB + 1] = a;
+            tab[r * ROWTAB + 2] = b;
+            tab[r * ROWTAB + 3] = w;
+        }
+    }
+    CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
+    const int64_t ncells = (int64_t)g->n_sectors * g->n_rows * STATIC_NZ;
+    const int B = 256;
+    const int gN = grid_for(n, B);
+    k_init_frame<<<1, 32, 0, st>>>(f);
+    k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
+                             g->z_max, v_drift, zlin, f);
+    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, STATIC_NZ, p->merge_dz * 1.1f + 0.5f, MAX_MERGE_CELLS);
+    // the histogram must start at zero: the scratch keeps the previous call's contents
+    CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(ncells + 1), st));
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
+    scan_u32(cstart, ncells, aux, st);
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs, ids,
+                                plane, f);
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f, p->dy_link,
+                                   p->dz_link, p->s_max_link, upr, dnr);
+    k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
+    k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);
+    CK(cudaGetLastError());
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &f->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return err ? err : TPC_OK;
 }
 
 const char* tpc_error_string(int code)
