@@ -467,6 +467,14 @@ __device__ __forceinline__ void copy_state(float* d, const float* s)
     for (int i = 0; i < NST; i++) d[i] = s[i];
 }
 
+// Phases of one tracklet (the operation sequence per tracklet is fixed; the
+// kernel only interleaves tracklets differently across lanes)
+enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
+
+// One lane = one tracklet at a time.  Each loop iteration advances the lane's
+// tracklet by one row step; a lane whose tracklet ends writes it out and takes
+// the next start hit from a global queue, so lanes stay busy however uneven
+// the tracklet lengths are.
 __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
 {
     if (A.f->err) return;
@@ -475,37 +483,77 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
     const int nt = min(A.f->n_starts, A.cap);
     const float INF = __int_as_float(0x7f800000);
     const int NR = A.nr;
-    unsigned nprop = 0, nupd = 0, ncand = 0, nsearch = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        const int h1 = A.starts[t];
-        const int pl1 = A.plane[h1];
-        const int s = pl1 / NR, r1 = pl1 - s * NR;
-        const int pbase = s * NR;
-        const int h2 = A.up[h1];
-        float st[NST], keep[NST];
-        const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
-        const float dx12 = x2 - x1;
-        const float y1 = A.ys[h1], z1 = A.zs[h1];
-        const float dy12 = A.ys[h2] - y1, dz12 = A.zs[h2] - z1;
-        const float ty = __fdiv_rn(dy12, dx12);
-        const float sp = __fdiv_rn(ty, __fsqrt_rn(__fmaf_rn(ty, ty, 1.0f)));
-        const float dl12 = __fsqrt_rn(__fmaf_rn(dx12, dx12, dy12 * dy12));
-        const float tl = __fdiv_rn(dz12, dl12);
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned nprop = 0, nupd = 0, ncand = 0;
+
+    float st[NST], keep[NST];
+    int t = -1, phase = PH_DONE;
+    int h1 = 0, r1 = 0, s = 0, pbase = 0, hc = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
+    bool ok = true;
+    int32_t* slot = nullptr;
+    for (;;) {
+        if (phase == PH_DONE) {
+            if (t >= 0) {
+                float* bot = A.t_bot + (int64_t)t * NST;
 #pragma unroll
-        for (int i = 0; i < NST; i++) st[i] = 0.0f;
-        st[0] = x1; st[1] = y1; st[2] = z1; st[3] = sp; st[4] = tl; st[5] = 0.0f;
-        st[6 + 0] = A.vy; st[6 + 2] = A.vz; st[6 + 5] = A.c0s; st[6 + 9] = A.c0t; st[6 + 14] = A.c0q;
-        int32_t* slot = A.t_hits + (int64_t)t * NR;
-        int nu = 0, nd = 0;
-        slot[nu++] = h1;
-        copy_state(keep, st);
-        int rc = r1;
-        bool ok = true;
-        // phase A: fit along the up links
-        for (int hc = h1; A.up[hc] >= 0;) {
+                for (int i = 0; i < NST; i++) bot[i] = keep[i];
+                A.t_start[t] = h1;
+                A.t_id[t] = A.ids[h1];
+                A.t_nhits[t] = nu + nd;
+                A.t_nup[t] = nu;
+            }
+            // next start hit from the queue (one atomic per group of lanes asking together)
+            const unsigned m = __activemask();
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if ((int)lane == leader) base = atomicAdd(&A.fw->trk_next, __popc(m));
+            base = __shfl_sync(m, base, leader);
+            t = base + __popc(m & ((1u << lane) - 1u));
+            if (t >= nt) break;
+            // initial state at the start hit: y, z measured, slopes from the first link
+            h1 = A.starts[t];
+            const int pl1 = A.plane[h1];
+            s = pl1 / NR;
+            r1 = pl1 - s * NR;
+            pbase = s * NR;
+            const int h2 = A.up[h1];
+            const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
+            const float dx12 = x2 - x1;
+            const float y1 = A.ys[h1], z1 = A.zs[h1];
+            const float dy12 = A.ys[h2] - y1, dz12 = A.zs[h2] - z1;
+            const float ty = __fdiv_rn(dy12, dx12);
+            const float sp = __fdiv_rn(ty, __fsqrt_rn(__fmaf_rn(ty, ty, 1.0f)));
+            const float dl12 = __fsqrt_rn(__fmaf_rn(dx12, dx12, dy12 * dy12));
+            const float tl = __fdiv_rn(dz12, dl12);
+#pragma unroll
+            for (int i = 0; i < NST; i++) st[i] = 0.0f;
+            st[0] = x1; st[1] = y1; st[2] = z1; st[3] = sp; st[4] = tl; st[5] = 0.0f;
+            st[6 + 0] = A.vy; st[6 + 2] = A.vz; st[6 + 5] = A.c0s; st[6 + 9] = A.c0t; st[6 + 14] = A.c0q;
+            slot = A.t_hits + (int64_t)t * NR;
+            nu = 0;
+            nd = 0;
+            slot[nu++] = h1;
+            copy_state(keep, st);
+            rc = r1;
+            hc = h1;
+            ok = true;
+            miss = 0;
+            phase = PH_A;
+        }
+        if (phase == PH_A) {
+            // phase A: fit along the up links
             const int hn = A.up[hc];
+            if (hn < 0) {
+                phase = PH_B;
+                miss = 0;
+                continue;
+            }
             const int rn = A.plane[hn] - pbase;
-            if (!prop32(st, A.rowtab[rn * ROWTAB], A.kb)) { ok = false; break; }
+            if (!prop32(st, A.rowtab[rn * ROWTAB], A.kb)) {
+                ok = false;
+                phase = PH_CSTART;
+                continue;
+            }
             nprop++;
             nupd++;
             rc = rn;
@@ -513,70 +561,85 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             slot[nu++] = hn;
             copy_state(keep, st);
             hc = hn;
+            continue;
         }
-        // phase B: follow row by row beyond the chain end
-        if (ok) {
-            int miss = 0;
-            for (int r = rc + 1; r < NR; r++) {
-                if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
-                nprop++;
-                rc = r;
-                if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
-                const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
-                const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
-                nsearch++;
-                if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
-                    nupd++;
-                    slot[nu++] = c;
-                    copy_state(keep, st);
-                    miss = 0;
-                } else if (++miss >= A.max_miss) {
-                    break;
-                }
+        if (phase == PH_B) {
+            // phase B: follow row by row beyond the chain end
+            const int rr = rc + 1;
+            if (!ok || rr >= NR || !prop32(st, A.rowtab[rr * ROWTAB], A.kb)) {
+                phase = PH_CSTART;
+                continue;
             }
+            nprop++;
+            rc = rr;
+            if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) {
+                phase = PH_CSTART;
+                continue;
+            }
+            const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
+            const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
+            const int c = find_nearest(A, pbase + rr, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
+            if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                nupd++;
+                slot[nu++] = c;
+                copy_state(keep, st);
+                miss = 0;
+            } else if (++miss >= A.max_miss) {
+                phase = PH_CSTART;
+            }
+            continue;
         }
-        float* top = A.t_top + (int64_t)t * NST;
+        if (phase == PH_CSTART) {
+            // end of the upward phases: the outer-end state is final
+            float* top = A.t_top + (int64_t)t * NST;
 #pragma unroll
-        for (int i = 0; i < NST; i++) top[i] = keep[i];
+            for (int i = 0; i < NST; i++) top[i] = keep[i];
+            if (rc == r1) copy_state(keep, st);
+            miss = 0;
+            r = rc - 1;
+            phase = PH_C;
+            continue;
+        }
         // phase C: back down through the fitted rows, then follow below the start
-        if (rc == r1) copy_state(keep, st);
+        if (r < 0 || !prop32(st, A.rowtab[r * ROWTAB], A.kb)) {
+            phase = PH_DONE;
+            continue;
+        }
+        nprop++;
+        if (r > r1) {
+            r--;
+            continue;
+        }
+        if (r == r1) {
+            copy_state(keep, st);
+            r--;
+            continue;
+        }
+        if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) {
+            phase = PH_DONE;
+            continue;
+        }
         {
-            int miss = 0;
-            for (int r = rc - 1; r >= 0; r--) {
-                if (!prop32(st, A.rowtab[r * ROWTAB], A.kb)) break;
-                nprop++;
-                if (r > r1) continue;
-                if (r == r1) { copy_state(keep, st); continue; }
-                if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) break;
-                const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
-                const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-                const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
-                nsearch++;
-                if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
-                    nupd++;
-                    nd++;
-                    slot[NR - nd] = c;
-                    copy_state(keep, st);
-                    miss = 0;
-                } else if (++miss >= A.max_miss) {
-                    break;
-                }
+            const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
+            const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
+            const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
+            if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+                nupd++;
+                nd++;
+                slot[NR - nd] = c;
+                copy_state(keep, st);
+                miss = 0;
+            } else if (++miss >= A.max_miss) {
+                phase = PH_DONE;
+                continue;
             }
         }
-        float* bot = A.t_bot + (int64_t)t * NST;
-#pragma unroll
-        for (int i = 0; i < NST; i++) bot[i] = keep[i];
-        A.t_start[t] = h1;
-        A.t_id[t] = A.ids[h1];
-        A.t_nhits[t] = nu + nd;
-        A.t_nup[t] = nu;
+        r--;
     }
     if (A.prof) {
         atomicAdd(&A.fw->w_prop, (unsigned long long)nprop);
         atomicAdd(&A.fw->w_upd, (unsigned long long)nupd);
         atomicAdd(&A.fw->w_cand, (unsigned long long)ncand);
-        (void)nsearch;
     }
 }
 
