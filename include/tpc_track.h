@@ -77,7 +77,9 @@ typedef struct {
                                     covariance times this factor (y, z from the first measurement) */
     /* acceleration structure and capacities (do not change results) */
     float z_cell;                /* minimum grid cell length in z (cm); must exceed dz_link, win_max */
-    int32_t max_z_cells;         /* maximum grid cells per pad row */
+    int32_t max_z_cells;         /* maximum grid z-cells per pad row */
+    int32_t y_bins;              /* grid y-bins per z-cell (reduced as needed to keep every bin
+                                    wider than the y search windows) */
     int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
     int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
     int32_t profile;             /* 1: record CUDA events on the stream at stage boundaries (tpc_tracks.stage_ms) */
@@ -201,7 +203,7 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
  *   - Enqueues on `stream`, then waits for it (to read the data-error flag).
  * Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_DATA, TPC_ERR_CUDA. */
 #define TPC_LINKS_STATIC_MAX_CLUSTERS 262144
-#define TPC_LINKS_STATIC_SCRATCH_BYTES 13365760
+#define TPC_LINKS_STATIC_SCRATCH_BYTES 13367808
 int tpc_links_static(const tpc_params *p, const tpc_geometry *g, float v_drift, const tpc_clusters *cl,
                      int32_t *link_up, int32_t *link_dn, uint8_t *is_start, void *stream);
 

@@ -15,6 +15,7 @@
 namespace tpc {
 
 constexpr int NST = 21;                // x, p[5], c[15]
+constexpr int ROWTAB = 6;              // per-row table: X, q_up, q_dn, w, y-bin origin, 1/y-bin width
 constexpr float SNP_MAX = 0.999f;
 constexpr float U_MAX = 0.1f;
 // asin(u)/u = 1 + u^2/6 + 3u^4/40 + 5u^6/112 + ..., and d/du of it
@@ -240,7 +241,8 @@ __device__ __forceinline__ float merge_chi2(const float* top, const float* bot, 
 struct Frame {
     unsigned zmin_key, zmax_key;   // order-preserving keys of the folded-z extrema
     float zmin, inv_cs;            // grid origin and 1 / cell length
-    int nz;                        // grid cells per plane
+    int nz;                        // grid z-cells per plane
+    int ny;                        // grid y-bins per z-cell
     float mzmin, minv_cs;          // merger grid
     int mnz;
     int err;                       // TPC_ERR_* set by kernels (0 = ok)

@@ -273,7 +273,7 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
             if (!rot<CT>(x, p, pl, c, cs, sn, R.kb)) return false;
             sec = s;
         }
-        if (!prop<CT>(x, p, pl, c, R.rowtab[R.row[id] * 4], R.kb)) return false;
+        if (!prop<CT>(x, p, pl, c, R.rowtab[R.row[id] * ROWTAB], R.kb)) return false;
         nprop++;
         const float my = R.y[id], mz = R.zlin[id] - zref;
         if (q == 0) {

@@ -25,7 +25,7 @@ constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
-constexpr int ROWTAB = 4;   // X, q_up, q_dn, w per row
+constexpr float Y_MARGIN = 1.0f;   // y-bin range beyond the sector edge (cm)
 constexpr uint32_t WS_MAGIC = 0x54504331u;
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -35,9 +35,9 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // ---------------------------------------------------------------------------
 struct Layout {
     uint32_t magic;
-    int32_t n, ns, nr, np, nzmax, ntcap, mnzmax;
+    int32_t n, ns, nr, np, nzmax, ntcap, mnzmax, ny;
     int64_t ncells;
-    size_t hdr, frame, rowtab, zlin, cell, slot, cstart, scan, ys, zs, ids, plane;
+    size_t hdr, frame, rowtab, zlin, cell, slot, cstart, scan, yz, ids, plane;
     size_t upr, dnr, up, dn, starts;
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
@@ -56,6 +56,41 @@ int64_t scan_aux_elems(int64_t n)
     return s + 16;
 }
 
+// y-bins per z-cell: as many as the narrowest row allows with every bin wider
+// than the largest y search window (link window, following window)
+int effective_ybins(const tpc_params* p, const tpc_geometry* g)
+{
+    const float w = std::max(p->dy_link, p->win_max) * 1.01f + 0.01f;
+    const float width = 2.0f * (g->row_x[0] * TAN10 + Y_MARGIN);
+    int ny = (int)std::floor(width / w);
+    return std::max(1, std::min(ny, std::max(1, p->y_bins)));
+}
+
+// per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r],
+// (X[r]-X[r-1]) / (X[r+1]-X[r-1]), then the y-bin origin and inverse width
+void fill_rowtab(float* tab, const tpc_geometry* g, int ny)
+{
+    memset(tab, 0, sizeof(float) * ROWTAB * 256);
+    const float* X = g->row_x;
+    for (int r = 0; r < g->n_rows; r++) {
+        volatile float xr = X[r];
+        tab[r * ROWTAB] = xr;
+        if (r >= 1 && r + 1 < g->n_rows) {
+            volatile float a = X[r + 1] / X[r];
+            volatile float b = X[r - 1] / X[r];
+            volatile float num = X[r] - X[r - 1];
+            volatile float den = X[r + 1] - X[r - 1];
+            volatile float w = num / den;
+            tab[r * ROWTAB + 1] = a;
+            tab[r * ROWTAB + 2] = b;
+            tab[r * ROWTAB + 3] = w;
+        }
+        const float half = xr * TAN10 + Y_MARGIN;
+        tab[r * ROWTAB + 4] = -half;
+        tab[r * ROWTAB + 5] = (float)ny / (2.0f * half);
+    }
+}
+
 Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
 {
     Layout L;
@@ -66,7 +101,8 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
     L.nr = g->n_rows;
     L.np = L.ns * L.nr;
     L.nzmax = p->max_z_cells;
-    L.ncells = (int64_t)L.np * L.nzmax;
+    L.ny = effective_ybins(p, g);
+    L.ncells = (int64_t)L.np * L.nzmax * L.ny;
     int64_t cap = std::max<int64_t>(4096, (n * (int64_t)p->tracklets_per_1k) / 1000);
     L.ntcap = (int32_t)std::min<int64_t>(cap, std::max<int64_t>(n, 4096));
     L.mnzmax = MAX_MERGE_CELLS;
@@ -84,8 +120,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
     L.slot = take(4 * N);
     L.cstart = take(4 * (L.ncells + 1));
     L.scan = take(4 * scan_aux_elems(scan_max));
-    L.ys = take(4 * N);
-    L.zs = take(4 * N);
+    L.yz = take(8 * N);
     L.ids = take(4 * N);
     L.plane = take(2 * N);
     L.upr = take(4 * N);
@@ -249,9 +284,10 @@ __global__ void k_prep(int n, const uint8_t* __restrict__ sector, const uint8_t*
     }
 }
 
-__global__ void k_grid_setup(Frame* f, float z_cell, int nzmax, float merge_cell, int mnzmax)
+__global__ void k_grid_setup(Frame* f, float z_cell, int nzmax, float merge_cell, int mnzmax, int ny)
 {
     if (threadIdx.x != 0) return;
+    f->ny = ny;
     float zmin = 0.0f, span = 0.0f;
     if (f->zmin_key != 0xFFFFFFFFu) {
         zmin = fkey_inv(f->zmin_key);
@@ -269,17 +305,27 @@ __global__ void k_grid_setup(Frame* f, float z_cell, int nzmax, float merge_cell
 
 __device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
 
+__device__ __forceinline__ int ybin(float y, const float* __restrict__ rowtab, int r, int ny)
+{
+    float t = (y - rowtab[r * ROWTAB + 4]) * rowtab[r * ROWTAB + 5];
+    t = fminf(fmaxf(t, 0.0f), (float)(ny - 1));   // NaN -> 0
+    return (int)t;
+}
+
+
 __global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
-                       const float* __restrict__ zlin, int nr, int ns, const Frame* __restrict__ f,
-                       uint32_t* __restrict__ count, uint32_t* __restrict__ cell, uint32_t* __restrict__ slot)
+                       const float* __restrict__ y, const float* __restrict__ zlin, const float* __restrict__ rowtab,
+                       int nr, int ns, const Frame* __restrict__ f, uint32_t* __restrict__ count,
+                       uint32_t* __restrict__ cell, uint32_t* __restrict__ slot)
 {
     if (f->err) return;   // invalid clusters: nothing after validation runs
     const float zmin = f->zmin, inv = f->inv_cs;
-    const int nz = f->nz;
+    const int nz = f->nz, ny = f->ny;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int s = sector[i], r = row[i];
         const int pl = s * nr + r;
-        const uint32_t c = (uint32_t)pl * (uint32_t)nz + (uint32_t)grid_cell(fold(zlin[i], s, ns), zmin, inv, nz);
+        const int zc = grid_cell(fold(zlin[i], s, ns), zmin, inv, nz);
+        const uint32_t c = ((uint32_t)pl * (uint32_t)nz + (uint32_t)zc) * (uint32_t)ny + (uint32_t)ybin(y[i], rowtab, r, ny);
         cell[i] = c;
         slot[i] = atomicAdd(&count[c], 1u);
     }
@@ -288,30 +334,40 @@ __global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t*
 __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
                           const float* __restrict__ y, const float* __restrict__ zlin, int nr,
                           const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
-                          const uint32_t* __restrict__ slot, float* __restrict__ ys, float* __restrict__ zs,
+                          const uint32_t* __restrict__ slot, float2* __restrict__ yz,
                           int32_t* __restrict__ ids, uint16_t* __restrict__ plane, const Frame* __restrict__ f)
 {
     if (f->err) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pos = cstart[cell[i]] + slot[i];
-        ys[pos] = y[i];
-        zs[pos] = zlin[i];
+        yz[pos] = make_float2(y[i], zlin[i]);
         ids[pos] = i;
         plane[pos] = (uint16_t)(sector[i] * nr + row[i]);
     }
 }
 
-// sorted-index range of cells c-1 .. c+1 of one plane
-struct Range {
-    int b, e;
+// sorted-index ranges of the 3 x 3 cells around (zc, yc) of one plane: for
+// each z-cell zc-1 .. zc+1 the y-bins yc-1 .. yc+1 are contiguous
+struct Ranges {
+    int b[3], e[3];
 };
-__device__ __forceinline__ Range cell_range(const uint32_t* __restrict__ cstart, int plane, int c, int nz)
+__device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstart, int plane, int zc, int yc, int nz,
+                                              int ny)
 {
-    const int lo = max(c - 1, 0), hi = min(c + 1, nz - 1);
-    Range r;
-    r.b = (int)cstart[(int64_t)plane * nz + lo];
-    r.e = (int)cstart[(int64_t)plane * nz + hi + 1];
-    return r;
+    Ranges R;
+    const int ylo = max(yc - 1, 0), yhi = min(yc + 1, ny - 1);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int zz = zc - 1 + k;
+        if (zz < 0 || zz >= nz) {
+            R.b[k] = R.e[k] = 0;
+        } else {
+            const int64_t base = ((int64_t)plane * nz + zz) * ny;
+            R.b[k] = (int)cstart[base + ylo];
+            R.e[k] = (int)cstart[base + yhi + 1];
+        }
+    }
+    return R;
 }
 
 // ---------------------------------------------------------------------------
@@ -320,60 +376,70 @@ __device__ __forceinline__ Range cell_range(const uint32_t* __restrict__ cstart,
 constexpr int MAXD = 8;
 
 __global__ void __launch_bounds__(256) k_neighbours(
-    int n, int nr, int ns, const float* __restrict__ rowtab, const float* __restrict__ ys,
-    const float* __restrict__ zs, const int32_t* __restrict__ ids, const uint16_t* __restrict__ plane,
-    const uint32_t* __restrict__ cstart, const Frame* __restrict__ f, float DY, float DZ, float SMAX,
-    int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
+    int n, int nr, int ns, const float* __restrict__ rowtab, const float2* __restrict__ yz,
+    const int32_t* __restrict__ ids, const uint16_t* __restrict__ plane, const uint32_t* __restrict__ cstart,
+    const Frame* __restrict__ f, float DY, float DZ, float SMAX, int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
 {
     if (f->err) return;
     const float zmin = f->zmin, inv = f->inv_cs;
-    const int nz = f->nz;
+    const int nz = f->nz, ny = f->ny;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
         const int pl = plane[h];
         const int s = pl / nr, r = pl - s * nr;
         int bu = -1, bd = -1, bidu = 0, bidd = 0;
         float bs = 0.0f;
         if (r >= 1 && r <= nr - 2) {
-            const float yh = ys[h], zh = zs[h];
+            const float2 ph = yz[h];
+            const float yh = ph.x, zh = ph.y;
             const float yu_pred = yh * rowtab[r * ROWTAB + 1];
             const float yd_pred = yh * rowtab[r * ROWTAB + 2];
             const float w = rowtab[r * ROWTAB + 3];
             const int c = grid_cell(fold(zh, s, ns), zmin, inv, nz);
-            const Range ru = cell_range(cstart, pl + 1, c, nz);
-            const Range rd = cell_range(cstart, pl - 1, c, nz);
+            const Ranges ru = cell_ranges(cstart, pl + 1, c, ybin(yu_pred, rowtab, r + 1, ny), nz, ny);
+            const Ranges rd = cell_ranges(cstart, pl - 1, c, ybin(yd_pred, rowtab, r - 1, ny), nz, ny);
             // down candidates inside the windows
             int dl[MAXD];
             int ndn = 0;
             bool overflow = false;
-            for (int q = rd.b; q < rd.e; q++) {
-                if (fabsf(ys[q] - yd_pred) <= DY && fabsf(zs[q] - zh) <= DZ) {
-                    if (ndn < MAXD) dl[ndn++] = q;
-                    else overflow = true;
-                }
-            }
-            if (ndn > 0) {
-                for (int u = ru.b; u < ru.e; u++) {
-                    const float yu = ys[u], zu = zs[u];
-                    if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
-                    const int idu = ids[u];
-                    auto consider = [&](int d) {
-                        const float yd = ys[d], zd = zs[d];
-                        const float ey = __fmaf_rn(yu - yd, w, yd) - yh;
-                        const float ez = __fmaf_rn(zu - zd, w, zd) - zh;
-                        const float sc = __fmaf_rn(ey, ey, ez * ez);
-                        if (!(sc < SMAX)) return;
-                        const int idd = ids[d];
-                        if (bu < 0 || sc < bs || (sc == bs && (idu < bidu || (idu == bidu && idd < bidd)))) {
-                            bu = u; bd = d; bs = sc; bidu = idu; bidd = idd;
-                        }
-                    };
-                    if (!overflow) {
-                        for (int k = 0; k < ndn; k++) consider(dl[k]);
-                    } else {
-                        for (int d = rd.b; d < rd.e; d++)
-                            if (fabsf(ys[d] - yd_pred) <= DY && fabsf(zs[d] - zh) <= DZ) consider(d);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                for (int q = rd.b[k]; q < rd.e[k]; q++) {
+                    const float2 pq = yz[q];
+                    if (fabsf(pq.x - yd_pred) <= DY && fabsf(pq.y - zh) <= DZ) {
+                        if (ndn < MAXD) dl[ndn++] = q;
+                        else overflow = true;
                     }
                 }
+            if (ndn > 0) {
+#pragma unroll
+                for (int ku = 0; ku < 3; ku++)
+                    for (int u = ru.b[ku]; u < ru.e[ku]; u++) {
+                        const float2 pu = yz[u];
+                        const float yu = pu.x, zu = pu.y;
+                        if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
+                        const int idu = ids[u];
+                        auto consider = [&](int d) {
+                            const float2 pd = yz[d];
+                            const float yd = pd.x, zd = pd.y;
+                            const float ey = __fmaf_rn(yu - yd, w, yd) - yh;
+                            const float ez = __fmaf_rn(zu - zd, w, zd) - zh;
+                            const float sc = __fmaf_rn(ey, ey, ez * ez);
+                            if (!(sc < SMAX)) return;
+                            const int idd = ids[d];
+                            if (bu < 0 || sc < bs || (sc == bs && (idu < bidu || (idu == bidu && idd < bidd)))) {
+                                bu = u; bd = d; bs = sc; bidu = idu; bidd = idd;
+                            }
+                        };
+                        if (!overflow) {
+                            for (int k = 0; k < ndn; k++) consider(dl[k]);
+                        } else {
+                            for (int k = 0; k < 3; k++)
+                                for (int d = rd.b[k]; d < rd.e[k]; d++) {
+                                    const float2 pd = yz[d];
+                                    if (fabsf(pd.x - yd_pred) <= DY && fabsf(pd.y - zh) <= DZ) consider(d);
+                                }
+                        }
+                    }
             }
         }
         upr[h] = bu;
@@ -423,8 +489,7 @@ __global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* _
 // ---------------------------------------------------------------------------
 struct TrkArgs {
     const float* rowtab;
-    const float* ys;
-    const float* zs;
+    const float2* yz;
     const int32_t* ids;
     const uint16_t* plane;
     const uint32_t* cstart;
@@ -440,22 +505,26 @@ struct TrkArgs {
     Frame* fw;
 };
 
-__device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int s, float yp, float zp, float wy, float wz,
-                                            float zmin, float inv, int nz, unsigned& ncand)
+__device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int r, int s, float yp, float zp, float wy,
+                                            float wz, float zmin, float inv, int nz, int ny, unsigned& ncand)
 {
     const int c = grid_cell(fold(zp, s, A.ns), zmin, inv, nz);
-    const Range rg = cell_range(A.cstart, pl, c, nz);
-    ncand += (unsigned)(rg.e - rg.b);
+    const Ranges rg = cell_ranges(A.cstart, pl, c, ybin(yp, A.rowtab, r, ny), nz, ny);
     int best = -1, bid = 0;
     float bd = 0.0f;
-    for (int q = rg.b; q < rg.e; q++) {
-        const float dy = A.ys[q] - yp;
-        const float dz = A.zs[q] - zp;
-        if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
-        const float d2 = __fmaf_rn(dy, dy, dz * dz);
-        const int id = A.ids[q];
-        if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
-            best = q; bd = d2; bid = id;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        ncand += (unsigned)(rg.e[k] - rg.b[k]);
+        for (int q = rg.b[k]; q < rg.e[k]; q++) {
+            const float2 pq = A.yz[q];
+            const float dy = pq.x - yp;
+            const float dz = pq.y - zp;
+            if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
+            const float d2 = __fmaf_rn(dy, dy, dz * dz);
+            const int id = A.ids[q];
+            if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
+                best = q; bd = d2; bid = id;
+            }
         }
     }
     return best;
@@ -479,7 +548,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
 {
     if (A.f->err) return;
     const float zmin = A.f->zmin, inv = A.f->inv_cs;
-    const int nz = A.f->nz;
+    const int nz = A.f->nz, ny = A.f->ny;
     const int nt = min(A.f->n_starts, A.cap);
     const float INF = __int_as_float(0x7f800000);
     const int NR = A.nr;
@@ -519,8 +588,9 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             const int h2 = A.up[h1];
             const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
             const float dx12 = x2 - x1;
-            const float y1 = A.ys[h1], z1 = A.zs[h1];
-            const float dy12 = A.ys[h2] - y1, dz12 = A.zs[h2] - z1;
+            const float2 p1 = A.yz[h1], p2 = A.yz[h2];
+            const float y1 = p1.x, z1 = p1.y;
+            const float dy12 = p2.x - y1, dz12 = p2.y - z1;
             const float ty = __fdiv_rn(dy12, dx12);
             const float sp = __fdiv_rn(ty, __fsqrt_rn(__fmaf_rn(ty, ty, 1.0f)));
             const float dl12 = __fsqrt_rn(__fmaf_rn(dx12, dx12, dy12 * dy12));
@@ -557,7 +627,8 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             nprop++;
             nupd++;
             rc = rn;
-            update32(st, A.ys[hn], A.zs[hn], A.vy, A.vz, INF);
+            const float2 pn = A.yz[hn];
+            update32(st, pn.x, pn.y, A.vy, A.vz, INF);
             slot[nu++] = hn;
             copy_state(keep, st);
             hc = hn;
@@ -578,8 +649,8 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             }
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            const int c = find_nearest(A, pbase + rr, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
-            if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+            const int c = find_nearest(A, pbase + rr, rr, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
+            if (c >= 0 && update32(st, A.yz[c].x, A.yz[c].y, A.vy, A.vz, A.chi2cut)) {
                 nupd++;
                 slot[nu++] = c;
                 copy_state(keep, st);
@@ -622,8 +693,8 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
         {
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            const int c = find_nearest(A, pbase + r, s, st[1], st[2], wy, wz, zmin, inv, nz, ncand);
-            if (c >= 0 && update32(st, A.ys[c], A.zs[c], A.vy, A.vz, A.chi2cut)) {
+            const int c = find_nearest(A, pbase + r, r, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
+            if (c >= 0 && update32(st, A.yz[c].x, A.yz[c].y, A.vy, A.vz, A.chi2cut)) {
                 nupd++;
                 nd++;
                 slot[NR - nd] = c;
@@ -985,7 +1056,7 @@ constexpr int STATIC_MAX_PLANES = 36 * 255;
 constexpr int64_t STATIC_NCELLS = (int64_t)STATIC_MAX_PLANES * STATIC_NZ;
 
 struct StaticLayout {
-    size_t frame, rowtab, zlin, cell, slot, cstart, scan, ys, zs, ids, plane, upr, dnr, up, dn, total;
+    size_t frame, rowtab, zlin, cell, slot, cstart, scan, yz, ids, plane, upr, dnr, up, dn, total;
 };
 
 constexpr size_t sa256(size_t v) { return (v + 255) / 256 * 256; }
@@ -1001,8 +1072,7 @@ constexpr StaticLayout static_layout()
     L.slot = o; o += sa256(4 * N);
     L.cstart = o; o += sa256(4 * (STATIC_NCELLS + 1));
     L.scan = o; o += sa256(4 * (STATIC_NCELLS / SCAN_TILE + 64));
-    L.ys = o; o += sa256(4 * N);
-    L.zs = o; o += sa256(4 * N);
+    L.yz = o; o += sa256(8 * N);
     L.ids = o; o += sa256(4 * N);
     L.plane = o; o += sa256(2 * N);
     L.upr = o; o += sa256(4 * N);
@@ -1069,6 +1139,7 @@ int tpc_params_default(tpc_params* p)
     p->refit_passes = 3;
     p->refit_inflate = 100.0f;
     p->z_cell = 3.5f;
+    p->y_bins = 8;
     p->max_z_cells = 1024;
     p->tracklets_per_1k = 125;
     p->fp64_final = 0;
@@ -1124,8 +1195,7 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     uint32_t* slot = at<uint32_t>(ws, L.slot);
     uint32_t* cstart = at<uint32_t>(ws, L.cstart);
     uint32_t* aux = at<uint32_t>(ws, L.scan);
-    float* ys = at<float>(ws, L.ys);
-    float* zs = at<float>(ws, L.zs);
+    float2* yz = at<float2>(ws, L.yz);
     int32_t* ids = at<int32_t>(ws, L.ids);
     uint16_t* plane = at<uint16_t>(ws, L.plane);
     int32_t* upr = at<int32_t>(ws, L.upr);
@@ -1146,22 +1216,7 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
 
     // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r], (X[r]-X[r-1])/(X[r+1]-X[r-1])
     float tab[ROWTAB * 256];
-    memset(tab, 0, sizeof(tab));
-    const float* X = g->row_x;
-    for (int r = 0; r < g->n_rows; r++) {
-        volatile float xr = X[r];
-        tab[r * ROWTAB] = xr;
-        if (r >= 1 && r + 1 < g->n_rows) {
-            volatile float a = X[r + 1] / X[r];
-            volatile float b = X[r - 1] / X[r];
-            volatile float num = X[r] - X[r - 1];
-            volatile float den = X[r + 1] - X[r - 1];
-            volatile float w = num / den;
-            tab[r * ROWTAB + 1] = a;
-            tab[r * ROWTAB + 2] = b;
-            tab[r * ROWTAB + 3] = w;
-        }
-    }
+    fill_rowtab(tab, g, L.ny);
     CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
     // a copy of the layout at the workspace base lets tpc_export_tracklets find the arrays
     static_assert(sizeof(Layout) <= 512, "layout header");
@@ -1192,19 +1247,20 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     k_init_frame<<<1, 32, 0, st>>>(f);
     k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
                              g->z_max, v_drift, zlin, f);
-    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, L.nzmax, p->merge_dz * 1.1f + 0.5f, L.mnzmax);
+    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, L.nzmax, p->merge_dz * 1.1f + 0.5f, L.mnzmax, L.ny);
     g_launches += 3;
     CK(mark(1));
     // a2: counting sort of the clusters into (sector, row, z-cell) order
     CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(L.ncells + 1), st));
-    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, rowtab, g->n_rows, g->n_sectors, f, cstart, cell,
+                             slot);
     g_launches++;
     scan_u32(cstart, L.ncells, aux, st);
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs, ids,
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, yz, ids,
                                 plane, f);
     g_launches++;
     CK(mark(2));
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f, p->dy_link,
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, yz, ids, plane, cstart, f, p->dy_link,
                                    p->dz_link, p->s_max_link, upr, dnr);
     g_launches++;
     CK(mark(3));
@@ -1214,7 +1270,7 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     CK(mark(4));
     // a6: tracklets
     TrkArgs TA;
-    TA.rowtab = rowtab; TA.ys = ys; TA.zs = zs; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
+    TA.rowtab = rowtab; TA.yz = yz; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
     TA.starts = starts; TA.f = f; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.cap = ntcap;
     TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
     TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
@@ -1403,8 +1459,7 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     uint32_t* slot = at<uint32_t>(base, SL.slot);
     uint32_t* cstart = at<uint32_t>(base, SL.cstart);
     uint32_t* aux = at<uint32_t>(base, SL.scan);
-    float* ys = at<float>(base, SL.ys);
-    float* zs = at<float>(base, SL.zs);
+    float2* yz = at<float2>(base, SL.yz);
     int32_t* ids = at<int32_t>(base, SL.ids);
     uint16_t* plane = at<uint16_t>(base, SL.plane);
     int32_t* upr = at<int32_t>(base, SL.upr);
@@ -1412,22 +1467,7 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     int32_t* up = at<int32_t>(base, SL.up);
     int32_t* dn = at<int32_t>(base, SL.dn);
     float tab[ROWTAB * 256];
-    memset(tab, 0, sizeof(tab));
-    const float* X = g->row_x;
-    for (int r = 0; r < g->n_rows; r++) {
-        volatile float xr = X[r];
-        tab[r * ROWTAB] = xr;
-        if (r >= 1 && r + 1 < g->n_rows) {
-            volatile float a = X[r + 1] / X[r];
-            volatile float b = X[r - 1] / X[r];
-            volatile float num = X[r] - X[r - 1];
-            volatile float den = X[r + 1] - X[r - 1];
-            volatile float w = num / den;
-            tab[r * ROWTAB + 1] = a;
-            tab[r * ROWTAB + 2] = b;
-            tab[r * ROWTAB + 3] = w;
-        }
-    }
+    fill_rowtab(tab, g, 1);   // one y-bin per z-cell: a smaller fixed array
     CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
     const int64_t ncells = (int64_t)g->n_sectors * g->n_rows * STATIC_NZ;
     const int B = 256;
@@ -1435,14 +1475,15 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     k_init_frame<<<1, 32, 0, st>>>(f);
     k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
                              g->z_max, v_drift, zlin, f);
-    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, STATIC_NZ, p->merge_dz * 1.1f + 0.5f, MAX_MERGE_CELLS);
+    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, STATIC_NZ, p->merge_dz * 1.1f + 0.5f, MAX_MERGE_CELLS, 1);
     // the histogram must start at zero: the scratch keeps the previous call's contents
     CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(ncells + 1), st));
-    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, zlin, g->n_rows, g->n_sectors, f, cstart, cell, slot);
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, rowtab, g->n_rows, g->n_sectors, f, cstart, cell,
+                             slot);
     scan_u32(cstart, ncells, aux, st);
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, ys, zs, ids,
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, yz, ids,
                                 plane, f);
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, ys, zs, ids, plane, cstart, f, p->dy_link,
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, yz, ids, plane, cstart, f, p->dy_link,
                                    p->dz_link, p->s_max_link, upr, dnr);
     k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
     k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);
