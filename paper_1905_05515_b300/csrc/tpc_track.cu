@@ -543,7 +543,10 @@ enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
 // One lane = one tracklet at a time.  Each loop iteration advances the lane's
 // tracklet by one row step; a lane whose tracklet ends writes it out and takes
 // the next start hit from a global queue, so lanes stay busy however uneven
-// the tracklet lengths are.
+// the tracklet lengths are.  The propagation, the window search and the
+// Kalman update each have a single call site shared by all phases, so a warp
+// whose lanes are in different phases still executes each of them once per
+// iteration.
 __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
 {
     if (A.f->err) return;
@@ -558,9 +561,9 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
     float st[NST], keep[NST];
     int t = -1, phase = PH_DONE;
     int h1 = 0, r1 = 0, s = 0, pbase = 0, hc = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
-    bool ok = true;
     int32_t* slot = nullptr;
     for (;;) {
+        // ---- bookkeeping transitions
         if (phase == PH_DONE) {
             if (t >= 0) {
                 float* bot = A.t_bot + (int64_t)t * NST;
@@ -606,59 +609,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             copy_state(keep, st);
             rc = r1;
             hc = h1;
-            ok = true;
-            miss = 0;
             phase = PH_A;
-        }
-        if (phase == PH_A) {
-            // phase A: fit along the up links
-            const int hn = A.up[hc];
-            if (hn < 0) {
-                phase = PH_B;
-                miss = 0;
-                continue;
-            }
-            const int rn = A.plane[hn] - pbase;
-            if (!prop32(st, A.rowtab[rn * ROWTAB], A.kb)) {
-                ok = false;
-                phase = PH_CSTART;
-                continue;
-            }
-            nprop++;
-            nupd++;
-            rc = rn;
-            const float2 pn = A.yz[hn];
-            update32(st, pn.x, pn.y, A.vy, A.vz, INF);
-            slot[nu++] = hn;
-            copy_state(keep, st);
-            hc = hn;
-            continue;
-        }
-        if (phase == PH_B) {
-            // phase B: follow row by row beyond the chain end
-            const int rr = rc + 1;
-            if (!ok || rr >= NR || !prop32(st, A.rowtab[rr * ROWTAB], A.kb)) {
-                phase = PH_CSTART;
-                continue;
-            }
-            nprop++;
-            rc = rr;
-            if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) {
-                phase = PH_CSTART;
-                continue;
-            }
-            const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
-            const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            const int c = find_nearest(A, pbase + rr, rr, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
-            if (c >= 0 && update32(st, A.yz[c].x, A.yz[c].y, A.vy, A.vz, A.chi2cut)) {
-                nupd++;
-                slot[nu++] = c;
-                copy_state(keep, st);
-                miss = 0;
-            } else if (++miss >= A.max_miss) {
-                phase = PH_CSTART;
-            }
-            continue;
         }
         if (phase == PH_CSTART) {
             // end of the upward phases: the outer-end state is final
@@ -669,32 +620,92 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             miss = 0;
             r = rc - 1;
             phase = PH_C;
-            continue;
         }
-        // phase C: back down through the fitted rows, then follow below the start
-        if (r < 0 || !prop32(st, A.rowtab[r * ROWTAB], A.kb)) {
-            phase = PH_DONE;
+        // ---- the row this step goes to
+        int target = -1, hn = -1;
+        if (phase == PH_A) {                    // fit along the up links
+            hn = A.up[hc];
+            if (hn < 0) {
+                phase = PH_B;
+                miss = 0;
+            } else {
+                target = A.plane[hn] - pbase;
+            }
+        }
+        if (phase == PH_B) {                    // follow beyond the chain end
+            if (rc + 1 < NR) target = rc + 1;
+            else phase = PH_CSTART;
+        }
+        if (phase == PH_C) {                    // back down, then below the start
+            if (r >= 0) target = r;
+            else phase = PH_DONE;
+        }
+        if (target < 0) continue;
+        // ---- propagation (one call site)
+        if (!prop32(st, A.rowtab[target * ROWTAB], A.kb)) {
+            phase = (phase == PH_C) ? PH_DONE : PH_CSTART;
             continue;
         }
         nprop++;
-        if (r > r1) {
-            r--;
-            continue;
+        bool search = false, upd = false;
+        float my = 0.0f, mz = 0.0f, cmax = INF;
+        int c = -1;
+        if (phase == PH_A) {
+            rc = target;
+            const float2 pn = A.yz[hn];
+            my = pn.x;
+            mz = pn.y;
+            upd = true;
+            nupd++;
+        } else if (phase == PH_B) {
+            rc = target;
+            search = true;
+        } else {
+            if (r > r1) {
+                r--;
+                continue;
+            }
+            if (r == r1) {
+                copy_state(keep, st);
+                r--;
+                continue;
+            }
+            search = true;
         }
-        if (r == r1) {
-            copy_state(keep, st);
-            r--;
-            continue;
-        }
-        if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) {
-            phase = PH_DONE;
-            continue;
-        }
-        {
+        if (search) {
+            if (fabsf(st[1]) > __fmaf_rn(st[0], TAN10, A.edge)) {
+                phase = (phase == PH_B) ? PH_CSTART : PH_DONE;
+                continue;
+            }
+            // ---- window search (one call site)
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            const int c = find_nearest(A, pbase + r, r, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
-            if (c >= 0 && update32(st, A.yz[c].x, A.yz[c].y, A.vy, A.vz, A.chi2cut)) {
+            c = find_nearest(A, pbase + target, target, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
+            if (c >= 0) {
+                const float2 pc = A.yz[c];
+                my = pc.x;
+                mz = pc.y;
+                cmax = A.chi2cut;
+                upd = true;
+            }
+        }
+        // ---- Kalman update (one call site)
+        const bool took = upd && update32(st, my, mz, A.vy, A.vz, cmax);
+        if (phase == PH_A) {
+            slot[nu++] = hn;
+            copy_state(keep, st);
+            hc = hn;
+        } else if (phase == PH_B) {
+            if (took) {
+                nupd++;
+                slot[nu++] = c;
+                copy_state(keep, st);
+                miss = 0;
+            } else if (++miss >= A.max_miss) {
+                phase = PH_CSTART;
+            }
+        } else {
+            if (took) {
                 nupd++;
                 nd++;
                 slot[NR - nd] = c;
@@ -704,8 +715,8 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
                 phase = PH_DONE;
                 continue;
             }
+            r--;
         }
-        r--;
     }
     if (A.prof) {
         atomicAdd(&A.fw->w_prop, (unsigned long long)nprop);
