@@ -547,8 +547,13 @@ enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
 // Kalman update each have a single call site shared by all phases, so a warp
 // whose lanes are in different phases still executes each of them once per
 // iteration.
-__global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
+constexpr int TRK_BLOCK = 128;
+
+__global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
 {
+    // the last accepted state of each lane (outer-end / inner-end candidate) lives
+    // in shared memory, element-major so that the lanes of a warp hit distinct banks
+    __shared__ float keep_sh[NST][TRK_BLOCK];
     if (A.f->err) return;
     const float zmin = A.f->zmin, inv = A.f->inv_cs;
     const int nz = A.f->nz, ny = A.f->ny;
@@ -558,9 +563,16 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
     const unsigned lane = threadIdx.x & 31u;
     unsigned nprop = 0, nupd = 0, ncand = 0;
 
-    float st[NST], keep[NST];
+    float st[NST];
+    auto save_keep = [&]() {
+#pragma unroll
+        for (int i = 0; i < NST; i++) keep_sh[i][threadIdx.x] = st[i];
+    };
     int t = -1, phase = PH_DONE;
     int h1 = 0, r1 = 0, s = 0, pbase = 0, hc = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
+    // next chain hit (phase A), loaded one step ahead
+    int nx_h = -1, nx_row = 0;
+    float2 nx_yz = make_float2(0.0f, 0.0f);
     int32_t* slot = nullptr;
     for (;;) {
         // ---- bookkeeping transitions
@@ -568,7 +580,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             if (t >= 0) {
                 float* bot = A.t_bot + (int64_t)t * NST;
 #pragma unroll
-                for (int i = 0; i < NST; i++) bot[i] = keep[i];
+                for (int i = 0; i < NST; i++) bot[i] = keep_sh[i][threadIdx.x];
                 A.t_start[t] = h1;
                 A.t_id[t] = A.ids[h1];
                 A.t_nhits[t] = nu + nd;
@@ -606,30 +618,41 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
             nu = 0;
             nd = 0;
             slot[nu++] = h1;
-            copy_state(keep, st);
+            save_keep();
             rc = r1;
             hc = h1;
             phase = PH_A;
+            nx_h = h2;
+            nx_row = A.plane[h2] - pbase;
+            nx_yz = p2;
         }
         if (phase == PH_CSTART) {
             // end of the upward phases: the outer-end state is final
             float* top = A.t_top + (int64_t)t * NST;
 #pragma unroll
-            for (int i = 0; i < NST; i++) top[i] = keep[i];
-            if (rc == r1) copy_state(keep, st);
+            for (int i = 0; i < NST; i++) top[i] = keep_sh[i][threadIdx.x];
+            if (rc == r1) save_keep();
             miss = 0;
             r = rc - 1;
             phase = PH_C;
         }
         // ---- the row this step goes to
         int target = -1, hn = -1;
+        float2 pn = make_float2(0.0f, 0.0f);
         if (phase == PH_A) {                    // fit along the up links
-            hn = A.up[hc];
+            hn = nx_h;
             if (hn < 0) {
                 phase = PH_B;
                 miss = 0;
             } else {
-                target = A.plane[hn] - pbase;
+                target = nx_row;
+                pn = nx_yz;
+                // load the following chain hit while this step computes
+                nx_h = A.up[hn];
+                if (nx_h >= 0) {
+                    nx_row = A.plane[nx_h] - pbase;
+                    nx_yz = A.yz[nx_h];
+                }
             }
         }
         if (phase == PH_B) {                    // follow beyond the chain end
@@ -652,7 +675,6 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
         int c = -1;
         if (phase == PH_A) {
             rc = target;
-            const float2 pn = A.yz[hn];
             my = pn.x;
             mz = pn.y;
             upd = true;
@@ -666,7 +688,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
                 continue;
             }
             if (r == r1) {
-                copy_state(keep, st);
+                save_keep();
                 r--;
                 continue;
             }
@@ -693,13 +715,13 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
         const bool took = upd && update32(st, my, mz, A.vy, A.vz, cmax);
         if (phase == PH_A) {
             slot[nu++] = hn;
-            copy_state(keep, st);
+            save_keep();
             hc = hn;
         } else if (phase == PH_B) {
             if (took) {
                 nupd++;
                 slot[nu++] = c;
-                copy_state(keep, st);
+                save_keep();
                 miss = 0;
             } else if (++miss >= A.max_miss) {
                 phase = PH_CSTART;
@@ -709,7 +731,7 @@ __global__ void __launch_bounds__(128) k_tracklets(TrkArgs A)
                 nupd++;
                 nd++;
                 slot[NR - nd] = c;
-                copy_state(keep, st);
+                save_keep();
                 miss = 0;
             } else if (++miss >= A.max_miss) {
                 phase = PH_DONE;
@@ -1290,7 +1312,7 @@ int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drif
     TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
     TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
     const int gT = grid_for(ntcap, 128);
-    k_tracklets<<<gT, 128, 0, st>>>(TA);
+    k_tracklets<<<gT, TRK_BLOCK, 0, st>>>(TA);
     g_launches++;
     CK(mark(5));
     // a7: selector
