@@ -121,6 +121,7 @@ typedef struct {
     int32_t *clus_offset;        /* [T+1] offsets into clus_index */
     int32_t *clus_index;         /* [capacity_clusters] input cluster indices, inner -> outer */
     int32_t *assign;             /* [n] track index of each input cluster, -1 if unassigned */
+    int32_t *frame;              /* nullable [T]: time frame of each track (tpc_track_batched) */
     double *cov64;               /* nullable [T][15]: binary64 covariance when fp64_final */
     double *chi2_64;             /* nullable [T]: binary64 chi2 when fp64_final */
     /* nullable intermediate results, indexed by input cluster (parity checks) */
@@ -161,6 +162,45 @@ int tpc_workspace_size(const tpc_params *p, const tpc_geometry *g, int64_t n_clu
 int tpc_track(const tpc_params *p, const tpc_geometry *g, float bz, float v_drift,
               const tpc_clusters *cl, void *workspace, size_t ws_bytes, tpc_tracks *out,
               void *stream);
+
+/* Workspace for tpc_track_batched / tpc_prepare: n_clusters in total over
+ * n_frames frames (1 .. 4096).  Errors: TPC_ERR_ARG. */
+int tpc_workspace_size_batched(const tpc_params *p, const tpc_geometry *g, int64_t n_clusters, int32_t n_frames,
+                               size_t *bytes);
+
+/* Track a batch of independent time frames (sub-time-frames of uneven sizes)
+ * in one pass: every stage is one launch over all frames.  The clusters of
+ * frame k are entries frame_offsets[k] .. frame_offsets[k+1]-1 of `cl`
+ * (host array, n_frames + 1 entries, frame_offsets[0] = 0,
+ * frame_offsets[n_frames] = cl->n).  Each frame is tracked exactly as
+ * tpc_track would track it alone (same links, tracklets, tracks and fits,
+ * with input indices offset by frame_offsets[k]); the tracks of all frames
+ * come in one list ordered by input index, out->frame (if not null) gives the
+ * frame of each track.  Workspace: tpc_workspace_size_batched.  Errors as
+ * tpc_track. */
+int tpc_track_batched(const tpc_params *p, const tpc_geometry *g, float bz, float v_drift, const tpc_clusters *cl,
+                      int32_t n_frames, const int32_t *frame_offsets, void *workspace, size_t ws_bytes,
+                      tpc_tracks *out, void *stream);
+
+/* Write the per-row tables, the frame offsets and the workspace header that
+ * tpc_track_async reads (pageable host copies; not capturable).  Call once
+ * per (workspace, geometry, parameters, frame offsets); synchronises the
+ * stream.  Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_CUDA. */
+int tpc_prepare(const tpc_params *p, const tpc_geometry *g, int32_t n_clusters, int32_t n_frames,
+                const int32_t *frame_offsets, void *workspace, size_t ws_bytes, void *stream);
+
+/* Enqueue the whole chain (as tpc_track_batched) without any host
+ * synchronisation or host copy, so that the call can be captured in a CUDA
+ * graph and replayed.  Requires a prior tpc_prepare on the same workspace with
+ * the same n_clusters and n_frames.  The host-visible fields of *out are not
+ * filled; instead dev_counts (device int32[6]) receives n_tracks,
+ * n_tracklets, n_segments, an error code (0, TPC_ERR_DATA or
+ * TPC_ERR_CAPACITY), clusters in tracks and start hits found.  params.profile
+ * is ignored.  Errors detected on the host: TPC_ERR_ARG, TPC_ERR_CAPACITY,
+ * TPC_ERR_CUDA. */
+int tpc_track_async(const tpc_params *p, const tpc_geometry *g, float bz, float v_drift, const tpc_clusters *cl,
+                    int32_t n_frames, void *workspace, size_t ws_bytes, tpc_tracks *out, int32_t *dev_counts,
+                    void *stream);
 
 /* Export the tracklets of the last tpc_track call that used `workspace`
  * (TrackletConstructor and TrackletSelector results, for parity checks).
@@ -203,7 +243,7 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
  *   - Enqueues on `stream`, then waits for it (to read the data-error flag).
  * Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_DATA, TPC_ERR_CUDA. */
 #define TPC_LINKS_STATIC_MAX_CLUSTERS 262144
-#define TPC_LINKS_STATIC_SCRATCH_BYTES 13367808
+#define TPC_LINKS_STATIC_SCRATCH_BYTES 14416896
 int tpc_links_static(const tpc_params *p, const tpc_geometry *g, float v_drift, const tpc_clusters *cl,
                      int32_t *link_up, int32_t *link_dn, uint8_t *is_start, void *stream);
 

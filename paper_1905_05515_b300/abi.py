@@ -48,6 +48,7 @@ class TpcTracks(C.Structure):
                 ("sector", C.c_void_p), ("x", C.c_void_p), ("param", C.c_void_p), ("cov", C.c_void_p),
                 ("chi2", C.c_void_p), ("ndf", C.c_void_p), ("status", C.c_void_p), ("nclus", C.c_void_p),
                 ("clus_offset", C.c_void_p), ("clus_index", C.c_void_p), ("assign", C.c_void_p),
+                ("frame", C.c_void_p),
                 ("cov64", C.c_void_p), ("chi2_64", C.c_void_p),
                 ("z", C.c_void_p), ("link_up_raw", C.c_void_p), ("link_dn_raw", C.c_void_p),
                 ("link_up", C.c_void_p), ("link_dn", C.c_void_p), ("is_start", C.c_void_p),
@@ -58,7 +59,9 @@ class TpcTracks(C.Structure):
 STAGES = ("prep", "bin", "neighbours", "clean_start", "tracklets", "select", "merge", "assemble", "refit")
 
 
-EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_track", "tpc_export_tracklets", "tpc_error_string")
+EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
+            "tpc_track_batched", "tpc_prepare", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
+            "tpc_error_string")
 
 _lib = None
 
@@ -80,6 +83,16 @@ def lib(build_if_missing: bool = True):
                                          C.POINTER(C.c_size_t)]
         L.tpc_track.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,
                                 C.POINTER(TpcClusters), C.c_void_p, C.c_size_t, C.POINTER(TpcTracks), C.c_void_p]
+        L.tpc_workspace_size_batched.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int64, C.c_int32,
+                                                 C.POINTER(C.c_size_t)]
+        L.tpc_track_batched.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,
+                                        C.POINTER(TpcClusters), C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
+                                        C.c_size_t, C.POINTER(TpcTracks), C.c_void_p]
+        L.tpc_prepare.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int32, C.c_int32,
+                                  C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.tpc_track_async.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,
+                                      C.POINTER(TpcClusters), C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(TpcTracks),
+                                      C.c_void_p, C.c_void_p]
         L.tpc_export_tracklets.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
         L.tpc_error_string.argtypes = [C.c_int]
@@ -112,9 +125,10 @@ def make_geometry(row_x, n_sectors: int, z_max: float, continuous: bool):
     return g
 
 
-def tpc_workspace_size(params: TpcParams, geometry: TpcGeometry, n_clusters: int) -> int:
+def tpc_workspace_size(params: TpcParams, geometry: TpcGeometry, n_clusters: int, n_frames: int = 1) -> int:
     out = C.c_size_t()
-    rc = lib().tpc_workspace_size(C.byref(params), C.byref(geometry), int(n_clusters), C.byref(out))
+    rc = lib().tpc_workspace_size_batched(C.byref(params), C.byref(geometry), int(n_clusters), int(n_frames),
+                                          C.byref(out))
     if rc:
         raise TpcError(rc, "tpc_workspace_size")
     return int(out.value)

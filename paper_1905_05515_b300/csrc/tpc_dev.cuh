@@ -239,12 +239,11 @@ __device__ __forceinline__ float merge_chi2(const float* top, const float* bot, 
 // shared layout of the per-call device state
 // ---------------------------------------------------------------------------
 struct Frame {
-    unsigned zmin_key, zmax_key;   // order-preserving keys of the folded-z extrema
-    float zmin, inv_cs;            // grid origin and 1 / cell length
-    int nz;                        // grid z-cells per plane
-    int ny;                        // grid y-bins per z-cell
-    float mzmin, minv_cs;          // merger grid
+    unsigned zmin_key, zmax_key;   // order-preserving keys of the folded-z extrema, all frames
+    float mzmin, minv_cs;          // merger grid (all frames)
     int mnz;
+    int ny;                        // grid y-bins per z-cell
+    unsigned total_cells;          // grid cells of all frames
     int err;                       // TPC_ERR_* set by kernels (0 = ok)
     int n_starts, n_seg, n_tracks, n_clus;
     int n_bad;                     // clusters rejected by validation
@@ -252,6 +251,14 @@ struct Frame {
     // work counters (params.profile): tracklet propagations, updates, window
     // candidates examined; refit propagations; merger chi2 evaluations
     unsigned long long w_prop, w_upd, w_cand, w_refit_prop, w_merge;
+};
+
+// per time frame: grid of that frame's clusters
+struct FrameGrid {
+    unsigned zmin_key, zmax_key;   // folded-z extrema of the frame
+    float zmin, inv_cs;            // grid origin and 1 / z-cell length
+    int nz;                        // z-cells per plane
+    unsigned cell_base;            // first cell of this frame
 };
 
 // order-preserving float <-> uint32 key

@@ -2,6 +2,11 @@
 // tracklet construction and selection, cross-sector merging, track assembly
 // and the C-ABI entry points (include/tpc_track.h).
 //
+// Every stage runs over a batch of independent time frames at once: a pad-row
+// plane is identified by (frame, sector, row), each frame has its own z grid,
+// and merges stay inside a frame, so a batch gives exactly the results of the
+// frames processed one by one.  A single frame is the batch of one.
+//
 // Compiled with -fmad=false: every binary32 decision (links, start hits,
 // tracklet hits, ownership, merges) follows the fixed operation order of the
 // method's specification and is bit-identical to any IEEE implementation of
@@ -25,8 +30,10 @@ constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
-constexpr float Y_MARGIN = 1.0f;   // y-bin range beyond the sector edge (cm)
-constexpr uint32_t WS_MAGIC = 0x54504331u;
+constexpr int MAX_FRAMES = 4096;
+constexpr int FRAME_NZ = 256;          // grid cell budget per extra frame, in z-cells per plane
+constexpr float Y_MARGIN = 1.0f;       // y-bin range beyond the sector edge (cm)
+constexpr uint32_t WS_MAGIC = 0x54504332u;
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -35,9 +42,9 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // ---------------------------------------------------------------------------
 struct Layout {
     uint32_t magic;
-    int32_t n, ns, nr, np, nzmax, ntcap, mnzmax, ny;
-    int64_t ncells;
-    size_t hdr, frame, rowtab, zlin, cell, slot, cstart, scan, yz, ids, plane;
+    int32_t n, ns, nr, np, nzmax, ntcap, mnzmax, ny, nframes;
+    int64_t ncells;                    // grid cell capacity (all frames)
+    size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, ids, plane;
     size_t upr, dnr, up, dn, starts;
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
@@ -91,7 +98,7 @@ void fill_rowtab(float* tab, const tpc_geometry* g, int ny)
     }
 }
 
-Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
+Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nframes)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
@@ -102,27 +109,31 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n)
     L.np = L.ns * L.nr;
     L.nzmax = p->max_z_cells;
     L.ny = effective_ybins(p, g);
-    L.ncells = (int64_t)L.np * L.nzmax * L.ny;
+    L.nframes = nframes;
+    L.ncells = (int64_t)L.np * L.ny * ((int64_t)L.nzmax + (int64_t)FRAME_NZ * (nframes - 1));
     int64_t cap = std::max<int64_t>(4096, (n * (int64_t)p->tracklets_per_1k) / 1000);
     L.ntcap = (int32_t)std::min<int64_t>(cap, std::max<int64_t>(n, 4096));
     L.mnzmax = MAX_MERGE_CELLS;
     const int64_t N = std::max<int64_t>(n, 1);
     const int64_t T = L.ntcap;
-    const int64_t mcells = (int64_t)L.ns * L.mnzmax;
+    const int64_t mcells = (int64_t)nframes * L.ns * L.mnzmax;
     int64_t scan_max = std::max({L.ncells + 1, N + 1, T + 1, mcells + 1});
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1), 256); return r; };
     L.hdr = take(sizeof(Layout));
     L.frame = take(sizeof(Frame));
+    L.fgrid = take(sizeof(FrameGrid) * nframes);
+    L.offsets = take(sizeof(int32_t) * (nframes + 1));
     L.rowtab = take(sizeof(float) * ROWTAB * 256);
     L.zlin = take(4 * N);
+    L.cfr = take(2 * N);
     L.cell = take(4 * N);
     L.slot = take(4 * N);
     L.cstart = take(4 * (L.ncells + 1));
     L.scan = take(4 * scan_aux_elems(scan_max));
     L.yz = take(8 * N);
     L.ids = take(4 * N);
-    L.plane = take(2 * N);
+    L.plane = take(4 * N);
     L.upr = take(4 * N);
     L.dnr = take(4 * N);
     L.up = take(4 * N);
@@ -171,17 +182,25 @@ int grid_for(int64_t n, int block)
 }
 
 // ---------------------------------------------------------------------------
-// generic exclusive scan (in place), total written at a[n]
+// exclusive scan (in place) of a[0..n], n+1 entries: a[n] (zero on entry)
+// receives the total.  With n_dev, the entries beyond *n_dev are left alone
+// (the launch covers the host-side bound n).
 // ---------------------------------------------------------------------------
-__global__ void k_scan_tiles(uint32_t* a, int64_t n, uint32_t* sums)
+__global__ void k_scan_tiles(uint32_t* a, int64_t n1, const unsigned* n_dev, uint32_t* sums)
 {
     __shared__ uint32_t sh[SCAN_BLOCK];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const int64_t lim = n_dev ? (int64_t)(*n_dev) + 1 : n1;
+    const int64_t tile0 = (int64_t)blockIdx.x * SCAN_TILE;
+    if (tile0 >= lim) {
+        if (threadIdx.x == 0) sums[blockIdx.x] = 0u;
+        return;
+    }
+    const int64_t base = tile0 + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS];
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-        v[k] = (base + k < n) ? a[base + k] : 0u;
+        v[k] = (base + k < lim) ? a[base + k] : 0u;
         s += v[k];
     }
     sh[threadIdx.x] = s;
@@ -195,34 +214,41 @@ __global__ void k_scan_tiles(uint32_t* a, int64_t n, uint32_t* sums)
     uint32_t run = sh[threadIdx.x] - s;   // exclusive prefix of this thread
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-        if (base + k < n) a[base + k] = run;
+        if (base + k < lim) a[base + k] = run;
         run += v[k];
     }
     if (threadIdx.x == SCAN_BLOCK - 1) sums[blockIdx.x] = sh[SCAN_BLOCK - 1];
 }
 
-__global__ void k_scan_add(uint32_t* a, int64_t n, const uint32_t* sums)
+__global__ void k_scan_add(uint32_t* a, int64_t n1, const unsigned* n_dev, const uint32_t* sums)
 {
-    const uint32_t add = sums[blockIdx.x];
+    const int64_t lim = n_dev ? (int64_t)(*n_dev) + 1 : n1;
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    if (base >= lim) return;
+    const uint32_t add = sums[blockIdx.x];
     for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_BLOCK)
-        if (base + k < n) a[base + k] += add;
+        if (base + k < lim) a[base + k] += add;
 }
 
-// exclusive scan of a[0..n), total stored in a[n]; aux holds the tile sums
-int g_launches = 0;   // kernels launched by the current tpc_track call (host thread)
+int g_launches = 0;   // kernels launched by the current call (host thread)
 
-void scan_u32(uint32_t* a, int64_t n, uint32_t* aux, cudaStream_t st)
+void scan_u32(uint32_t* a, int64_t n, uint32_t* aux, cudaStream_t st, const unsigned* n_dev = nullptr)
 {
-    const int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;    // include the total slot
-    // exclusive scan of the n+1 entries a[0..n]: a[n] (zero on entry) receives the total
-    k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+    const int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, n_dev, aux);
     g_launches++;
     if (tiles > 1) {
         scan_u32(aux, tiles - 1, aux + tiles + 1, st);   // exclusive scan of the tile sums
-        k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, aux);
+        k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(a, n + 1, n_dev, aux);
         g_launches++;
     }
+}
+
+__global__ void k_zero_cells(uint32_t* a, const Frame* __restrict__ f)
+{
+    const int64_t n1 = (int64_t)f->total_cells + 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = 0u;
 }
 
 // stage events for params.profile (created once per process, per device)
@@ -233,24 +259,34 @@ struct StageEvents {
 StageEvents g_events;
 
 // ---------------------------------------------------------------------------
-// a1 + a2: time -> z, validation, folded-z extrema; grid histogram / scatter
+// a1 + a2: time -> z, validation, folded-z extrema per frame; grid
 // ---------------------------------------------------------------------------
-__global__ void k_init_frame(Frame* f)
+__global__ void k_init_frame(Frame* f, FrameGrid* fg, int nframes)
 {
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         memset(f, 0, sizeof(Frame));
         f->zmin_key = 0xFFFFFFFFu;
         f->zmax_key = 0u;
     }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nframes; i += gridDim.x * blockDim.x) {
+        fg[i].zmin_key = 0xFFFFFFFFu;
+        fg[i].zmax_key = 0u;
+    }
 }
 
-__global__ void k_prep(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
-                       const float* __restrict__ y, const float* __restrict__ zt, int ns, int nr, int continuous,
-                       float zmax, float vdrift, float* __restrict__ zlin, Frame* f)
+__device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
+
+// blockIdx.y = frame; the blocks of one frame stride over its cluster range
+__global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
+                       const uint8_t* __restrict__ row, const float* __restrict__ y, const float* __restrict__ zt,
+                       int ns, int nr, int continuous, float zmax, float vdrift, float* __restrict__ zlin,
+                       uint16_t* __restrict__ cfr, Frame* f, FrameGrid* fg)
 {
+    const int fr = blockIdx.y;
+    const int b = offsets[fr], e = offsets[fr + 1];
     unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
     int bad = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
         const int s = sector[i], r = row[i];
         float z = zt[i];
         if (continuous) {
@@ -258,25 +294,28 @@ __global__ void k_prep(int n, const uint8_t* __restrict__ sector, const uint8_t*
             z = (ns == 36 && s >= 18) ? -zl : zl;
         }
         zlin[i] = z;
+        cfr[i] = (uint16_t)fr;
         const bool ok = s < ns && r < nr && isfinite(z) && isfinite(y[i]);
         if (!ok) {
             bad++;
             continue;
         }
-        const float zeta = (ns == 36 && s >= 18) ? -z : z;
-        const unsigned k = fkey(zeta);
+        const unsigned k = fkey(fold(z, s, ns));
         kmin = min(kmin, k);
         kmax = max(kmax, k);
     }
-    // warp then block reduction
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         bad += __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&f->zmin_key, kmin);
-        atomicMax(&f->zmax_key, kmax);
+        if (kmin != 0xFFFFFFFFu) {
+            atomicMin(&fg[fr].zmin_key, kmin);
+            atomicMax(&fg[fr].zmax_key, kmax);
+            atomicMin(&f->zmin_key, kmin);
+            atomicMax(&f->zmax_key, kmax);
+        }
         if (bad) {
             atomicAdd(&f->n_bad, bad);
             atomicExch(&f->err, TPC_ERR_DATA);
@@ -284,26 +323,52 @@ __global__ void k_prep(int n, const uint8_t* __restrict__ sector, const uint8_t*
     }
 }
 
-__global__ void k_grid_setup(Frame* f, float z_cell, int nzmax, float merge_cell, int mnzmax, int ny)
+// One thread: per-frame z grids inside the cell budget, the merger grid.
+__global__ void k_grid_setup(Frame* f, FrameGrid* fg, int nframes, int np, int ny, float z_cell, int nzmax,
+                             long long cell_cap, float merge_cell, int mnzmax)
 {
-    if (threadIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
     f->ny = ny;
+    long long need = 0;
+    for (int i = 0; i < nframes; i++) {
+        int nz = 1;
+        if (fg[i].zmin_key != 0xFFFFFFFFu) {
+            const float span = fkey_inv(fg[i].zmax_key) - fkey_inv(fg[i].zmin_key);
+            nz = min(nzmax, (int)(span / z_cell) + 1);
+        }
+        fg[i].nz = nz;
+        need += (long long)nz;
+    }
+    // cell budget: shrink every frame's z-cell count by the same factor
+    const long long per = (long long)np * ny;
+    const double scale = need * per > cell_cap ? (double)(cell_cap / per) / (double)need : 1.0;
+    unsigned base = 0;
+    for (int i = 0; i < nframes; i++) {
+        int nz = fg[i].nz;
+        if (scale < 1.0) nz = max(1, (int)(nz * scale));
+        float zmin = 0.0f, span = 0.0f;
+        if (fg[i].zmin_key != 0xFFFFFFFFu) {
+            zmin = fkey_inv(fg[i].zmin_key);
+            span = fkey_inv(fg[i].zmax_key) - zmin;
+        }
+        const float cs = fmaxf(z_cell, span * 1.001f / (float)max(nz - 1, 1));
+        fg[i].zmin = zmin;
+        fg[i].inv_cs = 1.0f / cs;
+        fg[i].nz = nz;
+        fg[i].cell_base = base;
+        base += (unsigned)(per * nz);
+    }
+    f->total_cells = base;
     float zmin = 0.0f, span = 0.0f;
     if (f->zmin_key != 0xFFFFFFFFu) {
         zmin = fkey_inv(f->zmin_key);
         span = fkey_inv(f->zmax_key) - zmin;
     }
-    float cs = fmaxf(z_cell, span / (float)(nzmax - 1) * 1.001f);
-    f->zmin = zmin;
-    f->inv_cs = 1.0f / cs;
-    f->nz = min(nzmax, (int)(span / cs) + 1);
-    float mcs = fmaxf(merge_cell, span / (float)(mnzmax - 1) * 1.001f);
+    const float mcs = fmaxf(merge_cell, span / (float)(mnzmax - 1) * 1.001f);
     f->mzmin = zmin;
     f->minv_cs = 1.0f / mcs;
     f->mnz = min(mnzmax, (int)(span / mcs) + 1);
 }
-
-__device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
 
 __device__ __forceinline__ int ybin(float y, const float* __restrict__ rowtab, int r, int ny)
 {
@@ -312,37 +377,38 @@ __device__ __forceinline__ int ybin(float y, const float* __restrict__ rowtab, i
     return (int)t;
 }
 
-
 __global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
-                       const float* __restrict__ y, const float* __restrict__ zlin, const float* __restrict__ rowtab,
-                       int nr, int ns, const Frame* __restrict__ f, uint32_t* __restrict__ count,
-                       uint32_t* __restrict__ cell, uint32_t* __restrict__ slot)
+                       const float* __restrict__ y, const float* __restrict__ zlin, const uint16_t* __restrict__ cfr,
+                       const float* __restrict__ rowtab, int nr, int ns, const Frame* __restrict__ f,
+                       const FrameGrid* __restrict__ fg, uint32_t* __restrict__ count, uint32_t* __restrict__ cell,
+                       uint32_t* __restrict__ slot)
 {
     if (f->err) return;   // invalid clusters: nothing after validation runs
-    const float zmin = f->zmin, inv = f->inv_cs;
-    const int nz = f->nz, ny = f->ny;
+    const int ny = f->ny;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int s = sector[i], r = row[i];
+        const FrameGrid G = fg[cfr[i]];
         const int pl = s * nr + r;
-        const int zc = grid_cell(fold(zlin[i], s, ns), zmin, inv, nz);
-        const uint32_t c = ((uint32_t)pl * (uint32_t)nz + (uint32_t)zc) * (uint32_t)ny + (uint32_t)ybin(y[i], rowtab, r, ny);
+        const int zc = grid_cell(fold(zlin[i], s, ns), G.zmin, G.inv_cs, G.nz);
+        const uint32_t c = G.cell_base + ((uint32_t)pl * (uint32_t)G.nz + (uint32_t)zc) * (uint32_t)ny +
+                           (uint32_t)ybin(y[i], rowtab, r, ny);
         cell[i] = c;
         slot[i] = atomicAdd(&count[c], 1u);
     }
 }
 
 __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
-                          const float* __restrict__ y, const float* __restrict__ zlin, int nr,
-                          const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
-                          const uint32_t* __restrict__ slot, float2* __restrict__ yz,
-                          int32_t* __restrict__ ids, uint16_t* __restrict__ plane, const Frame* __restrict__ f)
+                          const float* __restrict__ y, const float* __restrict__ zlin, const uint16_t* __restrict__ cfr,
+                          int nr, int np, const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
+                          const uint32_t* __restrict__ slot, float2* __restrict__ yz, int32_t* __restrict__ ids,
+                          uint32_t* __restrict__ plane, const Frame* __restrict__ f)
 {
     if (f->err) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pos = cstart[cell[i]] + slot[i];
         yz[pos] = make_float2(y[i], zlin[i]);
         ids[pos] = i;
-        plane[pos] = (uint16_t)(sector[i] * nr + row[i]);
+        plane[pos] = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
     }
 }
 
@@ -351,18 +417,18 @@ __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8
 struct Ranges {
     int b[3], e[3];
 };
-__device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstart, int plane, int zc, int yc, int nz,
-                                              int ny)
+__device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstart, const FrameGrid& G, int lplane,
+                                              int zc, int yc, int ny)
 {
     Ranges R;
     const int ylo = max(yc - 1, 0), yhi = min(yc + 1, ny - 1);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const int zz = zc - 1 + k;
-        if (zz < 0 || zz >= nz) {
+        if (zz < 0 || zz >= G.nz) {
             R.b[k] = R.e[k] = 0;
         } else {
-            const int64_t base = ((int64_t)plane * nz + zz) * ny;
+            const uint32_t base = G.cell_base + ((uint32_t)lplane * (uint32_t)G.nz + (uint32_t)zz) * (uint32_t)ny;
             R.b[k] = (int)cstart[base + ylo];
             R.e[k] = (int)cstart[base + yhi + 1];
         }
@@ -376,27 +442,30 @@ __device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstar
 constexpr int MAXD = 8;
 
 __global__ void __launch_bounds__(256) k_neighbours(
-    int n, int nr, int ns, const float* __restrict__ rowtab, const float2* __restrict__ yz,
-    const int32_t* __restrict__ ids, const uint16_t* __restrict__ plane, const uint32_t* __restrict__ cstart,
-    const Frame* __restrict__ f, float DY, float DZ, float SMAX, int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
+    int n, int nr, int ns, int np, const float* __restrict__ rowtab, const float2* __restrict__ yz,
+    const int32_t* __restrict__ ids, const uint32_t* __restrict__ plane, const uint32_t* __restrict__ cstart,
+    const Frame* __restrict__ f, const FrameGrid* __restrict__ fg, float DY, float DZ, float SMAX,
+    int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
 {
     if (f->err) return;
-    const float zmin = f->zmin, inv = f->inv_cs;
-    const int nz = f->nz, ny = f->ny;
+    const int ny = f->ny;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
-        const int pl = plane[h];
+        const uint32_t pg = plane[h];
+        const int fr = (int)(pg / (uint32_t)np);
+        const int pl = (int)(pg - (uint32_t)fr * np);
         const int s = pl / nr, r = pl - s * nr;
         int bu = -1, bd = -1, bidu = 0, bidd = 0;
         float bs = 0.0f;
         if (r >= 1 && r <= nr - 2) {
+            const FrameGrid G = fg[fr];
             const float2 ph = yz[h];
             const float yh = ph.x, zh = ph.y;
             const float yu_pred = yh * rowtab[r * ROWTAB + 1];
             const float yd_pred = yh * rowtab[r * ROWTAB + 2];
             const float w = rowtab[r * ROWTAB + 3];
-            const int c = grid_cell(fold(zh, s, ns), zmin, inv, nz);
-            const Ranges ru = cell_ranges(cstart, pl + 1, c, ybin(yu_pred, rowtab, r + 1, ny), nz, ny);
-            const Ranges rd = cell_ranges(cstart, pl - 1, c, ybin(yd_pred, rowtab, r - 1, ny), nz, ny);
+            const int c = grid_cell(fold(zh, s, ns), G.zmin, G.inv_cs, G.nz);
+            const Ranges ru = cell_ranges(cstart, G, pl + 1, c, ybin(yu_pred, rowtab, r + 1, ny), ny);
+            const Ranges rd = cell_ranges(cstart, G, pl - 1, c, ybin(yd_pred, rowtab, r - 1, ny), ny);
             // down candidates inside the windows
             int dl[MAXD];
             int ndn = 0;
@@ -485,18 +554,19 @@ __global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* _
 }
 
 // ---------------------------------------------------------------------------
-// a6: TrackletConstructor (one thread per start hit)
+// a6: TrackletConstructor
 // ---------------------------------------------------------------------------
 struct TrkArgs {
     const float* rowtab;
     const float2* yz;
     const int32_t* ids;
-    const uint16_t* plane;
+    const uint32_t* plane;
     const uint32_t* cstart;
     const int32_t* up;
     const int32_t* starts;
     const Frame* f;
-    int nr, ns, cap;
+    const FrameGrid* fg;
+    int nr, ns, np, cap;
     float kb, vy, vz, c0s, c0t, c0q, nsig, wmin, wmax, chi2cut, edge;
     int max_miss;
     int prof;
@@ -505,11 +575,13 @@ struct TrkArgs {
     Frame* fw;
 };
 
-__device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int r, int s, float yp, float zp, float wy,
-                                            float wz, float zmin, float inv, int nz, int ny, unsigned& ncand)
+// Nearest cluster of the plane inside |dy| <= wy, |dz| <= wz of (yp, zp):
+// minimum dy^2 + dz^2 (binary32, fused), ties to the smaller input index.
+__device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G, int lplane, int r, int s, float yp,
+                                            float zp, float wy, float wz, int ny, unsigned& ncand)
 {
-    const int c = grid_cell(fold(zp, s, A.ns), zmin, inv, nz);
-    const Ranges rg = cell_ranges(A.cstart, pl, c, ybin(yp, A.rowtab, r, ny), nz, ny);
+    const int c = grid_cell(fold(zp, s, A.ns), G.zmin, G.inv_cs, G.nz);
+    const Ranges rg = cell_ranges(A.cstart, G, lplane, c, ybin(yp, A.rowtab, r, ny), ny);
     int best = -1, bid = 0;
     float bd = 0.0f;
 #pragma unroll
@@ -530,15 +602,11 @@ __device__ __forceinline__ int find_nearest(const TrkArgs& A, int pl, int r, int
     return best;
 }
 
-__device__ __forceinline__ void copy_state(float* d, const float* s)
-{
-#pragma unroll
-    for (int i = 0; i < NST; i++) d[i] = s[i];
-}
-
 // Phases of one tracklet (the operation sequence per tracklet is fixed; the
 // kernel only interleaves tracklets differently across lanes)
 enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
+
+constexpr int TRK_BLOCK = 128;
 
 // One lane = one tracklet at a time.  Each loop iteration advances the lane's
 // tracklet by one row step; a lane whose tracklet ends writes it out and takes
@@ -547,16 +615,13 @@ enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
 // Kalman update each have a single call site shared by all phases, so a warp
 // whose lanes are in different phases still executes each of them once per
 // iteration.
-constexpr int TRK_BLOCK = 128;
-
 __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
 {
     // the last accepted state of each lane (outer-end / inner-end candidate) lives
     // in shared memory, element-major so that the lanes of a warp hit distinct banks
     __shared__ float keep_sh[NST][TRK_BLOCK];
     if (A.f->err) return;
-    const float zmin = A.f->zmin, inv = A.f->inv_cs;
-    const int nz = A.f->nz, ny = A.f->ny;
+    const int ny = A.f->ny;
     const int nt = min(A.f->n_starts, A.cap);
     const float INF = __int_as_float(0x7f800000);
     const int NR = A.nr;
@@ -569,7 +634,9 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
         for (int i = 0; i < NST; i++) keep_sh[i][threadIdx.x] = st[i];
     };
     int t = -1, phase = PH_DONE;
-    int h1 = 0, r1 = 0, s = 0, pbase = 0, hc = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
+    int h1 = 0, r1 = 0, s = 0, lbase = 0, pgbase = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
+    FrameGrid G;
+    G.zmin = 0.0f; G.inv_cs = 1.0f; G.nz = 1; G.cell_base = 0u; G.zmin_key = 0u; G.zmax_key = 0u;
     // next chain hit (phase A), loaded one step ahead
     int nx_h = -1, nx_row = 0;
     float2 nx_yz = make_float2(0.0f, 0.0f);
@@ -596,10 +663,14 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             if (t >= nt) break;
             // initial state at the start hit: y, z measured, slopes from the first link
             h1 = A.starts[t];
-            const int pl1 = A.plane[h1];
+            const uint32_t pg1 = A.plane[h1];
+            const int fr = (int)(pg1 / (uint32_t)A.np);
+            const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
+            G = A.fg[fr];
             s = pl1 / NR;
             r1 = pl1 - s * NR;
-            pbase = s * NR;
+            lbase = s * NR;
+            pgbase = (int)pg1 - r1;
             const int h2 = A.up[h1];
             const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
             const float dx12 = x2 - x1;
@@ -620,10 +691,9 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             slot[nu++] = h1;
             save_keep();
             rc = r1;
-            hc = h1;
             phase = PH_A;
             nx_h = h2;
-            nx_row = A.plane[h2] - pbase;
+            nx_row = (int)A.plane[h2] - pgbase;
             nx_yz = p2;
         }
         if (phase == PH_CSTART) {
@@ -650,7 +720,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
                 // load the following chain hit while this step computes
                 nx_h = A.up[hn];
                 if (nx_h >= 0) {
-                    nx_row = A.plane[nx_h] - pbase;
+                    nx_row = (int)A.plane[nx_h] - pgbase;
                     nx_yz = A.yz[nx_h];
                 }
             }
@@ -702,7 +772,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             // ---- window search (one call site)
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            c = find_nearest(A, pbase + target, target, s, st[1], st[2], wy, wz, zmin, inv, nz, ny, ncand);
+            c = find_nearest(A, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand);
             if (c >= 0) {
                 const float2 pc = A.yz[c];
                 my = pc.x;
@@ -716,7 +786,6 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
         if (phase == PH_A) {
             slot[nu++] = hn;
             save_keep();
-            hc = hn;
         } else if (phase == PH_B) {
             if (took) {
                 nupd++;
@@ -797,15 +866,22 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
 }
 
 // ---------------------------------------------------------------------------
-// a8: cross-sector merger
+// a8: cross-sector merger (adjacent sectors of one side, inside one frame)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
 {
     return grid_cell(zeta, f->mzmin, f->minv_cs, f->mnz);
 }
 
-__global__ void k_seg_keys(const Frame* __restrict__ f, int ns, const int32_t* __restrict__ seg,
-                           const uint16_t* __restrict__ plane, const int32_t* __restrict__ t_start, int nr,
+// global sector index (frame * n_sectors + sector) of a segment's start hit
+__device__ __forceinline__ int seg_gsector(const uint32_t* plane, const int32_t* t_start, const int32_t* seg, int a,
+                                           int nr)
+{
+    return (int)(plane[t_start[seg[a]]] / (uint32_t)nr);
+}
+
+__global__ void k_seg_keys(const Frame* __restrict__ f, int ns, int nr, const int32_t* __restrict__ seg,
+                           const uint32_t* __restrict__ plane, const int32_t* __restrict__ t_start,
                            const float* __restrict__ t_top, const float* __restrict__ t_bot,
                            uint32_t* __restrict__ cntb, uint32_t* __restrict__ cntt, uint32_t* __restrict__ keyb,
                            uint32_t* __restrict__ keyt, uint32_t* __restrict__ slotb, uint32_t* __restrict__ slott)
@@ -814,9 +890,10 @@ __global__ void k_seg_keys(const Frame* __restrict__ f, int ns, const int32_t* _
     const int mnz = f->mnz;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
         const int t = seg[a];
-        const int s = plane[t_start[t]] / nr;
-        const uint32_t kb = (uint32_t)s * mnz + merge_cell(fold(t_bot[(int64_t)t * NST + 2], s, ns), f);
-        const uint32_t kt = (uint32_t)s * mnz + merge_cell(fold(t_top[(int64_t)t * NST + 2], s, ns), f);
+        const int gs = seg_gsector(plane, t_start, seg, a, nr);
+        const int s = gs % ns;
+        const uint32_t kb = (uint32_t)gs * mnz + merge_cell(fold(t_bot[(int64_t)t * NST + 2], s, ns), f);
+        const uint32_t kt = (uint32_t)gs * mnz + merge_cell(fold(t_top[(int64_t)t * NST + 2], s, ns), f);
         keyb[a] = kb;
         keyt[a] = kt;
         slotb[a] = atomicAdd(&cntb[kb], 1u);
@@ -841,7 +918,7 @@ struct MergeArgs {
     int ns, nr;
     float kb, dz, chi2cut;
     const int32_t* seg;
-    const uint16_t* plane;
+    const uint32_t* plane;
     const int32_t* t_start;
     const int32_t* t_id;
     const float* t_top;
@@ -856,8 +933,6 @@ struct MergeArgs {
     Frame* fw;
 };
 
-__device__ __forceinline__ int seg_sector(const MergeArgs& M, int a) { return M.plane[M.t_start[M.seg[a]]] / M.nr; }
-
 // best B (outer piece) for every A: A's outer end against B's inner end
 __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 {
@@ -865,7 +940,8 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
     unsigned nchi = 0;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
         const int ta = M.seg[a];
-        const int sa = seg_sector(M, a);
+        const int gsa = seg_gsector(M.plane, M.t_start, M.seg, a, M.nr);
+        const int fr = gsa / M.ns, sa = gsa - fr * M.ns;
         float top[NST];
 #pragma unroll
         for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
@@ -875,9 +951,10 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
         for (int dir = 1; dir >= -1; dir -= 2) {
             const int sb = neighbour_sector(sa, dir, M.ns);
             if (sb < 0) continue;
+            const int gsb = fr * M.ns + sb;
             const float sn = dir > 0 ? SIN20 : -SIN20;
             const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
-            const int qb = M.cntb[sb * mnz + lo], qe = M.cntb[sb * mnz + hi + 1];
+            const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
                 const int b = M.byb[q];
                 const int tb = M.seg[b];
@@ -901,7 +978,8 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
         const int tb = M.seg[b];
-        const int sb = seg_sector(M, b);
+        const int gsb = seg_gsector(M.plane, M.t_start, M.seg, b, M.nr);
+        const int fr = gsb / M.ns, sb = gsb - fr * M.ns;
         float bot[NST];
 #pragma unroll
         for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
@@ -911,10 +989,11 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
         for (int d = 1; d >= -1; d -= 2) {
             const int sa = neighbour_sector(sb, d, M.ns);
             if (sa < 0) continue;
+            const int gsa = fr * M.ns + sa;
             // seen from A, B lies in direction -d
             const float sn = (-d) > 0 ? SIN20 : -SIN20;
             const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
-            const int qb = M.cntt[sa * mnz + lo], qe = M.cntt[sa * mnz + hi + 1];
+            const int qb = M.cntt[gsa * mnz + lo], qe = M.cntt[gsa * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
                 const int a = M.byt[q];
                 const int ta = M.seg[a];
@@ -975,15 +1054,17 @@ __global__ void k_merge_fix(const Frame* __restrict__ f, const int32_t* __restri
 // ---------------------------------------------------------------------------
 struct AsmArgs {
     Frame* f;
-    int nr, n, cap_tracks, cap_clus, ntcap;
+    int nr, np, n, cap_tracks, cap_clus, ntcap;
     const int32_t* seg;
     const int32_t* next2;
     const int32_t* prev2;
+    const int32_t* t_start;
     const int32_t* t_id;
     const int32_t* t_nhits;
     const int32_t* t_nup;
     const int32_t* t_hits;
     const int32_t* ids;
+    const uint32_t* plane;
     const unsigned long long* hitw;
     const uint32_t* headmark;   // scanned: rank of each head's start id
     uint32_t* tcount;           // [ntcap + 1]
@@ -993,6 +1074,7 @@ struct AsmArgs {
     int32_t* nclus;
     int32_t* clus_index;
     int32_t* assign;
+    int32_t* frame;             // nullable
 };
 
 __global__ void k_track_count(AsmArgs A)
@@ -1033,6 +1115,7 @@ __global__ void k_track_fill(AsmArgs A)
         A.clus_offset[r] = (int)off;
         if (r == T - 1) A.clus_offset[T] = (int)end;
         A.nclus[r] = (int)(end - off);
+        if (A.frame) A.frame[r] = (int)(A.plane[A.t_start[A.seg[a]]] / (uint32_t)A.np);
         uint32_t o = off;
         int steps = 0;
         for (int b = a; b >= 0 && steps <= MAX_CHAIN; b = A.next2[b], steps++) {
@@ -1049,6 +1132,20 @@ __global__ void k_track_fill(AsmArgs A)
                 }
             }
         }
+    }
+}
+
+// counts for the enqueue-only call: n_tracks, n_tracklets, n_segments, error,
+// clusters in tracks, start hits found
+__global__ void k_publish(const Frame* __restrict__ f, int cap, int32_t* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = f->n_tracks;
+        out[1] = min(f->n_starts, cap);
+        out[2] = f->n_seg;
+        out[3] = f->err ? f->err : (f->n_starts > cap ? TPC_ERR_CAPACITY : 0);
+        out[4] = f->n_clus;
+        out[5] = f->n_starts;
     }
 }
 
@@ -1081,15 +1178,16 @@ __global__ void k_export_links(int n, const int32_t* __restrict__ ids, const int
 // ---------------------------------------------------------------------------
 // Scratch for tpc_links_static: a file-scope device array, so that the entry
 // point needs no allocation by its caller or by the library.  Sized for
-// TPC_LINKS_STATIC_MAX_CLUSTERS clusters with a coarser grid (64 z-cells per
-// pad row; coarser cells scan more candidates but give the same links).
+// TPC_LINKS_STATIC_MAX_CLUSTERS clusters of one frame with a coarser grid (64
+// z-cells per pad row, one y-bin; coarser cells scan more candidates but give
+// the same links).
 // ---------------------------------------------------------------------------
 constexpr int STATIC_NZ = 64;
 constexpr int STATIC_MAX_PLANES = 36 * 255;
 constexpr int64_t STATIC_NCELLS = (int64_t)STATIC_MAX_PLANES * STATIC_NZ;
 
 struct StaticLayout {
-    size_t frame, rowtab, zlin, cell, slot, cstart, scan, yz, ids, plane, upr, dnr, up, dn, total;
+    size_t frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, ids, plane, upr, dnr, up, dn, total;
 };
 
 constexpr size_t sa256(size_t v) { return (v + 255) / 256 * 256; }
@@ -1099,15 +1197,18 @@ constexpr StaticLayout static_layout()
     StaticLayout L{};
     size_t o = 0;
     L.frame = o; o += sa256(sizeof(Frame));
+    L.fgrid = o; o += sa256(sizeof(FrameGrid));
+    L.offsets = o; o += sa256(2 * sizeof(int32_t));
     L.rowtab = o; o += sa256(sizeof(float) * ROWTAB * 256);
     L.zlin = o; o += sa256(4 * N);
+    L.cfr = o; o += sa256(2 * N);
     L.cell = o; o += sa256(4 * N);
     L.slot = o; o += sa256(4 * N);
     L.cstart = o; o += sa256(4 * (STATIC_NCELLS + 1));
     L.scan = o; o += sa256(4 * (STATIC_NCELLS / SCAN_TILE + 64));
     L.yz = o; o += sa256(8 * N);
     L.ids = o; o += sa256(4 * N);
-    L.plane = o; o += sa256(2 * N);
+    L.plane = o; o += sa256(4 * N);
     L.upr = o; o += sa256(4 * N);
     L.dnr = o; o += sa256(4 * N);
     L.up = o; o += sa256(4 * N);
@@ -1138,12 +1239,285 @@ int static_scratch(void** ptr)
     return TPC_OK;
 }
 
+int check_args(const tpc_params* p, const tpc_geometry* g)
+{
+    if (!p || !g || !g->row_x) return TPC_ERR_ARG;
+    if (!(g->n_sectors == 36 || g->n_sectors == 1)) return TPC_ERR_ARG;
+    if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
+    if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
+    if (!(p->refit_inflate >= 1.0f)) return TPC_ERR_ARG;
+    if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
+    for (int r = 0; r + 1 < g->n_rows; r++)
+        if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
+    return TPC_OK;
+}
+
+int check_frames(int32_t n, int32_t nframes, const int32_t* offsets)
+{
+    if (nframes < 1 || nframes > MAX_FRAMES || !offsets) return TPC_ERR_ARG;
+    if (offsets[0] != 0 || offsets[nframes] != n) return TPC_ERR_ARG;
+    for (int i = 0; i < nframes; i++)
+        if (offsets[i + 1] < offsets[i]) return TPC_ERR_ARG;
+    return TPC_OK;
+}
+
+int out_args(const tpc_params* p, const tpc_tracks* out)
+{
+    if (!out->sector || !out->x || !out->param || !out->cov || !out->chi2 || !out->ndf || !out->status ||
+        !out->nclus || !out->clus_offset || !out->clus_index || !out->assign)
+        return TPC_ERR_ARG;
+    if (out->capacity_tracks < 0 || out->capacity_clusters < 0) return TPC_ERR_ARG;
+    if (p->fp64_final && (!out->cov64 || !out->chi2_64)) return TPC_ERR_ARG;
+    return TPC_OK;
+}
+
 }  // namespace
 
 // refit launcher (tpc_refit.cu)
 int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const tpc_clusters* cl,
                      const float* zlin, const float* rowtab, const void* frame, const int32_t* ttail,
                      const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st);
+
+namespace {
+
+// Enqueue the whole chain on `st` (no host synchronisation, no pageable copy:
+// capturable in a CUDA graph once the tables are in the workspace).
+int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl, void* ws,
+            const Layout& L, tpc_tracks* out, int32_t* dev_counts, cudaStream_t st, bool prof)
+{
+    const int n = cl->n;
+    Frame* f = at<Frame>(ws, L.frame);
+    FrameGrid* fg = at<FrameGrid>(ws, L.fgrid);
+    const int32_t* offsets = at<int32_t>(ws, L.offsets);
+    float* rowtab = at<float>(ws, L.rowtab);
+    float* zlin = at<float>(ws, L.zlin);
+    uint16_t* cfr = at<uint16_t>(ws, L.cfr);
+    uint32_t* cell = at<uint32_t>(ws, L.cell);
+    uint32_t* slot = at<uint32_t>(ws, L.slot);
+    uint32_t* cstart = at<uint32_t>(ws, L.cstart);
+    uint32_t* aux = at<uint32_t>(ws, L.scan);
+    float2* yz = at<float2>(ws, L.yz);
+    int32_t* ids = at<int32_t>(ws, L.ids);
+    uint32_t* plane = at<uint32_t>(ws, L.plane);
+    int32_t* upr = at<int32_t>(ws, L.upr);
+    int32_t* dnr = at<int32_t>(ws, L.dnr);
+    int32_t* up = at<int32_t>(ws, L.up);
+    int32_t* dn = at<int32_t>(ws, L.dn);
+    int32_t* starts = at<int32_t>(ws, L.starts);
+    unsigned long long* hitw = at<unsigned long long>(ws, L.hitw);
+    volatile float vyv = p->sigma_y * p->sigma_y;
+    volatile float vzv = p->sigma_z * p->sigma_z;
+    volatile float kbv = KB_C * bz;
+    const float vy = vyv, vz = vzv, kb = kbv;
+    const int B = 256;
+    const int gN = grid_for(n, B);
+    const int ntcap = L.ntcap;
+    const int NF = L.nframes;
+    auto mark = [&](int k) -> cudaError_t { return prof ? cudaEventRecord(g_events.ev[k], st) : cudaSuccess; };
+    g_launches = 0;
+
+    CK(mark(0));
+    k_init_frame<<<std::max(1, (NF + 255) / 256), 256, 0, st>>>(f, fg, NF);
+    {
+        const int gx = std::max(1, std::min(grid_for(n, B), (148 * 16 + NF - 1) / NF));
+        k_prep<<<dim3(gx, NF), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
+                                          g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
+    }
+    k_grid_setup<<<1, 32, 0, st>>>(f, fg, NF, L.np, L.ny, p->z_cell, L.nzmax, (long long)L.ncells,
+                                   p->merge_dz * 1.1f + 0.5f, L.mnzmax);
+    g_launches += 3;
+    CK(mark(1));
+    // a2: counting sort of the clusters into (frame, sector, row, z-cell, y-bin) order
+    k_zero_cells<<<grid_for(L.ncells + 1, B), B, 0, st>>>(cstart, f);
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, rowtab, g->n_rows, g->n_sectors, f, fg, cstart,
+                             cell, slot);
+    g_launches += 2;
+    scan_u32(cstart, L.ncells, aux, st, &f->total_cells);
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, cstart, cell, slot, yz,
+                                ids, plane, f);
+    g_launches++;
+    CK(mark(2));
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f, fg,
+                                   p->dy_link, p->dz_link, p->s_max_link, upr, dnr);
+    g_launches++;
+    CK(mark(3));
+    k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
+    k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
+    g_launches += 2;
+    CK(mark(4));
+    // a6: tracklets
+    TrkArgs TA;
+    TA.rowtab = rowtab; TA.yz = yz; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
+    TA.starts = starts; TA.f = f; TA.fg = fg; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.np = L.np; TA.cap = ntcap;
+    TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
+    TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
+    TA.edge = p->edge_margin; TA.max_miss = p->max_miss; TA.prof = prof ? 1 : 0; TA.fw = f;
+    TA.t_start = at<int32_t>(ws, L.t_start); TA.t_id = at<int32_t>(ws, L.t_id);
+    TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
+    TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
+    const int gT = grid_for(ntcap, TRK_BLOCK);
+    k_tracklets<<<gT, TRK_BLOCK, 0, st>>>(TA);
+    g_launches++;
+    CK(mark(5));
+    // a7: selector
+    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)n, st));
+    const int gt2 = grid_for(ntcap, B);
+    uint8_t* kept = at<uint8_t>(ws, L.t_kept);
+    int32_t* seg = at<int32_t>(ws, L.seg);
+    k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
+    k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
+                                 TA.t_hits, hitw, kept, seg);
+    g_launches += 2;
+    CK(mark(6));
+    // a8: merger
+    const int64_t mcells = (int64_t)NF * g->n_sectors * L.mnzmax;
+    uint32_t* cntb = at<uint32_t>(ws, L.cntb);
+    uint32_t* cntt = at<uint32_t>(ws, L.cntt);
+    CK(cudaMemsetAsync(cntb, 0, 4 * (size_t)(mcells + 1), st));
+    CK(cudaMemsetAsync(cntt, 0, 4 * (size_t)(mcells + 1), st));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, st));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
+    uint32_t* headmark = at<uint32_t>(ws, L.headmark);
+    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), st));
+    k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, g->n_rows, seg, plane, TA.t_start, TA.t_top, TA.t_bot, cntb, cntt,
+                                  at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt), at<uint32_t>(ws, L.slotb),
+                                  at<uint32_t>(ws, L.slott));
+    g_launches++;
+    scan_u32(cntb, mcells, aux, st);
+    scan_u32(cntt, mcells, aux, st);
+    MergeArgs M;
+    M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
+    M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
+    M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
+    M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
+    k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
+                                     at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
+                                     at<int32_t>(ws, L.byt));
+    k_merge_next<<<gT, 128, 0, st>>>(M);
+    k_merge_prev<<<gT, 128, 0, st>>>(M);
+    k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
+    k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
+    k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
+                                   at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
+    g_launches += 6;
+    scan_u32(headmark, n, aux, st);
+    CK(mark(7));
+    // merged cluster lists and assignments
+    uint32_t* tcount = at<uint32_t>(ws, L.tcount);
+    CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), st));
+    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)n, st));
+    AsmArgs AA;
+    AA.f = f; AA.nr = g->n_rows; AA.np = L.np; AA.n = n; AA.cap_tracks = out->capacity_tracks;
+    AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
+    AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_start = TA.t_start; AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits;
+    AA.t_nup = TA.t_nup; AA.t_hits = TA.t_hits; AA.ids = ids; AA.plane = plane; AA.hitw = hitw;
+    AA.headmark = headmark; AA.tcount = tcount; AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail);
+    AA.clus_offset = out->clus_offset; AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
+    AA.frame = out->frame;
+    k_track_count<<<gt2, B, 0, st>>>(AA);
+    g_launches++;
+    scan_u32(tcount, ntcap, aux, st);
+    k_track_fill<<<gt2, B, 0, st>>>(AA);
+    g_launches++;
+    CK(mark(8));
+    // a9: refit
+    int rr = tpc_launch_refit(p, g, bz, cl, zlin, rowtab, f, AA.ttail, TA.t_top, out,
+                              std::min(out->capacity_tracks, ntcap), st);
+    if (rr) return rr;
+    g_launches++;
+    CK(mark(9));
+    // optional intermediate outputs
+    if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
+        k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
+                                         out->link_dn, out->is_start, f);
+        g_launches++;
+    }
+    if (dev_counts) {
+        k_publish<<<1, 32, 0, st>>>(f, ntcap, dev_counts);
+        g_launches++;
+    }
+    CK(cudaGetLastError());
+    return TPC_OK;
+}
+
+// tables and offsets a call reads from the workspace (pageable uploads)
+int upload(const tpc_geometry* g, const Layout& L, const int32_t* offsets, void* ws, cudaStream_t st)
+{
+    static_assert(sizeof(Layout) <= 512, "layout header");
+    float tab[ROWTAB * 256];
+    fill_rowtab(tab, g, L.ny);
+    CK(cudaMemcpyAsync(at<float>(ws, L.rowtab), tab, sizeof(tab), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(at<int32_t>(ws, L.offsets), offsets, sizeof(int32_t) * (L.nframes + 1),
+                       cudaMemcpyHostToDevice, st));
+    // a copy of the layout at the workspace base lets later calls find the arrays
+    CK(cudaMemcpyAsync(at<char>(ws, L.hdr), &L, sizeof(Layout), cudaMemcpyHostToDevice, st));
+    return TPC_OK;
+}
+
+int run_sync(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
+             int32_t nframes, const int32_t* offsets, void* ws, size_t ws_bytes, tpc_tracks* out, void* stream)
+{
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    if (!cl || !out || !ws || cl->n < 0) return TPC_ERR_ARG;
+    const int n = cl->n;
+    if (n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->zt)) return TPC_ERR_ARG;
+    if ((rc = out_args(p, out))) return rc;
+    if ((rc = check_frames(n, nframes, offsets))) return rc;
+    const Layout L = make_layout(p, g, n, nframes);
+    if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    out->n_tracks = out->n_tracklets = out->n_segments = 0;
+    out->tracklets_needed = out->tracks_needed = out->clusters_needed = 0;
+    out->n_launches = 0;
+    for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
+    for (int k = 0; k < 5; k++) out->work[k] = 0;
+    if (n == 0) {
+        CK(cudaMemsetAsync(out->clus_offset, 0, sizeof(int32_t), st));
+        CK(cudaStreamSynchronize(st));
+        return TPC_OK;
+    }
+    const bool prof = p->profile != 0;
+    if (prof) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (g_events.device != dev) {
+            for (int k = 0; k <= TPC_N_STAGES; k++) CK(cudaEventCreate(&g_events.ev[k]));
+            g_events.device = dev;
+        }
+    }
+    if ((rc = upload(g, L, offsets, ws, st))) return rc;
+    if ((rc = enqueue(p, g, bz, v_drift, cl, ws, L, out, nullptr, st, prof))) return rc;
+    Frame hf;
+    CK(cudaMemcpyAsync(&hf, at<Frame>(ws, L.frame), sizeof(Frame), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int ntcap = L.ntcap;
+    out->n_launches = g_launches;
+    out->work[0] = (int64_t)hf.w_prop;
+    out->work[1] = (int64_t)hf.w_upd;
+    out->work[2] = (int64_t)hf.w_cand;
+    out->work[3] = (int64_t)hf.w_refit_prop;
+    out->work[4] = (int64_t)hf.w_merge;
+    if (prof)
+        for (int k = 0; k < 9; k++) CK(cudaEventElapsedTime(&out->stage_ms[k], g_events.ev[k], g_events.ev[k + 1]));
+    out->n_tracklets = std::min(hf.n_starts, ntcap);
+    out->n_segments = hf.n_seg;
+    out->n_tracks = hf.n_tracks;
+    if (hf.err == TPC_ERR_DATA) return TPC_ERR_DATA;
+    if (hf.n_starts > ntcap) {
+        out->tracklets_needed = hf.n_starts;
+        return TPC_ERR_CAPACITY;
+    }
+    if (hf.err == TPC_ERR_CAPACITY) {
+        out->tracks_needed = hf.n_tracks;
+        out->clusters_needed = hf.n_clus;
+        return TPC_ERR_CAPACITY;
+    }
+    return TPC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1176,245 +1550,68 @@ int tpc_params_default(tpc_params* p)
     p->max_z_cells = 1024;
     p->tracklets_per_1k = 125;
     p->fp64_final = 0;
+    p->profile = 0;
     return TPC_OK;
 }
 
-static int check_args(const tpc_params* p, const tpc_geometry* g)
+int tpc_workspace_size_batched(const tpc_params* p, const tpc_geometry* g, int64_t n, int32_t n_frames, size_t* bytes)
 {
-    if (!p || !g || !g->row_x) return TPC_ERR_ARG;
-    if (!(g->n_sectors == 36 || g->n_sectors == 1)) return TPC_ERR_ARG;
-    if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
-    if (g->n_sectors * g->n_rows > 65535) return TPC_ERR_ARG;
-    if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
-    if (!(p->refit_inflate >= 1.0f)) return TPC_ERR_ARG;
-    if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
-    for (int r = 0; r + 1 < g->n_rows; r++)
-        if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
+    if (!bytes || n < 0 || n > (int64_t)INT32_MAX / 2 || n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    const Layout L = make_layout(p, g, n, n_frames);
+    if (L.ncells >= (int64_t)UINT32_MAX) return TPC_ERR_ARG;
+    *bytes = L.total;
     return TPC_OK;
 }
 
 int tpc_workspace_size(const tpc_params* p, const tpc_geometry* g, int64_t n, size_t* bytes)
 {
-    if (!bytes || n < 0 || n > (int64_t)INT32_MAX / 2) return TPC_ERR_ARG;
-    int rc = check_args(p, g);
-    if (rc) return rc;
-    *bytes = make_layout(p, g, n).total;
-    return TPC_OK;
+    return tpc_workspace_size_batched(p, g, n, 1, bytes);
 }
 
 int tpc_track(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
               void* ws, size_t ws_bytes, tpc_tracks* out, void* stream)
 {
+    if (!cl) return TPC_ERR_ARG;
+    const int32_t off[2] = {0, cl->n};
+    return run_sync(p, g, bz, v_drift, cl, 1, off, ws, ws_bytes, out, stream);
+}
+
+int tpc_track_batched(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
+                      int32_t n_frames, const int32_t* frame_offsets, void* ws, size_t ws_bytes, tpc_tracks* out,
+                      void* stream)
+{
+    return run_sync(p, g, bz, v_drift, cl, n_frames, frame_offsets, ws, ws_bytes, out, stream);
+}
+
+int tpc_prepare(const tpc_params* p, const tpc_geometry* g, int32_t n_clusters, int32_t n_frames,
+                const int32_t* frame_offsets, void* ws, size_t ws_bytes, void* stream)
+{
     int rc = check_args(p, g);
     if (rc) return rc;
-    if (!cl || !out || !ws || cl->n < 0) return TPC_ERR_ARG;
-    const int n = cl->n;
-    if (n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->zt)) return TPC_ERR_ARG;
-    if (!out->sector || !out->x || !out->param || !out->cov || !out->chi2 || !out->ndf || !out->status ||
-        !out->nclus || !out->clus_offset || !out->clus_index || !out->assign)
-        return TPC_ERR_ARG;
-    if (out->capacity_tracks < 0 || out->capacity_clusters < 0) return TPC_ERR_ARG;
-    if (p->fp64_final && (!out->cov64 || !out->chi2_64)) return TPC_ERR_ARG;
-    const Layout L = make_layout(p, g, n);
+    if (!ws || n_clusters < 1) return TPC_ERR_ARG;
+    if ((rc = check_frames(n_clusters, n_frames, frame_offsets))) return rc;
+    const Layout L = make_layout(p, g, n_clusters, n_frames);
     if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
     cudaStream_t st = (cudaStream_t)stream;
-    out->n_tracks = out->n_tracklets = out->n_segments = 0;
-    out->tracklets_needed = out->tracks_needed = out->clusters_needed = 0;
-
-    Frame* f = at<Frame>(ws, L.frame);
-    float* rowtab = at<float>(ws, L.rowtab);
-    float* zlin = at<float>(ws, L.zlin);
-    uint32_t* cell = at<uint32_t>(ws, L.cell);
-    uint32_t* slot = at<uint32_t>(ws, L.slot);
-    uint32_t* cstart = at<uint32_t>(ws, L.cstart);
-    uint32_t* aux = at<uint32_t>(ws, L.scan);
-    float2* yz = at<float2>(ws, L.yz);
-    int32_t* ids = at<int32_t>(ws, L.ids);
-    uint16_t* plane = at<uint16_t>(ws, L.plane);
-    int32_t* upr = at<int32_t>(ws, L.upr);
-    int32_t* dnr = at<int32_t>(ws, L.dnr);
-    int32_t* up = at<int32_t>(ws, L.up);
-    int32_t* dn = at<int32_t>(ws, L.dn);
-    int32_t* starts = at<int32_t>(ws, L.starts);
-    unsigned long long* hitw = at<unsigned long long>(ws, L.hitw);
-
-    if (n == 0) {
-        CK(cudaMemsetAsync(out->clus_offset, 0, sizeof(int32_t), st));
-        CK(cudaStreamSynchronize(st));
-        out->n_launches = 0;
-        for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
-        for (int k = 0; k < 5; k++) out->work[k] = 0;
-        return TPC_OK;
-    }
-
-    // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r], (X[r]-X[r-1])/(X[r+1]-X[r-1])
-    float tab[ROWTAB * 256];
-    fill_rowtab(tab, g, L.ny);
-    CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
-    // a copy of the layout at the workspace base lets tpc_export_tracklets find the arrays
-    static_assert(sizeof(Layout) <= 512, "layout header");
-    CK(cudaMemcpyAsync(at<char>(ws, L.hdr), &L, sizeof(Layout), cudaMemcpyHostToDevice, st));
-
-    volatile float vyv = p->sigma_y * p->sigma_y;
-    volatile float vzv = p->sigma_z * p->sigma_z;
-    volatile float kbv = KB_C * bz;
-    const float vy = vyv, vz = vzv, kb = kbv;
-    const int B = 256;
-    const int gN = grid_for(n, B);
-    const int ntcap = L.ntcap;
-
-    // stage events (params.profile): created once per device, recorded on the caller's stream
-    const bool prof = p->profile != 0;
-    if (prof) {
-        int dev = 0;
-        CK(cudaGetDevice(&dev));
-        if (g_events.device != dev) {
-            for (int k = 0; k <= TPC_N_STAGES; k++) CK(cudaEventCreate(&g_events.ev[k]));
-            g_events.device = dev;
-        }
-    }
-    auto mark = [&](int k) -> cudaError_t { return prof ? cudaEventRecord(g_events.ev[k], st) : cudaSuccess; };
-    g_launches = 0;
-
-    CK(mark(0));
-    k_init_frame<<<1, 32, 0, st>>>(f);
-    k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
-                             g->z_max, v_drift, zlin, f);
-    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, L.nzmax, p->merge_dz * 1.1f + 0.5f, L.mnzmax, L.ny);
-    g_launches += 3;
-    CK(mark(1));
-    // a2: counting sort of the clusters into (sector, row, z-cell) order
-    CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(L.ncells + 1), st));
-    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, rowtab, g->n_rows, g->n_sectors, f, cstart, cell,
-                             slot);
-    g_launches++;
-    scan_u32(cstart, L.ncells, aux, st);
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, yz, ids,
-                                plane, f);
-    g_launches++;
-    CK(mark(2));
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, yz, ids, plane, cstart, f, p->dy_link,
-                                   p->dz_link, p->s_max_link, upr, dnr);
-    g_launches++;
-    CK(mark(3));
-    k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
-    k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
-    g_launches += 2;
-    CK(mark(4));
-    // a6: tracklets
-    TrkArgs TA;
-    TA.rowtab = rowtab; TA.yz = yz; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
-    TA.starts = starts; TA.f = f; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.cap = ntcap;
-    TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
-    TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
-    TA.edge = p->edge_margin; TA.max_miss = p->max_miss; TA.prof = prof ? 1 : 0; TA.fw = f;
-    TA.t_start = at<int32_t>(ws, L.t_start); TA.t_id = at<int32_t>(ws, L.t_id);
-    TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
-    TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
-    const int gT = grid_for(ntcap, 128);
-    k_tracklets<<<gT, TRK_BLOCK, 0, st>>>(TA);
-    g_launches++;
-    CK(mark(5));
-    // a7: selector
-    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)n, st));
-    const int gt2 = grid_for(ntcap, B);
-    uint8_t* kept = at<uint8_t>(ws, L.t_kept);
-    int32_t* seg = at<int32_t>(ws, L.seg);
-    k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
-    k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
-                                 TA.t_hits, hitw, kept, seg);
-    g_launches += 2;
-    CK(mark(6));
-    // a8: merger
-    const int64_t mcells = (int64_t)g->n_sectors * L.mnzmax;
-    uint32_t* cntb = at<uint32_t>(ws, L.cntb);
-    uint32_t* cntt = at<uint32_t>(ws, L.cntt);
-    CK(cudaMemsetAsync(cntb, 0, 4 * (size_t)(mcells + 1), st));
-    CK(cudaMemsetAsync(cntt, 0, 4 * (size_t)(mcells + 1), st));
-    CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, st));
-    CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
-    uint32_t* headmark = at<uint32_t>(ws, L.headmark);
-    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), st));
-    k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, seg, plane, TA.t_start, g->n_rows, TA.t_top, TA.t_bot, cntb, cntt,
-                                  at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt), at<uint32_t>(ws, L.slotb),
-                                  at<uint32_t>(ws, L.slott));
-    g_launches++;
-    scan_u32(cntb, mcells, aux, st);
-    scan_u32(cntt, mcells, aux, st);
-    MergeArgs M;
-    M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
-    M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
-    M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
-    M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
-    k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
-                                     at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
-                                     at<int32_t>(ws, L.byt));
-    k_merge_next<<<gT, 128, 0, st>>>(M);
-    k_merge_prev<<<gT, 128, 0, st>>>(M);
-    k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
-    k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
-    k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
-                                   at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
-    g_launches += 6;
-    scan_u32(headmark, n, aux, st);
-    CK(mark(7));
-    // merged cluster lists and assignments
-    uint32_t* tcount = at<uint32_t>(ws, L.tcount);
-    CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), st));
-    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)n, st));
-    AsmArgs AA;
-    AA.f = f; AA.nr = g->n_rows; AA.n = n; AA.cap_tracks = out->capacity_tracks;
-    AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
-    AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits; AA.t_nup = TA.t_nup;
-    AA.t_hits = TA.t_hits; AA.ids = ids; AA.hitw = hitw; AA.headmark = headmark; AA.tcount = tcount;
-    AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail); AA.clus_offset = out->clus_offset;
-    AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
-    k_track_count<<<gt2, B, 0, st>>>(AA);
-    g_launches++;
-    scan_u32(tcount, ntcap, aux, st);
-    k_track_fill<<<gt2, B, 0, st>>>(AA);
-    g_launches++;
-    CK(mark(8));
-    // a9: refit
-    int rr = tpc_launch_refit(p, g, bz, cl, zlin, rowtab, f, AA.ttail, TA.t_top, out,
-                              std::min(out->capacity_tracks, ntcap), st);
-    if (rr) return rr;
-    g_launches++;
-    CK(mark(9));
-    // optional intermediate outputs
-    if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
-        k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
-                                         out->link_dn, out->is_start, f);
-        g_launches++;
-    }
-    CK(cudaGetLastError());
-    Frame hf;
-    CK(cudaMemcpyAsync(&hf, f, sizeof(Frame), cudaMemcpyDeviceToHost, st));
+    if ((rc = upload(g, L, frame_offsets, ws, st))) return rc;
     CK(cudaStreamSynchronize(st));
-    out->n_launches = g_launches;
-    out->work[0] = (int64_t)hf.w_prop;
-    out->work[1] = (int64_t)hf.w_upd;
-    out->work[2] = (int64_t)hf.w_cand;
-    out->work[3] = (int64_t)hf.w_refit_prop;
-    out->work[4] = (int64_t)hf.w_merge;
-    for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
-    if (prof)
-        for (int k = 0; k < 9; k++) CK(cudaEventElapsedTime(&out->stage_ms[k], g_events.ev[k], g_events.ev[k + 1]));
-    out->n_tracklets = std::min(hf.n_starts, ntcap);
-    out->n_segments = hf.n_seg;
-    out->n_tracks = hf.n_tracks;
-    if (hf.err == TPC_ERR_DATA) return TPC_ERR_DATA;
-    if (hf.n_starts > ntcap) {
-        out->tracklets_needed = hf.n_starts;
-        return TPC_ERR_CAPACITY;
-    }
-    if (hf.err == TPC_ERR_CAPACITY) {
-        out->tracks_needed = hf.n_tracks;
-        out->clusters_needed = hf.n_clus;
-        return TPC_ERR_CAPACITY;
-    }
     return TPC_OK;
+}
+
+int tpc_track_async(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
+                    int32_t n_frames, void* ws, size_t ws_bytes, tpc_tracks* out, int32_t* dev_counts, void* stream)
+{
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    if (!cl || !out || !ws || !dev_counts || cl->n < 1) return TPC_ERR_ARG;
+    if (!cl->sector || !cl->row || !cl->y || !cl->zt) return TPC_ERR_ARG;
+    if ((rc = out_args(p, out))) return rc;
+    if (n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
+    const Layout L = make_layout(p, g, cl->n, n_frames);
+    if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
+    return enqueue(p, g, bz, v_drift, cl, ws, L, out, dev_counts, (cudaStream_t)stream, false);
 }
 
 int tpc_export_tracklets(const void* ws, int32_t capacity, int32_t hits_stride, int32_t* start, int32_t* nhits,
@@ -1486,15 +1683,18 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Frame* f = at<Frame>(base, SL.frame);
+    FrameGrid* fg = at<FrameGrid>(base, SL.fgrid);
+    int32_t* offsets = at<int32_t>(base, SL.offsets);
     float* rowtab = at<float>(base, SL.rowtab);
     float* zlin = at<float>(base, SL.zlin);
+    uint16_t* cfr = at<uint16_t>(base, SL.cfr);
     uint32_t* cell = at<uint32_t>(base, SL.cell);
     uint32_t* slot = at<uint32_t>(base, SL.slot);
     uint32_t* cstart = at<uint32_t>(base, SL.cstart);
     uint32_t* aux = at<uint32_t>(base, SL.scan);
     float2* yz = at<float2>(base, SL.yz);
     int32_t* ids = at<int32_t>(base, SL.ids);
-    uint16_t* plane = at<uint16_t>(base, SL.plane);
+    uint32_t* plane = at<uint32_t>(base, SL.plane);
     int32_t* upr = at<int32_t>(base, SL.upr);
     int32_t* dnr = at<int32_t>(base, SL.dnr);
     int32_t* up = at<int32_t>(base, SL.up);
@@ -1502,21 +1702,25 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     float tab[ROWTAB * 256];
     fill_rowtab(tab, g, 1);   // one y-bin per z-cell: a smaller fixed array
     CK(cudaMemcpyAsync(rowtab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
-    const int64_t ncells = (int64_t)g->n_sectors * g->n_rows * STATIC_NZ;
+    const int32_t off[2] = {0, n};
+    CK(cudaMemcpyAsync(offsets, off, sizeof(off), cudaMemcpyHostToDevice, st));
+    const int np = g->n_sectors * g->n_rows;
+    const int64_t ncells = (int64_t)np * STATIC_NZ;
     const int B = 256;
     const int gN = grid_for(n, B);
-    k_init_frame<<<1, 32, 0, st>>>(f);
-    k_prep<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous,
-                             g->z_max, v_drift, zlin, f);
-    k_grid_setup<<<1, 32, 0, st>>>(f, p->z_cell, STATIC_NZ, p->merge_dz * 1.1f + 0.5f, MAX_MERGE_CELLS, 1);
+    k_init_frame<<<1, 32, 0, st>>>(f, fg, 1);
+    k_prep<<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
+                                      g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
+    k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, p->merge_dz * 1.1f + 0.5f,
+                                   MAX_MERGE_CELLS);
     // the histogram must start at zero: the scratch keeps the previous call's contents
-    CK(cudaMemsetAsync(cstart, 0, 4 * (size_t)(ncells + 1), st));
-    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, rowtab, g->n_rows, g->n_sectors, f, cstart, cell,
-                             slot);
-    scan_u32(cstart, ncells, aux, st);
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, g->n_rows, cstart, cell, slot, yz, ids,
+    k_zero_cells<<<grid_for(ncells + 1, B), B, 0, st>>>(cstart, f);
+    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, rowtab, g->n_rows, g->n_sectors, f, fg, cstart,
+                             cell, slot);
+    scan_u32(cstart, ncells, aux, st, &f->total_cells);
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, np, cstart, cell, slot, yz, ids,
                                 plane, f);
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, rowtab, yz, ids, plane, cstart, f, p->dy_link,
+    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, np, rowtab, yz, ids, plane, cstart, f, fg, p->dy_link,
                                    p->dz_link, p->s_max_link, upr, dnr);
     k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
     k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);

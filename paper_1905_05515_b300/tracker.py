@@ -50,7 +50,7 @@ class Tracker:
 
     def __init__(self, n_max: int, row_x, n_sectors: int = 36, z_max: float = 250.0, continuous: bool = False,
                  params: abi.TpcParams | None = None, device="cuda", capacity_tracks: int | None = None,
-                 debug: bool = False):
+                 debug: bool = False, n_frames: int = 1):
         if not torch.cuda.is_available():
             raise RuntimeError("the TPC tracker needs a CUDA device")
         self.lib = abi.lib()
@@ -58,7 +58,8 @@ class Tracker:
         self.geometry = abi.make_geometry(row_x, n_sectors, z_max, continuous)
         self.n_max = int(n_max)
         self.device = torch.device(device)
-        self.ws_bytes = abi.tpc_workspace_size(self.params, self.geometry, self.n_max)
+        self.n_frames = int(n_frames)
+        self.ws_bytes = abi.tpc_workspace_size(self.params, self.geometry, self.n_max, self.n_frames)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         cap_t = capacity_tracks if capacity_tracks is not None else max(1024, self.n_max // 16)
         cap_c = max(1, self.n_max)
@@ -76,6 +77,7 @@ class Tracker:
             clus_offset=torch.empty(cap_t + 1, dtype=torch.int32, device=d),
             clus_index=torch.empty(cap_c, dtype=torch.int32, device=d),
             assign=torch.empty(n1, dtype=torch.int32, device=d),
+            frame=torch.empty(cap_t, dtype=torch.int32, device=d),
         )
         if self.params.fp64_final:
             self.buf["cov64"] = torch.empty(cap_t, 15, dtype=torch.float64, device=d)
@@ -95,39 +97,32 @@ class Tracker:
         t.capacity_tracks = self.capacity_tracks
         t.capacity_clusters = self.capacity_clusters
         for k in ("sector", "x", "param", "cov", "chi2", "ndf", "status", "nclus", "clus_offset", "clus_index",
-                  "assign", "cov64", "chi2_64", "z", "link_up_raw", "link_dn_raw", "link_up", "link_dn", "is_start"):
+                  "assign", "frame", "cov64", "chi2_64", "z", "link_up_raw", "link_dn_raw", "link_up", "link_dn",
+                  "is_start"):
             setattr(t, k, b[k].data_ptr() if k in b else None)
         return t
 
-    def track(self, sector: torch.Tensor, row: torch.Tensor, y: torch.Tensor, zt: torch.Tensor, bz: float = 0.5,
-              v_drift: float = 2.58, stream: torch.cuda.Stream | None = None) -> TrackResult:
+    def _check_inputs(self, sector, row, y, zt):
         n = int(y.shape[0])
         if n > self.n_max:
             raise ValueError(f"{n} clusters > tracker capacity {self.n_max}")
         for a, dt in ((sector, torch.uint8), (row, torch.uint8), (y, torch.float32), (zt, torch.float32)):
             if a.dtype != dt or not a.is_cuda or not a.is_contiguous() or a.shape[0] != n:
                 raise ValueError("clusters must be contiguous CUDA tensors: sector/row uint8, y/zt float32")
-        cl = abi.TpcClusters(n, sector.data_ptr(), row.data_ptr(), y.data_ptr(), zt.data_ptr())
-        out = self._tracks_struct()
-        st = stream if stream is not None else torch.cuda.current_stream(self.device)
-        rc = self.lib.tpc_track(C.byref(self.params), C.byref(self.geometry), float(bz), float(v_drift),
-                                C.byref(cl), C.c_void_p(self.workspace.data_ptr()), self.ws_bytes, C.byref(out),
-                                C.c_void_p(st.cuda_stream))
-        if rc:
-            err = abi.TpcError(rc, "tpc_track")
-            err.needed = dict(tracklets=out.tracklets_needed, tracks=out.tracks_needed,
-                              clusters=out.clusters_needed)
-            raise err
-        T = out.n_tracks
+        return n
+
+    def _result(self, out, n, T) -> TrackResult:
         b = self.buf
         res = TrackResult(n_tracks=T, sector=b["sector"][:T], x=b["x"][:T], param=b["param"][:T],
                           cov=b["cov"][:T], chi2=b["chi2"][:T], ndf=b["ndf"][:T], status=b["status"][:T],
                           nclus=b["nclus"][:T], clus_offset=b["clus_offset"][:T + 1],
-                          clus_index=b["clus_index"], assign=b["assign"][:n],
-                          n_tracklets=out.n_tracklets, n_segments=out.n_segments, n_launches=out.n_launches,
-                          stage_ms={k: float(out.stage_ms[i]) for i, k in enumerate(abi.STAGES)},
-                          work=dict(zip(("trk_prop", "trk_upd", "trk_cand", "refit_prop", "merge_chi2"),
-                                        (int(v) for v in out.work))))
+                          clus_index=b["clus_index"], assign=b["assign"][:n])
+        res.frame = b["frame"][:T]
+        if out is not None:
+            res.n_tracklets, res.n_segments, res.n_launches = out.n_tracklets, out.n_segments, out.n_launches
+            res.stage_ms = {k: float(out.stage_ms[i]) for i, k in enumerate(abi.STAGES)}
+            res.work = dict(zip(("trk_prop", "trk_upd", "trk_cand", "refit_prop", "merge_chi2"),
+                                (int(v) for v in out.work)))
         if "cov64" in b:
             res.cov64, res.chi2_64 = b["cov64"][:T], b["chi2_64"][:T]
         if self.debug:
@@ -136,6 +131,79 @@ class Tracker:
             res.link_up, res.link_dn = b["link_up"][:n], b["link_dn"][:n]
             res.is_start = b["is_start"][:n]
         return res
+
+    @staticmethod
+    def _raise(rc, out, what):
+        err = abi.TpcError(rc, what)
+        err.needed = dict(tracklets=out.tracklets_needed, tracks=out.tracks_needed, clusters=out.clusters_needed)
+        raise err
+
+    def track(self, sector: torch.Tensor, row: torch.Tensor, y: torch.Tensor, zt: torch.Tensor, bz: float = 0.5,
+              v_drift: float = 2.58, stream: torch.cuda.Stream | None = None) -> TrackResult:
+        """One event or time frame (tpc_track)."""
+        n = self._check_inputs(sector, row, y, zt)
+        cl = abi.TpcClusters(n, sector.data_ptr(), row.data_ptr(), y.data_ptr(), zt.data_ptr())
+        out = self._tracks_struct()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rc = self.lib.tpc_track(C.byref(self.params), C.byref(self.geometry), float(bz), float(v_drift),
+                                C.byref(cl), C.c_void_p(self.workspace.data_ptr()), self.ws_bytes, C.byref(out),
+                                C.c_void_p(st.cuda_stream))
+        if rc:
+            self._raise(rc, out, "tpc_track")
+        return self._result(out, n, out.n_tracks)
+
+    def track_batched(self, sector, row, y, zt, frame_offsets, bz: float = 0.5, v_drift: float = 2.58,
+                      stream: torch.cuda.Stream | None = None) -> TrackResult:
+        """Several independent time frames in one pass (tpc_track_batched);
+        frame_offsets: n_frames + 1 cluster offsets (host)."""
+        n = self._check_inputs(sector, row, y, zt)
+        off = np.ascontiguousarray(frame_offsets, np.int32)
+        nf = off.shape[0] - 1
+        if nf > self.n_frames:
+            raise ValueError(f"{nf} frames > tracker capacity {self.n_frames}")
+        cl = abi.TpcClusters(n, sector.data_ptr(), row.data_ptr(), y.data_ptr(), zt.data_ptr())
+        out = self._tracks_struct()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ws_bytes = abi.tpc_workspace_size(self.params, self.geometry, n, nf)
+        rc = self.lib.tpc_track_batched(C.byref(self.params), C.byref(self.geometry), float(bz), float(v_drift),
+                                        C.byref(cl), nf, off.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        C.c_void_p(self.workspace.data_ptr()), ws_bytes, C.byref(out),
+                                        C.c_void_p(st.cuda_stream))
+        if rc:
+            self._raise(rc, out, "tpc_track_batched")
+        return self._result(out, n, out.n_tracks)
+
+    def capture(self, sector, row, y, zt, frame_offsets=None, bz: float = 0.5, v_drift: float = 2.58):
+        """Record the whole chain for these (fixed) input buffers as a CUDA
+        graph (tpc_prepare + tpc_track_async).  Returns a GraphRun whose
+        replay() re-runs it; results appear in this tracker's buffers."""
+        n = self._check_inputs(sector, row, y, zt)
+        off = np.ascontiguousarray(frame_offsets if frame_offsets is not None else [0, n], np.int32)
+        nf = off.shape[0] - 1
+        ws_bytes = abi.tpc_workspace_size(self.params, self.geometry, n, nf)
+        st = torch.cuda.Stream(self.device)
+        rc = self.lib.tpc_prepare(C.byref(self.params), C.byref(self.geometry), n, nf,
+                                  off.ctypes.data_as(C.POINTER(C.c_int32)), C.c_void_p(self.workspace.data_ptr()),
+                                  ws_bytes, C.c_void_p(st.cuda_stream))
+        if rc:
+            raise abi.TpcError(rc, "tpc_prepare")
+        counts = torch.zeros(8, dtype=torch.int32, device=self.device)
+        cl = abi.TpcClusters(n, sector.data_ptr(), row.data_ptr(), y.data_ptr(), zt.data_ptr())
+        out = self._tracks_struct()
+        args = (C.byref(self.params), C.byref(self.geometry), float(bz), float(v_drift), C.byref(cl), nf,
+                C.c_void_p(self.workspace.data_ptr()), ws_bytes, C.byref(out), C.c_void_p(counts.data_ptr()))
+        # one eager run on the capture stream, then the capture
+        with torch.cuda.stream(st):
+            rc = self.lib.tpc_track_async(*args, C.c_void_p(st.cuda_stream))
+            if rc:
+                raise abi.TpcError(rc, "tpc_track_async")
+        st.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=st):
+            rc = self.lib.tpc_track_async(*args, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        if rc:
+            raise abi.TpcError(rc, "tpc_track_async (capture)")
+        return GraphRun(self, graph, counts, n, (cl, out))
 
     def export_tracklets(self, stream: torch.cuda.Stream | None = None):
         """Tracklets of the last call (host numpy arrays, ascending start index)."""
@@ -160,6 +228,25 @@ class Tracker:
             raise abi.TpcError(rc, "tpc_export_tracklets")
         k = int(nt.value)
         return dict(start=start[:k], nhits=nhits[:k], kept=kept[:k], hits=hits[:k], top=top[:k], bot=bot[:k])
+
+
+class GraphRun:
+    """A captured tracking chain; replay() enqueues it on the current stream."""
+
+    def __init__(self, tracker: Tracker, graph, counts: torch.Tensor, n: int, keep):
+        self.tracker, self.graph, self.counts, self.n, self._keep = tracker, graph, counts, n, keep
+
+    def replay(self):
+        self.graph.replay()
+
+    def result(self) -> TrackResult:
+        """Synchronise and wrap the buffers (n_tracks read from the device counts)."""
+        c = self.counts.cpu().tolist()
+        if c[3]:
+            raise abi.TpcError(c[3], "captured tpc_track_async")
+        res = self.tracker._result(None, self.n, int(c[0]))
+        res.n_tracklets, res.n_segments = int(c[1]), int(c[2])
+        return res
 
 
 def tpc_track(sector, row, y, zt, row_x, n_sectors=36, z_max=250.0, continuous=False, bz=0.5, v_drift=2.58,
