@@ -94,64 +94,64 @@ class Event:
         return self.sector, self.row, self.y, self.zt, self.charge
 
 
-def _crossings(pt, phi0, eta, q, bz, alphas, wedge_sel, row_x64, loopers):
-    """All accepted plane crossings of a set of helices from the origin.
+_helix = None
 
-    Returns (track, wedge, row, y_local, z, snp_local, s) arrays.
-    The helix: direction phi(s) = phi0 + h s / R with h = -q sign(B),
-    position X = h R (sin phi - sin phi0), Y = -h R (cos phi - cos phi0),
-    z = s tan(lambda).  The plane of wedge a at x_local = X_r gives
-    sin(phi - alpha) = sin(phi0 - alpha) + h X_r / R.
+
+def _helix_lib():
+    """The compiled crossing routine (tpcgen/helix.c), built on first use."""
+    global _helix
+    if _helix is None:
+        import ctypes as C
+
+        from . import build as _b
+        L = C.CDLL(_b.build())
+        PD = C.POINTER(C.c_double)
+        P32 = C.POINTER(C.c_int32)
+        L.helix_crossings.restype = C.c_int64
+        L.helix_crossings.argtypes = [C.c_int64, PD, PD, PD, PD, PD, C.POINTER(C.c_uint8), C.c_int, PD, C.c_int, PD,
+                                      C.c_double, C.c_int, C.POINTER(C.c_int64), P32, P32, P32, PD, PD, PD, PD]
+        _helix = L
+    return _helix
+
+
+def _crossings(pt, phi0, eta, q, looper, bz, alphas, row_x64):
+    """All accepted plane crossings of helices from the origin.
+
+    Returns (track, wedge, row, y_local, z, snp_local, s).  The helix:
+    direction phi(s) = phi0 + h s / R with h = -q sign(B), z = s tan(lambda);
+    the plane of wedge a at x_local = X_r is crossed where
+    sin(phi - alpha) = sin(phi0 - alpha) + h X_r / R.  A track ends at
+    |z| > Z_MAX, at radius RHO_OUT, or after MAX_TURNS turns (loopers).
     """
+    import ctypes as C
+    L = _helix_lib()
     n = pt.shape[0]
-    R = pt / (C_LIGHT * abs(bz))
-    h = -q * np.sign(bz)
-    tgl = np.sinh(eta)
-    two_pi_r = 2.0 * np.pi * R
+    R = np.ascontiguousarray(pt / (C_LIGHT * abs(bz)))
+    h = np.ascontiguousarray(-q * np.sign(bz))
+    tgl = np.ascontiguousarray(np.sinh(eta))
     s_exit = np.where(2 * R > RHO_OUT, 2 * R * np.arcsin(np.minimum(RHO_OUT / (2 * R), 1.0)), np.inf)
     with np.errstate(divide="ignore"):
         s_z = np.where(np.abs(tgl) > 0, Z_MAX / np.abs(tgl), np.inf)
-    s_max = np.minimum(np.minimum(s_exit, MAX_TURNS * two_pi_r), s_z)
+    s_max = np.ascontiguousarray(np.minimum(np.minimum(s_exit, MAX_TURNS * 2.0 * np.pi * R), s_z))
+    phi0 = np.ascontiguousarray(phi0, np.float64)
+    lp = np.ascontiguousarray(looper, np.uint8)
+    al = np.ascontiguousarray(alphas, np.float64)
+    X = np.ascontiguousarray(row_x64, np.float64)
     tan_half = math.tan(math.radians(SECTOR_DPHI_DEG / 2))
-    n_turns = MAX_TURNS if loopers else 1
-    out = {k: [] for k in ("t", "a", "r", "y", "z", "snp", "s")}
-    idx_all = np.arange(n)
-    for r, xr in enumerate(row_x64):
-        for a, alpha in enumerate(alphas):
-            sel = wedge_sel(r, a)
-            idx = idx_all[sel]
-            if idx.size == 0:
-                continue
-            Ri, hi, p0 = R[idx], h[idx], phi0[idx]
-            w = np.sin(p0 - alpha) + hi * xr / Ri
-            ok = np.abs(w) <= 1.0
-            if not ok.any():
-                continue
-            idx, Ri, hi, p0, w = idx[ok], Ri[ok], hi[ok], p0[ok], w[ok]
-            asw = np.arcsin(w)
-            for psi in (asw, np.pi - asw):
-                dphi = np.mod(hi * (alpha + psi - p0), 2 * np.pi)
-                yl = hi * Ri * (np.cos(p0 - alpha) - np.cos(psi))
-                for turn in range(n_turns):
-                    s = Ri * (dphi + 2 * np.pi * turn)
-                    acc = (s <= s_max[idx]) & (np.abs(yl) <= xr * tan_half)
-                    if not acc.any():
-                        if turn > 0:
-                            break
-                        continue
-                    ii = idx[acc]
-                    out["t"].append(ii)
-                    out["a"].append(np.full(ii.size, a, np.int32))
-                    out["r"].append(np.full(ii.size, r, np.int32))
-                    out["y"].append(yl[acc])
-                    out["z"].append(s[acc] * tgl[ii])
-                    # psi is the direction of motion in the local frame
-                    out["snp"].append(np.sin(psi[acc]))
-                    out["s"].append(s[acc])
-    if not out["t"]:
-        e = np.zeros(0)
-        return (np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), e, e, e, e)
-    return tuple(np.concatenate(out[k]) for k in ("t", "a", "r", "y", "z", "snp", "s"))
+    PD = C.POINTER(C.c_double)
+    P32 = C.POINTER(C.c_int32)
+    counts = np.zeros(max(n, 1), np.int64)
+    args = [n, R.ctypes.data_as(PD), h.ctypes.data_as(PD), phi0.ctypes.data_as(PD), tgl.ctypes.data_as(PD),
+            s_max.ctypes.data_as(PD), lp.ctypes.data_as(C.POINTER(C.c_uint8)), al.size, al.ctypes.data_as(PD),
+            X.size, X.ctypes.data_as(PD), tan_half, MAX_TURNS, counts.ctypes.data_as(C.POINTER(C.c_int64))]
+    tot = L.helix_crossings(*args, None, None, None, None, None, None, None)
+    trk = np.empty(tot, np.int32)
+    wedge = np.empty(tot, np.int32)
+    row = np.empty(tot, np.int32)
+    y, z, snp, sp = (np.empty(tot) for _ in range(4))
+    L.helix_crossings(*args, trk.ctypes.data_as(P32), wedge.ctypes.data_as(P32), row.ctypes.data_as(P32),
+                      y.ctypes.data_as(PD), z.ctypes.data_as(PD), snp.ctypes.data_as(PD), sp.ctypes.data_as(PD))
+    return trk.astype(np.int64), wedge, row, y, z, snp, sp
 
 
 def _gen_tracks(rng, n, pt_lo, pt_hi, phi_lo, phi_hi):
@@ -200,31 +200,10 @@ def generate(n_sectors=36, n_tracks=None, n_collisions=0, mult_mean=2000.0,
     pt, phi0, eta, q = _gen_tracks(rng, n_prim, 0.2, 5.0, phi_lo, phi_hi)
     lpt, lphi0, leta, lq = _gen_tracks(rng, n_loop_total, 0.05, 0.2, phi_lo, phi_hi)
 
-    # primaries: only the wedges next to the track's azimuth at each radius
-    R = pt / (C_LIGHT * abs(bz))
-    h = -q * np.sign(bz)
-    if alphas.size == 1:
-        def sel_p(r, a):
-            return slice(None)
-    else:
-        wedge_at = []
-        for xr in row_x64:
-            ang = phi0 + h * np.arcsin(np.minimum(xr / (2 * R), 1.0))
-            wedge_at.append(np.floor(np.mod(ang, 2 * np.pi) / math.radians(SECTOR_DPHI_DEG)).astype(np.int64) % 18)
-
-        def sel_p(r, a):
-            d = (wedge_at[r] - a) % 18
-            return (d == 0) | (d == 1) | (d == 17)
-
-    cp = _crossings(pt, phi0, eta, q, bz, alphas, sel_p, row_x64, loopers=False)
-    cl = _crossings(lpt, lphi0, leta, lq, bz, alphas, lambda r, a: slice(None), row_x64, loopers=True)
-    t_idx = np.concatenate([cp[0], cl[0] + n_prim])
-    wedge = np.concatenate([cp[1], cl[1]])
-    row = np.concatenate([cp[2], cl[2]])
-    y_true = np.concatenate([cp[3], cl[3]])
-    z_true = np.concatenate([cp[4], cl[4]])
-    snp_true = np.concatenate([cp[5], cl[5]])
-    s_true = np.concatenate([cp[6], cl[6]])
+    cp = _crossings(np.concatenate([pt, lpt]), np.concatenate([phi0, lphi0]), np.concatenate([eta, leta]),
+                    np.concatenate([q, lq]), np.concatenate([np.zeros(n_prim, bool), np.ones(n_loop_total, bool)]),
+                    bz, alphas, row_x64)
+    t_idx, wedge, row, y_true, z_true, snp_true, s_true = cp
 
     trk_pt = np.concatenate([pt, lpt])
     trk_phi0 = np.concatenate([phi0, lphi0])
