@@ -81,6 +81,8 @@ typedef struct {
     int32_t y_bins;              /* grid y-bins per z-cell (reduced as needed to keep every bin
                                     wider than the y search windows) */
     int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
+    int32_t queue_blocks_per_sm; /* TrackletConstructor work-queue width: blocks per SM taking start
+                                    hits from the queue (0: as many as the capacity needs, up to 16) */
     int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
     int32_t profile;             /* 1: record CUDA events on the stream at stage boundaries (tpc_tracks.stage_ms) */
 } tpc_params;

@@ -29,7 +29,8 @@ class TpcParams(C.Structure):
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float), ("merge_dz", C.c_float),
                 ("merge_chi2", C.c_float), ("refit_passes", C.c_int32), ("refit_inflate", C.c_float),
                 ("z_cell", C.c_float),
-                ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32), ("fp64_final", C.c_int32),
+                ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32),
+                ("queue_blocks_per_sm", C.c_int32), ("fp64_final", C.c_int32),
                 ("profile", C.c_int32)]
 
 

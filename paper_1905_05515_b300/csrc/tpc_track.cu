@@ -1245,7 +1245,7 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (!(g->n_sectors == 36 || g->n_sectors == 1)) return TPC_ERR_ARG;
     if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
-    if (!(p->refit_inflate >= 1.0f)) return TPC_ERR_ARG;
+    if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0) return TPC_ERR_ARG;
     if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
@@ -1356,7 +1356,8 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     TA.t_nhits = at<int32_t>(ws, L.t_nhits); TA.t_nup = at<int32_t>(ws, L.t_nup);
     TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
     const int gT = grid_for(ntcap, TRK_BLOCK);
-    k_tracklets<<<gT, TRK_BLOCK, 0, st>>>(TA);
+    const int gQ = p->queue_blocks_per_sm > 0 ? std::min(gT, 148 * p->queue_blocks_per_sm) : gT;
+    k_tracklets<<<gQ, TRK_BLOCK, 0, st>>>(TA);
     g_launches++;
     CK(mark(5));
     // a7: selector
@@ -1549,6 +1550,7 @@ int tpc_params_default(tpc_params* p)
     p->y_bins = 8;
     p->max_z_cells = 1024;
     p->tracklets_per_1k = 125;
+    p->queue_blocks_per_sm = 0;
     p->fp64_final = 0;
     p->profile = 0;
     return TPC_OK;
