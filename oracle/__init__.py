@@ -68,6 +68,18 @@ def lib():
                                 _PD, _PD, _PD, C.c_int32, _PD, _PD]
         L.orc_merge_chi2.argtypes = [_PF, _PF, C.c_float, C.c_float, C.c_float]
         L.orc_merge_chi2.restype = C.c_float
+        L.orc_helix64.argtypes = [_PD, _PD, C.c_double, C.c_double, _PD]
+        L.orc_rotate64.argtypes = [_PD, _PD, C.c_double, C.c_double, C.c_double, _PD]
+        L.orc_calib.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcGeom), C.c_double, C.c_double, C.c_double,
+                                C.c_int32, _P32, _PF, _PF, _P32, _P32, _PU8, _PU8, _PF, _PF, _PF, _PD, _PD, _PD,
+                                _PU8, _PD]
+        L.orc_calib_measure.argtypes = [C.POINTER(OrcGeom), _PD, C.c_int32, _PU8, _PU8, _PF, _PF, _PF, _PD, _PD]
+        L.orc_calib_measure.restype = None
+        L.orc_calib_explain.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcGeom), C.c_double, C.c_double,
+                                        C.c_double, _P32, _PF, _PF, _P32, _P32, _PU8, _PU8, _PF, _PF, _PF, _PD,
+                                        C.c_int32, _PD, _PD, _PD, _PD, _PD]
+        L.orc_bspline_all.argtypes = [C.c_double, _PD, _PD]
+        L.orc_bspline_all.restype = None
         _lib = L
     return _lib
 
@@ -251,3 +263,138 @@ def merge_chi2(top, bot, cs, sn, kb):
     t = np.ascontiguousarray(top, np.float32)
     b = np.ascontiguousarray(bot, np.float32)
     return float(lib().orc_merge_chi2(_ptr(t, _PF), _ptr(b, _PF), cs, sn, kb))
+
+
+def helix64(x, p, x2, kb):
+    """FP64 helix step of a bare state with its Jacobian: (ok, x, p, F)."""
+    xx = np.array([x], np.float64)
+    pp = np.ascontiguousarray(p, np.float64).copy()
+    F = np.zeros((5, 5))
+    ok = lib().orc_helix64(_ptr(xx, _PD), _ptr(pp, _PD), x2, kb, _ptr(F, _PD))
+    return bool(ok), float(xx[0]), pp, F
+
+
+def rotate64(x, p, cs, sn, kb):
+    """FP64 frame rotation of a bare state with its Jacobian: (ok, x, p, J)."""
+    xx = np.array([x], np.float64)
+    pp = np.ascontiguousarray(p, np.float64).copy()
+    J = np.zeros((5, 5))
+    ok = lib().orc_rotate64(_ptr(xx, _PD), _ptr(pp, _PD), cs, sn, kb, _ptr(J, _PD))
+    return bool(ok), float(xx[0]), pp, J
+
+
+# ---- calibration chi2 and gradient ------------------------------------------------
+CALIB_NSPL = 8
+VERTEX_VAR = 0.01      # primary-vertex pseudo-measurement variance (cm^2)
+
+
+def calib_n_theta(n_sectors=36):
+    return 2 + n_sectors * CALIB_NSPL * CALIB_NSPL * 2
+
+
+@dataclasses.dataclass
+class CalibTracks:
+    """Tracks and clusters of a calibration problem (host arrays)."""
+    sector: np.ndarray       # [T] int32
+    x: np.ndarray            # [T] float32
+    param: np.ndarray        # [T, 5] float32 (tracker z frame)
+    off: np.ndarray          # [T+1] int32
+    clus: np.ndarray         # cluster indices, inner -> outer
+    tcoll: np.ndarray        # [T] float32, NaN = unused
+    cl_sector: np.ndarray    # [n] uint8
+    cl_row: np.ndarray       # [n] uint8
+    cl_y: np.ndarray         # [n] float32
+    cl_t: np.ndarray         # [n] float32 drift time (us)
+    row_x: np.ndarray        # float32
+    n_sectors: int = 36
+    z_max: float = 250.0
+    bz: float = 0.5
+    v_nom: float = 2.58
+
+    def __post_init__(self):
+        self.sector = np.ascontiguousarray(self.sector, np.int32)
+        self.x = np.ascontiguousarray(self.x, np.float32)
+        self.param = np.ascontiguousarray(self.param, np.float32)
+        self.off = np.ascontiguousarray(self.off, np.int32)
+        self.clus = np.ascontiguousarray(self.clus, np.int32)
+        self.tcoll = np.ascontiguousarray(self.tcoll, np.float32)
+        self.cl_sector = np.ascontiguousarray(self.cl_sector, np.uint8)
+        self.cl_row = np.ascontiguousarray(self.cl_row, np.uint8)
+        self.cl_y = np.ascontiguousarray(self.cl_y, np.float32)
+        self.cl_t = np.ascontiguousarray(self.cl_t, np.float32)
+        self.row_x = np.ascontiguousarray(self.row_x, np.float32)
+
+    @property
+    def n_tracks(self):
+        return int(self.x.shape[0])
+
+    def geom(self):
+        return OrcGeom(self.n_sectors, self.row_x.shape[0], _ptr(self.row_x, _PF), self.z_max, 1)
+
+
+def calib(tr: CalibTracks, theta, weight=None, grad=True, params: dict | None = None, vtx_var=VERTEX_VAR):
+    """Per-track calibration chi2, used flags and (optionally) the gradient of
+    sum_r weight[r] chi2_r with respect to theta (all binary64)."""
+    th = np.ascontiguousarray(theta, np.float64)
+    assert th.shape == (calib_n_theta(tr.n_sectors),)
+    T = tr.n_tracks
+    chi2 = np.zeros(T)
+    used = np.zeros(T, np.uint8)
+    g = np.zeros_like(th) if grad else None
+    w = None if weight is None else np.ascontiguousarray(weight, np.float64)
+    P = _params(params)
+    G = tr.geom()
+    rc = lib().orc_calib(C.byref(P), C.byref(G), tr.bz, tr.v_nom, vtx_var, T, _ptr(tr.sector, _P32),
+                         _ptr(tr.x, _PF), _ptr(tr.param, _PF), _ptr(tr.off, _P32), _ptr(tr.clus, _P32),
+                         _ptr(tr.cl_sector, _PU8), _ptr(tr.cl_row, _PU8), _ptr(tr.cl_y, _PF), _ptr(tr.cl_t, _PF),
+                         _ptr(tr.tcoll, _PF), _ptr(th, _PD), None if w is None else _ptr(w, _PD),
+                         _ptr(chi2, _PD), _ptr(used, _PU8), None if g is None else _ptr(g, _PD))
+    if rc:
+        raise ValueError(f"orc_calib failed ({rc})")
+    return chi2, used.astype(bool), g
+
+
+def calib_measure(tr: CalibTracks, theta, idx, tc):
+    """Calibrated (m_y, m_z) of clusters idx, each with collision time tc."""
+    th = np.ascontiguousarray(theta, np.float64)
+    idx = np.asarray(idx)
+    s = np.ascontiguousarray(tr.cl_sector[idx])
+    r = np.ascontiguousarray(tr.cl_row[idx])
+    y = np.ascontiguousarray(tr.cl_y[idx])
+    t = np.ascontiguousarray(tr.cl_t[idx])
+    tcc = np.ascontiguousarray(np.broadcast_to(np.asarray(tc, np.float32), idx.shape), np.float32)
+    my = np.zeros(idx.size)
+    mz = np.zeros(idx.size)
+    G = tr.geom()
+    lib().orc_calib_measure(C.byref(G), _ptr(th, _PD), idx.size, _ptr(s, _PU8), _ptr(r, _PU8), _ptr(y, _PF),
+                            _ptr(t, _PF), _ptr(tcc, _PF), _ptr(my, _PD), _ptr(mz, _PD))
+    return my, mz
+
+
+def calib_explain(tr: CalibTracks, theta, r, params: dict | None = None, vtx_var=VERTEX_VAR):
+    """One track's inward pass: per step F (5x5), reference (y, z), measurement
+    and variances, and the chi2; None when a reference step fails."""
+    th = np.ascontiguousarray(theta, np.float64)
+    n = int(tr.off[r + 1] - tr.off[r])
+    F = np.zeros((n + 1, 5, 5))
+    h = np.zeros((n + 1, 2))
+    m = np.zeros((n + 1, 2))
+    v = np.zeros((n + 1, 2))
+    chi2 = np.zeros(1)
+    P = _params(params)
+    G = tr.geom()
+    rc = lib().orc_calib_explain(C.byref(P), C.byref(G), tr.bz, tr.v_nom, vtx_var, _ptr(tr.sector, _P32),
+                                 _ptr(tr.x, _PF), _ptr(tr.param, _PF), _ptr(tr.off, _P32), _ptr(tr.clus, _P32),
+                                 _ptr(tr.cl_sector, _PU8), _ptr(tr.cl_row, _PU8), _ptr(tr.cl_y, _PF),
+                                 _ptr(tr.cl_t, _PF), _ptr(tr.tcoll, _PF), _ptr(th, _PD), r, _ptr(F, _PD),
+                                 _ptr(h, _PD), _ptr(m, _PD), _ptr(v, _PD), _ptr(chi2, _PD))
+    if rc:
+        return None
+    return F, h, m, v, float(chi2[0])
+
+
+def bspline_all(u):
+    b = np.zeros(CALIB_NSPL)
+    d = np.zeros(CALIB_NSPL)
+    lib().orc_bspline_all(float(u), _ptr(b, _PD), _ptr(d, _PD))
+    return b, d

@@ -304,10 +304,11 @@ static void sandwich64(double *c, double F[5][5])
         }
 }
 
-int orc_prop64(double *st, double x2, double kb)
+int orc_helix64(double *x, double *p, double x2, double kb, double F[5][5])
 {
-    double *p = st + 1, *c = st + 6;
-    double dx = x2 - st[0];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) F[i][j] = i == j;
+    double dx = x2 - *x;
     if (dx == 0.0) return 1;
     double k = kb * p[4];
     double s1 = p[2], s2 = s1 + k * dx;
@@ -329,38 +330,51 @@ int orc_prop64(double *st, double x2, double kb)
     double B = 1 / sqrt((1 - u) * (1 + u));
     double dS_ds = B * g * dy_ds;
     double dS_dk = B * g * dy_dk + 0.5 * dl * dl * Ap;
-    double F[5][5] = {{0}};
-    for (int i = 0; i < 5; i++) F[i][i] = 1;
     F[0][2] = dy_ds; F[0][4] = dy_dk * kb;
     F[1][2] = p[3] * dS_ds; F[1][3] = dS; F[1][4] = p[3] * dS_dk * kb;
     F[2][4] = dx * kb;
-    sandwich64(c, F);
-    st[0] = x2;
+    *x = x2;
     p[0] += dy;
     p[1] += dz;
     p[2] = s2;
     return 1;
 }
 
-int orc_rot64(double *st, double cs, double sn, double kb)
+int orc_prop64(double *st, double x2, double kb)
 {
-    double *p = st + 1, *c = st + 6;
-    double x = st[0], y = p[0], sp = p[2];
+    double F[5][5];
+    if (x2 == st[0]) return 1;
+    if (!orc_helix64(&st[0], st + 1, x2, kb, F)) return 0;
+    sandwich64(st + 6, F);
+    return 1;
+}
+
+int orc_rotate64(double *x, double *p, double cs, double sn, double kb, double J[5][5])
+{
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) J[i][j] = i == j;
+    double y = p[0], sp = p[2];
     double cf = sqrt((1 - sp) * (1 + sp));
     double spn = sp * cs - cf * sn;
     double cfn = cf * cs + sp * sn;
     if (!(fabs(spn) < 0.999) || !(cfn > 0)) return 0;
     double k = kb * p[4];
-    double J[5][5] = {{0}};
-    for (int i = 0; i < 5; i++) J[i][i] = 1;
     J[0][0] = cf / cfn;
     J[1][0] = -sn * p[3] / cfn;
     J[2][0] = -k * sn;
     J[2][2] = cfn / cf;
-    sandwich64(c, J);
-    st[0] = x * cs + y * sn;
-    p[0] = -x * sn + y * cs;
+    double x0 = *x;
+    *x = x0 * cs + y * sn;
+    p[0] = -x0 * sn + y * cs;
     p[2] = spn;
+    return 1;
+}
+
+int orc_rot64(double *st, double cs, double sn, double kb)
+{
+    double J[5][5];
+    if (!orc_rotate64(&st[0], st + 1, cs, sn, kb, J)) return 0;
+    sandwich64(st + 6, J);
     return 1;
 }
 

@@ -97,6 +97,10 @@ int orc_rot32(float *st21, float cs, float sn, float kb);
 int orc_update32(float *st21, float my, float mz, float vy, float vz, float chi2max, float *chi2);
 int orc_prop64(double *st21, double x2, double kb);
 int orc_rot64(double *st21, double cs, double sn, double kb);
+/* the same FP64 steps on a bare state (x, p[5]) with their 5x5 Jacobians
+ * (row = output parameter); on failure the state is left unchanged */
+int orc_helix64(double *x, double *p, double x2, double kb, double F[5][5]);
+int orc_rotate64(double *x, double *p, double cs, double sn, double kb, double J[5][5]);
 int orc_update64(double *st21, double my, double mz, double vy, double vz, double *chi2);
 /* FP64 multi-pass fit of a cluster list (inner -> outer); st21 in: initial
  * state in the outermost cluster's frame, out: state at the innermost cluster */
@@ -104,6 +108,35 @@ int orc_fit64(const orc_params *P, const orc_geom *G, double kb, int32_t n,
               const int32_t *sector, const double *x, const double *y, const double *z,
               int32_t n_passes, double *st21, double *chi2);
 float orc_merge_chi2(const float *top21, const float *bot21, float cs, float sn, float kb);
+
+/* ---- calibration chi2 of the refit and its gradient (tpc_oracle_calib.c) ----
+ * theta = {v_drift (cm/us), t0 (us), c[n_sectors][8][8][2]}: per sector an
+ * 8 x 8 clamped cubic B-spline of the cluster distortion (dy, dz) over
+ * ((x - x_first)/(x_last - x_first), |z|/z_max).  Tracks: the tracker's
+ * output (sector, x, 5 parameters in the tracker's z frame, cluster lists
+ * inner -> outer); tcoll[r] = collision time (us), NaN = track not used.
+ * chi2_out[r] / used[r] per track; grad (n_theta, may be NULL) = gradient of
+ * sum_r weight[r] chi2_r (weight NULL = all 1).  Returns 0, or -1 for a
+ * geometry without drift times. */
+#define ORC_CALIB_NSPL 8
+int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, double vtx_var, int32_t n_tracks,
+              const int32_t *tr_sector, const float *tr_x, const float *tr_p, const int32_t *tr_off,
+              const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y, const float *t,
+              const float *tcoll, const double *theta, const double *weight, double *chi2_out, uint8_t *used,
+              double *grad);
+/* the calibrated measurement of each cluster (for the pins) */
+void orc_calib_measure(const orc_geom *G, const double *theta, int32_t n, const uint8_t *sector,
+                       const uint8_t *row, const float *y, const float *t, const float *tc, double *my, double *mz);
+/* one track's pass laid out for the pins: per step k = 0..n the Jacobian
+ * F[k] (5x5, zero at k = 0), reference (y, z) h[k], measurement m[k] and its
+ * variances v[k]; returns 0, or 1 when a reference step fails */
+int orc_calib_explain(const orc_params *P, const orc_geom *G, double bz, double v_nom, double vtx_var,
+                      const int32_t *tr_sector, const float *tr_x, const float *tr_p, const int32_t *tr_off,
+                      const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y,
+                      const float *t, const float *tcoll, const double *theta, int32_t r, double *F, double *h,
+                      double *m, double *v, double *chi2);
+/* all 8 B-spline basis values and derivatives at u (for the pins) */
+void orc_bspline_all(double u, double *out, double *dout);
 
 #ifdef __cplusplus
 }

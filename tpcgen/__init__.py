@@ -354,3 +354,26 @@ def stf_batch(n_stf=64, seed0=1000, mult_mean=2000.0, max_coll=100, **kw):
     ncoll = rng.integers(1, max_coll + 1, n_stf)
     return [time_frame(seed=seed0 + 1 + i, n_collisions=int(nc), mult_mean=mult_mean,
                        frame_us=float(nc) * 20.0, **kw) for i, nc in enumerate(ncoll)]
+
+
+def track_collision_time(ev: Event, off, clus, min_frac: float = 0.5):
+    """Generator-truth collision time of reconstructed tracks: the collision of
+    the label that owns most of a track's clusters (at least ``min_frac`` of
+    them, and not noise), NaN otherwise.  Stands in for the time that matching
+    to the inner detectors would fix."""
+    off = np.asarray(off, np.int64)
+    clus = np.asarray(clus, np.int64)
+    T = off.size - 1
+    out = np.full(T, np.nan, np.float32)
+    if T == 0 or ev.trk_tc is None:
+        return out
+    lab = ev.label[clus]
+    for t in range(T):
+        a, b = off[t], off[t + 1]
+        if b <= a:
+            continue
+        vals, cnt = np.unique(lab[a:b], return_counts=True)
+        k = int(np.argmax(cnt))
+        if vals[k] >= 0 and cnt[k] >= min_frac * (b - a):
+            out[t] = np.float32(ev.trk_tc[vals[k]])
+    return out
