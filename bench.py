@@ -37,6 +37,10 @@ FLOPS_PROP = 181      # prop32: 71 for the state and Jacobian terms + 110 for F 
 FLOPS_UPDATE = 130    # update32: innovation, 2x2 inverse, chi2, gain, state, covariance
 FLOPS_CAND = 5        # one grid candidate in the following window: 2 sub + fused distance
 FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky solve (~250)
+# DRAM bytes (read + write) per cluster of the frame of one launch, from the
+# committed ncu capture of the same kernel build (profiles/k_tracklets_frame20.md,
+# 20-collision frame, scaled by clusters); None once the kernel changes
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 231.0}
 
 
 def parse():
@@ -48,12 +52,14 @@ def parse():
     ap.add_argument("--collisions", type=int, default=50)
     ap.add_argument("--cpu-sample-collisions", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("frame", "stf_batch"), default="frame",
+    ap.add_argument("--workload", choices=("frame", "stf_batch", "calib"), default="frame",
                     help="frame: the 50-collision frame; stf_batch: sub-time-frames of 1..max-coll collisions")
     ap.add_argument("--n-stf", type=int, default=64)
     ap.add_argument("--max-coll", type=int, default=100)
     ap.add_argument("--mult", type=float, default=2000.0)
     ap.add_argument("--tune", action="store_true", help="autotune grid and queue settings on the first 8 STFs")
+    ap.add_argument("--no-fp64-final", action="store_true",
+                    help="stf_batch: binary32 final refit (default: FP64 Joseph covariance and chi2 in the last pass)")
     return ap.parse_args()
 
 
@@ -314,6 +320,52 @@ def make_stf_batch(n_stf, max_coll, mult, seed0=1000):
     return cat, off, ncoll
 
 
+def batch_cpu_baseline(cat, off, k, res, fp64):
+    """cpu_baseline of the batch: the oracle, single-threaded, on sub-time-frame
+    k alone (the smallest of the batch), and the error of the batch's results
+    for that frame against it (decisions exact, fit relative to the FP64
+    oracle refit)."""
+    import numpy as np
+
+    import oracle
+    import tpcgen
+    a, b = int(off[k]), int(off[k + 1])
+    t0 = time.perf_counter()
+    r = oracle.track(cat["sector"][a:b], cat["row"][a:b], cat["y"][a:b], cat["zt"][a:b], tpcgen.row_x_f32(),
+                     n_sectors=36, z_max=250.0, continuous=True, bz=0.5, v_drift=tpcgen.V_DRIFT)
+    dt = time.perf_counter() - t0
+    fr = res.frame.cpu().numpy()
+    idx = np.nonzero(fr == k)[0]
+    err = {"frame": int(k), "clusters": b - a, "tracks_gpu": int(idx.size), "tracks_oracle": r.n_tracks}
+    if idx.size == r.n_tracks and idx.size > 0:
+        t_lo, t_hi = int(idx[0]), int(idx[-1]) + 1
+        co = res.clus_offset.cpu().numpy()
+        ci = res.clus_index[int(co[t_lo]):int(co[t_hi])].cpu().numpy() - a
+        asg = res.assign[a:b].cpu().numpy()
+        asg = np.where(asg >= 0, asg - t_lo, -1)
+        err["clusters_mismatch"] = int(ci.size != r.tr_clus.size or (ci != r.tr_clus).sum())
+        err["assign_mismatch"] = int((asg != r.assign).sum())
+        st = res.status[t_lo:t_hi].cpu().numpy()
+        ok = (st == 0) & (r.tr_status == 0)
+        err["status_mismatch"] = int((st != r.tr_status).sum())
+        p = res.param[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
+        floor = np.array([1.0, 1.0, 1e-2, 1e-2, 1e-2])
+        pe = np.abs(p - r.tr_p[ok]) / np.maximum(np.abs(r.tr_p[ok]), floor)
+        chi = (res.chi2_64 if fp64 else res.chi2)[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
+        ce = np.abs(chi - r.tr_chi2[ok]) / np.maximum(r.tr_chi2[ok], 1.0)
+        cov = (res.cov64 if fp64 else res.cov)[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
+        dg = [0, 2, 5, 9, 14]
+        ve = np.abs(cov[:, dg] - r.tr_c[ok][:, dg]) / np.abs(r.tr_c[ok][:, dg])
+        err.update(param_rel_max=pe.max(axis=0).tolist() if pe.size else None,
+                   param_rel_p99=np.percentile(pe, 99, axis=0).tolist() if pe.size else None,
+                   chi2_rel_max=float(ce.max()) if ce.size else None,
+                   cov_diag_rel_max=float(ve.max()) if ve.size else None)
+    return {"value": (b - a) / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+            "sample": f"sub-time-frame {k} of the batch alone ({b - a} clusters, the smallest), "
+                      f"{dt:.1f} s wall, single thread",
+            "error_vs_oracle": err}
+
+
 def run_batch(args, ws, rank, local, pg):
     """Batched mode: the whole STF batch per step (synchronous call and CUDA
     graph replay) against the per-STF loop, same outputs."""
@@ -333,7 +385,8 @@ def run_batch(args, ws, rank, local, pg):
     ins = (dv["sector"], dv["row"], dv["y"], dv["zt"])
     row_x = tpcgen.row_x_f32()
     off32 = off.astype(np.int32)
-    params = tpc.tpc_params_default(tracklets_per_1k=60)
+    fp64 = not args.no_fp64_final
+    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=int(fp64))
     tuned = None
     if args.tune:
         k = min(8, args.n_stf)
@@ -378,6 +431,16 @@ def run_batch(args, ws, rank, local, pg):
     with ClockSampler(local) as clk:
         ms_graph = timed(run.replay, args.steps)
     p_graph = run.result().param.cpu().numpy()
+    trk.params.profile = 1                  # one extra pass with stage events, outside the timed regions
+    stage_ms = trk.track_batched(*ins, off32, bz=bz, v_drift=vd).stage_ms
+    trk.params.profile = 0
+    one.params.profile = 1
+    pf_stage_ms = {k: 0.0 for k in stage_ms}
+    for i in range(nstf):
+        a, b = int(off[i]), int(off[i + 1])
+        for k, v in one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd).stage_ms.items():
+            pf_stage_ms[k] += v
+    one.params.profile = 0
     for _ in range(min(args.warmup, 1)):
         per_frame()
     ms_frame = timed(per_frame, max(1, args.steps // 2))
@@ -405,11 +468,143 @@ def run_batch(args, ws, rank, local, pg):
                    "clusters": n, "collisions": int(ncoll.sum()), "tracks_found": rb.n_tracks,
                    "per_frame_ms": ms_frame, "batched_sync_ms": ms_batch, "graph_ms": ms_graph,
                    "speedup_vs_per_frame": ms_frame / ms_graph, "identical_to_per_frame": same,
-                   "tuned": tuned["best"] if tuned else None},
+                   "tuned": tuned["best"] if tuned else None,
+                   "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+                   "per_frame_stage_ms": {k: round(v, 3) for k, v in pf_stage_ms.items()}},
         "e2e": {"value": n / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
     }
+    line["config"]["final_refit"] = "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32"
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(cat, off, int(np.argmin(np.diff(off))), rb, fp64)
+    print(json.dumps(line), flush=True)
+
+
+# binary32 flops per cluster step of the calibration pass, counted from the
+# operation lists in tpc_calib.cu / tpc_fit.cuh: reference helix step 60,
+# deviation propagation 12, covariance transport 100, update 80, calibrated
+# measurement (two B-spline bases, 16-term sums, chain rule) 150; the backward
+# recomputes the forward step and adds the reverse sweep (60) and the gradient
+# scatter (measurement again + 32 products)
+FLOPS_CALIB_FWD = 460
+FLOPS_CALIB_BWD = 460 + 60 + 190
+
+
+def run_calib(args, ws, rank, local, pg):
+    """Calibration workload: the 50-collision frame generated with v_drift
+    +0.3 %, t0 = 200 ns and a 36 x 8 x 8 spline distortion map; the tracker
+    (untimed) finds the tracks, then one step = the calibration chi2 of every
+    selected track and its gradient with respect to theta through
+    torch.autograd (tpc_calib_forward + tpc_calib_backward)."""
+    import numpy as np
+    import torch
+
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ev = tpcgen.calib_frame(seed=5 + rank, n_collisions=args.collisions)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    cl = (t(ev.sector), t(ev.row), t(ev.y), t(ev.zt))
+    trk = tpc.Tracker(ev.n, ev.row_x, continuous=True, device=dev)
+    res = trk.track(*cl, bz=ev.bz, v_drift=ev.v_drift)
+    T = res.n_tracks
+    off = res.clus_offset[:T + 1].cpu().numpy()
+    clus = res.clus_index[:int(off[-1])].cpu().numpy()
+    tc = tpc.calib.select_tracks(t(tpcgen.track_collision_time(ev, off, clus)), res.status[:T], res.param[:T])
+    calib = tpc.CalibRefit.from_result(res, tc, *cl, ev.row_x, bz=ev.bz, v_nominal=ev.v_drift)
+    theta = tpc.calib.nominal_theta(ev.v_drift, device=dev).requires_grad_(True)
+
+    def step():
+        theta.grad = None
+        chi2, used = tpc.calib_chi2(theta, calib)
+        chi2.sum().backward()
+        return used
+
+    for _ in range(args.warmup):
+        used = step()
+    torch.cuda.synchronize()
+    u = used.cpu().numpy().astype(bool)
+    n_steps = int((np.diff(off)[u] + 1).sum())        # clusters + the vertex of every used track
+    stream = torch.cuda.current_stream(dev)
+    ev_f = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms = b_ms = 0.0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            theta.grad = None
+            ev_f[0].record(stream)
+            chi2, used = tpc.calib_chi2(theta, calib)
+            ev_f[1].record(stream)
+            chi2.sum().backward()
+            ev_f[2].record(stream)
+            torch.cuda.synchronize()
+            f_ms += ev_f[0].elapsed_time(ev_f[1])
+            b_ms += ev_f[1].elapsed_time(ev_f[2])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    f_ms /= args.steps
+    b_ms /= args.steps
+    grad = theta.grad.detach().cpu().numpy()
+    # end to end: theta from pinned host memory, chi2 sum and gradient back
+    h_theta = theta.detach().cpu().pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.no_grad():
+            theta.copy_(h_theta, non_blocking=True)
+        theta.grad = None
+        chi2, used = tpc.calib_chi2(theta, calib)
+        loss = chi2.sum()
+        loss.backward()
+        float(loss.item())
+        theta.grad.cpu()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if rank != 0:
+        return
+    pk = FP32_PEAK_TFLOPS
+    bw_tf = n_steps * FLOPS_CALIB_BWD / (b_ms * 1e-3) / 1e12
+    line = {
+        "metric": "calibration chi2 + adjoint gradient, track clusters/s on 1 B300",
+        "value": n_steps / (ms / 1e3), "unit": "track clusters/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.collisions}-collision calibration frame (v_drift +0.3 %, t0 200 ns, "
+                               "36 x 8 x 8 spline map), theta at the nominal calibration",
+                   "tracks": T, "tracks_used": int(u.sum()), "pass_steps": n_steps, "forward_ms": f_ms,
+                   "backward_ms": b_ms, "grad_v_t0": grad[:2].tolist(),
+                   "l2": "clusters (160 MB) and checkpoints exceed the 126 MB L2; no flush"},
+        "roofline": {"bound": "alu", "stage": "calib_backward", "achieved": bw_tf, "peak": pk, "unit": "TFLOP/s",
+                     "frac": bw_tf / pk, "traffic": None,
+                     "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"},
+        "e2e": {"value": n_steps / e2e_s, "unit": "track clusters/s",
+                "h2d_bytes_per_step": 4 * theta.numel(), "d2h_bytes_per_step": 4 + 4 * theta.numel()},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(0)
+        pick = np.sort(rng.choice(np.nonzero(u)[0], min(3000, int(u.sum())), replace=False))
+        n = np.diff(off)
+        o_off = np.concatenate([[0], np.cumsum(n[pick])]).astype(np.int32)
+        o_cl = np.concatenate([clus[off[k]:off[k + 1]] for k in pick]).astype(np.int32)
+        h = lambda x: x[:T].cpu().numpy()  # noqa: E731
+        tr = oracle.CalibTracks(h(res.sector)[pick], h(res.x)[pick], h(res.param)[pick], o_off, o_cl,
+                                tc.cpu().numpy()[pick], ev.sector, ev.row, ev.y, ev.zt, ev.row_x, bz=ev.bz,
+                                v_nom=ev.v_drift)
+        th0 = np.zeros(tr_n := oracle.calib_n_theta(36))
+        th0[0] = np.float32(ev.v_drift)
+        c0 = time.perf_counter()
+        _, uo, _ = oracle.calib(tr, th0)
+        dt = time.perf_counter() - c0
+        steps_o = int((n[pick][uo] + 1).sum())
+        line["cpu_baseline"] = {"value": steps_o / dt, "unit": "track clusters/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{pick.size} of the used tracks ({steps_o} pass steps), chi2 + gradient "
+                                          f"in binary64, {dt:.1f} s, single thread, theta of {tr_n} values"}
     print(json.dumps(line), flush=True)
 
 
@@ -425,8 +620,9 @@ def roofline(stage, per_step, w, n, pk):
         else:
             flops = w["refit_prop"] * (FLOPS_PROP + FLOPS_UPDATE)
         ach = flops / t / 1e12
+        tb = NCU_TRAFFIC_B_PER_CLUSTER.get(stage)
         return {"bound": "alu", "stage": stage, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": tb * n if tb is not None else None,
                 "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"}
     bytes_per = {"prep": 18, "bin": 40, "neighbours": 22, "clean_start": 28}.get(stage, 0)
     hbm = pk.get("hbm_gbs", 6400.0)
@@ -442,6 +638,8 @@ def main():
         run_reference(args, ws, rank, pg)
     elif args.workload == "stf_batch":
         run_batch(args, ws, rank, local, pg)
+    elif args.workload == "calib":
+        run_calib(args, ws, rank, local, pg)
     else:
         run_ours(args, ws, rank, local, pg)
     if pg is not None:

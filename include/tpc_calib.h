@@ -1,0 +1,105 @@
+/*
+ * tpc_calib.h -- C ABI of the calibration chi2 of the refit and of its
+ * adjoint (gradient with respect to the calibration parameters).
+ *
+ * Paper: section "Tracking" (continuous read-out: the drift time is turned
+ * into z with the drift velocity; once the collision time is fixed by
+ * matching, the final refit applies the calibration under the primary-track
+ * assumption) and section "TPC Tracking" (online drift-velocity
+ * calibration).  The paper gives no formulas for this part; the model below
+ * is this library's reading.
+ *
+ * Calibration parameters theta (binary32, device, TPC_CALIB_N_THETA(ns)):
+ *   theta[0] = v, drift velocity (cm/us); theta[1] = t0, time offset (us);
+ *   theta[2 + ((s*8 + i)*8 + j)*2 + k] = spline coefficient of sector s,
+ *   i along u = (x - x_first)/(x_last - x_first) (pad-row radius), j along
+ *   w = |z|/z_max, k = 0: dy, k = 1: dz (cm), of an 8 x 8 uniform clamped
+ *   cubic B-spline per sector.
+ * A cluster (sector s, row, y, drift time t) of a track from a collision at
+ * time t_c (side sgn = +1 for sectors 0-17, -1 for 18-35) is measured at
+ *   zl = z_max - v (t - t_c - t0),  w = clamp(zl/z_max, 0, 1),
+ *   m_y = y - dy(u, w),  m_z = sgn (zl - dz(u, w)).
+ * The calibration chi2 of a track is the chi2 of one inward Kalman pass over
+ * its clusters (outermost first) ending with a primary-vertex
+ * pseudo-measurement (y = z = 0 at the origin, variance vertex_var; the last
+ * step rotates the frame about the origin onto the innermost reference
+ * position, then follows the helix to x = 0), linearised
+ * around a reference helix that does not depend on theta: the tracker's
+ * output state (tpc_tracks.param etc.), its z moved from the tracker's frame
+ * to absolute z by sgn v_nominal t_c, carried along the cluster planes.  Step
+ * 0 sets the deviation from the reference to (m_y - y_ref, m_z - z_ref, 0, 0,
+ * 0) with covariance diag(sigma_y^2, sigma_z^2, c0_snp, c0_tgl, c0_qpt) from
+ * tpc_params.  A track is left out (used = 0) when its reference reaches
+ * |sin(phi)| >= 0.9 at one of its clusters.  The gradient is the reverse sweep of that pass; the forward
+ * pass stores the state every 16 steps and the backward pass recomputes each
+ * 16-step segment from its checkpoint.
+ *
+ * Arithmetic: binary32 (the state with compensated sums), gradient sums in
+ * binary64.  All pointers in tpc_calib_tracks and the theta / chi2 / used /
+ * dchi2 / grad arrays are device pointers owned by the caller; the
+ * workspace is a caller-owned device buffer.  The forward and backward calls
+ * only enqueue work on `stream` (no host synchronisation; capturable in a
+ * CUDA graph); tpc_calib_status reads the error flag the kernels set.
+ */
+#ifndef TPC_CALIB_H
+#define TPC_CALIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "tpc_track.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPC_CALIB_NSPL 8
+#define TPC_CALIB_N_THETA(n_sectors) (2 + (n_sectors) * TPC_CALIB_NSPL * TPC_CALIB_NSPL * 2)
+#define TPC_CALIB_CKPT_STEPS 16           /* steps between stored states */
+
+typedef struct {
+    int32_t n_tracks;
+    const int32_t *sector;        /* [T] sector of the reference state */
+    const float *x;               /* [T] x of the reference state (cm) */
+    const float *param;           /* [T][5] y, z (tracker frame), sin(phi), tan(lambda), q/pT */
+    const int32_t *clus_offset;   /* [T+1], clus_offset[0] == 0, non-decreasing */
+    const int32_t *clus_index;    /* cluster indices of each track, innermost first */
+    const float *t_coll;          /* [T] collision time (us); NaN: the track is not used */
+    int64_t n_clusters;           /* clusters in the arrays below (>= clus_offset[T]) */
+    const uint8_t *cl_sector;     /* [n] */
+    const uint8_t *cl_row;        /* [n] */
+    const float *cl_y;            /* [n] local y (cm) */
+    const float *cl_t;            /* [n] drift time (us) */
+} tpc_calib_tracks;
+
+/* Device workspace (bytes) for n_tracks tracks holding at most n_clusters
+ * clusters in total.  Errors: TPC_ERR_ARG. */
+int tpc_calib_workspace_size(const tpc_geometry *g, int32_t n_tracks, int64_t n_clusters, size_t *bytes);
+
+/* Forward pass: chi2[r] (binary32) and used[r] (1: the track entered the
+ * sum; 0: t_coll is NaN, fewer than 2 clusters, or a reference step left the
+ * helix domain) for every track, and the checkpoints in `workspace`.
+ * g must have drift times (g->continuous).  Errors: TPC_ERR_ARG,
+ * TPC_ERR_CAPACITY (ws_bytes too small), TPC_ERR_CUDA.  Invalid data
+ * (cluster index, sector or row out of range, decreasing offsets) mark the
+ * track unused and set the flag tpc_calib_status reports. */
+int tpc_calib_forward(const tpc_params *p, const tpc_geometry *g, float bz, float v_nominal, float vertex_var,
+                      const tpc_calib_tracks *tr, const float *theta, float *chi2, uint8_t *used,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* Backward pass: grad (binary64, TPC_CALIB_N_THETA(g->n_sectors), zeroed
+ * by the call) = d/dtheta of sum_r dchi2[r] chi2_r over the tracks with
+ * used[r] = 1, from the checkpoints of the last tpc_calib_forward on this
+ * workspace with the same tracks and theta.  Errors as tpc_calib_forward. */
+int tpc_calib_backward(const tpc_params *p, const tpc_geometry *g, float bz, float v_nominal, float vertex_var,
+                       const tpc_calib_tracks *tr, const float *theta, const float *dchi2, const uint8_t *used,
+                       const void *workspace, size_t ws_bytes, double *grad, void *stream);
+
+/* Synchronises `stream` and writes the workspace's error flag to *err
+ * (0: none; 1: invalid track data seen).  Errors: TPC_ERR_ARG, TPC_ERR_CUDA. */
+int tpc_calib_status(const void *workspace, int32_t *err, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

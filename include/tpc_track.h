@@ -145,11 +145,14 @@ typedef struct {
                                     chi2 evaluations */
 } tpc_tracks;
 
+#define TPC_MAX_CLUSTERS 2145386495LL   /* INT32_MAX - 2^21 */
+
 /* Fill *p with the default parameters.  Returns TPC_OK, or TPC_ERR_ARG for p == NULL. */
 int tpc_params_default(tpc_params *p);
 
 /* Bytes of device workspace tpc_track needs for n_clusters clusters with
- * these parameters and geometry; written to *bytes.  Errors: TPC_ERR_ARG. */
+ * these parameters and geometry; written to *bytes.  n_clusters is at most
+ * TPC_MAX_CLUSTERS (cluster indices are int32).  Errors: TPC_ERR_ARG. */
 int tpc_workspace_size(const tpc_params *p, const tpc_geometry *g, int64_t n_clusters, size_t *bytes);
 
 /* Track one event or continuous read-out frame (sections "Tracking" and

@@ -22,7 +22,11 @@
  *       m_y = y - dy(u, w),   m_z = sgn (zl - dz(u, w)).
  *   The calibration chi2 of a track is the chi2 of one inward Kalman pass over
  *   its clusters, outermost first, ending with a primary-vertex
- *   pseudo-measurement (y = z = 0 at x = 0, variance vtx_var).  The pass is
+ *   pseudo-measurement (y = z = 0 at the origin, variance vtx_var; the last
+ *   step rotates the frame about the origin onto the innermost reference
+ *   position and then follows the helix to x = 0, so that it stays well
+ *   conditioned for tracks that bend far from the sector axis).  Tracks whose
+ *   reference reaches |sin(phi)| >= 0.9 at a cluster are left out.  The pass is
  *   linearised around a reference helix that does not depend on theta: the
  *   tracker's output state, its z moved from the tracker's frame (nominal
  *   drift velocity v_nom, no t0, no collision time) to absolute z by
@@ -180,6 +184,11 @@ static void mat_mul(double A[5][5], double B[5][5], double C[5][5])
     memcpy(C, T, sizeof(T));
 }
 
+/* the calibration pass leaves out tracks whose reference runs at more than
+ * asin(0.9) = 64 degrees to the pad-row normal at any of their clusters
+ * (nearly tangent to the rows, where the helix step is ill conditioned) */
+#define SNP_CALIB 0.9
+
 /* reference step to the plane x2 of sector s2: rotation when the sector
  * changes, then the helix; F = (helix Jacobian)(rotation Jacobian) */
 static int ref_step(const orc_geom *G, double kb, int *sec, double *x, double *q, int s2, double x2, double F[5][5])
@@ -195,6 +204,22 @@ static int ref_step(const orc_geom *G, double kb, int *sec, double *x, double *q
         *sec = s2;
     }
     if (!orc_helix64(x, q, x2, kb, H)) return 0;
+    if (!(fabs(q[2]) < SNP_CALIB)) return 0;
+    mat_mul(H, J, F);
+    return 1;
+}
+
+/* reference step to the primary vertex: rotate the frame about the origin
+ * onto the reference position (new x along it, y = 0), then the helix to
+ * x = 0; the track crosses x = 0 at a small angle to the new axis, where the
+ * step is well conditioned.  F = (helix Jacobian)(rotation Jacobian). */
+static int vertex_step(double kb, double *x, double *q, double F[5][5])
+{
+    double J[5][5], H[5][5];
+    const double r = hypot(*x, q[0]);
+    if (!(r > 0.0)) return 0;
+    if (!orc_rotate64(x, q, *x / r, q[0] / r, kb, J)) return 0;
+    if (!orc_helix64(x, q, 0.0, kb, H)) return 0;
     mat_mul(H, J, F);
     return 1;
 }
@@ -222,6 +247,7 @@ static int track_pass(const orc_params *P, const orc_geom *G, double kb, double 
     int sec = tr_sector[r];
     double x = tr_x[r], q[5];
     for (int k = 0; k < 5; k++) q[k] = tr_p[5 * r + k];
+    if (!(fabs(q[2]) < SNP_CALIB)) return 0;
     q[1] += side_of(sec, G->n_sectors) * v_nom * tc;      /* tracker frame -> absolute z */
     double F[5][5];
     /* out to the outermost cluster along the cluster list */
@@ -243,7 +269,7 @@ static int track_pass(const orc_params *P, const orc_geom *G, double kb, double 
             st->vy = vy;
             st->vz = vz;
         } else {
-            if (!ref_step(G, kb, &sec, &x, q, sec, 0.0, st->F)) return 0;
+            if (!vertex_step(kb, &x, q, st->F)) return 0;
             st->my = 0.0;
             st->mz = 0.0;
             st->vy = vtx_var;

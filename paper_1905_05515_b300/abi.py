@@ -1,4 +1,4 @@
-"""ctypes mirror of include/tpc_track.h (argument marshalling only)."""
+"""ctypes mirror of include/tpc_track.h and include/tpc_calib.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -57,12 +57,28 @@ class TpcTracks(C.Structure):
                 ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64),
                 ("n_launches", C.c_int32), ("stage_ms", C.c_float * 10), ("work", C.c_int64 * 5)]
 
+class TpcCalibTracks(C.Structure):
+    _fields_ = [("n_tracks", C.c_int32), ("sector", C.c_void_p), ("x", C.c_void_p), ("param", C.c_void_p),
+                ("clus_offset", C.c_void_p), ("clus_index", C.c_void_p), ("t_coll", C.c_void_p),
+                ("n_clusters", C.c_int64), ("cl_sector", C.c_void_p), ("cl_row", C.c_void_p),
+                ("cl_y", C.c_void_p), ("cl_t", C.c_void_p)]
+
+
+CALIB_NSPL = 8
+CALIB_CKPT_STEPS = 16
+
+
+def calib_n_theta(n_sectors: int) -> int:
+    return 2 + n_sectors * CALIB_NSPL * CALIB_NSPL * 2
+
+
 STAGES = ("prep", "bin", "neighbours", "clean_start", "tracklets", "select", "merge", "assemble", "refit")
 
 
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
             "tpc_track_batched", "tpc_prepare", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
-            "tpc_error_string")
+            "tpc_error_string", "tpc_calib_workspace_size", "tpc_calib_forward", "tpc_calib_backward",
+            "tpc_calib_status")
 
 _lib = None
 
@@ -96,6 +112,14 @@ def lib(build_if_missing: bool = True):
                                       C.c_void_p, C.c_void_p]
         L.tpc_export_tracklets.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
+        L.tpc_calib_workspace_size.argtypes = [C.POINTER(TpcGeometry), C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]
+        L.tpc_calib_forward.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float, C.c_float,
+                                        C.POINTER(TpcCalibTracks), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_size_t, C.c_void_p]
+        L.tpc_calib_backward.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,
+                                         C.c_float, C.POINTER(TpcCalibTracks), C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+        L.tpc_calib_status.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
         L.tpc_error_string.argtypes = [C.c_int]
         L.tpc_error_string.restype = C.c_char_p
         _lib = L

@@ -2,7 +2,8 @@
 
 Decision-path translation units are compiled with -fmad=false so that every
 binary32 operation keeps the order written in the source (bit-exact links and
-assignments); the refit unit lets the compiler contract multiply-adds.
+assignments); the refit and calibration units let the compiler contract
+multiply-adds.
 """
 import os
 import subprocess
@@ -20,6 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
 UNITS = {
     "tpc_track.cu": ["-fmad=false"],
     "tpc_refit.cu": ["-fmad=true"],
+    "tpc_calib.cu": ["-fmad=true"],
 }
 
 
@@ -32,7 +34,7 @@ def _nvcc():
 
 def sources():
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    out.append(os.path.join(INCLUDE, "tpc_track.h"))
+    out.extend(os.path.join(INCLUDE, h) for h in ("tpc_track.h", "tpc_calib.h"))
     out.append(os.path.abspath(__file__))
     return out
 

@@ -31,7 +31,10 @@ constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
 constexpr int MAX_FRAMES = 4096;
-constexpr int FRAME_NZ = 256;          // grid cell budget per extra frame, in z-cells per plane
+// grid cell budget of a batch beyond the first frame's max_z_cells: two
+// cells per cluster (a 50-collision frame occupies about 0.6 clusters per
+// cell at the default cell size), never more than max_z_cells per frame
+constexpr int64_t CELLS_PER_CLUSTER = 2;
 constexpr float Y_MARGIN = 1.0f;       // y-bin range beyond the sector edge (cm)
 constexpr uint32_t WS_MAGIC = 0x54504332u;
 
@@ -110,7 +113,12 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.nzmax = p->max_z_cells;
     L.ny = effective_ybins(p, g);
     L.nframes = nframes;
-    L.ncells = (int64_t)L.np * L.ny * ((int64_t)L.nzmax + (int64_t)FRAME_NZ * (nframes - 1));
+    {
+        const int64_t per = (int64_t)L.np * L.ny;
+        const int64_t extra_z = nframes > 1 ? (CELLS_PER_CLUSTER * n + per - 1) / per + nframes : 0;
+        const int64_t zcells = std::min<int64_t>((int64_t)L.nzmax * nframes, L.nzmax + extra_z);
+        L.ncells = std::min<int64_t>(per * zcells, ((int64_t)UINT32_MAX - 1) / per * per);
+    }
     int64_t cap = std::max<int64_t>(4096, (n * (int64_t)p->tracklets_per_1k) / 1000);
     L.ntcap = (int32_t)std::min<int64_t>(cap, std::max<int64_t>(n, 4096));
     L.mnzmax = MAX_MERGE_CELLS;
@@ -174,6 +182,12 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
 
 template <typename T>
 inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+// Cluster indices are int32 and the grid-stride loops step an int index by at
+// most 148 * 16 blocks x 256 threads (grid_for's cap): with n below
+// INT32_MAX - 2^21 the index after the last step still fits.
+constexpr int64_t MAX_CLUSTERS = (int64_t)INT32_MAX - (1 << 21);
+static_assert(MAX_CLUSTERS == TPC_MAX_CLUSTERS, "limit stated in tpc_track.h");
 
 int grid_for(int64_t n, int block)
 {
@@ -1558,7 +1572,7 @@ int tpc_params_default(tpc_params* p)
 
 int tpc_workspace_size_batched(const tpc_params* p, const tpc_geometry* g, int64_t n, int32_t n_frames, size_t* bytes)
 {
-    if (!bytes || n < 0 || n > (int64_t)INT32_MAX / 2 || n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
+    if (!bytes || n < 0 || n > MAX_CLUSTERS || n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
     int rc = check_args(p, g);
     if (rc) return rc;
     const Layout L = make_layout(p, g, n, n_frames);

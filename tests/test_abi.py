@@ -1,5 +1,5 @@
 """CPU-side checks of the C ABI library: it builds for sm_103a, loads, and
-exports every function include/tpc_track.h declares; host-only entry points
+exports every function include/*.h declares; host-only entry points
 validate their arguments (no GPU needed for these)."""
 import ctypes as C
 import os
@@ -12,18 +12,25 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "tpc_track.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpc_\w+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"#define[^\n]*", "", src)
+        names |= set(re.findall(r"\b(tpc_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
     import paper_1905_05515_b300 as tpc
     L = tpc.lib()
     names = _declared()
-    assert "tpc_track" in names and len(names) >= 5
+    assert "tpc_track" in names and "tpc_calib_backward" in names
     for nm in names:
         assert hasattr(L, nm), nm
+    assert set(tpc.abi.EXPORTED) == set(names)
 
 
 def test_params_and_workspace_size_host_only():
@@ -52,4 +59,30 @@ def test_track_rejects_null_arguments_without_touching_the_gpu():
     p = tpc.tpc_params_default()
     g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, False)
     rc = L.tpc_track(C.byref(p), C.byref(g), 0.5, 2.58, None, None, 0, None, None)
+    assert rc == tpc.TPC_ERR_ARG
+
+
+def test_calib_entry_points_validate_arguments_without_the_gpu():
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    L = tpc.lib()
+    g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
+    b = C.c_size_t(0)
+    assert L.tpc_calib_workspace_size(C.byref(g), 100, 15000, C.byref(b)) == tpc.TPC_OK
+    assert b.value == 256 + (15000 // 16 + 100 + 1) * 128
+    assert L.tpc_calib_workspace_size(C.byref(g), -1, 10, C.byref(b)) == tpc.TPC_ERR_ARG
+    p = tpc.tpc_params_default()
+    tr = tpc.abi.TpcCalibTracks()
+    tr.n_tracks = 0
+    theta = (C.c_float * tpc.abi.calib_n_theta(36))()
+    gz = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, False)     # no drift times
+    rc = L.tpc_calib_forward(C.byref(p), C.byref(gz), 0.5, 2.58, 0.01, C.byref(tr), C.cast(theta, C.c_void_p),
+                             None, None, None, 0, None)
+    assert rc == tpc.TPC_ERR_ARG
+    rc = L.tpc_calib_forward(C.byref(p), C.byref(g), 0.5, 2.58, 0.0, C.byref(tr), C.cast(theta, C.c_void_p),
+                             None, None, None, 0, None)
+    assert rc == tpc.TPC_ERR_ARG                                           # vertex variance must be > 0
+    tr.n_tracks = 5                                                        # null track arrays
+    rc = L.tpc_calib_forward(C.byref(p), C.byref(g), 0.5, 2.58, 0.01, C.byref(tr), C.cast(theta, C.c_void_p),
+                             None, None, None, 0, None)
     assert rc == tpc.TPC_ERR_ARG
