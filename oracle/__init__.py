@@ -24,7 +24,7 @@ class OrcParams(C.Structure):
                 ("chi2_cut", C.c_float), ("max_miss", C.c_int32), ("min_hits", C.c_int32),
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float),
                 ("merge_dz", C.c_float), ("merge_chi2", C.c_float), ("refit_passes", C.c_int32),
-                ("refit_inflate", C.c_float)]
+                ("refit_inflate", C.c_float), ("packed_links", C.c_int32)]
 
 
 class OrcGeom(C.Structure):

@@ -68,6 +68,7 @@ void orc_params_default(orc_params *p)
     p->merge_dz = 10.0f; p->merge_chi2 = 50.0f;
     p->refit_passes = 3;
     p->refit_inflate = 100.0f;
+    p->packed_links = 0;
 }
 
 /* ===================================================================== *
@@ -593,13 +594,29 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
      * smaller (up, down) cluster indices. */
     R->up_raw = (int32_t *)malloc(sizeof(int32_t) * nz(n));
     R->dn_raw = (int32_t *)malloc(sizeof(int32_t) * nz(n));
+    /* Packed-coordinate variant (configuration of the batched workload): the
+     * link pass sees every coordinate rounded to the nearest multiple of
+     * 2^-8 cm (ties to even), i.e. the value a 16-bit packed field of a
+     * fixed-point coordinate with that step decodes to. */
+    const float *ly = y, *lzc = R->z;
+    float *qy = NULL, *qz = NULL;
+    if (P->packed_links) {
+        qy = (float *)malloc(sizeof(float) * nz(n));
+        qz = (float *)malloc(sizeof(float) * nz(n));
+        for (int i = 0; i < n; i++) {
+            qy[i] = rintf(y[i] * 256.0f) * 0.00390625f;
+            qz[i] = rintf(R->z[i] * 256.0f) * 0.00390625f;
+        }
+        ly = qy;
+        lzc = qz;
+    }
     ivec U = {0, 0, NULL}, D = {0, 0, NULL};
     for (int h = 0; h < n; h++) {
         R->up_raw[h] = -1; R->dn_raw[h] = -1;
         int r = row[h];
         if (r < 1 || r > NR - 2) continue;
         int s = sector[h];
-        float yh = y[h], zh = R->z[h];
+        float yh = ly[h], zh = lzc[h];
         float yu_pred = yh * R->row_qup[r];
         float yd_pred = yh * R->row_qdn[r];
         U.n = 0; D.n = 0;
@@ -610,7 +627,7 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
             for (int q = plane_lower(&g, plq, (double)zh - 2.0 * P->dz_link - 1.0); q < end; q++) {
                 if ((double)g.zs[q] > (double)zh + 2.0 * P->dz_link + 1.0) break;
                 int c = g.ord[q];
-                if (fabsf(y[c] - ypred) <= P->dy_link && fabsf(R->z[c] - zh) <= P->dz_link)
+                if (fabsf(ly[c] - ypred) <= P->dy_link && fabsf(lzc[c] - zh) <= P->dz_link)
                     iv_push(side == 0 ? &U : &D, c);
             }
         }
@@ -621,8 +638,8 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
             int u = U.v[a];
             for (int b = 0; b < D.n; b++) {
                 int d = D.v[b];
-                float ey = fmaf(y[u] - y[d], w, y[d]) - yh;
-                float ez = fmaf(R->z[u] - R->z[d], w, R->z[d]) - zh;
+                float ey = fmaf(ly[u] - ly[d], w, ly[d]) - yh;
+                float ez = fmaf(lzc[u] - lzc[d], w, lzc[d]) - zh;
                 float sc = fmaf(ey, ey, ez * ez);
                 if (!(sc < P->s_max_link)) continue;
                 if (bu < 0 || sc < bs || (sc == bs && (u < bu || (u == bu && d < bd)))) {
@@ -634,6 +651,7 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
         R->dn_raw[h] = bd;
     }
     free(U.v); free(D.v);
+    free(qy); free(qz);
 
     /* ---- a4: NeighboursCleaner: keep only mutual links */
     R->up = (int32_t *)malloc(sizeof(int32_t) * nz(n));

@@ -39,6 +39,7 @@ typedef struct {
     float merge_dz, merge_chi2;           /* merger candidate window (cm) and chi2 (5 dof) cut */
     int32_t refit_passes;                 /* Kalman refit passes, alternating direction */
     float refit_inflate;                  /* factor on the previous angular covariance at each pass start */
+    int32_t packed_links;                 /* 1: the link pass sees y, z rounded to 1/256 cm (16-bit packed) */
 } orc_params;
 
 typedef struct {

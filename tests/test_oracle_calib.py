@@ -11,7 +11,10 @@ What pins it to something other than itself:
 * chi2/ndf ~ 1 at the true calibration on clean primaries;
 * invariance of the chi2 under a shift of the reference z (the reference is a
   linearisation point only);
-* the gradient against central finite differences of the chi2.
+* the gradient against central finite differences of the chi2;
+* the derivative with respect to a measurement against twice the weighted
+  smoothed residual of the least-squares solution (the identity the GPU
+  backward pass uses).
 """
 import numpy as np
 import pytest
@@ -174,3 +177,51 @@ def test_gradient_is_linear_in_the_weights(orc, problem):
     _, _, g2 = orc.calib(tr, th_true, weight=w2)
     _, _, g12 = orc.calib(tr, th_true, weight=2 * w1 - w2)
     np.testing.assert_allclose(g12, 2 * g1 - g2, rtol=1e-9, atol=1e-9 * np.abs(g12).max())
+
+
+def test_measurement_derivative_is_twice_the_weighted_smoothed_residual(orc, problem):
+    """The identity the GPU backward pass is built on: d chi2 / d m_k =
+    2 V_k^-1 (m_k - h_k - H Phi_k d*), with d* the least-squares deviation at
+    step 0 (checked against central finite differences of the oracle's chi2
+    in a cluster's y; the chi2 is quadratic in it, so the difference is exact
+    up to rounding)."""
+    import dataclasses
+    ev, r, tr, th_true, th_nom = problem
+    p = orc.default_params()
+    c0 = np.array([np.float32(p["sigma_y"]) ** 2, np.float32(p["sigma_z"]) ** 2, p["c0_snp"], p["c0_tgl"],
+                   p["c0_qpt"]], np.float64)
+    chi2, used, _ = orc.calib(tr, th_true, grad=False)
+    cand = np.nonzero(used)[0][::97][:6]
+    for t in cand:
+        F, h, m, v, c2 = orc.calib_explain(tr, th_true, int(t))
+        n1 = F.shape[0]
+        rows, rhs = [], []
+        mu0 = np.array([m[0, 0] - h[0, 0], m[0, 1] - h[0, 1], 0, 0, 0])
+        for i in range(5):
+            e = np.zeros(5)
+            e[i] = 1 / np.sqrt(c0[i])
+            rows.append(e)
+            rhs.append(mu0[i] / np.sqrt(c0[i]))
+        Phis = [np.eye(5)]
+        for k in range(1, n1):
+            Phis.append(F[k] @ Phis[-1])
+            for e in range(2):
+                rows.append(Phis[-1][e] / np.sqrt(v[k, e]))
+                rhs.append((m[k, e] - h[k, e]) / np.sqrt(v[k, e]))
+        d0, *_ = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)
+        n = n1 - 1
+        for k in (0, n // 2, n - 1):
+            dk = Phis[k] @ d0
+            a_y = 2 * (m[k, 0] - h[k, 0] - dk[0]) / v[k, 0]
+            # step k measures cluster n-1-k of the track's list (inner -> outer)
+            c = int(tr.clus[tr.off[t] + n - 1 - k])
+
+            def f(yc):
+                y = tr.cl_y.copy()
+                y[c] = yc
+                cc, uu, _ = orc.calib(dataclasses.replace(tr, cl_y=y), th_true, grad=False)
+                return cc[t]
+
+            yp, ym = np.float32(tr.cl_y[c] + 1e-2), np.float32(tr.cl_y[c] - 1e-2)   # the binary32 inputs
+            fd = (f(yp) - f(ym)) / (float(yp) - float(ym))
+            assert a_y == pytest.approx(fd, rel=1e-5, abs=1e-6), (t, k)

@@ -161,3 +161,45 @@ def test_empty_and_degenerate_inputs(orc):
     with pytest.raises(ValueError):
         orc.track(np.full(1, 40, np.uint8), np.zeros(1, np.uint8), np.zeros(1, np.float32),
                   np.zeros(1, np.float32), row_x)
+
+
+def _q256(v):
+    """Nearest multiple of 2^-8 (ties to even), computed exactly with
+    Python's rational arithmetic: the decoded 16-bit packed coordinate."""
+    from fractions import Fraction
+    out = np.empty(v.size, np.float32)
+    for i, x in enumerate(np.asarray(v, np.float32)):
+        out[i] = F(float(round(Fraction(float(x)) * 256) / 256))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_packed_link_pass_equals_brute_force_on_rounded_coordinates(orc, seed):
+    """Packed-coordinate variant: the link pass sees y, z rounded to 1/256 cm;
+    the links equal an exhaustive search on the rounded values, and the
+    tracker's other stages still see the full-precision clusters (z output
+    unchanged)."""
+    rng = np.random.default_rng(300 + seed)
+    sector, row, y, z, row_x = _tiny_event(rng, spread=1.2)
+    # coordinates on a 1/512 grid put many values exactly half-way between
+    # two 1/256 steps: the ties-to-even rounding is exercised
+    y = (np.round(y * 512) / 512).astype(np.float32)
+    z = (np.round(z * 512) / 512).astype(np.float32)
+    r = orc.track(sector, row, y, z, row_x, n_sectors=36, params={"packed_links": 1})
+    up, dn = brute_links(sector, row, _q256(y), _q256(z), row_x)
+    assert (up >= 0).sum() > 20
+    np.testing.assert_array_equal(r.up_raw, up)
+    np.testing.assert_array_equal(r.dn_raw, dn)
+    np.testing.assert_array_equal(r.z, z)
+    r0 = orc.track(sector, row, y, z, row_x, n_sectors=36)
+    assert not np.array_equal(r.up_raw, r0.up_raw) or not np.array_equal(r.dn_raw, r0.dn_raw)
+
+
+def test_packed_links_change_few_links_on_a_frame(orc):
+    """On a continuous frame the rounding to 1/256 cm changes few links."""
+    import tpcgen
+    ev = tpcgen.time_frame(seed=31, n_collisions=1, mult_mean=800.0, with_truth=False)
+    a = orc.track_event(ev)
+    b = orc.track_event(ev, params={"packed_links": 1})
+    diff = np.mean((a.up != b.up) | (a.dn != b.dn))
+    assert diff < 2e-3
