@@ -58,6 +58,13 @@ def parse():
     ap.add_argument("--max-coll", type=int, default=100)
     ap.add_argument("--mult", type=float, default=2000.0)
     ap.add_argument("--tune", action="store_true", help="autotune grid and queue settings on the first 8 STFs")
+    ap.add_argument("--group-clusters", type=int, default=32_000_000,
+                    help="stf_batch: clusters per frame group of the graph (without --tune)")
+    ap.add_argument("--n-streams", type=int, default=2, help="stf_batch: concurrent frame groups (without --tune)")
+    ap.add_argument("--no-single-call", action="store_true",
+                    help="stf_batch: skip the one-call-over-all-frames comparison (its workspace holds the batch)")
+    ap.add_argument("--no-packed", action="store_true",
+                    help="stf_batch: full-precision link pass (default: 16-bit packed link coordinates)")
     ap.add_argument("--no-fp64-final", action="store_true",
                     help="stf_batch: binary32 final refit (default: FP64 Joseph covariance and chi2 in the last pass)")
     return ap.parse_args()
@@ -320,11 +327,12 @@ def make_stf_batch(n_stf, max_coll, mult, seed0=1000):
     return cat, off, ncoll
 
 
-def batch_cpu_baseline(cat, off, k, res, fp64):
+def batch_cpu_baseline(cat, off, k, res, fp64, base=0, packed=False):
     """cpu_baseline of the batch: the oracle, single-threaded, on sub-time-frame
     k alone (the smallest of the batch), and the error of the batch's results
     for that frame against it (decisions exact, fit relative to the FP64
-    oracle refit)."""
+    oracle refit).  res: the result holding frame k, whose cluster indices
+    count from cluster `base` of the batch."""
     import numpy as np
 
     import oracle
@@ -332,7 +340,8 @@ def batch_cpu_baseline(cat, off, k, res, fp64):
     a, b = int(off[k]), int(off[k + 1])
     t0 = time.perf_counter()
     r = oracle.track(cat["sector"][a:b], cat["row"][a:b], cat["y"][a:b], cat["zt"][a:b], tpcgen.row_x_f32(),
-                     n_sectors=36, z_max=250.0, continuous=True, bz=0.5, v_drift=tpcgen.V_DRIFT)
+                     n_sectors=36, z_max=250.0, continuous=True, bz=0.5, v_drift=tpcgen.V_DRIFT,
+                     params={"packed_links": int(packed)})
     dt = time.perf_counter() - t0
     fr = res.frame.cpu().numpy()
     idx = np.nonzero(fr == k)[0]
@@ -340,8 +349,8 @@ def batch_cpu_baseline(cat, off, k, res, fp64):
     if idx.size == r.n_tracks and idx.size > 0:
         t_lo, t_hi = int(idx[0]), int(idx[-1]) + 1
         co = res.clus_offset.cpu().numpy()
-        ci = res.clus_index[int(co[t_lo]):int(co[t_hi])].cpu().numpy() - a
-        asg = res.assign[a:b].cpu().numpy()
+        ci = res.clus_index[int(co[t_lo]):int(co[t_hi])].cpu().numpy() - (a - base)
+        asg = res.assign[a - base:b - base].cpu().numpy()
         asg = np.where(asg >= 0, asg - t_lo, -1)
         err["clusters_mismatch"] = int(ci.size != r.tr_clus.size or (ci != r.tr_clus).sum())
         err["assign_mismatch"] = int((asg != r.assign).sum())
@@ -367,8 +376,10 @@ def batch_cpu_baseline(cat, off, k, res, fp64):
 
 
 def run_batch(args, ws, rank, local, pg):
-    """Batched mode: the whole STF batch per step (synchronous call and CUDA
-    graph replay) against the per-STF loop, same outputs."""
+    """Batched mode: the whole sub-time-frame batch per step, tracked as a
+    graph-captured GroupedBatch (frame groups on several streams), against
+    the per-frame loop (one tpc_track call per frame) and one
+    tpc_track_batched call over all frames; all three give the same tracks."""
     import numpy as np
     cat, off, ncoll = make_stf_batch(args.n_stf, args.max_coll, args.mult, seed0=1000 + 100 * rank)
     import torch
@@ -378,36 +389,29 @@ def run_batch(args, ws, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = int(off[-1])
-    if n >= 2**31 - 1:
-        raise SystemExit("batch too large for 32-bit cluster indices")
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in cat.items()}
     dv = {k: v.to(dev) for k, v in host.items()}
     ins = (dv["sector"], dv["row"], dv["y"], dv["zt"])
     row_x = tpcgen.row_x_f32()
     off32 = off.astype(np.int32)
     fp64 = not args.no_fp64_final
-    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=int(fp64))
-    tuned = None
-    if args.tune:
-        k = min(8, args.n_stf)
-        sub_n = int(off[k])
-        sub = tuple(t[:sub_n] for t in ins)
-        tuned = tpc.autotune.autotune(*sub, off32[:k + 1], row_x, base=params,
-                                      log=lambda m: print(m, file=sys.stderr))
-        tpc.autotune.apply(params, tuned["best"])
+    packed = not args.no_packed
+    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=int(fp64), packed_links=int(packed))
     nstf = len(ncoll)
-    trk = tpc.Tracker(n, row_x, continuous=True, params=params, n_frames=nstf)
-    big = int(np.max(np.diff(off)))
-    one = tpc.Tracker(big, row_x, continuous=True, params=params)
     vd, bz = tpcgen.V_DRIFT, 0.5
-
-    def per_frame():
-        ps = []
-        for i in range(nstf):
-            a, b = int(off[i]), int(off[i + 1])
-            r = one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd)
-            ps.append(r.param.clone())
-        return ps
+    log = lambda m: print(m, file=sys.stderr)  # noqa: E731
+    tuned = {}
+    if args.tune:
+        k = min(8, nstf)
+        sub = tuple(t[:int(off[k])] for t in ins)
+        t1 = tpc.autotune.autotune(*sub, off32[:k + 1], row_x, base=params, log=log)
+        tpc.autotune.apply(params, t1["best"])
+        k = min(16, nstf)
+        sub = tuple(t[:int(off[k])] for t in ins)
+        t2 = tpc.autotune.autotune_groups(*sub, off[:k + 1], row_x, params, bz=bz, v_drift=vd, log=log)
+        tuned = {**t1["best"], **t2["best"]}
+    group = {"group_clusters": tuned.get("group_clusters", args.group_clusters),
+             "n_streams": tuned.get("n_streams", args.n_streams)}
 
     def timed(fn, steps):
         torch.cuda.synchronize()
@@ -419,44 +423,70 @@ def run_batch(args, ws, rank, local, pg):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    for _ in range(args.warmup):
-        rb = trk.track_batched(*ins, off32, bz=bz, v_drift=vd)
-    ms_batch = timed(lambda: trk.track_batched(*ins, off32, bz=bz, v_drift=vd), args.steps)
-    rb = trk.track_batched(*ins, off32, bz=bz, v_drift=vd)
-    p_batch = rb.param.cpu().numpy().copy()
-    launches = rb.n_launches
-    run = trk.capture(*ins, off32, bz=bz, v_drift=vd)
-    for _ in range(args.warmup):
-        run.replay()
-    with ClockSampler(local) as clk:
-        ms_graph = timed(run.replay, args.steps)
-    p_graph = run.result().param.cpu().numpy()
-    trk.params.profile = 1                  # one extra pass with stage events, outside the timed regions
-    stage_ms = trk.track_batched(*ins, off32, bz=bz, v_drift=vd).stage_ms
-    trk.params.profile = 0
+    # ---- per-frame loop
+    big = int(np.max(np.diff(off)))
+    one = tpc.Tracker(big, row_x, continuous=True, params=params)
+
+    def per_frame():
+        ps = []
+        for i in range(nstf):
+            a, b = int(off[i]), int(off[i + 1])
+            ps.append(one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd).param.clone())
+        return ps
+
+    for _ in range(min(args.warmup, 1)):
+        per_frame()
+    ms_frame = timed(per_frame, max(1, args.steps // 2))
+    p_frame = torch.cat(per_frame()).cpu().numpy()
     one.params.profile = 1
-    pf_stage_ms = {k: 0.0 for k in stage_ms}
+    pf_stage_ms = {k: 0.0 for k in tpc.abi.STAGES}
     for i in range(nstf):
         a, b = int(off[i]), int(off[i + 1])
         for k, v in one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd).stage_ms.items():
             pf_stage_ms[k] += v
     one.params.profile = 0
-    for _ in range(min(args.warmup, 1)):
-        per_frame()
-    ms_frame = timed(per_frame, max(1, args.steps // 2))
-    p_frame = torch.cat(per_frame()).cpu().numpy()
-    same = bool(np.array_equal(p_frame, p_batch) and np.array_equal(p_graph, p_batch))
+    del one
+    torch.cuda.empty_cache()
+
+    # ---- one tpc_track_batched call over every frame
+    ms_batch, same_batch, stage_ms = None, None, None
+    if not args.no_single_call:
+        trk = tpc.Tracker(n, row_x, continuous=True, params=params, n_frames=nstf)
+        trk.track_batched(*ins, off32, bz=bz, v_drift=vd)
+        ms_batch = timed(lambda: trk.track_batched(*ins, off32, bz=bz, v_drift=vd), max(1, args.steps // 2))
+        same_batch = bool(np.array_equal(trk.track_batched(*ins, off32, bz=bz, v_drift=vd).param.cpu().numpy(),
+                                         p_frame))
+        trk.params.profile = 1
+        stage_ms = trk.track_batched(*ins, off32, bz=bz, v_drift=vd).stage_ms
+        trk.params.profile = 0
+        del trk
+        torch.cuda.empty_cache()
+
+    # ---- grouped graph (the timed headline)
+    gb = tpc.GroupedBatch(*ins, off, row_x, params=params, bz=bz, v_drift=vd, **group)
+    gb.capture()
+    for _ in range(args.warmup):
+        gb.replay()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms_graph = timed(gb.replay, args.steps)
+    res = gb.results()
+    p_graph = torch.cat([r.param for r in res]).cpu().numpy()
+    n_tracks = sum(r.n_tracks for r in res)
+    same = bool(np.array_equal(p_graph, p_frame))
     # end to end: host buffers in, results out
     t0 = time.perf_counter()
+    d2h = 0
     for _ in range(args.steps):
         for k in dv:
             dv[k].copy_(host[k], non_blocking=True)
-        r = trk.track_batched(*ins, off32, bz=bz, v_drift=vd)
-        T = r.n_tracks
-        r.param.cpu(), r.chi2.cpu(), r.assign.cpu()
+        gb.replay()
+        d2h = 0
+        for r in gb.results():
+            r.param.cpu(), r.chi2.cpu(), r.assign.cpu()
+            d2h += r.n_tracks * 6 * 4 + 4 * int(r.assign.numel())
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
-    d2h = rb.n_tracks * 6 * 4 + 4 * n
     if rank != 0:
         return
     line = {
@@ -465,30 +495,36 @@ def run_batch(args, ws, rank, local, pg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{nstf} sub-time-frames of U{{1..{args.max_coll}}} collisions, "
                                f"multiplicity Exp({args.mult:g}), one batch per step",
-                   "clusters": n, "collisions": int(ncoll.sum()), "tracks_found": rb.n_tracks,
-                   "per_frame_ms": ms_frame, "batched_sync_ms": ms_batch, "graph_ms": ms_graph,
+                   "clusters": n, "collisions": int(ncoll.sum()), "tracks_found": n_tracks,
+                   "groups": len(gb.groups), **group,
+                   "graph_ms": ms_graph, "per_frame_ms": ms_frame, "single_call_ms": ms_batch,
                    "speedup_vs_per_frame": ms_frame / ms_graph, "identical_to_per_frame": same,
-                   "tuned": tuned["best"] if tuned else None,
-                   "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
-                   "per_frame_stage_ms": {k: round(v, 3) for k, v in pf_stage_ms.items()}},
+                   "single_call_identical": same_batch, "tuned": tuned or None,
+                   "single_call_stage_ms": {k: round(v, 3) for k, v in stage_ms.items()} if stage_ms else None,
+                   "per_frame_stage_ms": {k: round(v, 3) for k, v in pf_stage_ms.items()},
+                   "final_refit": "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32",
+                   "link_coordinates": "16-bit packed (1/256 cm)" if packed else "fp32",
+                   "l2": "inputs (10 B/cluster) exceed the 126 MB L2; no flush"},
         "e2e": {"value": n / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches * args.steps,
+        "gpu_launches": gb.n_launches * args.steps,
         "clocks": clk.summary(),
     }
-    line["config"]["final_refit"] = "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32"
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = batch_cpu_baseline(cat, off, int(np.argmin(np.diff(off))), rb, fp64)
+        k = int(np.argmin(np.diff(off)))
+        gi = next(i for i, g in enumerate(gb.groups) if g.f0 <= k < g.f1)
+        line["cpu_baseline"] = batch_cpu_baseline(cat, off, k, res[gi], fp64, base=gb.groups[gi].a, packed=packed)
     print(json.dumps(line), flush=True)
 
 
-# binary32 flops per cluster step of the calibration pass, counted from the
-# operation lists in tpc_calib.cu / tpc_fit.cuh: reference helix step 60,
-# deviation propagation 12, covariance transport 100, update 80, calibrated
-# measurement (two B-spline bases, 16-term sums, chain rule) 150; the backward
-# recomputes the forward step and adds the reverse sweep (60) and the gradient
-# scatter (measurement again + 32 products)
-FLOPS_CALIB_FWD = 460
-FLOPS_CALIB_BWD = 460 + 60 + 190
+# binary32 flops per step of the calibration pass, counted from the operation
+# lists in tpc_calib.cu / tpc_fit.cuh: reference helix step 60, deviation
+# propagation 12, covariance transport 100, update 80, calibrated measurement
+# (w B-spline basis 40, 4 x 4 spline sums 64, chain rule 10) 114; the backward
+# recomputes the reference step (60) and the measurement (114), forms the
+# smoothed residual (6), applies the inverse step Jacobians (16) and adds the
+# 4 x 4 x 2 gradient products (70)
+FLOPS_CALIB_FWD = 366
+FLOPS_CALIB_BWD = 266
 
 
 def run_calib(args, ws, rank, local, pg):
@@ -550,6 +586,24 @@ def run_calib(args, ws, rank, local, pg):
     f_ms /= args.steps
     b_ms /= args.steps
     grad = theta.grad.detach().cpu().numpy()
+    # the two kernels alone (no autograd, no status read), CUDA events on the stream
+    th_d = theta.detach()
+    ones = torch.ones(calib.n_tracks, device=dev)
+    c_, used_k, ws_k = calib.forward(th_d, check=False)
+    kf = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fk_ms = bk_ms = 0.0
+    for _ in range(args.steps):
+        kf[0].record(stream)
+        c_, used_k, ws_k = calib.forward(th_d, check=False)
+        kf[1].record(stream)
+        calib.backward(th_d, ones, used_k, ws_k, check=False)
+        kf[2].record(stream)
+        torch.cuda.synchronize()
+        fk_ms += kf[0].elapsed_time(kf[1])
+        bk_ms += kf[1].elapsed_time(kf[2])
+    fk_ms /= args.steps
+    bk_ms /= args.steps
+    calib.check(ws_k)
     # end to end: theta from pinned host memory, chi2 sum and gradient back
     h_theta = theta.detach().cpu().pin_memory()
     t0 = time.perf_counter()
@@ -566,7 +620,9 @@ def run_calib(args, ws, rank, local, pg):
     if rank != 0:
         return
     pk = FP32_PEAK_TFLOPS
-    bw_tf = n_steps * FLOPS_CALIB_BWD / (b_ms * 1e-3) / 1e12
+    dom, t_dom, fl = (("calib_backward", bk_ms, FLOPS_CALIB_BWD) if bk_ms >= fk_ms
+                      else ("calib_forward", fk_ms, FLOPS_CALIB_FWD))
+    bw_tf = n_steps * fl / (t_dom * 1e-3) / 1e12
     line = {
         "metric": "calibration chi2 + adjoint gradient, track clusters/s on 1 B300",
         "value": n_steps / (ms / 1e3), "unit": "track clusters/s", "n_gpus": ws, "steps": args.steps,
@@ -575,9 +631,10 @@ def run_calib(args, ws, rank, local, pg):
         "config": {"workload": f"{args.collisions}-collision calibration frame (v_drift +0.3 %, t0 200 ns, "
                                "36 x 8 x 8 spline map), theta at the nominal calibration",
                    "tracks": T, "tracks_used": int(u.sum()), "pass_steps": n_steps, "forward_ms": f_ms,
-                   "backward_ms": b_ms, "grad_v_t0": grad[:2].tolist(),
+                   "backward_ms": b_ms, "forward_kernel_ms": fk_ms, "backward_kernel_ms": bk_ms,
+                   "grad_v_t0": grad[:2].tolist(),
                    "l2": "clusters (160 MB) and checkpoints exceed the 126 MB L2; no flush"},
-        "roofline": {"bound": "alu", "stage": "calib_backward", "achieved": bw_tf, "peak": pk, "unit": "TFLOP/s",
+        "roofline": {"bound": "alu", "stage": dom, "achieved": bw_tf, "peak": pk, "unit": "TFLOP/s",
                      "frac": bw_tf / pk, "traffic": None,
                      "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"},
         "e2e": {"value": n_steps / e2e_s, "unit": "track clusters/s",

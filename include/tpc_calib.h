@@ -30,9 +30,14 @@
  * 0 sets the deviation from the reference to (m_y - y_ref, m_z - z_ref, 0, 0,
  * 0) with covariance diag(sigma_y^2, sigma_z^2, c0_snp, c0_tgl, c0_qpt) from
  * tpc_params.  A track is left out (used = 0) when its reference reaches
- * |sin(phi)| >= 0.9 at one of its clusters.  The gradient is the reverse sweep of that pass; the forward
- * pass stores the state every 16 steps and the backward pass recomputes each
- * 16-step segment from its checkpoint.
+ * |sin(phi)| >= 0.9 at one of its clusters.  The gradient comes from a
+ * reverse sweep: the forward pass stores the reference state every 16 steps
+ * and the deviation after the last step; the backward pass recomputes each
+ * 16-step segment's reference from its checkpoint and carries the smoothed
+ * deviation back through the inverse step Jacobians, since the derivative of
+ * the chi2 with respect to a measurement is twice its weighted smoothed
+ * residual (the pass is a linear least-squares problem without process
+ * noise).
  *
  * Arithmetic: binary32 (the state with compensated sums), gradient sums in
  * binary64.  All pointers in tpc_calib_tracks and the theta / chi2 / used /

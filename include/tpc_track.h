@@ -85,6 +85,10 @@ typedef struct {
                                     hits from the queue (0: as many as the capacity needs, up to 16) */
     int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
     int32_t profile;             /* 1: record CUDA events on the stream at stage boundaries (tpc_tracks.stage_ms) */
+    int32_t packed_links;        /* 1: the link pass reads y, z as 16-bit packed fields of a fixed-point
+                                    coordinate with step 2^-8 cm (decoded relative to the middle hit), i.e.
+                                    it sees both rounded to the nearest 1/256 cm; other stages see full
+                                    precision.  Needs z_cell >= dz_link + 1/64 and z-cells under 60 cm. */
 } tpc_params;
 
 /* Detector geometry (host memory). */
@@ -194,13 +198,30 @@ int tpc_track_batched(const tpc_params *p, const tpc_geometry *g, float bz, floa
 int tpc_prepare(const tpc_params *p, const tpc_geometry *g, int32_t n_clusters, int32_t n_frames,
                 const int32_t *frame_offsets, void *workspace, size_t ws_bytes, void *stream);
 
+/* Bytes of pinned host staging that tpc_prepare_async needs for n_frames
+ * frames.  Errors: TPC_ERR_ARG. */
+int tpc_prepare_staging_size(int32_t n_frames, size_t *bytes);
+
+/* tpc_prepare without host synchronisation, capturable in a CUDA graph: the
+ * tables, offsets and header are written into host_staging (caller-owned
+ * page-locked host memory of tpc_prepare_staging_size bytes, which must stay
+ * valid and unchanged while the copies may run, i.e. for the lifetime of a
+ * graph that captured them) and copied from there on `stream`.  Lets one
+ * workspace serve several frame groups in turn: prepare group A, track A,
+ * prepare group B, track B on the same stream.  Errors: TPC_ERR_ARG,
+ * TPC_ERR_CAPACITY, TPC_ERR_CUDA. */
+int tpc_prepare_async(const tpc_params *p, const tpc_geometry *g, int32_t n_clusters, int32_t n_frames,
+                      const int32_t *frame_offsets, void *host_staging, size_t staging_bytes, void *workspace,
+                      size_t ws_bytes, void *stream);
+
 /* Enqueue the whole chain (as tpc_track_batched) without any host
  * synchronisation or host copy, so that the call can be captured in a CUDA
- * graph and replayed.  Requires a prior tpc_prepare on the same workspace with
- * the same n_clusters and n_frames.  The host-visible fields of *out are not
- * filled; instead dev_counts (device int32[6]) receives n_tracks,
- * n_tracklets, n_segments, an error code (0, TPC_ERR_DATA or
- * TPC_ERR_CAPACITY), clusters in tracks and start hits found.  params.profile
+ * graph and replayed.  Requires a prior tpc_prepare or tpc_prepare_async on
+ * the same workspace with the same n_clusters and n_frames.  Of the
+ * host-visible fields of *out only n_launches (kernels enqueued) is filled;
+ * instead dev_counts (device int32[6]) receives n_tracks, n_tracklets,
+ * n_segments, an error code (0, TPC_ERR_DATA or TPC_ERR_CAPACITY), clusters
+ * in tracks and start hits found.  params.profile
  * is ignored.  Errors detected on the host: TPC_ERR_ARG, TPC_ERR_CAPACITY,
  * TPC_ERR_CUDA. */
 int tpc_track_async(const tpc_params *p, const tpc_geometry *g, float bz, float v_drift, const tpc_clusters *cl,

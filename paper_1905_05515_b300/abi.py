@@ -31,7 +31,7 @@ class TpcParams(C.Structure):
                 ("z_cell", C.c_float),
                 ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32),
                 ("queue_blocks_per_sm", C.c_int32), ("fp64_final", C.c_int32),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("packed_links", C.c_int32)]
 
 
 class TpcGeometry(C.Structure):
@@ -76,7 +76,7 @@ STAGES = ("prep", "bin", "neighbours", "clean_start", "tracklets", "select", "me
 
 
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
-            "tpc_track_batched", "tpc_prepare", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
+            "tpc_track_batched", "tpc_prepare", "tpc_prepare_staging_size", "tpc_prepare_async", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
             "tpc_error_string", "tpc_calib_workspace_size", "tpc_calib_forward", "tpc_calib_backward",
             "tpc_calib_status")
 
@@ -107,6 +107,10 @@ def lib(build_if_missing: bool = True):
                                         C.c_size_t, C.POINTER(TpcTracks), C.c_void_p]
         L.tpc_prepare.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int32, C.c_int32,
                                   C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.tpc_prepare_staging_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
+        L.tpc_prepare_async.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int32, C.c_int32,
+                                        C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                                        C.c_void_p]
         L.tpc_track_async.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,
                                       C.POINTER(TpcClusters), C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(TpcTracks),
                                       C.c_void_p, C.c_void_p]

@@ -2,7 +2,10 @@
 
 * y_bins, z_cell -- granularity of the per-row grid (tile shape of the
   cluster binning and of every window search);
-* queue_blocks_per_sm -- width of the TrackletConstructor work queue.
+* queue_blocks_per_sm -- width of the TrackletConstructor work queue;
+* group_clusters, n_streams -- granularity of a graph-captured batch of
+  sub-time-frames (frames per launch group) and how many groups run
+  concurrently (GroupedBatch).
 
 Every candidate runs the given (batched) input with CUDA events; the fastest
 median wins.  Results are identical for every candidate (the searches are
@@ -18,9 +21,11 @@ import numpy as np
 import torch
 
 from . import abi
+from .batch import GroupedBatch
 from .tracker import Tracker
 
 DEFAULT_SPACE = {"y_bins": (4, 8, 12), "z_cell": (3.5, 5.0, 7.0), "queue_blocks_per_sm": (0, 6, 12)}
+GROUP_SPACE = {"group_clusters": (0, 8_000_000, 16_000_000, 32_000_000, 64_000_000), "n_streams": (1, 2, 3)}
 
 
 def autotune(sector, row, y, zt, frame_offsets, row_x, n_sectors=36, z_max=250.0, continuous=True, bz=0.5,
@@ -65,6 +70,38 @@ def autotune(sector, row, y, zt, frame_offsets, row_x, n_sectors=36, z_max=250.0
         if log:
             log(f"autotune {cfg} {ms:.3f} ms")
     trackers.clear()
+    best_cfg, best_ms = min(table, key=lambda t: t[1])
+    return {"best": best_cfg, "ms": best_ms, "table": table}
+
+
+def autotune_groups(sector, row, y, zt, frame_offsets, row_x, params: abi.TpcParams, n_sectors=36, z_max=250.0,
+                    continuous=True, bz=0.5, v_drift=2.58, space: dict | None = None, reps: int = 3,
+                    log=None) -> dict:
+    """Time graph replays of GroupedBatch for every (group_clusters,
+    n_streams) of `space` on this input; same return shape as autotune."""
+    space = space or GROUP_SPACE
+    keys = list(space)
+    table = []
+    for combo in itertools.product(*(space[k] for k in keys)):
+        cfg = dict(zip(keys, combo))
+        gb = GroupedBatch(sector, row, y, zt, frame_offsets, row_x, params=params, n_sectors=n_sectors,
+                          z_max=z_max, continuous=continuous, bz=bz, v_drift=v_drift, **cfg)
+        gb.capture()
+        gb.replay()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gb.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        del gb
+        torch.cuda.empty_cache()
+        ms = statistics.median(times)
+        table.append((cfg, ms))
+        if log:
+            log(f"autotune {cfg} {ms:.3f} ms")
     best_cfg, best_ms = min(table, key=lambda t: t[1])
     return {"best": best_cfg, "ms": best_ms, "table": table}
 

@@ -8,14 +8,15 @@
 // One thread per track.  The forward kernel carries the reference helix (the
 // tracker's output state) out to the outermost cluster, then runs the inward
 // Kalman pass on the deviation from it and stores the pass state every
-// TPC_CALIB_CKPT_STEPS steps.  The backward kernel walks the segments from the
-// vertex end back: it recomputes one segment from its checkpoint into local
-// memory (Jacobian entries, gain, inverse innovation covariance, innovation
-// of every step), then sweeps it in reverse with the adjoint recursion
-//   a_k = 2 W_k r_k + K_k^T lam_k        (d chi2 / d measurement k)
-//   lam_{k-1} = F_k^T (lam_k - H^T a_k)  (d chi2 / d deviation before step k)
-// and scatters a_k dm_k/dtheta into the gradient: the spline part through
-// block-private binary64 shared-memory sums, v and t0 through per-track
+// TPC_CALIB_CKPT_STEPS steps and its final deviation.  The backward kernel
+// walks the segments from the vertex end back: it recomputes one segment's
+// reference from its checkpoint into local memory (Jacobian entries and
+// reference position of every step), then sweeps the smoothed deviation back
+// through the inverse Jacobians; the derivative of the chi2 with respect to
+// each measurement is twice its weighted smoothed residual (k_calib_bwd
+// states why), and a_k dm_k/dtheta goes into the gradient: the spline part through
+// per-thread register sums over the clusters that share a spline support,
+// added to the binary64 global sums, v and t0 through per-track
 // binary32 sums added to block-private binary64 sums, all flushed once per
 // block into binary64 global sums.  Tolerance path: multiply-add
 // contraction allowed.
@@ -33,7 +34,7 @@ namespace {
 
 constexpr int NSPL = TPC_CALIB_NSPL;
 constexpr int SEG = TPC_CALIB_CKPT_STEPS;
-constexpr int CK_FLOATS = 32;          // x, sector, p[5], pl[5], dp[5], C[15]
+constexpr int CK_FLOATS = 12;          // reference: x, sector, p[5], pl[5]
 constexpr int CALIB_BLOCK = 128;
 constexpr int MAX_SPL_SECTORS = 36;
 // workspace: a 256-byte header (int32 error flags at offset 0, bit 0: invalid
@@ -64,6 +65,7 @@ struct CalibArgs {
     const float* dchi2;
     double* grad;
     float4* ckpt;
+    float4* dfin;                       // [T][2]: deviation after the vertex step
     int32_t* err;
     float rowx[256];
 };
@@ -129,16 +131,37 @@ struct Meas {
     float Bu[4], Bw[4];
 };
 
-__device__ __forceinline__ void measure(const CalibArgs& A, const float* __restrict__ spl, int c, float tc, Meas& m)
+// per-row u-basis table in shared memory: ub[4 r + a] the four non-zero
+// basis values at row r's u, ui[r] the index of the first
+struct RowBasis {
+    float* ub;
+    int* ui;
+};
+
+__device__ __forceinline__ void load_row_basis(const CalibArgs& A, RowBasis rb)
+{
+    for (int r = threadIdx.x; r < A.nr; r += blockDim.x) {
+        float B[4], dB[4];
+        rb.ui[r] = bspline((A.rowx[r] - A.x_first) * A.inv_dx, B, dB);
+#pragma unroll
+        for (int a = 0; a < 4; a++) rb.ub[4 * r + a] = B[a];
+    }
+}
+
+__device__ __forceinline__ void measure(const CalibArgs& A, const float* __restrict__ spl, RowBasis rb, int c,
+                                        float tc, Meas& m)
 {
     const int s = A.cs[c];
+    const int row = A.cr[c];
     const float v = A.theta[0], t0 = A.theta[1];
     const float tau = (A.ct[c] - tc) - t0;
     const float zl = A.zmax - v * tau;
     const float w = zl / A.zmax;
     const float dwdz = (w > 0.0f && w < 1.0f) ? 1.0f / A.zmax : 0.0f;
-    float dBu[4], dBw[4];
-    m.i0 = bspline((A.rowx[A.cr[c]] - A.x_first) * A.inv_dx, m.Bu, dBu);
+    float dBw[4];
+    m.i0 = rb.ui[row];
+#pragma unroll
+    for (int a = 0; a < 4; a++) m.Bu[a] = rb.ub[4 * row + a];
     m.j0 = bspline(w, m.Bw, dBw);
     const float* cc = spl + (s * NSPL * NSPL + m.i0 * NSPL + m.j0) * 2;
     float dy = 0.0f, dz = 0.0f, dyw = 0.0f, dzw = 0.0f;
@@ -280,42 +303,26 @@ __device__ __forceinline__ bool filter_step(PassState& S, StepRec& R, float my, 
 
 __device__ __forceinline__ void save_ckpt(float4* dst, const PassState& S)
 {
-    float v[CK_FLOATS];
-    v[0] = S.x;
-    v[1] = __int_as_float(S.sec);
-#pragma unroll
-    for (int i = 0; i < 5; i++) {
-        v[2 + i] = S.p[i];
-        v[7 + i] = S.pl[i];
-        v[12 + i] = S.dp[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 15; i++) v[17 + i] = S.C[i];
-#pragma unroll
-    for (int q = 0; q < CK_FLOATS / 4; q++) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    dst[0] = make_float4(S.x, __int_as_float(S.sec), S.p[0], S.p[1]);
+    dst[1] = make_float4(S.p[2], S.p[3], S.p[4], S.pl[0]);
+    dst[2] = make_float4(S.pl[1], S.pl[2], S.pl[3], S.pl[4]);
 }
 
 __device__ __forceinline__ void load_ckpt(const float4* src, PassState& S)
 {
-    float v[CK_FLOATS];
-#pragma unroll
-    for (int q = 0; q < CK_FLOATS / 4; q++) {
-        const float4 t = src[q];
-        v[4 * q] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
-    S.x = v[0];
-    S.sec = __float_as_int(v[1]);
-#pragma unroll
-    for (int i = 0; i < 5; i++) {
-        S.p[i] = v[2 + i];
-        S.pl[i] = v[7 + i];
-        S.dp[i] = v[12 + i];
-    }
-#pragma unroll
-    for (int i = 0; i < 15; i++) S.C[i] = v[17 + i];
+    const float4 a = src[0], b = src[1], c = src[2];
+    S.x = a.x;
+    S.sec = __float_as_int(a.y);
+    S.p[0] = a.z;
+    S.p[1] = a.w;
+    S.p[2] = b.x;
+    S.p[3] = b.y;
+    S.p[4] = b.z;
+    S.pl[0] = b.w;
+    S.pl[1] = c.x;
+    S.pl[2] = c.y;
+    S.pl[3] = c.z;
+    S.pl[4] = c.w;
 }
 
 // checkpoint slot of track r: clus_offset[r] / SEG + r (slots of consecutive
@@ -376,7 +383,11 @@ __device__ __forceinline__ void load_spline(const CalibArgs& A, float* spl)
 __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
 {
     __shared__ float spl[MAX_SPL_SECTORS * NSPL * NSPL * 2];
+    __shared__ float ub[4 * 256];
+    __shared__ int ui[256];
+    const RowBasis rb{ub, ui};
     load_spline(A, spl);
+    load_row_basis(A, rb);
     __syncthreads();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < A.T; r += gridDim.x * blockDim.x) {
         int off, n;
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
         float4* ck = A.ckpt + ckpt_base(A, r) * (CK_FLOATS / 4);
         if (ok) {
             Meas m;
-            measure(A, spl, A.clus[off + n - 1], tc, m);
+            measure(A, spl, rb, A.clus[off + n - 1], tc, m);
             S.dp[0] = (m.my - S.p[0]) - S.pl[0];
             S.dp[1] = (m.mz - S.p[1]) - S.pl[1];
             S.dp[2] = S.dp[3] = S.dp[4] = 0.0f;
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
                     const int c = A.clus[off + n - 1 - k];
                     ok = ref_step(A, S, A.cs[c], A.rowx[A.cr[c]], R);
                     if (!ok) break;
-                    measure(A, spl, c, tc, m);
+                    measure(A, spl, rb, c, tc, m);
                     my = m.my;
                     mz = m.mz;
                     vy = A.vy;
@@ -421,44 +432,114 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
                 ok = filter_step(S, R, my, mz, vy, vz, chi2);
                 if (ok && k % SEG == 0 && k < n) save_ckpt(ck + (k / SEG) * (CK_FLOATS / 4), S);
             }
+            if (ok) {
+                A.dfin[2 * (int64_t)r] = make_float4(S.dp[0], S.dp[1], S.dp[2], S.dp[3]);
+                A.dfin[2 * (int64_t)r + 1] = make_float4(S.dp[4], 0.0f, 0.0f, 0.0f);
+            }
         }
         A.chi2[r] = ok ? chi2 : 0.0f;
         A.used[r] = ok ? 1 : 0;
     }
 }
 
-__device__ __forceinline__ void scatter_grad(const CalibArgs& A, const float* spl, double* gspl, int c, float tc,
-                                             float a0, float a1, float& gv, float& gt0)
+// Spline-gradient sums of one thread: the 4 x 4 (dy, dz) coefficients of
+// the current support (sector, first u index, first w index) are summed in
+// registers and added to the binary64 global gradient only when the support
+// changes (consecutive clusters of a track mostly share it).
+struct GradAcc {
+    int key;             // s * 64 + i0 * 8 + j0, -1: empty
+    float g[32];         // [(i * 4 + j) * 2 + k]
+};
+
+__device__ __forceinline__ void flush(GradAcc& G, double* grad)
 {
-    Meas m;
-    measure(A, spl, c, tc, m);
-    gv += a0 * m.dy_v + a1 * m.dz_v;
-    gt0 += a0 * m.dy_t0 + a1 * m.dz_t0;
-    double* g = gspl + (m.s * NSPL * NSPL + m.i0 * NSPL + m.j0) * 2;
-    const float ay = -a0, az = -a1 * m.sgn;
+    if (G.key < 0) return;
+    const int s = G.key >> 6, i0 = (G.key >> 3) & 7, j0 = G.key & 7;
+    double* g = grad + 2 + (s * NSPL * NSPL + i0 * NSPL + j0) * 2;
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const float b = m.Bu[i] * m.Bw[j];
-            atomicAdd(&g[(i * NSPL + j) * 2], (double)(ay * b));
-            atomicAdd(&g[(i * NSPL + j) * 2 + 1], (double)(az * b));
+            atomicAdd(&g[(i * NSPL + j) * 2], (double)G.g[(i * 4 + j) * 2]);
+            atomicAdd(&g[(i * NSPL + j) * 2 + 1], (double)G.g[(i * 4 + j) * 2 + 1]);
         }
+#pragma unroll
+    for (int q = 0; q < 32; q++) G.g[q] = 0.0f;
+    G.key = -1;
 }
 
+// adds a0 dm_y/dtheta + a1 dm_z/dtheta of measurement m
+__device__ __forceinline__ void scatter_grad(const CalibArgs& A, const float* spl, RowBasis rb, GradAcc& G,
+                                             const Meas& m, float a0, float a1, float& gv, float& gt0, double* grad)
+{
+    gv += a0 * m.dy_v + a1 * m.dz_v;
+    gt0 += a0 * m.dy_t0 + a1 * m.dz_t0;
+    const int key = m.s * 64 + m.i0 * 8 + m.j0;
+    if (key != G.key) {
+        flush(G, grad);
+        G.key = key;
+    }
+    const float ay = -a0, az = -a1 * m.sgn;      // m_y = y - dy, m_z = sgn (zl - dz)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float by = ay * m.Bu[i], bz = az * m.Bu[i];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            G.g[(i * 4 + j) * 2] += by * m.Bw[j];
+            G.g[(i * 4 + j) * 2 + 1] += bz * m.Bw[j];
+        }
+    }
+}
+
+// reference of one step for the backward sweep: the step's Jacobians and
+// the reference (y, z) as compensated pairs
+struct BackRec {
+    float j00, j10, j20, j22;
+    HelixJac h;
+    float y, yl, z, zl;
+};
+
+// v <- F^-1 v for F = Jh Jr: back substitution through the unit upper
+// triangular helix Jacobian, then the lower triangular rotation Jacobian
+__device__ __forceinline__ void inv_step(const BackRec& R, float* v)
+{
+    const float u4 = v[4], u3 = v[3];
+    const float u2 = v[2] - R.h.f * u4;
+    const float u1 = v[1] - R.h.c * u2 - R.h.d * u3 - R.h.e * u4;
+    const float u0 = v[0] - R.h.a * u2 - R.h.b * u4;
+    v[0] = u0 / R.j00;
+    v[1] = u1 - R.j10 * v[0];
+    v[2] = (u2 - R.j20 * v[0]) / R.j22;
+    v[3] = u3;
+    v[4] = u4;
+}
+
+// The pass is a linear least-squares problem in the deviation at step 0
+// (prior at step 0, no process noise), its chi2 the minimum of that problem.
+// By the envelope theorem the derivative of the minimum with respect to a
+// cluster measurement m_k is the partial derivative at the optimum:
+//   d chi2 / d m_k = 2 V_k^-1 (m_k - h_k - H dev*_k),
+// with dev*_k the smoothed deviation.  Without process noise the smoothed
+// track is deterministic: dev*_{k-1} = F_k^-1 dev*_k, starting from the
+// filtered deviation after the last (vertex) step.  Step 0 is the prior
+// centred on the outermost measurement, which enters the same way with
+// V_0 = diag(sigma_y^2, sigma_z^2).  The backward kernel therefore
+// recomputes only the reference of each segment from its checkpoint (no
+// covariance work) and sweeps the smoothed deviation back.
 __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
 {
-    // dynamic shared memory: binary64 spline-gradient sums, then the spline
-    extern __shared__ double smem[];
+    // dynamic shared memory: the spline, then the per-row u-basis table
+    extern __shared__ float smem[];
     __shared__ double gvt[2];
     const int nc = A.ns * NSPL * NSPL * 2;
-    double* gspl = smem;
-    float* spl = reinterpret_cast<float*>(smem + nc);
+    float* spl = smem;
+    const RowBasis rb{spl + nc, reinterpret_cast<int*>(spl + nc + 4 * 256)};
     load_spline(A, spl);
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) gspl[i] = 0.0;
+    load_row_basis(A, rb);
     if (threadIdx.x < 2) gvt[threadIdx.x] = 0.0;
     __syncthreads();
-    StepRec rec[SEG];
+    const float ivy = 1.0f / A.vy, ivz = 1.0f / A.vz;
+    BackRec rec[SEG];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < A.T; r += gridDim.x * blockDim.x) {
         if (!A.used_in[r]) continue;
         const float wr = A.dchi2[r];
@@ -466,66 +547,71 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
         if (wr == 0.0f || !track_ok(A, r, off, n) || n < 1) continue;
         const float tc = A.tcoll[r];
         const float4* ck = A.ckpt + ckpt_base(A, r) * (CK_FLOATS / 4);
-        float lam[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float4 d0 = A.dfin[2 * (int64_t)r], d1 = A.dfin[2 * (int64_t)r + 1];
+        float dev[5] = {d0.x, d0.y, d0.z, d0.w, d1.x};
         float gv = 0.0f, gt0 = 0.0f;
+        GradAcc G;
+        G.key = -1;
+#pragma unroll
+        for (int q = 0; q < 32; q++) G.g[q] = 0.0f;
         const int nseg = (n + SEG - 1) / SEG;
+        bool ok = true;
+        float hy = 0.0f, hyl = 0.0f, hz = 0.0f, hzl = 0.0f;
         for (int sgi = nseg - 1; sgi >= 0; sgi--) {
             PassState S;
             load_ckpt(ck + sgi * (CK_FLOATS / 4), S);
+            hy = S.p[0];
+            hyl = S.pl[0];
+            hz = S.p[1];
+            hzl = S.pl[1];
             const int k0 = sgi * SEG + 1, k1 = min(sgi * SEG + SEG, n);
-            float chi2 = 0.0f;
-            bool ok = true;
             for (int k = k0; k <= k1; k++) {
-                StepRec& R = rec[k - k0];
-                float my, mz, vy, vz;
+                BackRec& R = rec[k - k0];
+                StepRec J;
                 if (k < n) {
                     const int c = A.clus[off + n - 1 - k];
-                    ok = ok && ref_step(A, S, A.cs[c], A.rowx[A.cr[c]], R);
-                    Meas m;
-                    measure(A, spl, c, tc, m);
-                    my = m.my;
-                    mz = m.mz;
-                    vy = A.vy;
-                    vz = A.vz;
+                    ok = ok && ref_step(A, S, A.cs[c], A.rowx[A.cr[c]], J);
                 } else {
-                    ok = ok && vertex_step(A, S, R);
-                    my = mz = 0.0f;
-                    vy = vz = A.vtx;
+                    ok = ok && vertex_step(A, S, J);
                 }
-                ok = ok && filter_step(S, R, my, mz, vy, vz, chi2);
+                R.j00 = J.j00;
+                R.j10 = J.j10;
+                R.j20 = J.j20;
+                R.j22 = J.j22;
+                R.h = J.h;
+                R.y = S.p[0];
+                R.yl = S.pl[0];
+                R.z = S.p[1];
+                R.zl = S.pl[1];
             }
-            if (!ok) atomicOr(A.err, 2);   // the forward pass succeeded on the same data
             for (int k = k1; k >= k0; k--) {
-                const StepRec& R = rec[k - k0];
-                float a0 = 2.0f * (R.W[0] * R.r[0] + R.W[1] * R.r[1]);
-                float a1 = 2.0f * (R.W[1] * R.r[0] + R.W[2] * R.r[1]);
-#pragma unroll
-                for (int i = 0; i < 5; i++) {
-                    a0 += R.K[2 * i] * lam[i];
-                    a1 += R.K[2 * i + 1] * lam[i];
+                const BackRec& R = rec[k - k0];
+                if (k < n) {
+                    const int c = A.clus[off + n - 1 - k];
+                    Meas m;
+                    measure(A, spl, rb, c, tc, m);
+                    const float r0 = ((m.my - R.y) - R.yl) - dev[0];
+                    const float r1 = ((m.mz - R.z) - R.zl) - dev[1];
+                    scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * ivz * r1, gv, gt0, A.grad);
                 }
-                // mu = lam - H^T a; lam = Jr^T Jh^T mu
-                const float m0 = lam[0] - a0, m1 = lam[1] - a1, m2 = lam[2], m3 = lam[3], m4 = lam[4];
-                const float n0 = m0, n1 = m1;
-                const float n2 = m2 + R.h.a * m0 + R.h.c * m1;
-                const float n3 = m3 + R.h.d * m1;
-                const float n4 = m4 + R.h.b * m0 + R.h.e * m1 + R.h.f * m2;
-                lam[0] = R.j00 * n0 + R.j10 * n1 + R.j20 * n2;
-                lam[1] = n1;
-                lam[2] = R.j22 * n2;
-                lam[3] = n3;
-                lam[4] = n4;
-                if (k < n) scatter_grad(A, spl, gspl, A.clus[off + n - 1 - k], tc, wr * a0, wr * a1, gv, gt0);
+                inv_step(R, dev);
             }
         }
-        // step 0: the deviation was set from the outermost measurement
-        scatter_grad(A, spl, gspl, A.clus[off + n - 1], tc, wr * lam[0], wr * lam[1], gv, gt0);
+        if (!ok) atomicOr(A.err, 2);       // the forward pass succeeded on the same data
+        // step 0: the prior centred on the outermost measurement
+        {
+            const int c = A.clus[off + n - 1];
+            Meas m;
+            measure(A, spl, rb, c, tc, m);
+            const float r0 = ((m.my - hy) - hyl) - dev[0];
+            const float r1 = ((m.mz - hz) - hzl) - dev[1];
+            scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * ivz * r1, gv, gt0, A.grad);
+        }
+        flush(G, A.grad);
         atomicAdd(&gvt[0], (double)gv);
         atomicAdd(&gvt[1], (double)gt0);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nc; i += blockDim.x)
-        if (gspl[i] != 0.0) atomicAdd(&A.grad[2 + i], gspl[i]);
     if (threadIdx.x < 2 && gvt[threadIdx.x] != 0.0) atomicAdd(&A.grad[threadIdx.x], gvt[threadIdx.x]);
 }
 
@@ -575,6 +661,8 @@ int fill_args(const tpc_params* p, const tpc_geometry* g, float bz, float v_nomi
 }
 
 size_t ckpt_slots(int32_t T, int64_t ncl) { return (size_t)(ncl / SEG) + (size_t)T + 1; }
+// workspace: header, checkpoints (CK_FLOATS per slot), final deviations (8 floats per track)
+size_t dfin_offset(int32_t T, int64_t ncl) { return HDR_BYTES + ckpt_slots(T, ncl) * CK_FLOATS * sizeof(float); }
 
 int calib_grid(int T)
 {
@@ -589,7 +677,7 @@ extern "C" {
 int tpc_calib_workspace_size(const tpc_geometry* g, int32_t n_tracks, int64_t n_clusters, size_t* bytes)
 {
     if (!g || !bytes || n_tracks < 0 || n_clusters < 0 || n_clusters > (int64_t)INT32_MAX) return TPC_ERR_ARG;
-    *bytes = HDR_BYTES + ckpt_slots(n_tracks, n_clusters) * CK_FLOATS * sizeof(float);
+    *bytes = dfin_offset(n_tracks, n_clusters) + (size_t)n_tracks * 8 * sizeof(float);
     return TPC_OK;
 }
 
@@ -608,6 +696,7 @@ int tpc_calib_forward(const tpc_params* p, const tpc_geometry* g, float bz, floa
     if (cudaMemsetAsync(workspace, 0, HDR_BYTES, st) != cudaSuccess) return TPC_ERR_CUDA;
     A.err = static_cast<int32_t*>(workspace);
     A.ckpt = reinterpret_cast<float4*>(static_cast<char*>(workspace) + HDR_BYTES);
+    A.dfin = reinterpret_cast<float4*>(static_cast<char*>(workspace) + dfin_offset(A.T, A.ncl));
     A.chi2 = chi2;
     A.used = used;
     if (A.T == 0) return TPC_OK;
@@ -632,11 +721,12 @@ int tpc_calib_backward(const tpc_params* p, const tpc_geometry* g, float bz, flo
     char* ws = static_cast<char*>(const_cast<void*>(workspace));
     A.err = reinterpret_cast<int32_t*>(ws);
     A.ckpt = reinterpret_cast<float4*>(ws + HDR_BYTES);
+    A.dfin = reinterpret_cast<float4*>(ws + dfin_offset(A.T, A.ncl));
     A.used_in = used;
     A.dchi2 = dchi2;
     A.grad = grad;
     if (A.T == 0) return TPC_OK;
-    const size_t smem = (size_t)TPC_CALIB_N_THETA(A.ns) * (sizeof(double) + sizeof(float));
+    const size_t smem = (size_t)TPC_CALIB_N_THETA(A.ns) * sizeof(float) + 256 * (4 * sizeof(float) + sizeof(int));
     if (cudaFuncSetAttribute(k_calib_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return TPC_ERR_CUDA;
     k_calib_bwd<<<calib_grid(A.T), CALIB_BLOCK, smem, st>>>(A);

@@ -47,7 +47,7 @@ struct Layout {
     uint32_t magic;
     int32_t n, ns, nr, np, nzmax, ntcap, mnzmax, ny, nframes;
     int64_t ncells;                    // grid cell capacity (all frames)
-    size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, ids, plane;
+    size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, yzp, ids, plane;
     size_t upr, dnr, up, dn, starts;
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
@@ -140,6 +140,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.cstart = take(4 * (L.ncells + 1));
     L.scan = take(4 * scan_aux_elems(scan_max));
     L.yz = take(8 * N);
+    L.yzp = p->packed_links ? take(4 * N) : 0;
     L.ids = take(4 * N);
     L.plane = take(4 * N);
     L.upr = take(4 * N);
@@ -339,7 +340,7 @@ __global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __res
 
 // One thread: per-frame z grids inside the cell budget, the merger grid.
 __global__ void k_grid_setup(Frame* f, FrameGrid* fg, int nframes, int np, int ny, float z_cell, int nzmax,
-                             long long cell_cap, float merge_cell, int mnzmax)
+                             long long cell_cap, float merge_cell, int mnzmax, int packed)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     f->ny = ny;
@@ -366,6 +367,8 @@ __global__ void k_grid_setup(Frame* f, FrameGrid* fg, int nframes, int np, int n
             span = fkey_inv(fg[i].zmax_key) - zmin;
         }
         const float cs = fmaxf(z_cell, span * 1.001f / (float)max(nz - 1, 1));
+        // packed link coordinates are unwrapped within 128 cm of the hit
+        if (packed && !(cs < 60.0f)) f->err = TPC_ERR_CAPACITY;
         fg[i].zmin = zmin;
         fg[i].inv_cs = 1.0f / cs;
         fg[i].nz = nz;
@@ -411,16 +414,33 @@ __global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t*
     }
 }
 
+// Packed link coordinates: a coordinate v is the fixed-point integer
+// q = rint(v * 256) (step 2^-8 cm, exact in binary32 for |v| < 2^16 cm); the
+// packed word holds the low 16 bits of q_y and q_z.  A reader recovers q from
+// its low bits and a reference q_ref within 2^15 steps (128 cm): the
+// neighbours of a hit lie within three grid cells of it.
+__device__ __forceinline__ int fixq(float v) { return __float2int_rn(v * 256.0f); }
+__device__ __forceinline__ float unfixq(int q) { return (float)q * 0.00390625f; }
+__device__ __forceinline__ uint32_t pack_yz(float y, float z)
+{
+    return ((uint32_t)fixq(y) & 0xFFFFu) | ((uint32_t)fixq(z) << 16);
+}
+__device__ __forceinline__ int unwrap16(uint32_t lo, int qref)
+{
+    return qref + (int)(int16_t)(uint16_t)(lo - (uint32_t)qref);
+}
+
 __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
                           const float* __restrict__ y, const float* __restrict__ zlin, const uint16_t* __restrict__ cfr,
                           int nr, int np, const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
                           const uint32_t* __restrict__ slot, float2* __restrict__ yz, int32_t* __restrict__ ids,
-                          uint32_t* __restrict__ plane, const Frame* __restrict__ f)
+                          uint32_t* __restrict__ plane, const Frame* __restrict__ f, uint32_t* __restrict__ yzp)
 {
     if (f->err) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pos = cstart[cell[i]] + slot[i];
         yz[pos] = make_float2(y[i], zlin[i]);
+        if (yzp) yzp[pos] = pack_yz(y[i], zlin[i]);
         ids[pos] = i;
         plane[pos] = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
     }
@@ -455,11 +475,14 @@ __device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstar
 // ---------------------------------------------------------------------------
 constexpr int MAXD = 8;
 
+// PACKED: the pass reads candidates from the 16-bit packed words and sees
+// every coordinate, the middle hit's too, rounded to the nearest 1/256 cm.
+template <bool PACKED>
 __global__ void __launch_bounds__(256) k_neighbours(
     int n, int nr, int ns, int np, const float* __restrict__ rowtab, const float2* __restrict__ yz,
     const int32_t* __restrict__ ids, const uint32_t* __restrict__ plane, const uint32_t* __restrict__ cstart,
     const Frame* __restrict__ f, const FrameGrid* __restrict__ fg, float DY, float DZ, float SMAX,
-    int32_t* __restrict__ upr, int32_t* __restrict__ dnr)
+    int32_t* __restrict__ upr, int32_t* __restrict__ dnr, const uint32_t* __restrict__ yzp)
 {
     if (f->err) return;
     const int ny = f->ny;
@@ -473,7 +496,19 @@ __global__ void __launch_bounds__(256) k_neighbours(
         if (r >= 1 && r <= nr - 2) {
             const FrameGrid G = fg[fr];
             const float2 ph = yz[h];
-            const float yh = ph.x, zh = ph.y;
+            float yh = ph.x, zh = ph.y;
+            int qyh = 0, qzh = 0;
+            if (PACKED) {
+                qyh = fixq(yh);
+                qzh = fixq(zh);
+                yh = unfixq(qyh);
+                zh = unfixq(qzh);
+            }
+            auto coord = [&](int q) -> float2 {
+                if (!PACKED) return yz[q];
+                const uint32_t wd = yzp[q];
+                return make_float2(unfixq(unwrap16(wd & 0xFFFFu, qyh)), unfixq(unwrap16(wd >> 16, qzh)));
+            };
             const float yu_pred = yh * rowtab[r * ROWTAB + 1];
             const float yd_pred = yh * rowtab[r * ROWTAB + 2];
             const float w = rowtab[r * ROWTAB + 3];
@@ -487,7 +522,7 @@ __global__ void __launch_bounds__(256) k_neighbours(
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 for (int q = rd.b[k]; q < rd.e[k]; q++) {
-                    const float2 pq = yz[q];
+                    const float2 pq = coord(q);
                     if (fabsf(pq.x - yd_pred) <= DY && fabsf(pq.y - zh) <= DZ) {
                         if (ndn < MAXD) dl[ndn++] = q;
                         else overflow = true;
@@ -497,12 +532,12 @@ __global__ void __launch_bounds__(256) k_neighbours(
 #pragma unroll
                 for (int ku = 0; ku < 3; ku++)
                     for (int u = ru.b[ku]; u < ru.e[ku]; u++) {
-                        const float2 pu = yz[u];
+                        const float2 pu = coord(u);
                         const float yu = pu.x, zu = pu.y;
                         if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
                         const int idu = ids[u];
                         auto consider = [&](int d) {
-                            const float2 pd = yz[d];
+                            const float2 pd = coord(d);
                             const float yd = pd.x, zd = pd.y;
                             const float ey = __fmaf_rn(yu - yd, w, yd) - yh;
                             const float ez = __fmaf_rn(zu - zd, w, zd) - zh;
@@ -518,7 +553,7 @@ __global__ void __launch_bounds__(256) k_neighbours(
                         } else {
                             for (int k = 0; k < 3; k++)
                                 for (int d = rd.b[k]; d < rd.e[k]; d++) {
-                                    const float2 pd = yz[d];
+                                    const float2 pd = coord(d);
                                     if (fabsf(pd.x - yd_pred) <= DY && fabsf(pd.y - zh) <= DZ) consider(d);
                                 }
                         }
@@ -1261,6 +1296,8 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
     if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0) return TPC_ERR_ARG;
     if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
+    // packed coordinates are off by up to 2^-9 cm: the cell must still cover the window
+    if (p->packed_links && !(p->z_cell >= p->dz_link + 1.0f / 64)) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
     return TPC_OK;
@@ -1338,7 +1375,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                           g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
     }
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, NF, L.np, L.ny, p->z_cell, L.nzmax, (long long)L.ncells,
-                                   p->merge_dz * 1.1f + 0.5f, L.mnzmax);
+                                   p->merge_dz * 1.1f + 0.5f, L.mnzmax, p->packed_links);
     g_launches += 3;
     CK(mark(1));
     // a2: counting sort of the clusters into (frame, sector, row, z-cell, y-bin) order
@@ -1347,12 +1384,17 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                              cell, slot);
     g_launches += 2;
     scan_u32(cstart, L.ncells, aux, st, &f->total_cells);
+    uint32_t* yzp = p->packed_links ? at<uint32_t>(ws, L.yzp) : nullptr;
     k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, cstart, cell, slot, yz,
-                                ids, plane, f);
+                                ids, plane, f, yzp);
     g_launches++;
     CK(mark(2));
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f, fg,
-                                   p->dy_link, p->dz_link, p->s_max_link, upr, dnr);
+    if (yzp)
+        k_neighbours<true><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f, fg,
+                                             p->dy_link, p->dz_link, p->s_max_link, upr, dnr, yzp);
+    else
+        k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f,
+                                              fg, p->dy_link, p->dz_link, p->s_max_link, upr, dnr, nullptr);
     g_launches++;
     CK(mark(3));
     k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
@@ -1567,6 +1609,7 @@ int tpc_params_default(tpc_params* p)
     p->queue_blocks_per_sm = 0;
     p->fp64_final = 0;
     p->profile = 0;
+    p->packed_links = 0;
     return TPC_OK;
 }
 
@@ -1616,6 +1659,43 @@ int tpc_prepare(const tpc_params* p, const tpc_geometry* g, int32_t n_clusters, 
     return TPC_OK;
 }
 
+// staging: the layout header (512 bytes), the row table, the frame offsets
+constexpr size_t STAGE_HDR = 512;
+constexpr size_t STAGE_TAB = sizeof(float) * ROWTAB * 256;
+
+int tpc_prepare_staging_size(int32_t n_frames, size_t* bytes)
+{
+    if (!bytes || n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
+    *bytes = STAGE_HDR + STAGE_TAB + sizeof(int32_t) * ((size_t)n_frames + 1);
+    return TPC_OK;
+}
+
+int tpc_prepare_async(const tpc_params* p, const tpc_geometry* g, int32_t n_clusters, int32_t n_frames,
+                      const int32_t* frame_offsets, void* host_staging, size_t staging_bytes, void* ws,
+                      size_t ws_bytes, void* stream)
+{
+    int rc = check_args(p, g);
+    if (rc) return rc;
+    if (!ws || !host_staging || n_clusters < 1) return TPC_ERR_ARG;
+    if ((rc = check_frames(n_clusters, n_frames, frame_offsets))) return rc;
+    size_t need;
+    if ((rc = tpc_prepare_staging_size(n_frames, &need))) return rc;
+    if (staging_bytes < need) return TPC_ERR_CAPACITY;
+    const Layout L = make_layout(p, g, n_clusters, n_frames);
+    if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
+    static_assert(sizeof(Layout) <= STAGE_HDR, "layout header");
+    char* h = static_cast<char*>(host_staging);
+    memcpy(h, &L, sizeof(Layout));
+    fill_rowtab(reinterpret_cast<float*>(h + STAGE_HDR), g, L.ny);
+    memcpy(h + STAGE_HDR + STAGE_TAB, frame_offsets, sizeof(int32_t) * ((size_t)n_frames + 1));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(at<char>(ws, L.hdr), h, sizeof(Layout), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(at<float>(ws, L.rowtab), h + STAGE_HDR, STAGE_TAB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(at<int32_t>(ws, L.offsets), h + STAGE_HDR + STAGE_TAB, sizeof(int32_t) * ((size_t)n_frames + 1),
+                       cudaMemcpyHostToDevice, st));
+    return TPC_OK;
+}
+
 int tpc_track_async(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl,
                     int32_t n_frames, void* ws, size_t ws_bytes, tpc_tracks* out, int32_t* dev_counts, void* stream)
 {
@@ -1627,7 +1707,9 @@ int tpc_track_async(const tpc_params* p, const tpc_geometry* g, float bz, float 
     if (n_frames < 1 || n_frames > MAX_FRAMES) return TPC_ERR_ARG;
     const Layout L = make_layout(p, g, cl->n, n_frames);
     if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
-    return enqueue(p, g, bz, v_drift, cl, ws, L, out, dev_counts, (cudaStream_t)stream, false);
+    rc = enqueue(p, g, bz, v_drift, cl, ws, L, out, dev_counts, (cudaStream_t)stream, false);
+    out->n_launches = g_launches;
+    return rc;
 }
 
 int tpc_export_tracklets(const void* ws, int32_t capacity, int32_t hits_stride, int32_t* start, int32_t* nhits,
@@ -1728,16 +1810,16 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     k_prep<<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
                                       g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, p->merge_dz * 1.1f + 0.5f,
-                                   MAX_MERGE_CELLS);
+                                   MAX_MERGE_CELLS, 0);
     // the histogram must start at zero: the scratch keeps the previous call's contents
     k_zero_cells<<<grid_for(ncells + 1, B), B, 0, st>>>(cstart, f);
     k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, rowtab, g->n_rows, g->n_sectors, f, fg, cstart,
                              cell, slot);
     scan_u32(cstart, ncells, aux, st, &f->total_cells);
     k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, np, cstart, cell, slot, yz, ids,
-                                plane, f);
-    k_neighbours<<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, np, rowtab, yz, ids, plane, cstart, f, fg, p->dy_link,
-                                   p->dz_link, p->s_max_link, upr, dnr);
+                                plane, f, nullptr);
+    k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, np, rowtab, yz, ids, plane, cstart, f, fg,
+                                          p->dy_link, p->dz_link, p->s_max_link, upr, dnr, nullptr);
     k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
     k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);
     CK(cudaGetLastError());

@@ -87,3 +87,14 @@ def test_calib_entry_points_validate_arguments_without_the_gpu():
     rc = L.tpc_calib_forward(C.byref(p), C.byref(g), 0.5, 2.58, 0.01, C.byref(tr), C.cast(theta, C.c_void_p),
                              None, None, None, 0, None)
     assert rc == tpc.TPC_ERR_ARG
+
+
+def test_packed_links_need_a_cell_longer_than_window_plus_rounding():
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
+    with pytest.raises(tpc.TpcError):
+        tpc.tpc_workspace_size(tpc.tpc_params_default(packed_links=1, z_cell=3.01), g, 1000)
+    plain = tpc.tpc_workspace_size(tpc.tpc_params_default(z_cell=3.5), g, 1000)
+    packed = tpc.tpc_workspace_size(tpc.tpc_params_default(packed_links=1, z_cell=3.5), g, 1000)
+    assert packed >= plain + 4 * 1000          # the 4-byte packed words

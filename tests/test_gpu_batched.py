@@ -109,3 +109,53 @@ def test_graph_replay_reproduces_the_synchronous_call(frames):
         assert res.n_tracks == ref.n_tracks
         np.testing.assert_array_equal(res.param.cpu().numpy(), p_ref)
         np.testing.assert_array_equal(res.clus_index[: int(res.clus_offset[-1])].cpu().numpy(), c_ref)
+
+
+@pytest.mark.parametrize("group_clusters,n_streams", [(0, 1), (0, 3), (150_000, 2), (10**9, 2)])
+def test_grouped_graph_equals_per_frame(frames, group_clusters, n_streams):
+    """GroupedBatch (frame groups on several streams, one CUDA graph) gives
+    every frame's tracks exactly as a per-frame tpc_track call does, on
+    eager runs and on graph replays."""
+    import torch
+
+    import paper_1905_05515_b300 as tpc
+    cat, off = _concat(frames)
+    ev0 = frames[0]
+    ins = _dev(cat)
+    one = tpc.Tracker(int(np.diff(off).max()), ev0.row_x, continuous=True)
+    ref = []
+    for f in range(len(frames)):
+        a, b = int(off[f]), int(off[f + 1])
+        r = one.track(*(t[a:b] for t in ins), bz=ev0.bz, v_drift=ev0.v_drift)
+        T = r.n_tracks
+        ref.append(dict(param=r.param.cpu().numpy(), chi2=r.chi2.cpu().numpy(), assign=r.assign.cpu().numpy(),
+                        clus=r.clus_index[:int(r.clus_offset[T].item()) if T else 0].cpu().numpy()))
+    gb = tpc.GroupedBatch(*ins, off, ev0.row_x, group_clusters=group_clusters, n_streams=n_streams,
+                          bz=ev0.bz, v_drift=ev0.v_drift)
+    assert len(gb.groups) == len(tpc.batch.partition(off, group_clusters))
+    for mode in ("eager", "graph", "graph"):
+        if mode == "eager":
+            gb.run()
+        else:
+            gb.replay()
+        res = gb.results()
+        for g, r in zip(gb.groups, res):
+            fr = r.frame.cpu().numpy()
+            co = r.clus_offset.cpu().numpy()
+            asg = r.assign.cpu().numpy()
+            t0 = 0
+            for f in range(g.f0, g.f1):
+                e = ref[f]
+                T = e["param"].shape[0]
+                sel = np.nonzero(fr == f)[0]
+                assert sel.size == T and (T == 0 or sel[0] == t0)
+                np.testing.assert_array_equal(r.param[t0:t0 + T].cpu().numpy(), e["param"])
+                np.testing.assert_array_equal(r.chi2[t0:t0 + T].cpu().numpy(), e["chi2"])
+                lo = int(off[f] - off[g.f0])
+                clus = r.clus_index[int(co[t0]):int(co[t0 + T])].cpu().numpy() - lo
+                np.testing.assert_array_equal(clus, e["clus"])
+                a = asg[lo:lo + e["assign"].size]
+                np.testing.assert_array_equal(np.where(a >= 0, a - t0, -1), e["assign"])
+                t0 += T
+    assert gb.n_launches > 0
+    torch.cuda.synchronize()

@@ -17,9 +17,9 @@ PARAM_TOL = 1e-4
 CHI2_TOL = 1e-3
 
 
-def _check(ev, orc, params=None, fit=True):
+def _check(ev, orc, params=None, fit=True, orc_params=None):
     g = run_gpu(ev, params=params)
-    r = orc.track_event(ev)
+    r = orc.track_event(ev, params=orc_params)
     bad = compare_decisions(ev, g, r)
     assert all(v == 0 for v in bad.values()), bad
     if fit:
@@ -89,6 +89,21 @@ def test_fp64_final_refit(orc):
     cov_rel = np.abs(g["cov64"][ok] - r.tr_c[ok]) / np.maximum(np.abs(r.tr_c[ok]), 1e-12)
     diag = [0, 2, 5, 9, 14]
     assert np.median(cov_rel[:, diag]) < 1e-4
+
+
+@pytest.mark.parametrize("make", [lambda: tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False),
+                                  lambda: tpcgen.central_event(seed=2, n_tracks=1500, with_truth=False)])
+def test_packed_link_coordinates(orc, make):
+    """Packed-coordinate link pass: every decision bit-exact with the oracle
+    running the same rounding, the fit within tolerance; the share of links
+    the rounding changes is reported against the unpacked run."""
+    import paper_1905_05515_b300 as tpc
+    ev = make()
+    g, r = _check(ev, orc, params=tpc.tpc_params_default(packed_links=1), orc_params={"packed_links": 1})
+    g0 = run_gpu(ev)
+    changed = np.mean((g["link_up"] != g0["link_up"]) | (g["link_dn"] != g0["link_dn"]))
+    print(f"links changed by packing: {changed:.2e} of {ev.n} clusters")
+    assert changed < 2e-3
 
 
 @pytest.mark.slow
