@@ -39,6 +39,7 @@
 /* ---------------------------------------------------------------- constants */
 #define SNP_MAX   0.999f
 #define U_MAX     0.1f
+#define BACK_JUMP 32      /* rows per back-propagation jump of the TrackletConstructor's phase C */
 /* arcsine series asin(u)/u = 1 + u^2/6 + 3u^4/40 + 5u^6/112 + ... and its derivative */
 #define AS1 0.16666666666666666667f
 #define AS2 0.075f
@@ -734,15 +735,29 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
                 }
             }
         }
-        /* phase C: back down through the fitted rows, then follow below the start */
+        /* phase C: back to the start row in jumps of at most BACK_JUMP rows
+         * (a refused jump -- |u| or |sin(phi)| out of range -- is retried
+         * with half as many rows; a refused single-row step ends the
+         * tracklet), then follow row by row below the start */
         memcpy(bot, top, sizeof(st));
         if (rc == r1) memcpy(bot, st, sizeof(st));
-        {
+        int back_ok = 1;
+        for (int jump = BACK_JUMP; rc > r1;) {
+            int tgt = rc - jump > r1 ? rc - jump : r1;
+            if (orc_prop32(st, X[tgt], kb)) {
+                rc = tgt;
+                if (rc == r1) memcpy(bot, st, sizeof(st));
+            } else if (jump > 1) {
+                jump >>= 1;
+            } else {
+                back_ok = 0;
+                break;
+            }
+        }
+        if (back_ok) {
             int miss = 0;
-            for (int r = rc - 1; r >= 0; r--) {
+            for (int r = r1 - 1; r >= 0; r--) {
                 if (!orc_prop32(st, X[r], kb)) break;
-                if (r > r1) continue;
-                if (r == r1) { memcpy(bot, st, sizeof(st)); continue; }
                 if (fabsf(st[1]) > fmaf(st[0], TAN10, P->edge_margin)) break;
                 float wy = fminf(fmaxf(P->win_nsigma * sqrtf(st[6 + 0] + vy), P->win_min), P->win_max);
                 float wz = fminf(fmaxf(P->win_nsigma * sqrtf(st[6 + 2] + vz), P->win_min), P->win_max);
@@ -828,6 +843,15 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
                 int tb = R->seg_trk[b];
                 const float *bot = R->trk_bot + (size_t)tb * NST;
                 if (!(fabsf(bot[2] - top[2]) <= P->merge_dz)) continue;
+                /* screen: tan(lambda) and q/pT (and their variances) are not
+                 * changed by the rotation or the propagation, and each pull
+                 * alone bounds the 5-parameter chi2 from below (d_i^2 / S_ii
+                 * <= d^T S^-1 d for the SPD sum S): a candidate with either
+                 * pull above twice the cut is not evaluated */
+                float dtl = top[4] - bot[4], dqp = top[5] - bot[5];
+                float lim = 2.0f * P->merge_chi2;
+                if (dtl * dtl > lim * (top[6 + 9] + bot[6 + 9]) || dqp * dqp > lim * (top[6 + 14] + bot[6 + 14]))
+                    continue;
                 float c2 = orc_merge_chi2(top, bot, COS20, sn, kb);
                 if (!(c2 < P->merge_chi2)) continue;
                 int ida = R->trk_start[ta], idb = R->trk_start[tb];
