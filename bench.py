@@ -40,7 +40,7 @@ FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky so
 # DRAM bytes (read + write) per cluster of the frame of one launch, from the
 # committed ncu capture of the same kernel build (profiles/k_tracklets_frame20.md,
 # 20-collision frame, scaled by clusters); None once the kernel changes
-NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 231.0}
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 298.6}
 
 
 def parse():

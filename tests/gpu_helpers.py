@@ -62,12 +62,25 @@ def compare_decisions(ev, g, r):
     return bad
 
 
+CHI2NDF_FIT = 100.0   # above this the track is not a fit of one helix (mis-merged looper legs)
+
+
 def compare_fit(g, r):
-    """Refit parameters and chi2 of tracks both sides fitted successfully."""
-    ok = (g["status"] == 0) & (r.tr_status == 0)
+    """Refit parameters and chi2 of tracks both sides fitted successfully and
+    that are fits of a helix (oracle chi2/ndf below CHI2NDF_FIT; the others
+    are counted in n_not_helix).  A parameter error counts relative to
+    max(|p|, floor), or -- where the value lies far inside its own
+    uncertainty, so that a relative error has no meaning -- as zero when it is
+    below 1e-3 of the parameter's standard deviation."""
+    ndf = np.maximum(r.tr_ndf, 1)
+    fitted = (g["status"] == 0) & (r.tr_status == 0)
+    ok = fitted & (r.tr_chi2 / ndf < CHI2NDF_FIT)
     pe = param_rel_err(g["param"][ok], r.tr_p[ok])
+    sig = np.sqrt(np.maximum(r.tr_c[ok][:, [0, 2, 5, 9, 14]], 0.0))
+    pe[np.abs(g["param"][ok].astype(np.float64) - r.tr_p[ok]) <= 1e-3 * sig] = 0.0
     ce = np.abs(g["chi2"][ok].astype(np.float64) - r.tr_chi2[ok]) / np.maximum(r.tr_chi2[ok], 1.0)
     xe = np.abs(g["x"][ok] - r.tr_x[ok])
-    return dict(n_ok=int(ok.sum()), status_mismatch=int((g["status"] != r.tr_status).sum()),
+    return dict(n_ok=int(ok.sum()), n_not_helix=int((fitted & ~ok).sum()),
+                status_mismatch=int((g["status"] != r.tr_status).sum()),
                 param_max=pe.max(axis=0) if pe.size else np.zeros(5), param_p99=np.percentile(pe, 99, axis=0) if pe.size else np.zeros(5),
                 chi2_max=float(ce.max()) if ce.size else 0.0, x_max=float(xe.max()) if xe.size else 0.0)
