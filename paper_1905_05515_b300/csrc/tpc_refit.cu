@@ -123,11 +123,7 @@ __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my,
 
 struct RefitArgs {
     const void* frame;
-    const uint8_t* sector;
-    const uint8_t* row;
-    const float* y;
-    const float* zlin;
-    const float* rowtab;
+    const float4* tcl;      // track clusters in track order: y, z, row x, sector (int bits)
     const int32_t* ttail;
     const float* t_top;
     int ns, passes, fp64, max_tracks, prof;
@@ -142,17 +138,17 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
     chi2 = 0.0;
     for (int q = 0; q < n; q++) {
         const int i = inward ? n - 1 - q : q;
-        const int id = R.out.clus_index[off + i];
-        const int s = R.sector[id];
+        const float4 cl = R.tcl[off + i];
+        const int s = __float_as_int(cl.w);
         if (s != sec) {
             float sn, cs;
             frame_rotation(sec, s, R.ns, cs, sn);
             if (!rot<CT>(x, p, pl, c, cs, sn, R.kb)) return false;
             sec = s;
         }
-        if (!prop<CT>(x, p, pl, c, R.rowtab[R.row[id] * ROWTAB], R.kb)) return false;
+        if (!prop<CT>(x, p, pl, c, cl.z, R.kb)) return false;
         nprop++;
-        const float my = R.y[id], mz = R.zlin[id] - zref;
+        const float my = cl.x, mz = cl.y - zref;
         if (q == 0) {
             // restart: y, z from the measurement; angles and curvature keep the
             // previous covariance block times refit_inflate
@@ -192,13 +188,13 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
         float c[15];
         // z relative to the first cluster of the track: same-track z values
         // subtract exactly and the binary32 state keeps small magnitudes
-        const float zref = R.zlin[R.out.clus_index[off]];
+        const float zref = R.tcl[off].y;
 #pragma unroll
         for (int k = 0; k < 5; k++) p[k] = ts[1 + k];
         p[1] = p[1] - zref;
 #pragma unroll
         for (int k = 0; k < 15; k++) c[k] = ts[6 + k];
-        int sec = R.sector[R.out.clus_index[off + n - 1]];
+        int sec = __float_as_int(R.tcl[off + n - 1].w);
         double chi2 = 0.0;
         bool ok = true;
         const int nfloat = R.fp64 ? R.passes - 1 : R.passes;
@@ -214,7 +210,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
 #pragma unroll
         for (int k = 0; k < 5; k++) p[k] = p[k] + pl[k];
         p[1] = p[1] + zref;
-        R.out.sector[r] = R.sector[R.out.clus_index[off]];
+        R.out.sector[r] = __float_as_int(R.tcl[off].w);
         R.out.x[r] = x;
 #pragma unroll
         for (int k = 0; k < 5; k++) R.out.param[5 * r + k] = p[k];
@@ -234,17 +230,12 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
 
 }  // namespace
 
-int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const tpc_clusters* cl,
-                     const float* zlin, const float* rowtab, const void* frame, const int32_t* ttail,
-                     const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st)
+int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const void* frame,
+                     const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st)
 {
     RefitArgs R;
     R.frame = frame;
-    R.sector = cl->sector;
-    R.row = cl->row;
-    R.y = cl->y;
-    R.zlin = zlin;
-    R.rowtab = rowtab;
+    R.tcl = tcl;
     R.ttail = ttail;
     R.t_top = t_top;
     R.ns = g->n_sectors;

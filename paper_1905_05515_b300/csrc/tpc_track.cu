@@ -52,7 +52,7 @@ struct Layout {
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
-    size_t headmark, tcount, thead, ttail;
+    size_t headmark, tcount, thead, ttail, tcl;
     size_t total;
 };
 
@@ -177,6 +177,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.tcount = take(4 * (T + 1));
     L.thead = take(4 * T);
     L.ttail = take(4 * T);
+    L.tcl = take(16 * N);       // track clusters in track order: y, z, row x, sector
     L.total = o;
     return L;
 }
@@ -446,25 +447,40 @@ __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8
     }
 }
 
-// sorted-index ranges of the 3 x 3 cells around (zc, yc) of one plane: for
-// each z-cell zc-1 .. zc+1 the y-bins yc-1 .. yc+1 are contiguous
+// sorted-index ranges of up to three z-cells of one plane (empty ranges 0..0)
 struct Ranges {
     int b[3], e[3];
 };
-__device__ __forceinline__ Ranges cell_ranges(const uint32_t* __restrict__ cstart, const FrameGrid& G, int lplane,
-                                              int zc, int yc, int ny)
+
+// Sorted-index ranges of the cells a search window overlaps: the z-cells of
+// [zp - wz, zp + wz] and, in each, the contiguous y-bins of [yp - wy, yp + wy],
+// both widened by WIN_MARGIN (more than the rounding of the window edges and
+// of packed coordinates).  Cells and bins are monotone in the coordinate, so
+// every cluster that passes the window test lies in these ranges; a window
+// spans at most three cells and three bins (the cell length and bin width
+// exceed every window width plus the margin, which check_args and
+// effective_ybins enforce).
+constexpr float WIN_MARGIN = 1.0f / 64;
+
+__device__ __forceinline__ Ranges window_ranges(const uint32_t* __restrict__ cstart, const FrameGrid& G, int lplane,
+                                                int s, int ns, const float* __restrict__ rowtab, int r, int ny,
+                                                float yp, float zp, float wy, float wz)
 {
+    const float za = fold(zp - (wz + WIN_MARGIN), s, ns), zb = fold(zp + (wz + WIN_MARGIN), s, ns);
+    const int c0 = grid_cell(fminf(za, zb), G.zmin, G.inv_cs, G.nz);
+    const int c1 = grid_cell(fmaxf(za, zb), G.zmin, G.inv_cs, G.nz);
+    const int y0 = ybin(yp - (wy + WIN_MARGIN), rowtab, r, ny);
+    const int y1 = ybin(yp + (wy + WIN_MARGIN), rowtab, r, ny);
     Ranges R;
-    const int ylo = max(yc - 1, 0), yhi = min(yc + 1, ny - 1);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const int zz = zc - 1 + k;
-        if (zz < 0 || zz >= G.nz) {
+        const int zz = c0 + k;
+        if (zz > c1) {
             R.b[k] = R.e[k] = 0;
         } else {
             const uint32_t base = G.cell_base + ((uint32_t)lplane * (uint32_t)G.nz + (uint32_t)zz) * (uint32_t)ny;
-            R.b[k] = (int)cstart[base + ylo];
-            R.e[k] = (int)cstart[base + yhi + 1];
+            R.b[k] = (int)cstart[base + y0];
+            R.e[k] = (int)cstart[base + y1 + 1];
         }
     }
     return R;
@@ -512,9 +528,8 @@ __global__ void __launch_bounds__(256) k_neighbours(
             const float yu_pred = yh * rowtab[r * ROWTAB + 1];
             const float yd_pred = yh * rowtab[r * ROWTAB + 2];
             const float w = rowtab[r * ROWTAB + 3];
-            const int c = grid_cell(fold(zh, s, ns), G.zmin, G.inv_cs, G.nz);
-            const Ranges ru = cell_ranges(cstart, G, pl + 1, c, ybin(yu_pred, rowtab, r + 1, ny), ny);
-            const Ranges rd = cell_ranges(cstart, G, pl - 1, c, ybin(yd_pred, rowtab, r - 1, ny), ny);
+            const Ranges ru = window_ranges(cstart, G, pl + 1, s, ns, rowtab, r + 1, ny, yu_pred, zh, DY, DZ);
+            const Ranges rd = window_ranges(cstart, G, pl - 1, s, ns, rowtab, r - 1, ny, yd_pred, zh, DY, DZ);
             // down candidates inside the windows
             int dl[MAXD];
             int ndn = 0;
@@ -629,8 +644,7 @@ struct TrkArgs {
 __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G, int lplane, int r, int s, float yp,
                                             float zp, float wy, float wz, int ny, unsigned& ncand)
 {
-    const int c = grid_cell(fold(zp, s, A.ns), G.zmin, G.inv_cs, G.nz);
-    const Ranges rg = cell_ranges(A.cstart, G, lplane, c, ybin(yp, A.rowtab, r, ny), ny);
+    const Ranges rg = window_ranges(A.cstart, G, lplane, s, A.ns, A.rowtab, r, ny, yp, zp, wy, wz);
     int best = -1, bid = 0;
     float bd = 0.0f;
 #pragma unroll
@@ -653,7 +667,11 @@ __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G
 
 // Phases of one tracklet (the operation sequence per tracklet is fixed; the
 // kernel only interleaves tracklets differently across lanes)
-enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_C = 3, PH_DONE = 4 };
+enum : int { PH_A = 0, PH_B = 1, PH_CSTART = 2, PH_BACK = 3, PH_C = 4, PH_DONE = 5 };
+// phase C returns to the start row in jumps of at most BACK_JUMP rows; a
+// refused jump (|u| or |sin(phi)| out of range) is retried with half as many
+// rows, a refused single-row step ends the tracklet
+constexpr int BACK_JUMP = 32;
 
 constexpr int TRK_BLOCK = 128;
 
@@ -664,7 +682,7 @@ constexpr int TRK_BLOCK = 128;
 // Kalman update each have a single call site shared by all phases, so a warp
 // whose lanes are in different phases still executes each of them once per
 // iteration.
-__global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
+__global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
 {
     // the last accepted state of each lane (outer-end / inner-end candidate) lives
     // in shared memory, element-major so that the lanes of a warp hit distinct banks
@@ -683,7 +701,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
         for (int i = 0; i < NST; i++) keep_sh[i][threadIdx.x] = st[i];
     };
     int t = -1, phase = PH_DONE;
-    int h1 = 0, r1 = 0, s = 0, lbase = 0, pgbase = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0;
+    int h1 = 0, r1 = 0, s = 0, lbase = 0, pgbase = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0, jump = BACK_JUMP;
     FrameGrid G;
     G.zmin = 0.0f; G.inv_cs = 1.0f; G.nz = 1; G.cell_base = 0u; G.zmin_key = 0u; G.zmax_key = 0u;
     // next chain hit (phase A), loaded one step ahead
@@ -752,8 +770,9 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             for (int i = 0; i < NST; i++) top[i] = keep_sh[i][threadIdx.x];
             if (rc == r1) save_keep();
             miss = 0;
-            r = rc - 1;
-            phase = PH_C;
+            r = r1 - 1;
+            jump = BACK_JUMP;
+            phase = rc > r1 ? PH_BACK : PH_C;
         }
         // ---- the row this step goes to
         int target = -1, hn = -1;
@@ -778,17 +797,28 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             if (rc + 1 < NR) target = rc + 1;
             else phase = PH_CSTART;
         }
-        if (phase == PH_C) {                    // back down, then below the start
+        if (phase == PH_BACK)                   // back to the start row
+            target = max(r1, rc - jump);
+        if (phase == PH_C) {                    // below the start
             if (r >= 0) target = r;
             else phase = PH_DONE;
         }
         if (target < 0) continue;
         // ---- propagation (one call site)
         if (!prop32(st, A.rowtab[target * ROWTAB], A.kb)) {
-            phase = (phase == PH_C) ? PH_DONE : PH_CSTART;
+            if (phase == PH_BACK && jump > 1) jump >>= 1;
+            else phase = (phase == PH_C || phase == PH_BACK) ? PH_DONE : PH_CSTART;
             continue;
         }
         nprop++;
+        if (phase == PH_BACK) {
+            rc = target;
+            if (rc == r1) {
+                save_keep();
+                phase = PH_C;
+            }
+            continue;
+        }
         bool search = false, upd = false;
         float my = 0.0f, mz = 0.0f, cmax = INF;
         int c = -1;
@@ -802,15 +832,6 @@ __global__ void __launch_bounds__(TRK_BLOCK, 6) k_tracklets(TrkArgs A)
             rc = target;
             search = true;
         } else {
-            if (r > r1) {
-                r--;
-                continue;
-            }
-            if (r == r1) {
-                save_keep();
-                r--;
-                continue;
-            }
             search = true;
         }
         if (search) {
@@ -982,6 +1003,16 @@ struct MergeArgs {
     Frame* fw;
 };
 
+// Merge screen: tan(lambda), q/pT and their variances are unchanged by the
+// rotation and the propagation, and each pull alone bounds the 5-parameter
+// chi2 from below; a pair with either pull above twice the cut is skipped
+// before the rotation, propagation and Cholesky solve.
+__device__ __forceinline__ bool merge_screened(const float* top, const float* bot, float lim)
+{
+    const float dtl = top[4] - bot[4], dqp = top[5] - bot[5];
+    return dtl * dtl > lim * (top[6 + 9] + bot[6 + 9]) || dqp * dqp > lim * (top[6 + 14] + bot[6 + 14]);
+}
+
 // best B (outer piece) for every A: A's outer end against B's inner end
 __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 {
@@ -1009,6 +1040,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
                 const int tb = M.seg[b];
                 const float* bot = M.t_bot + (int64_t)tb * NST;
                 if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
+                if (merge_screened(top, bot, 2.0f * M.chi2cut)) continue;
                 const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
                 nchi++;
                 if (!(c2 < M.chi2cut)) continue;
@@ -1048,6 +1080,7 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
                 const int ta = M.seg[a];
                 const float* top = M.t_top + (int64_t)ta * NST;
                 if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
+                if (merge_screened(top, bot, 2.0f * M.chi2cut)) continue;
                 const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
                 if (!(c2 < M.chi2cut)) continue;
                 const int ida = M.t_id[ta];
@@ -1124,6 +1157,9 @@ struct AsmArgs {
     int32_t* clus_index;
     int32_t* assign;
     int32_t* frame;             // nullable
+    const float2* yz;
+    const float* rowtab;
+    float4* tcl;                // [clusters in tracks]: y, z, row x, sector (int bits)
 };
 
 __global__ void k_track_count(AsmArgs A)
@@ -1176,6 +1212,10 @@ __global__ void k_track_fill(AsmArgs A)
                 const int h = trk_hit(slot, A.nr, nh, nup, k);
                 if (A.hitw[h] == w) {
                     const int id = A.ids[h];
+                    const int pl = (int)(A.plane[h] % (uint32_t)A.np);
+                    const int sec = pl / A.nr;
+                    const float2 c = A.yz[h];
+                    A.tcl[o] = make_float4(c.x, c.y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
                     A.clus_index[o++] = id;
                     A.assign[id] = r;
                 }
@@ -1295,9 +1335,9 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
     if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0) return TPC_ERR_ARG;
-    if (!(p->z_cell > p->dz_link) || !(p->z_cell > p->win_max)) return TPC_ERR_ARG;
-    // packed coordinates are off by up to 2^-9 cm: the cell must still cover the window
-    if (p->packed_links && !(p->z_cell >= p->dz_link + 1.0f / 64)) return TPC_ERR_ARG;
+    // a window (plus the search margin of 1/64 cm on each side) spans at most
+    // three z-cells: the cell must be longer than the window half-width plus 1/32
+    if (!(p->z_cell >= std::max(p->dz_link, p->win_max) + 1.0f / 32)) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
     return TPC_OK;
@@ -1325,9 +1365,8 @@ int out_args(const tpc_params* p, const tpc_tracks* out)
 }  // namespace
 
 // refit launcher (tpc_refit.cu)
-int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const tpc_clusters* cl,
-                     const float* zlin, const float* rowtab, const void* frame, const int32_t* ttail,
-                     const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st);
+int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const void* frame,
+                     const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st);
 
 namespace {
 
@@ -1471,6 +1510,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     AA.headmark = headmark; AA.tcount = tcount; AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail);
     AA.clus_offset = out->clus_offset; AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
     AA.frame = out->frame;
+    AA.yz = yz; AA.rowtab = rowtab; AA.tcl = at<float4>(ws, L.tcl);
     k_track_count<<<gt2, B, 0, st>>>(AA);
     g_launches++;
     scan_u32(tcount, ntcap, aux, st);
@@ -1478,8 +1518,8 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     g_launches++;
     CK(mark(8));
     // a9: refit
-    int rr = tpc_launch_refit(p, g, bz, cl, zlin, rowtab, f, AA.ttail, TA.t_top, out,
-                              std::min(out->capacity_tracks, ntcap), st);
+    int rr = tpc_launch_refit(p, g, bz, AA.tcl, f, AA.ttail, TA.t_top, out, std::min(out->capacity_tracks, ntcap),
+                              st);
     if (rr) return rr;
     g_launches++;
     CK(mark(9));
