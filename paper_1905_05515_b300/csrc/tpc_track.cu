@@ -50,7 +50,7 @@ struct Layout {
     size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, yzp, ids, plane;
     size_t upr, dnr, up, dn, starts;
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
-    size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt;
+    size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
     size_t headmark, tcount, thead, ttail, tcl;
     size_t total;
@@ -166,6 +166,8 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.cntt = take(4 * (mcells + 1));
     L.byb = take(4 * T);
     L.byt = take(4 * T);
+    L.recb = take(32 * T);      // merge-grid order: inner-end (z, tan lambda, q/pT, their variances, id)
+    L.rect = take(32 * T);      // merge-grid order: outer-end record
     L.bnext = take(4 * T);
     L.bprev = take(4 * T);
     L.snext = take(4 * T);
@@ -971,15 +973,39 @@ __global__ void k_seg_keys(const Frame* __restrict__ f, int ns, int nr, const in
     }
 }
 
+// Merge-candidate record of one segment end, stored in merge-grid order so
+// that a candidate scan reads 32 contiguous bytes per candidate: z, tan(lambda),
+// q/pT and the variances of the last two (the window test and the screen),
+// the start-hit id (tie-break) and the tracklet index.
+struct MergeRec {
+    float4 a;   // z, tan(lambda), q/pT, var(tan(lambda))
+    float4 b;   // var(q/pT), id (int bits), tracklet (int bits), 0
+};
+
+__device__ __forceinline__ MergeRec merge_rec(const float* st, int id, int t)
+{
+    MergeRec m;
+    m.a = make_float4(st[2], st[4], st[5], st[6 + 9]);
+    m.b = make_float4(st[6 + 14], __int_as_float(id), __int_as_float(t), 0.0f);
+    return m;
+}
+
 __global__ void k_seg_scatter(const Frame* __restrict__ f, const uint32_t* __restrict__ cntb,
                               const uint32_t* __restrict__ cntt, const uint32_t* __restrict__ keyb,
                               const uint32_t* __restrict__ keyt, const uint32_t* __restrict__ slotb,
-                              const uint32_t* __restrict__ slott, int32_t* __restrict__ byb, int32_t* __restrict__ byt)
+                              const uint32_t* __restrict__ slott, int32_t* __restrict__ byb, int32_t* __restrict__ byt,
+                              const int32_t* __restrict__ seg, const int32_t* __restrict__ t_id,
+                              const float* __restrict__ t_top, const float* __restrict__ t_bot,
+                              MergeRec* __restrict__ recb, MergeRec* __restrict__ rect)
 {
     const int nseg = f->n_seg;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
-        byb[cntb[keyb[a]] + slotb[a]] = a;
-        byt[cntt[keyt[a]] + slott[a]] = a;
+        const int t = seg[a], id = t_id[t];
+        const uint32_t pb = cntb[keyb[a]] + slotb[a], pt = cntt[keyt[a]] + slott[a];
+        byb[pb] = a;
+        byt[pt] = a;
+        recb[pb] = merge_rec(t_bot + (int64_t)t * NST, id, t);
+        rect[pt] = merge_rec(t_top + (int64_t)t * NST, id, t);
     }
 }
 
@@ -999,6 +1025,8 @@ struct MergeArgs {
     const int32_t* byt;
     int32_t* bnext;
     int32_t* bprev;
+    const MergeRec* recb;   // merge-grid order, as byb
+    const MergeRec* rect;   // merge-grid order, as byt
     int prof;
     Frame* fw;
 };
@@ -1007,10 +1035,10 @@ struct MergeArgs {
 // rotation and the propagation, and each pull alone bounds the 5-parameter
 // chi2 from below; a pair with either pull above twice the cut is skipped
 // before the rotation, propagation and Cholesky solve.
-__device__ __forceinline__ bool merge_screened(const float* top, const float* bot, float lim)
+__device__ __forceinline__ bool merge_screened(const MergeRec& top, const MergeRec& bot, float lim)
 {
-    const float dtl = top[4] - bot[4], dqp = top[5] - bot[5];
-    return dtl * dtl > lim * (top[6 + 9] + bot[6 + 9]) || dqp * dqp > lim * (top[6 + 14] + bot[6 + 14]);
+    const float dtl = top.a.y - bot.a.y, dqp = top.a.z - bot.a.z;
+    return dtl * dtl > lim * (top.a.w + bot.a.w) || dqp * dqp > lim * (top.b.x + bot.b.x);
 }
 
 // best B (outer piece) for every A: A's outer end against B's inner end
@@ -1025,6 +1053,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
         float top[NST];
 #pragma unroll
         for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
+        const MergeRec ra = merge_rec(top, 0, ta);
         const int mc = merge_cell(fold(top[2], sa, M.ns), M.f);
         int best = -1, bid = 0;
         float bc = 0.0f;
@@ -1036,16 +1065,15 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
             const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
-                const int b = M.byb[q];
-                const int tb = M.seg[b];
-                const float* bot = M.t_bot + (int64_t)tb * NST;
-                if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
-                if (merge_screened(top, bot, 2.0f * M.chi2cut)) continue;
-                const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
+                const MergeRec rb = M.recb[q];
+                if (!(fabsf(rb.a.x - top[2]) <= M.dz)) continue;
+                if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
+                const int tb = __float_as_int(rb.b.z);
+                const float c2 = merge_chi2(top, M.t_bot + (int64_t)tb * NST, COS20, sn, M.kb);
                 nchi++;
                 if (!(c2 < M.chi2cut)) continue;
-                const int idb = M.t_id[tb];
-                if (best < 0 || c2 < bc || (c2 == bc && idb < bid)) { best = b; bc = c2; bid = idb; }
+                const int idb = __float_as_int(rb.b.y);
+                if (best < 0 || c2 < bc || (c2 == bc && idb < bid)) { best = M.byb[q]; bc = c2; bid = idb; }
             }
         }
         M.bnext[a] = best;
@@ -1064,6 +1092,7 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
         float bot[NST];
 #pragma unroll
         for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
+        const MergeRec rb = merge_rec(bot, 0, tb);
         const int mc = merge_cell(fold(bot[2], sb, M.ns), M.f);
         int best = -1, bid = 0;
         float bc = 0.0f;
@@ -1076,15 +1105,14 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
             const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
             const int qb = M.cntt[gsa * mnz + lo], qe = M.cntt[gsa * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
-                const int a = M.byt[q];
-                const int ta = M.seg[a];
-                const float* top = M.t_top + (int64_t)ta * NST;
-                if (!(fabsf(bot[2] - top[2]) <= M.dz)) continue;
-                if (merge_screened(top, bot, 2.0f * M.chi2cut)) continue;
-                const float c2 = merge_chi2(top, bot, COS20, sn, M.kb);
+                const MergeRec ra = M.rect[q];
+                if (!(fabsf(bot[2] - ra.a.x) <= M.dz)) continue;
+                if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
+                const int ta = __float_as_int(ra.b.z);
+                const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, bot, COS20, sn, M.kb);
                 if (!(c2 < M.chi2cut)) continue;
-                const int ida = M.t_id[ta];
-                if (best < 0 || c2 < bc || (c2 == bc && ida < bid)) { best = a; bc = c2; bid = ida; }
+                const int ida = __float_as_int(ra.b.y);
+                if (best < 0 || c2 < bc || (c2 == bc && ida < bid)) { best = M.byt[q]; bc = c2; bid = ida; }
             }
         }
         M.bprev[b] = best;
@@ -1485,10 +1513,12 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
     M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
     M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
+    M.recb = at<MergeRec>(ws, L.recb); M.rect = at<MergeRec>(ws, L.rect);
     M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
     k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
-                                     at<int32_t>(ws, L.byt));
+                                     at<int32_t>(ws, L.byt), seg, TA.t_id, TA.t_top, TA.t_bot,
+                                     at<MergeRec>(ws, L.recb), at<MergeRec>(ws, L.rect));
     k_merge_next<<<gT, 128, 0, st>>>(M);
     k_merge_prev<<<gT, 128, 0, st>>>(M);
     k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
