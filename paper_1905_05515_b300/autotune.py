@@ -24,7 +24,7 @@ from . import abi
 from .batch import GroupedBatch
 from .tracker import Tracker
 
-DEFAULT_SPACE = {"y_bins": (4, 8, 12), "z_cell": (3.5, 5.0, 7.0), "queue_blocks_per_sm": (0, 8, 16)}
+DEFAULT_SPACE = {"y_bins": (8, 16, 24), "z_cell": (2.0, 3.5, 5.0), "queue_blocks_per_sm": (0, 8)}
 GROUP_SPACE = {"group_clusters": (0, 8_000_000, 16_000_000, 32_000_000, 64_000_000), "n_streams": (1, 2, 3)}
 
 

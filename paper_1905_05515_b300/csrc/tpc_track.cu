@@ -66,15 +66,10 @@ int64_t scan_aux_elems(int64_t n)
     return s + 16;
 }
 
-// y-bins per z-cell: as many as the narrowest row allows with every bin wider
-// than the largest y search window (link window, following window)
-int effective_ybins(const tpc_params* p, const tpc_geometry* g)
-{
-    const float w = std::max(p->dy_link, p->win_max) * 1.01f + 0.01f;
-    const float width = 2.0f * (g->row_x[0] * TAN10 + Y_MARGIN);
-    int ny = (int)std::floor(width / w);
-    return std::max(1, std::min(ny, std::max(1, p->y_bins)));
-}
+// y-bins per z-cell (the searches visit whatever bins a window overlaps, so
+// any count works; the grid grows with it)
+constexpr int MAX_YBINS = 64;
+int effective_ybins(const tpc_params* p, const tpc_geometry*) { return std::max(1, std::min(p->y_bins, MAX_YBINS)); }
 
 // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r],
 // (X[r]-X[r-1]) / (X[r+1]-X[r-1]), then the y-bin origin and inverse width
@@ -449,43 +444,41 @@ __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8
     }
 }
 
-// sorted-index ranges of up to three z-cells of one plane (empty ranges 0..0)
-struct Ranges {
-    int b[3], e[3];
-};
 
-// Sorted-index ranges of the cells a search window overlaps: the z-cells of
-// [zp - wz, zp + wz] and, in each, the contiguous y-bins of [yp - wy, yp + wy],
-// both widened by WIN_MARGIN (more than the rounding of the window edges and
-// of packed coordinates).  Cells and bins are monotone in the coordinate, so
-// every cluster that passes the window test lies in these ranges; a window
-// spans at most three cells and three bins (the cell length and bin width
-// exceed every window width plus the margin, which check_args and
-// effective_ybins enforce).
+// The cells a search window overlaps: the z-cells c0..c1 of
+// [zp - wz, zp + wz] and, in each, the contiguous y-bins y0..y1 of
+// [yp - wy, yp + wy], both widened by WIN_MARGIN (more than the rounding of
+// the window edges and of packed coordinates).  Cells and bins are monotone
+// in the coordinate, so every cluster that passes the window test lies in
+// these ranges, whatever the cell and bin sizes.
 constexpr float WIN_MARGIN = 1.0f / 64;
 
-__device__ __forceinline__ Ranges window_ranges(const uint32_t* __restrict__ cstart, const FrameGrid& G, int lplane,
-                                                int s, int ns, const float* __restrict__ rowtab, int r, int ny,
-                                                float yp, float zp, float wy, float wz)
+struct WinCells {
+    uint32_t base;      // cell of (plane, z-cell c0, y-bin 0)
+    int nzc, y0, y1, ny;
+    // sorted-index range [b, e) of the window's bins in its k-th z-cell
+    __device__ __forceinline__ void range(const uint32_t* __restrict__ cstart, int k, int& b, int& e) const
+    {
+        const uint32_t c = base + (uint32_t)k * (uint32_t)ny;
+        b = (int)cstart[c + y0];
+        e = (int)cstart[c + y1 + 1];
+    }
+};
+
+__device__ __forceinline__ WinCells window_cells(const FrameGrid& G, int lplane, int s, int ns,
+                                                 const float* __restrict__ rowtab, int r, int ny, float yp, float zp,
+                                                 float wy, float wz)
 {
     const float za = fold(zp - (wz + WIN_MARGIN), s, ns), zb = fold(zp + (wz + WIN_MARGIN), s, ns);
     const int c0 = grid_cell(fminf(za, zb), G.zmin, G.inv_cs, G.nz);
     const int c1 = grid_cell(fmaxf(za, zb), G.zmin, G.inv_cs, G.nz);
-    const int y0 = ybin(yp - (wy + WIN_MARGIN), rowtab, r, ny);
-    const int y1 = ybin(yp + (wy + WIN_MARGIN), rowtab, r, ny);
-    Ranges R;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const int zz = c0 + k;
-        if (zz > c1) {
-            R.b[k] = R.e[k] = 0;
-        } else {
-            const uint32_t base = G.cell_base + ((uint32_t)lplane * (uint32_t)G.nz + (uint32_t)zz) * (uint32_t)ny;
-            R.b[k] = (int)cstart[base + y0];
-            R.e[k] = (int)cstart[base + y1 + 1];
-        }
-    }
-    return R;
+    WinCells W;
+    W.base = G.cell_base + ((uint32_t)lplane * (uint32_t)G.nz + (uint32_t)c0) * (uint32_t)ny;
+    W.nzc = c1 - c0 + 1;
+    W.y0 = ybin(yp - (wy + WIN_MARGIN), rowtab, r, ny);
+    W.y1 = ybin(yp + (wy + WIN_MARGIN), rowtab, r, ny);
+    W.ny = ny;
+    return W;
 }
 
 // ---------------------------------------------------------------------------
@@ -530,25 +523,28 @@ __global__ void __launch_bounds__(256) k_neighbours(
             const float yu_pred = yh * rowtab[r * ROWTAB + 1];
             const float yd_pred = yh * rowtab[r * ROWTAB + 2];
             const float w = rowtab[r * ROWTAB + 3];
-            const Ranges ru = window_ranges(cstart, G, pl + 1, s, ns, rowtab, r + 1, ny, yu_pred, zh, DY, DZ);
-            const Ranges rd = window_ranges(cstart, G, pl - 1, s, ns, rowtab, r - 1, ny, yd_pred, zh, DY, DZ);
+            const WinCells wu = window_cells(G, pl + 1, s, ns, rowtab, r + 1, ny, yu_pred, zh, DY, DZ);
+            const WinCells wd = window_cells(G, pl - 1, s, ns, rowtab, r - 1, ny, yd_pred, zh, DY, DZ);
             // down candidates inside the windows
             int dl[MAXD];
             int ndn = 0;
             bool overflow = false;
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                for (int q = rd.b[k]; q < rd.e[k]; q++) {
+            for (int k = 0; k < wd.nzc; k++) {
+                int qb, qe;
+                wd.range(cstart, k, qb, qe);
+                for (int q = qb; q < qe; q++) {
                     const float2 pq = coord(q);
                     if (fabsf(pq.x - yd_pred) <= DY && fabsf(pq.y - zh) <= DZ) {
                         if (ndn < MAXD) dl[ndn++] = q;
                         else overflow = true;
                     }
                 }
+            }
             if (ndn > 0) {
-#pragma unroll
-                for (int ku = 0; ku < 3; ku++)
-                    for (int u = ru.b[ku]; u < ru.e[ku]; u++) {
+                for (int ku = 0; ku < wu.nzc; ku++) {
+                    int ub, ue;
+                    wu.range(cstart, ku, ub, ue);
+                    for (int u = ub; u < ue; u++) {
                         const float2 pu = coord(u);
                         const float yu = pu.x, zu = pu.y;
                         if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
@@ -568,13 +564,17 @@ __global__ void __launch_bounds__(256) k_neighbours(
                         if (!overflow) {
                             for (int k = 0; k < ndn; k++) consider(dl[k]);
                         } else {
-                            for (int k = 0; k < 3; k++)
-                                for (int d = rd.b[k]; d < rd.e[k]; d++) {
+                            for (int k = 0; k < wd.nzc; k++) {
+                                int db, de;
+                                wd.range(cstart, k, db, de);
+                                for (int d = db; d < de; d++) {
                                     const float2 pd = coord(d);
                                     if (fabsf(pd.x - yd_pred) <= DY && fabsf(pd.y - zh) <= DZ) consider(d);
                                 }
+                            }
                         }
                     }
+                }
             }
         }
         upr[h] = bu;
@@ -646,13 +646,14 @@ struct TrkArgs {
 __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G, int lplane, int r, int s, float yp,
                                             float zp, float wy, float wz, int ny, unsigned& ncand)
 {
-    const Ranges rg = window_ranges(A.cstart, G, lplane, s, A.ns, A.rowtab, r, ny, yp, zp, wy, wz);
+    const WinCells W = window_cells(G, lplane, s, A.ns, A.rowtab, r, ny, yp, zp, wy, wz);
     int best = -1, bid = 0;
     float bd = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        ncand += (unsigned)(rg.e[k] - rg.b[k]);
-        for (int q = rg.b[k]; q < rg.e[k]; q++) {
+    for (int k = 0; k < W.nzc; k++) {
+        int qb, qe;
+        W.range(A.cstart, k, qb, qe);
+        ncand += (unsigned)(qe - qb);
+        for (int q = qb; q < qe; q++) {
             const float2 pq = A.yz[q];
             const float dy = pq.x - yp;
             const float dz = pq.y - zp;
@@ -1363,9 +1364,7 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
     if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0) return TPC_ERR_ARG;
-    // a window (plus the search margin of 1/64 cm on each side) spans at most
-    // three z-cells: the cell must be longer than the window half-width plus 1/32
-    if (!(p->z_cell >= std::max(p->dz_link, p->win_max) + 1.0f / 32)) return TPC_ERR_ARG;
+    if (!(p->z_cell >= 0.25f) || p->y_bins < 1 || p->y_bins > MAX_YBINS) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
     return TPC_OK;

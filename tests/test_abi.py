@@ -46,7 +46,7 @@ def test_params_and_workspace_size_host_only():
         tpc.tpc_workspace_size(p, tpc.abi.make_geometry(np.array([1, 2], np.float32), 36, 250.0, False), 10)
     with pytest.raises(tpc.TpcError):
         tpc.tpc_workspace_size(p, tpc.abi.make_geometry(tpcgen.row_x_f32(), 5, 250.0, False), 10)
-    bad = tpc.tpc_params_default(z_cell=2.0)       # cell shorter than the link window
+    bad = tpc.tpc_params_default(z_cell=0.2)       # cell below the 0.25 cm minimum
     with pytest.raises(tpc.TpcError):
         tpc.tpc_workspace_size(bad, g, 10)
     assert tpc.tpc_error_string(tpc.TPC_ERR_DATA).startswith("invalid cluster")
@@ -89,12 +89,15 @@ def test_calib_entry_points_validate_arguments_without_the_gpu():
     assert rc == tpc.TPC_ERR_ARG
 
 
-def test_packed_links_need_a_cell_longer_than_window_plus_rounding():
+def test_grid_parameter_limits_and_packed_workspace():
     import paper_1905_05515_b300 as tpc
     import tpcgen
     g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
-    with pytest.raises(tpc.TpcError):
-        tpc.tpc_workspace_size(tpc.tpc_params_default(packed_links=1, z_cell=3.01), g, 1000)
+    for bad in (dict(z_cell=0.1), dict(y_bins=0), dict(y_bins=65)):
+        with pytest.raises(tpc.TpcError):
+            tpc.tpc_workspace_size(tpc.tpc_params_default(**bad), g, 1000)
+    # any cell size at or above 0.25 cm works: searches visit the cells a window overlaps
+    assert tpc.tpc_workspace_size(tpc.tpc_params_default(z_cell=1.0, y_bins=32), g, 1000) > 0
     plain = tpc.tpc_workspace_size(tpc.tpc_params_default(z_cell=3.5), g, 1000)
     packed = tpc.tpc_workspace_size(tpc.tpc_params_default(packed_links=1, z_cell=3.5), g, 1000)
     assert packed >= plain + 4 * 1000          # the 4-byte packed words
