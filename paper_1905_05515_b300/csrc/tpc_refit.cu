@@ -124,6 +124,7 @@ __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my,
 struct RefitArgs {
     const void* frame;
     const float4* tcl;      // track clusters in track order: y, z, row x, sector (int bits)
+    const int32_t* order;   // tracks by decreasing cluster count (nullable)
     const int32_t* ttail;
     const float* t_top;
     int ns, passes, fp64, max_tracks, prof;
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
     if (f->err) return;
     unsigned nprop = 0;
     const int T = min(f->n_tracks, R.max_tracks);
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        const int r = R.order ? R.order[i] : i;       // longest tracks first: similar lengths share a warp
         const int off = R.out.clus_offset[r];
         const int n = R.out.nclus[r];
         const float* ts = R.t_top + (int64_t)R.ttail[r] * NST;
@@ -230,12 +232,14 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
 
 }  // namespace
 
-int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const void* frame,
-                     const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st)
+int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const int32_t* order,
+                     const void* frame, const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks,
+                     cudaStream_t st)
 {
     RefitArgs R;
     R.frame = frame;
     R.tcl = tcl;
+    R.order = order;
     R.ttail = ttail;
     R.t_top = t_top;
     R.ns = g->n_sectors;

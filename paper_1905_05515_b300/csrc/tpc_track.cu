@@ -30,6 +30,7 @@ constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
+constexpr int LEN_BUCKETS = 512;        // refit ordering: cluster counts above 511 share a bucket
 constexpr int MAX_FRAMES = 4096;
 // grid cell budget of a batch beyond the first frame's max_z_cells: two
 // cells per cluster (a 50-collision frame occupies about 0.6 clusters per
@@ -49,10 +50,10 @@ struct Layout {
     int64_t ncells;                    // grid cell capacity (all frames)
     size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, yzp, ids, plane;
     size_t upr, dnr, up, dn, starts;
-    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept;
+    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, segoff, segrank;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
-    size_t headmark, tcount, thead, ttail, tcl;
+    size_t headmark, tcount, thead, ttail, tcl, lencnt, order;
     size_t total;
 };
 
@@ -152,7 +153,10 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.t_bot = take(4 * T * NST);
     L.hitw = take(8 * N);
     L.t_kept = take(T);
+    L.t_own = take(4 * T);      // hits each tracklet owns after the selector
     L.seg = take(4 * T);
+    L.segoff = take(4 * T);     // per segment: first cluster within its track
+    L.segrank = take(4 * T);    // per segment: its track (-1: in no track)
     L.keyb = take(4 * T);
     L.keyt = take(4 * T);
     L.slotb = take(4 * T);
@@ -175,6 +179,8 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.thead = take(4 * T);
     L.ttail = take(4 * T);
     L.tcl = take(16 * N);       // track clusters in track order: y, z, row x, sector
+    L.lencnt = take(4 * (LEN_BUCKETS + 1));
+    L.order = take(4 * T);      // refit order
     L.total = o;
     return L;
 }
@@ -917,17 +923,17 @@ __global__ void k_sel_weight(const Frame* __restrict__ f, int cap, int nr, int m
 __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned, const int32_t* __restrict__ t_id,
                           const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
                           const int32_t* __restrict__ t_hits, const unsigned long long* __restrict__ hitw,
-                          uint8_t* __restrict__ kept, int32_t* __restrict__ seg)
+                          uint8_t* __restrict__ kept, int32_t* __restrict__ seg, int32_t* __restrict__ t_own)
 {
     const int nt = min(f->n_starts, cap);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const int nh = t_nhits[t];
         uint8_t k = 0;
+        int own = 0;
         if (nh >= min_hits) {
             const unsigned long long w = tracklet_weight(nh, t_id[t]);
             const int32_t* slot = t_hits + (int64_t)t * nr;
             const int nup = t_nup[t];
-            int own = 0;
             for (int q = 0; q < nh; q++) own += hitw[trk_hit(slot, nr, nh, nup, q)] == w;
             if (own >= min_owned && 2 * own >= nh) {
                 k = 1;
@@ -935,6 +941,7 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
             }
         }
         kept[t] = k;
+        t_own[t] = own;
     }
 }
 
@@ -1189,8 +1196,13 @@ struct AsmArgs {
     const float2* yz;
     const float* rowtab;
     float4* tcl;                // [clusters in tracks]: y, z, row x, sector (int bits)
+    const int32_t* t_own;       // owned hits per tracklet (selector)
+    int32_t* segoff;            // per segment: first cluster within its track
+    int32_t* segrank;           // per segment: its track, -1 if in none
 };
 
+// per track head: walk the chain, give every segment its track and its
+// first cluster within the track (owned hits of the segments before it)
 __global__ void k_track_count(AsmArgs A)
 {
     const int nseg = A.f->n_seg;
@@ -1199,11 +1211,9 @@ __global__ void k_track_count(AsmArgs A)
         const int rank = (int)A.headmark[A.t_id[A.seg[a]]];
         int cnt = 0, tail = a, steps = 0;
         for (int b = a; b >= 0 && steps <= MAX_CHAIN; b = A.next2[b], steps++) {
-            const int t = A.seg[b];
-            const int nh = A.t_nhits[t], nup = A.t_nup[t];
-            const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
-            const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
-            for (int k = 0; k < nh; k++) cnt += A.hitw[trk_hit(slot, A.nr, nh, nup, k)] == w;
+            A.segoff[b] = cnt;
+            A.segrank[b] = rank;
+            cnt += A.t_own[A.seg[b]];
             tail = b;
         }
         A.tcount[rank] = (uint32_t)cnt;
@@ -1212,6 +1222,12 @@ __global__ void k_track_count(AsmArgs A)
     }
 }
 
+__device__ __forceinline__ bool asm_overflow(const AsmArgs& A, int T, uint32_t total)
+{
+    return T > A.cap_tracks || total > (uint32_t)A.cap_clus;
+}
+
+// per track: offsets, sizes, frame
 __global__ void k_track_fill(AsmArgs A)
 {
     const int T = (int)A.headmark[A.n];
@@ -1219,9 +1235,9 @@ __global__ void k_track_fill(AsmArgs A)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.f->n_tracks = T;
         A.f->n_clus = (int)total;
-        if (T > A.cap_tracks || total > (uint32_t)A.cap_clus) atomicExch(&A.f->err, TPC_ERR_CAPACITY);
+        if (asm_overflow(A, T, total)) atomicExch(&A.f->err, TPC_ERR_CAPACITY);
     }
-    if (T > A.cap_tracks || total > (uint32_t)A.cap_clus) return;
+    if (asm_overflow(A, T, total)) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
         const int a = A.thead[r];
         const uint32_t off = A.tcount[r];
@@ -1230,27 +1246,69 @@ __global__ void k_track_fill(AsmArgs A)
         if (r == T - 1) A.clus_offset[T] = (int)end;
         A.nclus[r] = (int)(end - off);
         if (A.frame) A.frame[r] = (int)(A.plane[A.t_start[A.seg[a]]] / (uint32_t)A.np);
-        uint32_t o = off;
-        int steps = 0;
-        for (int b = a; b >= 0 && steps <= MAX_CHAIN; b = A.next2[b], steps++) {
-            const int t = A.seg[b];
-            const int nh = A.t_nhits[t], nup = A.t_nup[t];
-            const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
-            const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
-            for (int k = 0; k < nh; k++) {
-                const int h = trk_hit(slot, A.nr, nh, nup, k);
-                if (A.hitw[h] == w) {
-                    const int id = A.ids[h];
-                    const int pl = (int)(A.plane[h] % (uint32_t)A.np);
-                    const int sec = pl / A.nr;
-                    const float2 c = A.yz[h];
-                    A.tcl[o] = make_float4(c.x, c.y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
-                    A.clus_index[o++] = id;
-                    A.assign[id] = r;
-                }
+    }
+}
+
+// one warp per segment: its owned hits, in ascending row, at the segment's
+// place in its track's cluster list (ballot compaction keeps the order)
+__global__ void k_seg_fill(AsmArgs A)
+{
+    const int T = (int)A.headmark[A.n];
+    const uint32_t total = A.tcount[A.ntcap];
+    if (asm_overflow(A, T, total)) return;
+    const int nseg = A.f->n_seg;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nseg; b += nwarp) {
+        const int r = A.segrank[b];
+        if (r < 0) continue;
+        const int t = A.seg[b];
+        const int nh = A.t_nhits[t], nup = A.t_nup[t];
+        const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
+        const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
+        uint32_t o = A.tcount[r] + (uint32_t)A.segoff[b];
+        for (int k0 = 0; k0 < nh; k0 += 32) {
+            const int k = k0 + lane;
+            const int h = k < nh ? trk_hit(slot, A.nr, nh, nup, k) : 0;
+            const bool mine = k < nh && A.hitw[h] == w;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+            if (mine) {
+                const uint32_t q = o + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                const int id = A.ids[h];
+                const int pl = (int)(A.plane[h] % (uint32_t)A.np);
+                const int sec = pl / A.nr;
+                const float2 c = A.yz[h];
+                A.tcl[q] = make_float4(c.x, c.y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
+                A.clus_index[q] = id;
+                A.assign[id] = r;
             }
+            o += (uint32_t)__popc(m);
         }
     }
+}
+
+// Longest-first order of the tracks for the refit (one thread per track: a
+// warp then holds tracks of similar length).  Bucket = LEN_BUCKETS-1 -
+// min(n, LEN_BUCKETS-1).  Only the schedule depends on this order (each
+// track's refit is independent), so the atomic placement within a bucket may
+// vary from run to run without changing any result.
+__device__ __forceinline__ int len_bucket(int n) { return LEN_BUCKETS - 1 - min(n, LEN_BUCKETS - 1); }
+
+__global__ void k_len_hist(const Frame* __restrict__ f, const int32_t* __restrict__ nclus, int cap,
+                           uint32_t* __restrict__ cnt)
+{
+    const int T = f->err ? 0 : min(f->n_tracks, cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[len_bucket(nclus[r])], 1u);
+}
+
+// cnt: exclusive starts of the buckets on entry
+__global__ void k_len_scatter(const Frame* __restrict__ f, const int32_t* __restrict__ nclus, int cap,
+                              uint32_t* __restrict__ cnt, int32_t* __restrict__ order)
+{
+    const int T = f->err ? 0 : min(f->n_tracks, cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x)
+        order[atomicAdd(&cnt[len_bucket(nclus[r])], 1u)] = r;
 }
 
 // counts for the enqueue-only call: n_tracks, n_tracklets, n_segments, error,
@@ -1392,8 +1450,9 @@ int out_args(const tpc_params* p, const tpc_tracks* out)
 }  // namespace
 
 // refit launcher (tpc_refit.cu)
-int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const void* frame,
-                     const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks, cudaStream_t st);
+int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const float4* tcl, const int32_t* order,
+                     const void* frame, const int32_t* ttail, const float* t_top, tpc_tracks* out, int max_tracks,
+                     cudaStream_t st);
 
 namespace {
 
@@ -1487,9 +1546,10 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     const int gt2 = grid_for(ntcap, B);
     uint8_t* kept = at<uint8_t>(ws, L.t_kept);
     int32_t* seg = at<int32_t>(ws, L.seg);
+    const int gt2w = grid_for((int64_t)ntcap * 32, B);      // one warp per tracklet
     k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
     k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
-                                 TA.t_hits, hitw, kept, seg);
+                                 TA.t_hits, hitw, kept, seg, at<int32_t>(ws, L.t_own));
     g_launches += 2;
     CK(mark(6));
     // a8: merger
@@ -1540,15 +1600,26 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     AA.clus_offset = out->clus_offset; AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
     AA.frame = out->frame;
     AA.yz = yz; AA.rowtab = rowtab; AA.tcl = at<float4>(ws, L.tcl);
+    AA.t_own = at<int32_t>(ws, L.t_own); AA.segoff = at<int32_t>(ws, L.segoff); AA.segrank = at<int32_t>(ws, L.segrank);
+    CK(cudaMemsetAsync(AA.segrank, 0xFF, sizeof(int32_t) * (size_t)ntcap, st));   // -1: in no track
     k_track_count<<<gt2, B, 0, st>>>(AA);
     g_launches++;
     scan_u32(tcount, ntcap, aux, st);
     k_track_fill<<<gt2, B, 0, st>>>(AA);
-    g_launches++;
+    k_seg_fill<<<gt2w, B, 0, st>>>(AA);
+    g_launches += 2;
     CK(mark(8));
     // a9: refit
-    int rr = tpc_launch_refit(p, g, bz, AA.tcl, f, AA.ttail, TA.t_top, out, std::min(out->capacity_tracks, ntcap),
-                              st);
+    // refit order: tracks by decreasing cluster count (counting sort over LEN_BUCKETS)
+    uint32_t* lcnt = at<uint32_t>(ws, L.lencnt);
+    int32_t* order = at<int32_t>(ws, L.order);
+    CK(cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * (LEN_BUCKETS + 1), st));
+    k_len_hist<<<gt2, B, 0, st>>>(f, out->nclus, out->capacity_tracks, lcnt);
+    scan_u32(lcnt, LEN_BUCKETS, aux, st);
+    k_len_scatter<<<gt2, B, 0, st>>>(f, out->nclus, out->capacity_tracks, lcnt, order);
+    g_launches += 2;
+    int rr = tpc_launch_refit(p, g, bz, AA.tcl, order, f, AA.ttail, TA.t_top, out,
+                              std::min(out->capacity_tracks, ntcap), st);
     if (rr) return rr;
     g_launches++;
     CK(mark(9));
