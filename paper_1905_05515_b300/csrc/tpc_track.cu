@@ -48,7 +48,7 @@ struct Layout {
     uint32_t magic;
     int32_t n, ns, nr, np, nzmax, ntcap, mnzmax, ny, nframes;
     int64_t ncells;                    // grid cell capacity (all frames)
-    size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, yzp, ids, plane;
+    size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, sc, yzp;
     size_t upr, dnr, up, dn, starts;
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, segoff, segrank;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
@@ -135,10 +135,8 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.slot = take(4 * N);
     L.cstart = take(4 * (L.ncells + 1));
     L.scan = take(4 * scan_aux_elems(scan_max));
-    L.yz = take(8 * N);
+    L.sc = take(16 * N);        // sorted clusters: y, z, input index, plane
     L.yzp = p->packed_links ? take(4 * N) : 0;
-    L.ids = take(4 * N);
-    L.plane = take(4 * N);
     L.upr = take(4 * N);
     L.dnr = take(4 * N);
     L.up = take(4 * N);
@@ -418,6 +416,11 @@ __global__ void k_hist(int n, const uint8_t* __restrict__ sector, const uint8_t*
     }
 }
 
+// Sorted cluster record (16 bytes): y, z, input index, plane
+// (frame * planes + sector * rows + row), loaded with one vector access.
+__device__ __forceinline__ int sc_id(const float4& c) { return __float_as_int(c.z); }
+__device__ __forceinline__ uint32_t sc_plane(const float4& c) { return __float_as_uint(c.w); }
+
 // Packed link coordinates: a coordinate v is the fixed-point integer
 // q = rint(v * 256) (step 2^-8 cm, exact in binary32 for |v| < 2^16 cm); the
 // packed word holds the low 16 bits of q_y and q_z.  A reader recovers q from
@@ -437,16 +440,15 @@ __device__ __forceinline__ int unwrap16(uint32_t lo, int qref)
 __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
                           const float* __restrict__ y, const float* __restrict__ zlin, const uint16_t* __restrict__ cfr,
                           int nr, int np, const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ cell,
-                          const uint32_t* __restrict__ slot, float2* __restrict__ yz, int32_t* __restrict__ ids,
-                          uint32_t* __restrict__ plane, const Frame* __restrict__ f, uint32_t* __restrict__ yzp)
+                          const uint32_t* __restrict__ slot, float4* __restrict__ sc, const Frame* __restrict__ f,
+                          uint32_t* __restrict__ yzp)
 {
     if (f->err) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pos = cstart[cell[i]] + slot[i];
-        yz[pos] = make_float2(y[i], zlin[i]);
+        const uint32_t pg = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
+        sc[pos] = make_float4(y[i], zlin[i], __int_as_float(i), __uint_as_float(pg));
         if (yzp) yzp[pos] = pack_yz(y[i], zlin[i]);
-        ids[pos] = i;
-        plane[pos] = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
     }
 }
 
@@ -496,15 +498,16 @@ constexpr int MAXD = 8;
 // every coordinate, the middle hit's too, rounded to the nearest 1/256 cm.
 template <bool PACKED>
 __global__ void __launch_bounds__(256) k_neighbours(
-    int n, int nr, int ns, int np, const float* __restrict__ rowtab, const float2* __restrict__ yz,
-    const int32_t* __restrict__ ids, const uint32_t* __restrict__ plane, const uint32_t* __restrict__ cstart,
+    int n, int nr, int ns, int np, const float* __restrict__ rowtab, const float4* __restrict__ sc,
+    const uint32_t* __restrict__ cstart,
     const Frame* __restrict__ f, const FrameGrid* __restrict__ fg, float DY, float DZ, float SMAX,
     int32_t* __restrict__ upr, int32_t* __restrict__ dnr, const uint32_t* __restrict__ yzp)
 {
     if (f->err) return;
     const int ny = f->ny;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
-        const uint32_t pg = plane[h];
+        const float4 ch = sc[h];
+        const uint32_t pg = sc_plane(ch);
         const int fr = (int)(pg / (uint32_t)np);
         const int pl = (int)(pg - (uint32_t)fr * np);
         const int s = pl / nr, r = pl - s * nr;
@@ -512,8 +515,7 @@ __global__ void __launch_bounds__(256) k_neighbours(
         float bs = 0.0f;
         if (r >= 1 && r <= nr - 2) {
             const FrameGrid G = fg[fr];
-            const float2 ph = yz[h];
-            float yh = ph.x, zh = ph.y;
+            float yh = ch.x, zh = ch.y;
             int qyh = 0, qzh = 0;
             if (PACKED) {
                 qyh = fixq(yh);
@@ -522,7 +524,10 @@ __global__ void __launch_bounds__(256) k_neighbours(
                 zh = unfixq(qzh);
             }
             auto coord = [&](int q) -> float2 {
-                if (!PACKED) return yz[q];
+                if (!PACKED) {
+                    const float4 c = sc[q];
+                    return make_float2(c.x, c.y);
+                }
                 const uint32_t wd = yzp[q];
                 return make_float2(unfixq(unwrap16(wd & 0xFFFFu, qyh)), unfixq(unwrap16(wd >> 16, qzh)));
             };
@@ -554,17 +559,17 @@ __global__ void __launch_bounds__(256) k_neighbours(
                         const float2 pu = coord(u);
                         const float yu = pu.x, zu = pu.y;
                         if (!(fabsf(yu - yu_pred) <= DY && fabsf(zu - zh) <= DZ)) continue;
-                        const int idu = ids[u];
+                        const int idu = sc_id(sc[u]);
                         auto consider = [&](int d) {
                             const float2 pd = coord(d);
                             const float yd = pd.x, zd = pd.y;
                             const float ey = __fmaf_rn(yu - yd, w, yd) - yh;
                             const float ez = __fmaf_rn(zu - zd, w, zd) - zh;
-                            const float sc = __fmaf_rn(ey, ey, ez * ez);
-                            if (!(sc < SMAX)) return;
-                            const int idd = ids[d];
-                            if (bu < 0 || sc < bs || (sc == bs && (idu < bidu || (idu == bidu && idd < bidd)))) {
-                                bu = u; bd = d; bs = sc; bidu = idu; bidd = idd;
+                            const float score = __fmaf_rn(ey, ey, ez * ez);
+                            if (!(score < SMAX)) return;
+                            const int idd = sc_id(sc[d]);
+                            if (bu < 0 || score < bs || (score == bs && (idu < bidu || (idu == bidu && idd < bidd)))) {
+                                bu = u; bd = d; bs = score; bidu = idu; bidd = idd;
                             }
                         };
                         if (!overflow) {
@@ -630,9 +635,7 @@ __global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* _
 // ---------------------------------------------------------------------------
 struct TrkArgs {
     const float* rowtab;
-    const float2* yz;
-    const int32_t* ids;
-    const uint32_t* plane;
+    const float4* sc;
     const uint32_t* cstart;
     const int32_t* up;
     const int32_t* starts;
@@ -660,12 +663,12 @@ __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G
         W.range(A.cstart, k, qb, qe);
         ncand += (unsigned)(qe - qb);
         for (int q = qb; q < qe; q++) {
-            const float2 pq = A.yz[q];
+            const float4 pq = A.sc[q];
             const float dy = pq.x - yp;
             const float dz = pq.y - zp;
             if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
             const float d2 = __fmaf_rn(dy, dy, dz * dz);
-            const int id = A.ids[q];
+            const int id = sc_id(pq);
             if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
                 best = q; bd = d2; bid = id;
             }
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
 #pragma unroll
                 for (int i = 0; i < NST; i++) bot[i] = keep_sh[i][threadIdx.x];
                 A.t_start[t] = h1;
-                A.t_id[t] = A.ids[h1];
+                A.t_id[t] = sc_id(A.sc[h1]);
                 A.t_nhits[t] = nu + nd;
                 A.t_nup[t] = nu;
             }
@@ -739,7 +742,8 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             if (t >= nt) break;
             // initial state at the start hit: y, z measured, slopes from the first link
             h1 = A.starts[t];
-            const uint32_t pg1 = A.plane[h1];
+            const float4 c1 = A.sc[h1];
+            const uint32_t pg1 = sc_plane(c1);
             const int fr = (int)(pg1 / (uint32_t)A.np);
             const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
             G = A.fg[fr];
@@ -750,7 +754,8 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             const int h2 = A.up[h1];
             const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
             const float dx12 = x2 - x1;
-            const float2 p1 = A.yz[h1], p2 = A.yz[h2];
+            const float4 c2 = A.sc[h2];
+            const float2 p1 = make_float2(c1.x, c1.y), p2 = make_float2(c2.x, c2.y);
             const float y1 = p1.x, z1 = p1.y;
             const float dy12 = p2.x - y1, dz12 = p2.y - z1;
             const float ty = __fdiv_rn(dy12, dx12);
@@ -769,7 +774,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             rc = r1;
             phase = PH_A;
             nx_h = h2;
-            nx_row = (int)A.plane[h2] - pgbase;
+            nx_row = (int)sc_plane(c2) - pgbase;
             nx_yz = p2;
         }
         if (phase == PH_CSTART) {
@@ -797,8 +802,9 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
                 // load the following chain hit while this step computes
                 nx_h = A.up[hn];
                 if (nx_h >= 0) {
-                    nx_row = (int)A.plane[nx_h] - pgbase;
-                    nx_yz = A.yz[nx_h];
+                    const float4 cn = A.sc[nx_h];
+                    nx_row = (int)sc_plane(cn) - pgbase;
+                    nx_yz = make_float2(cn.x, cn.y);
                 }
             }
         }
@@ -853,7 +859,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
             c = find_nearest(A, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand);
             if (c >= 0) {
-                const float2 pc = A.yz[c];
+                const float4 pc = A.sc[c];
                 my = pc.x;
                 mz = pc.y;
                 cmax = A.chi2cut;
@@ -954,14 +960,13 @@ __device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
 }
 
 // global sector index (frame * n_sectors + sector) of a segment's start hit
-__device__ __forceinline__ int seg_gsector(const uint32_t* plane, const int32_t* t_start, const int32_t* seg, int a,
-                                           int nr)
+__device__ __forceinline__ int seg_gsector(const float4* sc, const int32_t* t_start, const int32_t* seg, int a, int nr)
 {
-    return (int)(plane[t_start[seg[a]]] / (uint32_t)nr);
+    return (int)(sc_plane(sc[t_start[seg[a]]]) / (uint32_t)nr);
 }
 
 __global__ void k_seg_keys(const Frame* __restrict__ f, int ns, int nr, const int32_t* __restrict__ seg,
-                           const uint32_t* __restrict__ plane, const int32_t* __restrict__ t_start,
+                           const float4* __restrict__ sc, const int32_t* __restrict__ t_start,
                            const float* __restrict__ t_top, const float* __restrict__ t_bot,
                            uint32_t* __restrict__ cntb, uint32_t* __restrict__ cntt, uint32_t* __restrict__ keyb,
                            uint32_t* __restrict__ keyt, uint32_t* __restrict__ slotb, uint32_t* __restrict__ slott)
@@ -970,7 +975,7 @@ __global__ void k_seg_keys(const Frame* __restrict__ f, int ns, int nr, const in
     const int mnz = f->mnz;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
         const int t = seg[a];
-        const int gs = seg_gsector(plane, t_start, seg, a, nr);
+        const int gs = seg_gsector(sc, t_start, seg, a, nr);
         const int s = gs % ns;
         const uint32_t kb = (uint32_t)gs * mnz + merge_cell(fold(t_bot[(int64_t)t * NST + 2], s, ns), f);
         const uint32_t kt = (uint32_t)gs * mnz + merge_cell(fold(t_top[(int64_t)t * NST + 2], s, ns), f);
@@ -1022,7 +1027,7 @@ struct MergeArgs {
     int ns, nr;
     float kb, dz, chi2cut;
     const int32_t* seg;
-    const uint32_t* plane;
+    const float4* sc;
     const int32_t* t_start;
     const int32_t* t_id;
     const float* t_top;
@@ -1056,7 +1061,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
     unsigned nchi = 0;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
         const int ta = M.seg[a];
-        const int gsa = seg_gsector(M.plane, M.t_start, M.seg, a, M.nr);
+        const int gsa = seg_gsector(M.sc, M.t_start, M.seg, a, M.nr);
         const int fr = gsa / M.ns, sa = gsa - fr * M.ns;
         float top[NST];
 #pragma unroll
@@ -1095,7 +1100,7 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
         const int tb = M.seg[b];
-        const int gsb = seg_gsector(M.plane, M.t_start, M.seg, b, M.nr);
+        const int gsb = seg_gsector(M.sc, M.t_start, M.seg, b, M.nr);
         const int fr = gsb / M.ns, sb = gsb - fr * M.ns;
         float bot[NST];
 #pragma unroll
@@ -1181,8 +1186,7 @@ struct AsmArgs {
     const int32_t* t_nhits;
     const int32_t* t_nup;
     const int32_t* t_hits;
-    const int32_t* ids;
-    const uint32_t* plane;
+    const float4* sc;
     const unsigned long long* hitw;
     const uint32_t* headmark;   // scanned: rank of each head's start id
     uint32_t* tcount;           // [ntcap + 1]
@@ -1193,7 +1197,6 @@ struct AsmArgs {
     int32_t* clus_index;
     int32_t* assign;
     int32_t* frame;             // nullable
-    const float2* yz;
     const float* rowtab;
     float4* tcl;                // [clusters in tracks]: y, z, row x, sector (int bits)
     const int32_t* t_own;       // owned hits per tracklet (selector)
@@ -1245,7 +1248,7 @@ __global__ void k_track_fill(AsmArgs A)
         A.clus_offset[r] = (int)off;
         if (r == T - 1) A.clus_offset[T] = (int)end;
         A.nclus[r] = (int)(end - off);
-        if (A.frame) A.frame[r] = (int)(A.plane[A.t_start[A.seg[a]]] / (uint32_t)A.np);
+        if (A.frame) A.frame[r] = (int)(sc_plane(A.sc[A.t_start[A.seg[a]]]) / (uint32_t)A.np);
     }
 }
 
@@ -1274,10 +1277,10 @@ __global__ void k_seg_fill(AsmArgs A)
             const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
             if (mine) {
                 const uint32_t q = o + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                const int id = A.ids[h];
-                const int pl = (int)(A.plane[h] % (uint32_t)A.np);
+                const float4 c = A.sc[h];
+                const int id = sc_id(c);
+                const int pl = (int)(sc_plane(c) % (uint32_t)A.np);
                 const int sec = pl / A.nr;
-                const float2 c = A.yz[h];
                 A.tcl[q] = make_float4(c.x, c.y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
                 A.clus_index[q] = id;
                 A.assign[id] = r;
@@ -1328,19 +1331,19 @@ __global__ void k_publish(const Frame* __restrict__ f, int cap, int32_t* out)
 // ---------------------------------------------------------------------------
 // intermediate results in input-index space (optional outputs)
 // ---------------------------------------------------------------------------
-__global__ void k_export_links(int n, const int32_t* __restrict__ ids, const int32_t* __restrict__ upr,
+__global__ void k_export_links(int n, const float4* __restrict__ sc, const int32_t* __restrict__ upr,
                                const int32_t* __restrict__ dnr, const int32_t* __restrict__ up,
                                const int32_t* __restrict__ dn, int32_t* o_upr, int32_t* o_dnr, int32_t* o_up,
                                int32_t* o_dn, uint8_t* o_start, const Frame* __restrict__ f)
 {
     if (f->err) return;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
-        const int id = ids[h];
+        const int id = sc_id(sc[h]);
         const int a = upr[h], b = dnr[h], c = up[h], d = dn[h];
-        if (o_upr) o_upr[id] = a >= 0 ? ids[a] : -1;
-        if (o_dnr) o_dnr[id] = b >= 0 ? ids[b] : -1;
-        if (o_up) o_up[id] = c >= 0 ? ids[c] : -1;
-        if (o_dn) o_dn[id] = d >= 0 ? ids[d] : -1;
+        if (o_upr) o_upr[id] = a >= 0 ? sc_id(sc[a]) : -1;
+        if (o_dnr) o_dnr[id] = b >= 0 ? sc_id(sc[b]) : -1;
+        if (o_up) o_up[id] = c >= 0 ? sc_id(sc[c]) : -1;
+        if (o_dn) o_dn[id] = d >= 0 ? sc_id(sc[d]) : -1;
         if (o_start) o_start[id] = (c >= 0 && d < 0 && up[c] >= 0) ? 1 : 0;
     }
 }
@@ -1363,7 +1366,7 @@ constexpr int STATIC_MAX_PLANES = 36 * 255;
 constexpr int64_t STATIC_NCELLS = (int64_t)STATIC_MAX_PLANES * STATIC_NZ;
 
 struct StaticLayout {
-    size_t frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, yz, ids, plane, upr, dnr, up, dn, total;
+    size_t frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, sc, upr, dnr, up, dn, total;
 };
 
 constexpr size_t sa256(size_t v) { return (v + 255) / 256 * 256; }
@@ -1382,9 +1385,7 @@ constexpr StaticLayout static_layout()
     L.slot = o; o += sa256(4 * N);
     L.cstart = o; o += sa256(4 * (STATIC_NCELLS + 1));
     L.scan = o; o += sa256(4 * (STATIC_NCELLS / SCAN_TILE + 64));
-    L.yz = o; o += sa256(8 * N);
-    L.ids = o; o += sa256(4 * N);
-    L.plane = o; o += sa256(4 * N);
+    L.sc = o; o += sa256(16 * N);
     L.upr = o; o += sa256(4 * N);
     L.dnr = o; o += sa256(4 * N);
     L.up = o; o += sa256(4 * N);
@@ -1472,9 +1473,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     uint32_t* slot = at<uint32_t>(ws, L.slot);
     uint32_t* cstart = at<uint32_t>(ws, L.cstart);
     uint32_t* aux = at<uint32_t>(ws, L.scan);
-    float2* yz = at<float2>(ws, L.yz);
-    int32_t* ids = at<int32_t>(ws, L.ids);
-    uint32_t* plane = at<uint32_t>(ws, L.plane);
+    float4* sc = at<float4>(ws, L.sc);
     int32_t* upr = at<int32_t>(ws, L.upr);
     int32_t* dnr = at<int32_t>(ws, L.dnr);
     int32_t* up = at<int32_t>(ws, L.up);
@@ -1510,15 +1509,15 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     g_launches += 2;
     scan_u32(cstart, L.ncells, aux, st, &f->total_cells);
     uint32_t* yzp = p->packed_links ? at<uint32_t>(ws, L.yzp) : nullptr;
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, cstart, cell, slot, yz,
-                                ids, plane, f, yzp);
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, cstart, cell, slot, sc, f,
+                                yzp);
     g_launches++;
     CK(mark(2));
     if (yzp)
-        k_neighbours<true><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f, fg,
+        k_neighbours<true><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, sc, cstart, f, fg,
                                              p->dy_link, p->dz_link, p->s_max_link, upr, dnr, yzp);
     else
-        k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, yz, ids, plane, cstart, f,
+        k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, sc, cstart, f,
                                               fg, p->dy_link, p->dz_link, p->s_max_link, upr, dnr, nullptr);
     g_launches++;
     CK(mark(3));
@@ -1528,7 +1527,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     CK(mark(4));
     // a6: tracklets
     TrkArgs TA;
-    TA.rowtab = rowtab; TA.yz = yz; TA.ids = ids; TA.plane = plane; TA.cstart = cstart; TA.up = up;
+    TA.rowtab = rowtab; TA.sc = sc; TA.cstart = cstart; TA.up = up;
     TA.starts = starts; TA.f = f; TA.fg = fg; TA.nr = g->n_rows; TA.ns = g->n_sectors; TA.np = L.np; TA.cap = ntcap;
     TA.kb = kb; TA.vy = vy; TA.vz = vz; TA.c0s = p->c0_snp; TA.c0t = p->c0_tgl; TA.c0q = p->c0_qpt;
     TA.nsig = p->win_nsigma; TA.wmin = p->win_min; TA.wmax = p->win_max; TA.chi2cut = p->chi2_cut;
@@ -1562,7 +1561,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
     uint32_t* headmark = at<uint32_t>(ws, L.headmark);
     CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), st));
-    k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, g->n_rows, seg, plane, TA.t_start, TA.t_top, TA.t_bot, cntb, cntt,
+    k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, g->n_rows, seg, sc, TA.t_start, TA.t_top, TA.t_bot, cntb, cntt,
                                   at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt), at<uint32_t>(ws, L.slotb),
                                   at<uint32_t>(ws, L.slott));
     g_launches++;
@@ -1570,7 +1569,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     scan_u32(cntt, mcells, aux, st);
     MergeArgs M;
     M.f = f; M.ns = g->n_sectors; M.nr = g->n_rows; M.kb = kb; M.dz = p->merge_dz; M.chi2cut = p->merge_chi2;
-    M.seg = seg; M.plane = plane; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
+    M.seg = seg; M.sc = sc; M.t_start = TA.t_start; M.t_id = TA.t_id; M.t_top = TA.t_top; M.t_bot = TA.t_bot;
     M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
     M.recb = at<MergeRec>(ws, L.recb); M.rect = at<MergeRec>(ws, L.rect);
     M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
@@ -1595,11 +1594,11 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     AA.f = f; AA.nr = g->n_rows; AA.np = L.np; AA.n = n; AA.cap_tracks = out->capacity_tracks;
     AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
     AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_start = TA.t_start; AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits;
-    AA.t_nup = TA.t_nup; AA.t_hits = TA.t_hits; AA.ids = ids; AA.plane = plane; AA.hitw = hitw;
+    AA.t_nup = TA.t_nup; AA.t_hits = TA.t_hits; AA.sc = sc; AA.hitw = hitw;
     AA.headmark = headmark; AA.tcount = tcount; AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail);
     AA.clus_offset = out->clus_offset; AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
     AA.frame = out->frame;
-    AA.yz = yz; AA.rowtab = rowtab; AA.tcl = at<float4>(ws, L.tcl);
+    AA.rowtab = rowtab; AA.tcl = at<float4>(ws, L.tcl);
     AA.t_own = at<int32_t>(ws, L.t_own); AA.segoff = at<int32_t>(ws, L.segoff); AA.segrank = at<int32_t>(ws, L.segrank);
     CK(cudaMemsetAsync(AA.segrank, 0xFF, sizeof(int32_t) * (size_t)ntcap, st));   // -1: in no track
     k_track_count<<<gt2, B, 0, st>>>(AA);
@@ -1626,7 +1625,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     // optional intermediate outputs
     if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
     if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
-        k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
+        k_export_links<<<gN, B, 0, st>>>(n, sc, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
                                          out->link_dn, out->is_start, f);
         g_launches++;
     }
@@ -1883,7 +1882,10 @@ int tpc_export_tracklets(const void* ws, int32_t capacity, int32_t hits_stride, 
     CK(get(tp.data(), L.t_top, 4 * (size_t)nt * NST));
     CK(get(bt.data(), L.t_bot, 4 * (size_t)nt * NST));
     CK(get(kp.data(), L.t_kept, (size_t)nt));
-    CK(get(ids.data(), L.ids, 4 * (size_t)L.n));
+    // the input index is the third word of each 16-byte sorted-cluster record
+    if (L.n > 0)
+        CK(cudaMemcpy2D(ids.data(), sizeof(int32_t), static_cast<const char*>(ws) + L.sc + 2 * sizeof(float),
+                        4 * sizeof(float), sizeof(int32_t), (size_t)L.n, cudaMemcpyDeviceToHost));
     std::vector<int> order(nt);
     for (int i = 0; i < nt; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return id[a] < id[b]; });
@@ -1930,9 +1932,7 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     uint32_t* slot = at<uint32_t>(base, SL.slot);
     uint32_t* cstart = at<uint32_t>(base, SL.cstart);
     uint32_t* aux = at<uint32_t>(base, SL.scan);
-    float2* yz = at<float2>(base, SL.yz);
-    int32_t* ids = at<int32_t>(base, SL.ids);
-    uint32_t* plane = at<uint32_t>(base, SL.plane);
+    float4* sc = at<float4>(base, SL.sc);
     int32_t* upr = at<int32_t>(base, SL.upr);
     int32_t* dnr = at<int32_t>(base, SL.dnr);
     int32_t* up = at<int32_t>(base, SL.up);
@@ -1956,12 +1956,12 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, rowtab, g->n_rows, g->n_sectors, f, fg, cstart,
                              cell, slot);
     scan_u32(cstart, ncells, aux, st, &f->total_cells);
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, np, cstart, cell, slot, yz, ids,
-                                plane, f, nullptr);
-    k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, np, rowtab, yz, ids, plane, cstart, f, fg,
+    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, np, cstart, cell, slot, sc, f,
+                                nullptr);
+    k_neighbours<false><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, np, rowtab, sc, cstart, f, fg,
                                           p->dy_link, p->dz_link, p->s_max_link, upr, dnr, nullptr);
     k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
-    k_export_links<<<gN, B, 0, st>>>(n, ids, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);
+    k_export_links<<<gN, B, 0, st>>>(n, sc, upr, dnr, up, dn, nullptr, nullptr, link_up, link_dn, is_start, f);
     CK(cudaGetLastError());
     int err = 0;
     CK(cudaMemcpyAsync(&err, &f->err, sizeof(int), cudaMemcpyDeviceToHost, st));
