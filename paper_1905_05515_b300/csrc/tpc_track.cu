@@ -959,6 +959,15 @@ __device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
     return grid_cell(zeta, f->mzmin, f->minv_cs, f->mnz);
 }
 
+// merge cells [lo, hi] overlapping the candidate window |z' - z| <= dz (plus
+// WIN_MARGIN) of an end at z in sector s
+__device__ __forceinline__ void merge_window(float z, float dz, int s, int ns, const Frame* f, int& lo, int& hi)
+{
+    const float za = fold(z - (dz + WIN_MARGIN), s, ns), zb = fold(z + (dz + WIN_MARGIN), s, ns);
+    lo = merge_cell(fminf(za, zb), f);
+    hi = merge_cell(fmaxf(za, zb), f);
+}
+
 // global sector index (frame * n_sectors + sector) of a segment's start hit
 __device__ __forceinline__ int seg_gsector(const float4* sc, const int32_t* t_start, const int32_t* seg, int a, int nr)
 {
@@ -1067,7 +1076,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 #pragma unroll
         for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
         const MergeRec ra = merge_rec(top, 0, ta);
-        const int mc = merge_cell(fold(top[2], sa, M.ns), M.f);
+
         int best = -1, bid = 0;
         float bc = 0.0f;
         for (int dir = 1; dir >= -1; dir -= 2) {
@@ -1075,7 +1084,8 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
             if (sb < 0) continue;
             const int gsb = fr * M.ns + sb;
             const float sn = dir > 0 ? SIN20 : -SIN20;
-            const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
+            int lo, hi;
+            merge_window(top[2], M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
                 const MergeRec rb = M.recb[q];
@@ -1106,7 +1116,7 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
 #pragma unroll
         for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
         const MergeRec rb = merge_rec(bot, 0, tb);
-        const int mc = merge_cell(fold(bot[2], sb, M.ns), M.f);
+
         int best = -1, bid = 0;
         float bc = 0.0f;
         for (int d = 1; d >= -1; d -= 2) {
@@ -1115,7 +1125,8 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
             const int gsa = fr * M.ns + sa;
             // seen from A, B lies in direction -d
             const float sn = (-d) > 0 ? SIN20 : -SIN20;
-            const int lo = max(mc - 1, 0), hi = min(mc + 1, mnz - 1);
+            int lo, hi;
+            merge_window(bot[2], M.dz, sa, M.ns, M.f, lo, hi);
             const int qb = M.cntt[gsa * mnz + lo], qe = M.cntt[gsa * mnz + hi + 1];
             for (int q = qb; q < qe; q++) {
                 const MergeRec ra = M.rect[q];
@@ -1499,7 +1510,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                           g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
     }
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, NF, L.np, L.ny, p->z_cell, L.nzmax, (long long)L.ncells,
-                                   p->merge_dz * 1.1f + 0.5f, L.mnzmax, p->packed_links);
+                                   0.25f * p->merge_dz, L.mnzmax, p->packed_links);
     g_launches += 3;
     CK(mark(1));
     // a2: counting sort of the clusters into (frame, sector, row, z-cell, y-bin) order
@@ -1949,7 +1960,7 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     k_init_frame<<<1, 32, 0, st>>>(f, fg, 1);
     k_prep<<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
                                       g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
-    k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, p->merge_dz * 1.1f + 0.5f,
+    k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, 0.25f * p->merge_dz,
                                    MAX_MERGE_CELLS, 0);
     // the histogram must start at zero: the scratch keeps the previous call's contents
     k_zero_cells<<<grid_for(ncells + 1, B), B, 0, st>>>(cstart, f);
