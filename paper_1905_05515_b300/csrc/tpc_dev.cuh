@@ -247,7 +247,8 @@ struct Frame {
     int err;                       // TPC_ERR_* set by kernels (0 = ok)
     int n_starts, n_seg, n_tracks, n_clus;
     int n_bad;                     // clusters rejected by validation
-    int trk_next;                  // work queue head of the tracklet constructor
+    int trk_next;                  // work queue heads of the tracklet constructor's two passes
+    int trk_next2;
     // work counters (params.profile): tracklet propagations, updates, window
     // candidates examined; refit propagations; merger chi2 evaluations
     unsigned long long w_prop, w_upd, w_cand, w_refit_prop, w_merge;

@@ -50,7 +50,7 @@ struct Layout {
     int64_t ncells;                    // grid cell capacity (all frames)
     size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, sc, yzp;
     size_t upr, dnr, up, dn, starts;
-    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, segoff, segrank;
+    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, segoff, segrank, t_state;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
     size_t headmark, tcount, thead, ttail, tcl, lencnt, order;
@@ -152,6 +152,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.hitw = take(8 * N);
     L.t_kept = take(T);
     L.t_own = take(4 * T);      // hits each tracklet owns after the selector
+    L.t_state = take(4 * T * (size_t)(NST + 4));   // tracklet state between the constructor's passes
     L.seg = take(4 * T);
     L.segoff = take(4 * T);     // per segment: first cluster within its track
     L.segrank = take(4 * T);    // per segment: its track (-1: in no track)
@@ -636,6 +637,7 @@ __global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* _
 struct TrkArgs {
     const float* rowtab;
     const float4* sc;
+    float* t_state;             // [cap][NST + 4]: state after phase A, phase, rc, nu (two-pass mode)
     const uint32_t* cstart;
     const int32_t* up;
     const int32_t* starts;
@@ -694,6 +696,14 @@ constexpr int TRK_BLOCK = 128;
 // Kalman update each have a single call site shared by all phases, so a warp
 // whose lanes are in different phases still executes each of them once per
 // iteration.
+// PASS 0: the whole tracklet in one pass.  PASS 1: phase A only (the chain
+// fit, no window searches), then the state is saved.  PASS 2: phases B, C
+// from the saved states.  Split, the warps of pass 1 never wait for a search
+// (a warp otherwise pays the search latency whenever any of its lanes
+// searches), and the search phases of pass 2 run densely.  The operation
+// sequence of every tracklet is the same in either mode.
+constexpr int TSAVE = NST + 4;
+template <int PASS>
 __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
 {
     // the last accepted state of each lane (outer-end / inner-end candidate) lives
@@ -722,8 +732,18 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
     int32_t* slot = nullptr;
     for (;;) {
         // ---- bookkeeping transitions
+        if (PASS == 1 && (phase == PH_B || phase == PH_CSTART)) {
+            // end of phase A: save the state for the second pass
+            float* sv = A.t_state + (int64_t)t * TSAVE;
+#pragma unroll
+            for (int i = 0; i < NST; i++) sv[i] = st[i];
+            sv[NST] = __int_as_float(phase);
+            sv[NST + 1] = __int_as_float(rc);
+            sv[NST + 2] = __int_as_float(nu);
+            phase = PH_DONE;
+        }
         if (phase == PH_DONE) {
-            if (t >= 0) {
+            if (t >= 0 && PASS != 1) {
                 float* bot = A.t_bot + (int64_t)t * NST;
 #pragma unroll
                 for (int i = 0; i < NST; i++) bot[i] = keep_sh[i][threadIdx.x];
@@ -736,7 +756,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             const unsigned m = __activemask();
             const int leader = __ffs(m) - 1;
             int base = 0;
-            if ((int)lane == leader) base = atomicAdd(&A.fw->trk_next, __popc(m));
+            if ((int)lane == leader) base = atomicAdd(PASS == 2 ? &A.fw->trk_next2 : &A.fw->trk_next, __popc(m));
             base = __shfl_sync(m, base, leader);
             t = base + __popc(m & ((1u << lane) - 1u));
             if (t >= nt) break;
@@ -751,6 +771,20 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             r1 = pl1 - s * NR;
             lbase = s * NR;
             pgbase = (int)pg1 - r1;
+            if (PASS == 2) {
+                // continue from the state phase A left
+                const float* sv = A.t_state + (int64_t)t * TSAVE;
+#pragma unroll
+                for (int i = 0; i < NST; i++) st[i] = sv[i];
+                phase = __float_as_int(sv[NST]);
+                rc = __float_as_int(sv[NST + 1]);
+                nu = __float_as_int(sv[NST + 2]);
+                nd = 0;
+                miss = 0;
+                slot = A.t_hits + (int64_t)t * NR;
+                save_keep();
+                continue;
+            }
             const int h2 = A.up[h1];
             const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
             const float dx12 = x2 - x1;
@@ -808,6 +842,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
                 }
             }
         }
+        if (PASS == 1 && phase != PH_A) continue;   // saved at the top of the next iteration
         if (phase == PH_B) {                    // follow beyond the chain end
             if (rc + 1 < NR) target = rc + 1;
             else phase = PH_CSTART;
@@ -1548,8 +1583,10 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     TA.t_hits = at<int32_t>(ws, L.t_hits); TA.t_top = at<float>(ws, L.t_top); TA.t_bot = at<float>(ws, L.t_bot);
     const int gT = grid_for(ntcap, TRK_BLOCK);
     const int gQ = p->queue_blocks_per_sm > 0 ? std::min(gT, 148 * p->queue_blocks_per_sm) : gT;
-    k_tracklets<<<gQ, TRK_BLOCK, 0, st>>>(TA);
-    g_launches++;
+    TA.t_state = at<float>(ws, L.t_state);
+    k_tracklets<1><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    k_tracklets<2><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    g_launches += 2;
     CK(mark(5));
     // a7: selector
     CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)n, st));
