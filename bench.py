@@ -37,10 +37,11 @@ FLOPS_PROP = 181      # prop32: 71 for the state and Jacobian terms + 110 for F 
 FLOPS_UPDATE = 130    # update32: innovation, 2x2 inverse, chi2, gain, state, covariance
 FLOPS_CAND = 5        # one grid candidate in the following window: 2 sub + fused distance
 FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky solve (~250)
-# DRAM bytes (read + write) per cluster of the frame of one launch, from the
-# committed ncu capture of the same kernel build (profiles/k_tracklets_frame20.md,
-# 20-collision frame, scaled by clusters); None once the kernel changes
-NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 298.6}
+# DRAM bytes (read + write) per cluster of the frame of one stage (both
+# tracklet passes), from the committed ncu capture of the same kernel build
+# (profiles/k_tracklets_frame20.md, 20-collision frame, scaled by clusters);
+# None once the kernel changes
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 207.5}
 
 
 def parse():
@@ -81,6 +82,19 @@ def dist_setup(args):
         dist.init_process_group(backend)
         pg = dist
     return ws, rank, local, pg
+
+
+def over_ranks(pg, dev, times, counts):
+    """Replicas: the slowest rank's times (max over ranks) and the work of all
+    ranks (sum); without a process group the local values."""
+    if pg is None:
+        return tuple(times), tuple(counts)
+    import torch
+    t = torch.tensor(list(times), dtype=torch.float64, device=dev)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(c, op=pg.ReduceOp.SUM)
+    return tuple(float(x) for x in t.tolist()), tuple(float(x) for x in c.tolist())
 
 
 class ClockSampler:
@@ -260,15 +274,7 @@ def run_ours(args, ws, rank, local, pg):
     barrier()
 
     # ---- max over ranks, totals
-    vals = torch.tensor([ms, e2e_s, float(n)], dtype=torch.float64, device=dev)
-    if pg is not None:
-        mx = vals.clone()
-        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
-        tot = vals.clone()
-        pg.all_reduce(tot, op=pg.ReduceOp.SUM)
-        ms_max, e2e_max, n_total = float(mx[0]), float(mx[1]), float(tot[2])
-    else:
-        ms_max, e2e_max, n_total = ms, e2e_s, float(n)
+    (ms_max, e2e_max), (n_total,) = over_ranks(pg, dev, (ms, e2e_s), (float(n),))
     if rank != 0:
         return
     value = n_total * args.steps / (ms_max / 1e3)
@@ -487,10 +493,11 @@ def run_batch(args, ws, rank, local, pg):
             d2h += r.n_tracks * 6 * 4 + 4 * int(r.assign.numel())
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
+    (ms_graph, e2e_s), (n_all,) = over_ranks(pg, dev, (ms_graph, e2e_s), (float(n),))
     if rank != 0:
         return
     line = {
-        "metric": METRIC + " (batched sub-time-frames)", "value": n / (ms_graph / 1e3), "unit": "clusters/s",
+        "metric": METRIC + " (batched sub-time-frames)", "value": n_all / (ms_graph / 1e3), "unit": "clusters/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{nstf} sub-time-frames of U{{1..{args.max_coll}}} collisions, "
@@ -505,7 +512,7 @@ def run_batch(args, ws, rank, local, pg):
                    "final_refit": "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32",
                    "link_coordinates": "16-bit packed (1/256 cm)" if packed else "fp32",
                    "l2": "inputs (10 B/cluster) exceed the 126 MB L2; no flush"},
-        "e2e": {"value": n / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": n_all / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": gb.n_launches * args.steps,
         "clocks": clk.summary(),
     }
@@ -617,6 +624,7 @@ def run_calib(args, ws, rank, local, pg):
         float(loss.item())
         theta.grad.cpu()
     e2e_s = (time.perf_counter() - t0) / args.steps
+    (ms, e2e_s), (steps_all,) = over_ranks(pg, dev, (ms, e2e_s), (float(n_steps),))
     if rank != 0:
         return
     pk = FP32_PEAK_TFLOPS
@@ -625,7 +633,7 @@ def run_calib(args, ws, rank, local, pg):
     bw_tf = n_steps * fl / (t_dom * 1e-3) / 1e12
     line = {
         "metric": "calibration chi2 + adjoint gradient, track clusters/s on 1 B300",
-        "value": n_steps / (ms / 1e3), "unit": "track clusters/s", "n_gpus": ws, "steps": args.steps,
+        "value": steps_all / (ms / 1e3), "unit": "track clusters/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.collisions}-collision calibration frame (v_drift +0.3 %, t0 200 ns, "
@@ -637,7 +645,7 @@ def run_calib(args, ws, rank, local, pg):
         "roofline": {"bound": "alu", "stage": dom, "achieved": bw_tf, "peak": pk, "unit": "TFLOP/s",
                      "frac": bw_tf / pk, "traffic": None,
                      "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"},
-        "e2e": {"value": n_steps / e2e_s, "unit": "track clusters/s",
+        "e2e": {"value": steps_all / e2e_s, "unit": "track clusters/s",
                 "h2d_bytes_per_step": 4 * theta.numel(), "d2h_bytes_per_step": 4 + 4 * theta.numel()},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),

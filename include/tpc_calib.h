@@ -78,7 +78,11 @@ typedef struct {
 } tpc_calib_tracks;
 
 /* Device workspace (bytes) for n_tracks tracks holding at most n_clusters
- * clusters in total.  Errors: TPC_ERR_ARG. */
+ * clusters in total: a 256-byte header (error flag), one 48-byte reference
+ * checkpoint per TPC_CALIB_CKPT_STEPS steps of each track, the deviation
+ * after each track's last step (32 B) and the order in which both passes
+ * visit the tracks (by decreasing cluster count; 4 B).  Errors:
+ * TPC_ERR_ARG. */
 int tpc_calib_workspace_size(const tpc_geometry *g, int32_t n_tracks, int64_t n_clusters, size_t *bytes);
 
 /* Forward pass: chi2[r] (binary32) and used[r] (1: the track entered the

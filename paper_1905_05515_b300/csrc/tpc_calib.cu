@@ -66,6 +66,7 @@ struct CalibArgs {
     double* grad;
     float4* ckpt;
     float4* dfin;                       // [T][2]: deviation after the vertex step
+    int32_t* order;                     // [T]: tracks by decreasing cluster count
     int32_t* err;
     float rowx[256];
 };
@@ -389,7 +390,8 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
     load_spline(A, spl);
     load_row_basis(A, rb);
     __syncthreads();
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < A.T; r += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.T; i += gridDim.x * blockDim.x) {
+        const int r = A.order[i];               // longest tracks first: similar lengths share a warp
         int off, n;
         const float tc = A.tcoll[r];
         float chi2 = 0.0f;
@@ -540,7 +542,8 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
     __syncthreads();
     const float ivy = 1.0f / A.vy, ivz = 1.0f / A.vz;
     BackRec rec[SEG];
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < A.T; r += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.T; i += gridDim.x * blockDim.x) {
+        const int r = A.order[i];               // longest tracks first: similar lengths share a warp
         if (!A.used_in[r]) continue;
         const float wr = A.dchi2[r];
         int off, n;
@@ -615,6 +618,36 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
     if (threadIdx.x < 2 && gvt[threadIdx.x] != 0.0) atomicAdd(&A.grad[threadIdx.x], gvt[threadIdx.x]);
 }
 
+// One block: counting sort of the tracks by decreasing cluster count into
+// A.order (schedule only; every track's results are independent of it).
+constexpr int ORDER_BUCKETS = 1024;
+__global__ void __launch_bounds__(ORDER_BUCKETS) k_calib_order(CalibArgs A)
+{
+    __shared__ unsigned cnt[ORDER_BUCKETS];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [&](int r) {
+        const int n = A.off[r + 1] - A.off[r];
+        return ORDER_BUCKETS - 1 - min(max(n, 0), ORDER_BUCKETS - 1);
+    };
+    for (int r = threadIdx.x; r < A.T; r += blockDim.x) atomicAdd(&cnt[bucket(r)], 1u);
+    __syncthreads();
+    // exclusive scan of the bucket counts (Hillis-Steele on the inclusive sums)
+    unsigned v = cnt[threadIdx.x];
+    for (int o = 1; o < ORDER_BUCKETS; o <<= 1) {
+        __syncthreads();
+        const unsigned add = threadIdx.x >= (unsigned)o ? cnt[threadIdx.x - o] : 0u;
+        __syncthreads();
+        cnt[threadIdx.x] += add;
+    }
+    __syncthreads();
+    const unsigned excl = cnt[threadIdx.x] - v;
+    __syncthreads();
+    cnt[threadIdx.x] = excl;
+    __syncthreads();
+    for (int r = threadIdx.x; r < A.T; r += blockDim.x) A.order[atomicAdd(&cnt[bucket(r)], 1u)] = r;
+}
+
 int fill_args(const tpc_params* p, const tpc_geometry* g, float bz, float v_nominal, float vertex_var,
               const tpc_calib_tracks* tr, const float* theta, CalibArgs& A)
 {
@@ -661,8 +694,10 @@ int fill_args(const tpc_params* p, const tpc_geometry* g, float bz, float v_nomi
 }
 
 size_t ckpt_slots(int32_t T, int64_t ncl) { return (size_t)(ncl / SEG) + (size_t)T + 1; }
-// workspace: header, checkpoints (CK_FLOATS per slot), final deviations (8 floats per track)
+// workspace: header, checkpoints (CK_FLOATS per slot), final deviations (8
+// floats per track), the track order (1 int per track, 16-byte padded)
 size_t dfin_offset(int32_t T, int64_t ncl) { return HDR_BYTES + ckpt_slots(T, ncl) * CK_FLOATS * sizeof(float); }
+size_t order_offset(int32_t T, int64_t ncl) { return dfin_offset(T, ncl) + (size_t)T * 8 * sizeof(float); }
 
 int calib_grid(int T)
 {
@@ -677,7 +712,7 @@ extern "C" {
 int tpc_calib_workspace_size(const tpc_geometry* g, int32_t n_tracks, int64_t n_clusters, size_t* bytes)
 {
     if (!g || !bytes || n_tracks < 0 || n_clusters < 0 || n_clusters > (int64_t)INT32_MAX) return TPC_ERR_ARG;
-    *bytes = dfin_offset(n_tracks, n_clusters) + (size_t)n_tracks * 8 * sizeof(float);
+    *bytes = order_offset(n_tracks, n_clusters) + ((size_t)n_tracks + 3) / 4 * 16;
     return TPC_OK;
 }
 
@@ -697,9 +732,11 @@ int tpc_calib_forward(const tpc_params* p, const tpc_geometry* g, float bz, floa
     A.err = static_cast<int32_t*>(workspace);
     A.ckpt = reinterpret_cast<float4*>(static_cast<char*>(workspace) + HDR_BYTES);
     A.dfin = reinterpret_cast<float4*>(static_cast<char*>(workspace) + dfin_offset(A.T, A.ncl));
+    A.order = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + order_offset(A.T, A.ncl));
     A.chi2 = chi2;
     A.used = used;
     if (A.T == 0) return TPC_OK;
+    k_calib_order<<<1, ORDER_BUCKETS, 0, st>>>(A);        // the backward pass reuses this order
     k_calib_fwd<<<calib_grid(A.T), CALIB_BLOCK, 0, st>>>(A);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }
@@ -722,6 +759,7 @@ int tpc_calib_backward(const tpc_params* p, const tpc_geometry* g, float bz, flo
     A.err = reinterpret_cast<int32_t*>(ws);
     A.ckpt = reinterpret_cast<float4*>(ws + HDR_BYTES);
     A.dfin = reinterpret_cast<float4*>(ws + dfin_offset(A.T, A.ncl));
+    A.order = reinterpret_cast<int32_t*>(ws + order_offset(A.T, A.ncl));
     A.used_in = used;
     A.dchi2 = dchi2;
     A.grad = grad;

@@ -69,8 +69,9 @@ def test_calib_entry_points_validate_arguments_without_the_gpu():
     g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
     b = C.c_size_t(0)
     assert L.tpc_calib_workspace_size(C.byref(g), 100, 15000, C.byref(b)) == tpc.TPC_OK
-    # header, 48-byte reference checkpoints (one per 16 clusters plus one per track), 32 bytes per track
-    assert b.value == 256 + (15000 // 16 + 100 + 1) * 48 + 100 * 32
+    # header, 48-byte reference checkpoints (one per 16 clusters plus one per track), 32 bytes per
+    # track (final deviation), the track order (4 bytes per track, 16-byte padded)
+    assert b.value == 256 + (15000 // 16 + 100 + 1) * 48 + 100 * 32 + (100 + 3) // 4 * 16
     assert L.tpc_calib_workspace_size(C.byref(g), -1, 10, C.byref(b)) == tpc.TPC_ERR_ARG
     p = tpc.tpc_params_default()
     tr = tpc.abi.TpcCalibTracks()
