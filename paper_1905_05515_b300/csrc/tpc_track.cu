@@ -1100,12 +1100,39 @@ __device__ __forceinline__ bool merge_screened(const MergeRec& top, const MergeR
     return dtl * dtl > lim * (top.a.w + bot.a.w) || dqp * dqp > lim * (top.b.x + bot.b.x);
 }
 
+// Lane-local best merge partner: the smallest chi2, ties to the smaller
+// start-hit id.  (chi2, id) orders the candidates of one end totally, so the
+// warp's reduction gives the same partner for any scan order.
+struct MergeBest {
+    int q;          // index in merge-grid order, -1: none
+    int id;
+    float c2;
+    __device__ __forceinline__ void offer(int q2, int id2, float c2b)
+    {
+        if (q < 0 || c2b < c2 || (c2b == c2 && id2 < id)) { q = q2; id = id2; c2 = c2b; }
+    }
+    __device__ __forceinline__ void warp_reduce()
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int q2 = __shfl_xor_sync(0xffffffffu, q, o);
+            const int id2 = __shfl_xor_sync(0xffffffffu, id, o);
+            const float c2b = __shfl_xor_sync(0xffffffffu, c2, o);
+            if (q2 >= 0) offer(q2, id2, c2b);
+        }
+    }
+};
+
+// One warp per segment end: the lanes read 32 consecutive candidate records
+// of the window at a time, screen them, and evaluate the chi2 of those left.
+
 // best B (outer piece) for every A: A's outer end against B's inner end
 __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 {
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     unsigned nchi = 0;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nseg; a += gridDim.x * blockDim.x) {
+    for (int a = blockIdx.x * wpb + (threadIdx.x >> 5); a < nseg; a += gridDim.x * wpb) {
         const int ta = M.seg[a];
         const int gsa = seg_gsector(M.sc, M.t_start, M.seg, a, M.nr);
         const int fr = gsa / M.ns, sa = gsa - fr * M.ns;
@@ -1113,9 +1140,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 #pragma unroll
         for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
         const MergeRec ra = merge_rec(top, 0, ta);
-
-        int best = -1, bid = 0;
-        float bc = 0.0f;
+        MergeBest b{-1, 0, 0.0f};
         for (int dir = 1; dir >= -1; dir -= 2) {
             const int sb = neighbour_sector(sa, dir, M.ns);
             if (sb < 0) continue;
@@ -1124,28 +1149,28 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
             int lo, hi;
             merge_window(top[2], M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
-            for (int q = qb; q < qe; q++) {
+            for (int q = qb + lane; q < qe; q += 32) {
                 const MergeRec rb = M.recb[q];
                 if (!(fabsf(rb.a.x - top[2]) <= M.dz)) continue;
                 if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
                 const int tb = __float_as_int(rb.b.z);
                 const float c2 = merge_chi2(top, M.t_bot + (int64_t)tb * NST, COS20, sn, M.kb);
                 nchi++;
-                if (!(c2 < M.chi2cut)) continue;
-                const int idb = __float_as_int(rb.b.y);
-                if (best < 0 || c2 < bc || (c2 == bc && idb < bid)) { best = M.byb[q]; bc = c2; bid = idb; }
+                if (c2 < M.chi2cut) b.offer(q, __float_as_int(rb.b.y), c2);
             }
         }
-        M.bnext[a] = best;
+        b.warp_reduce();
+        if (lane == 0) M.bnext[a] = b.q < 0 ? -1 : M.byb[b.q];
     }
-    if (M.prof) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
+    if (M.prof && nchi) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
 }
 
 // best A (inner piece) for every B
 __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
 {
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < nseg; b += gridDim.x * wpb) {
         const int tb = M.seg[b];
         const int gsb = seg_gsector(M.sc, M.t_start, M.seg, b, M.nr);
         const int fr = gsb / M.ns, sb = gsb - fr * M.ns;
@@ -1153,9 +1178,7 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
 #pragma unroll
         for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
         const MergeRec rb = merge_rec(bot, 0, tb);
-
-        int best = -1, bid = 0;
-        float bc = 0.0f;
+        MergeBest best{-1, 0, 0.0f};
         for (int d = 1; d >= -1; d -= 2) {
             const int sa = neighbour_sector(sb, d, M.ns);
             if (sa < 0) continue;
@@ -1165,18 +1188,17 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
             int lo, hi;
             merge_window(bot[2], M.dz, sa, M.ns, M.f, lo, hi);
             const int qb = M.cntt[gsa * mnz + lo], qe = M.cntt[gsa * mnz + hi + 1];
-            for (int q = qb; q < qe; q++) {
+            for (int q = qb + lane; q < qe; q += 32) {
                 const MergeRec ra = M.rect[q];
                 if (!(fabsf(bot[2] - ra.a.x) <= M.dz)) continue;
                 if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
                 const int ta = __float_as_int(ra.b.z);
                 const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, bot, COS20, sn, M.kb);
-                if (!(c2 < M.chi2cut)) continue;
-                const int ida = __float_as_int(ra.b.y);
-                if (best < 0 || c2 < bc || (c2 == bc && ida < bid)) { best = M.byt[q]; bc = c2; bid = ida; }
+                if (c2 < M.chi2cut) best.offer(q, __float_as_int(ra.b.y), c2);
             }
         }
-        M.bprev[b] = best;
+        best.warp_reduce();
+        if (lane == 0) M.bprev[b] = best.q < 0 ? -1 : M.byt[best.q];
     }
 }
 
@@ -1627,8 +1649,9 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
                                      at<int32_t>(ws, L.byt), seg, TA.t_id, TA.t_top, TA.t_bot,
                                      at<MergeRec>(ws, L.recb), at<MergeRec>(ws, L.rect));
-    k_merge_next<<<gT, 128, 0, st>>>(M);
-    k_merge_prev<<<gT, 128, 0, st>>>(M);
+    const int gTw = grid_for((int64_t)ntcap * 32, 128);    // one warp per segment end
+    k_merge_next<<<gTw, 128, 0, st>>>(M);
+    k_merge_prev<<<gTw, 128, 0, st>>>(M);
     k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
     k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
     k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
