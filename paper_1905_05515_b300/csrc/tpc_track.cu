@@ -50,7 +50,7 @@ struct Layout {
     int64_t ncells;                    // grid cell capacity (all frames)
     size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, sc, yzp;
     size_t upr, dnr, up, dn, starts;
-    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, segoff, segrank, t_state;
+    size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, ownmask, segoff, segrank, t_state;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
     size_t headmark, tcount, thead, ttail, tcl, lencnt, order;
@@ -152,6 +152,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.hitw = take(8 * N);
     L.t_kept = take(T);
     L.t_own = take(4 * T);      // hits each tracklet owns after the selector
+    L.ownmask = take(4 * T * (size_t)((L.nr + 31) / 32));   // [word][tracklet]: which of its hits it owns
     L.t_state = take(4 * T * (size_t)(NST + 4));   // tracklet state between the constructor's passes
     L.seg = take(4 * T);
     L.segoff = take(4 * T);     // per segment: first cluster within its track
@@ -966,7 +967,8 @@ __global__ void k_sel_weight(const Frame* __restrict__ f, int cap, int nr, int m
 __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned, const int32_t* __restrict__ t_id,
                           const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
                           const int32_t* __restrict__ t_hits, const unsigned long long* __restrict__ hitw,
-                          uint8_t* __restrict__ kept, int32_t* __restrict__ seg, int32_t* __restrict__ t_own)
+                          uint8_t* __restrict__ kept, int32_t* __restrict__ seg, int32_t* __restrict__ t_own,
+                          uint32_t* __restrict__ ownmask)
 {
     const int nt = min(f->n_starts, cap);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
@@ -977,7 +979,17 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
             const unsigned long long w = tracklet_weight(nh, t_id[t]);
             const int32_t* slot = t_hits + (int64_t)t * nr;
             const int nup = t_nup[t];
-            for (int q = 0; q < nh; q++) own += hitw[trk_hit(slot, nr, nh, nup, q)] == w;
+            // owned hits in ascending row order, as bits of words [q / 32][t]
+            uint32_t word = 0u;
+            for (int q = 0; q < nh; q++) {
+                const bool o = hitw[trk_hit(slot, nr, nh, nup, q)] == w;
+                own += o;
+                word |= (uint32_t)o << (q & 31);
+                if ((q & 31) == 31 || q == nh - 1) {
+                    ownmask[(int64_t)(q >> 5) * cap + t] = word;
+                    word = 0u;
+                }
+            }
             if (own >= min_owned && 2 * own >= nh) {
                 k = 1;
                 seg[atomicAdd(&f->n_seg, 1)] = t;
@@ -1257,7 +1269,7 @@ struct AsmArgs {
     const int32_t* t_nup;
     const int32_t* t_hits;
     const float4* sc;
-    const unsigned long long* hitw;
+    const uint32_t* ownmask;    // [word][ntcap]: owned hits of each tracklet (selector)
     const uint32_t* headmark;   // scanned: rank of each head's start id
     uint32_t* tcount;           // [ntcap + 1]
     int32_t* thead;
@@ -1337,15 +1349,12 @@ __global__ void k_seg_fill(AsmArgs A)
         if (r < 0) continue;
         const int t = A.seg[b];
         const int nh = A.t_nhits[t], nup = A.t_nup[t];
-        const unsigned long long w = tracklet_weight(nh, A.t_id[t]);
         const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
         uint32_t o = A.tcount[r] + (uint32_t)A.segoff[b];
         for (int k0 = 0; k0 < nh; k0 += 32) {
-            const int k = k0 + lane;
-            const int h = k < nh ? trk_hit(slot, A.nr, nh, nup, k) : 0;
-            const bool mine = k < nh && A.hitw[h] == w;
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
-            if (mine) {
+            const unsigned m = A.ownmask[(int64_t)(k0 >> 5) * A.ntcap + t];   // bits past nh are 0
+            if ((m >> lane) & 1u) {
+                const int h = trk_hit(slot, A.nr, nh, nup, k0 + lane);
                 const uint32_t q = o + (uint32_t)__popc(m & ((1u << lane) - 1u));
                 const float4 c = A.sc[h];
                 const int id = sc_id(c);
@@ -1620,7 +1629,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     const int gt2w = grid_for((int64_t)ntcap * 32, B);      // one warp per tracklet
     k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
     k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
-                                 TA.t_hits, hitw, kept, seg, at<int32_t>(ws, L.t_own));
+                                 TA.t_hits, hitw, kept, seg, at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
     g_launches += 2;
     CK(mark(6));
     // a8: merger
@@ -1667,7 +1676,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     AA.f = f; AA.nr = g->n_rows; AA.np = L.np; AA.n = n; AA.cap_tracks = out->capacity_tracks;
     AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
     AA.prev2 = at<int32_t>(ws, L.prev2); AA.t_start = TA.t_start; AA.t_id = TA.t_id; AA.t_nhits = TA.t_nhits;
-    AA.t_nup = TA.t_nup; AA.t_hits = TA.t_hits; AA.sc = sc; AA.hitw = hitw;
+    AA.t_nup = TA.t_nup; AA.t_hits = TA.t_hits; AA.sc = sc; AA.ownmask = at<uint32_t>(ws, L.ownmask);
     AA.headmark = headmark; AA.tcount = tcount; AA.thead = at<int32_t>(ws, L.thead); AA.ttail = at<int32_t>(ws, L.ttail);
     AA.clus_offset = out->clus_offset; AA.nclus = out->nclus; AA.clus_index = out->clus_index; AA.assign = out->assign;
     AA.frame = out->frame;
