@@ -87,7 +87,8 @@ __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my,
     const double s00 = c[0] + vy, s01 = c[1], s11 = c[2] + vz;
     const double det = s00 * s11 - s01 * s01;
     if (!(det > 0.0)) return false;
-    const double i00 = s11 / det, i01 = -s01 / det, i11 = s00 / det;
+    const double idet = 1.0 / det;       // one binary64 division (the FP64 pipe is the bound here)
+    const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
     chi2 += r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
     double K0[5], K1[5], C[5][5];
 #pragma unroll
@@ -104,19 +105,26 @@ __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my,
         acc(p[i], pl[i], (float)(K0[i] * r0 + K1[i] * r1));
         renorm(p[i], pl[i]);
     }
-    // A = I - K H (only columns 0, 1 differ from I); M = A C
+    // A = I - K H (only columns 0, 1 differ from I); M = A C, of which the
+    // lower triangle and columns 0, 1 are used (16 entries)
     double M[5][5];
 #pragma unroll
     for (int i = 0; i < 5; i++)
 #pragma unroll
-        for (int j = 0; j < 5; j++) M[i][j] = C[i][j] - K0[i] * C[0][j] - K1[i] * C[1][j];
+        for (int j = 0; j < 5; j++)
+            if (j <= i || j < 2) M[i][j] = C[i][j] - K0[i] * C[0][j] - K1[i] * C[1][j];
+    // C+ = M A^T + K V K^T, V = diag(vy, vz)
+    double VK0[5], VK1[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        VK0[j] = vy * K0[j];
+        VK1[j] = vz * K1[j];
+    }
 #pragma unroll
     for (int i = 0; i < 5; i++)
 #pragma unroll
-        for (int j = 0; j <= i; j++) {
-            const double mat = M[i][j] - M[i][0] * K0[j] - M[i][1] * K1[j];
-            c[CI(i, j)] = mat + K0[i] * vy * K0[j] + K1[i] * vz * K1[j];
-        }
+        for (int j = 0; j <= i; j++)
+            c[CI(i, j)] = M[i][j] - M[i][0] * K0[j] - M[i][1] * K1[j] + K0[i] * VK0[j] + K1[i] * VK1[j];
     return true;
 }
 
@@ -174,6 +182,9 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
     return true;
 }
 
+// FP64: the final pass in binary64 (a separate instance, so that the
+// binary32-only refit is not held to the binary64 pass's register count)
+template <bool FP64>
 __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
 {
     Frame* f = static_cast<Frame*>(const_cast<void*>(R.frame));
@@ -199,13 +210,13 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
         int sec = __float_as_int(R.tcl[off + n - 1].w);
         double chi2 = 0.0;
         bool ok = true;
-        const int nfloat = R.fp64 ? R.passes - 1 : R.passes;
+        const int nfloat = FP64 ? R.passes - 1 : R.passes;
         for (int pass = 0; pass < nfloat && ok; pass++) ok = run_pass<float>(R, off, n, (pass % 2) == 0, sec, x, p, pl, c, chi2, nprop, zref);
         double c64[15];
-        if (R.fp64 && ok) {
+        if (FP64) {
 #pragma unroll
             for (int k = 0; k < 15; k++) c64[k] = c[k];
-            ok = run_pass<double>(R, off, n, ((R.passes - 1) % 2) == 0, sec, x, p, pl, c64, chi2, nprop, zref);
+            if (ok) ok = run_pass<double>(R, off, n, ((R.passes - 1) % 2) == 0, sec, x, p, pl, c64, chi2, nprop, zref);
 #pragma unroll
             for (int k = 0; k < 15; k++) c[k] = (float)c64[k];
         }
@@ -221,7 +232,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
         R.out.chi2[r] = (float)chi2;
         R.out.ndf[r] = 2 * n - 5;
         R.out.status[r] = ok ? 0 : 1;
-        if (R.fp64) {
+        if (FP64) {
 #pragma unroll
             for (int k = 0; k < 15; k++) R.out.cov64[15 * (int64_t)r + k] = c64[k];
             R.out.chi2_64[r] = chi2;
@@ -257,6 +268,7 @@ int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const
     R.out = *out;
     const int64_t want = (max_tracks + 127) / 128;
     const int grid = (int)(want < 1 ? 1 : (want > 148 * 16 ? 148 * 16 : want));
-    k_refit<<<grid, 128, 0, st>>>(R);
+    if (R.fp64) k_refit<true><<<grid, 128, 0, st>>>(R);
+    else k_refit<false><<<grid, 128, 0, st>>>(R);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }

@@ -655,25 +655,37 @@ struct TrkArgs {
 
 // Nearest cluster of the plane inside |dy| <= wy, |dz| <= wz of (yp, zp):
 // minimum dy^2 + dz^2 (binary32, fused), ties to the smaller input index.
+// The index ranges of up to NZR z-cells are loaded before their candidates
+// are scanned, so that the lane waits for one round of grid loads, not one
+// per z-cell.
+constexpr int NZR = 2;
 __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G, int lplane, int r, int s, float yp,
                                             float zp, float wy, float wz, int ny, unsigned& ncand)
 {
     const WinCells W = window_cells(G, lplane, s, A.ns, A.rowtab, r, ny, yp, zp, wy, wz);
     int best = -1, bid = 0;
     float bd = 0.0f;
-    for (int k = 0; k < W.nzc; k++) {
-        int qb, qe;
-        W.range(A.cstart, k, qb, qe);
-        ncand += (unsigned)(qe - qb);
-        for (int q = qb; q < qe; q++) {
-            const float4 pq = A.sc[q];
-            const float dy = pq.x - yp;
-            const float dz = pq.y - zp;
-            if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
-            const float d2 = __fmaf_rn(dy, dy, dz * dz);
-            const int id = sc_id(pq);
-            if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
-                best = q; bd = d2; bid = id;
+    for (int k0 = 0; k0 < W.nzc; k0 += NZR) {
+        int qb[NZR], qe[NZR];
+#pragma unroll
+        for (int j = 0; j < NZR; j++) {
+            qb[j] = 0;
+            qe[j] = 0;
+            if (k0 + j < W.nzc) W.range(A.cstart, k0 + j, qb[j], qe[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NZR; j++) {
+            ncand += (unsigned)(qe[j] - qb[j]);
+            for (int q = qb[j]; q < qe[j]; q++) {
+                const float4 pq = A.sc[q];
+                const float dy = pq.x - yp;
+                const float dz = pq.y - zp;
+                if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
+                const float d2 = __fmaf_rn(dy, dy, dz * dz);
+                const int id = sc_id(pq);
+                if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
+                    best = q; bd = d2; bid = id;
+                }
             }
         }
     }
@@ -743,6 +755,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             sv[NST] = __int_as_float(phase);
             sv[NST + 1] = __int_as_float(rc);
             sv[NST + 2] = __int_as_float(nu);
+            sv[NST + 3] = __int_as_float(pgbase + r1);   // the start hit's plane
             phase = PH_DONE;
         }
         if (phase == PH_DONE) {
@@ -750,8 +763,10 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
                 float* bot = A.t_bot + (int64_t)t * NST;
 #pragma unroll
                 for (int i = 0; i < NST; i++) bot[i] = keep_sh[i][threadIdx.x];
-                A.t_start[t] = h1;
-                A.t_id[t] = sc_id(A.sc[h1]);
+                if (PASS == 0) {
+                    A.t_start[t] = h1;
+                    A.t_id[t] = sc_id(A.sc[h1]);
+                }
                 A.t_nhits[t] = nu + nd;
                 A.t_nup[t] = nu;
             }
@@ -763,6 +778,29 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             base = __shfl_sync(m, base, leader);
             t = base + __popc(m & ((1u << lane) - 1u));
             if (t >= nt) break;
+            if (PASS == 2) {
+                // continue from the state phase A left (the start hit's plane
+                // included: no load of the start hit itself)
+                const float* sv = A.t_state + (int64_t)t * TSAVE;
+                const uint32_t pg1 = (uint32_t)__float_as_int(sv[NST + 3]);
+                const int fr = (int)(pg1 / (uint32_t)A.np);
+                const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
+                G = A.fg[fr];
+                s = pl1 / NR;
+                r1 = pl1 - s * NR;
+                lbase = s * NR;
+                pgbase = (int)pg1 - r1;
+#pragma unroll
+                for (int i = 0; i < NST; i++) st[i] = sv[i];
+                phase = __float_as_int(sv[NST]);
+                rc = __float_as_int(sv[NST + 1]);
+                nu = __float_as_int(sv[NST + 2]);
+                nd = 0;
+                miss = 0;
+                slot = A.t_hits + (int64_t)t * NR;
+                save_keep();
+                continue;
+            }
             // initial state at the start hit: y, z measured, slopes from the first link
             h1 = A.starts[t];
             const float4 c1 = A.sc[h1];
@@ -774,19 +812,9 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             r1 = pl1 - s * NR;
             lbase = s * NR;
             pgbase = (int)pg1 - r1;
-            if (PASS == 2) {
-                // continue from the state phase A left
-                const float* sv = A.t_state + (int64_t)t * TSAVE;
-#pragma unroll
-                for (int i = 0; i < NST; i++) st[i] = sv[i];
-                phase = __float_as_int(sv[NST]);
-                rc = __float_as_int(sv[NST + 1]);
-                nu = __float_as_int(sv[NST + 2]);
-                nd = 0;
-                miss = 0;
-                slot = A.t_hits + (int64_t)t * NR;
-                save_keep();
-                continue;
+            if (PASS == 1) {
+                A.t_start[t] = h1;
+                A.t_id[t] = sc_id(c1);
             }
             const int h2 = A.up[h1];
             const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
