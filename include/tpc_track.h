@@ -76,10 +76,13 @@ typedef struct {
     float refit_inflate;         /* each pass restarts with the previous sin(phi), tan(lambda), q/pT
                                     covariance times this factor (y, z from the first measurement) */
     /* acceleration structure and capacities (do not change results) */
-    float z_cell;                /* minimum grid cell length in z (cm); must exceed dz_link, win_max */
+    float z_cell;                /* minimum grid cell length in z (cm, >= 0.25; default 5): the length
+                                    grows so that at most max_z_cells cells cover a frame's z extent.
+                                    Every search visits all cells its window overlaps, so any cell
+                                    size gives the same results. */
     int32_t max_z_cells;         /* maximum grid z-cells per pad row */
-    int32_t y_bins;              /* grid y-bins per z-cell (reduced as needed to keep every bin
-                                    wider than the y search windows) */
+    int32_t y_bins;              /* grid y-bins per z-cell, 1..64 (default 16): each pad row's width
+                                    split evenly */
     int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
     int32_t queue_blocks_per_sm; /* TrackletConstructor work-queue width: blocks per SM taking start
                                     hits from the queue (0: as many as the capacity needs, up to 16) */
@@ -88,7 +91,7 @@ typedef struct {
     int32_t packed_links;        /* 1: the link pass reads y, z as 16-bit packed fields of a fixed-point
                                     coordinate with step 2^-8 cm (decoded relative to the middle hit), i.e.
                                     it sees both rounded to the nearest 1/256 cm; other stages see full
-                                    precision.  Needs z_cell >= dz_link + 1/64 and z-cells under 60 cm. */
+                                    precision.  Needs z-cells under 60 cm (TPC_ERR_CAPACITY otherwise). */
 } tpc_params;
 
 /* Detector geometry (host memory). */

@@ -32,6 +32,11 @@ constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
 constexpr int LEN_BUCKETS = 512;        // refit ordering: cluster counts above 511 share a bucket
 constexpr int MAX_FRAMES = 4096;
+// Binning: every plane's count is split over PSPLIT counters (by cluster
+// index), so that the thousands of clusters of one plane do not all meet at
+// one atomic; a plane's counters are consecutive, so its clusters stay one
+// range.  Planes x PSPLIT < 2^32 (36 x 255 x MAX_FRAMES x 16).
+constexpr int PSPLIT = 16;
 // grid cell budget of a batch beyond the first frame's max_z_cells: two
 // cells per cluster (a 50-collision frame occupies about 0.6 clusters per
 // cell at the default cell size), never more than max_z_cells per frame
@@ -50,6 +55,7 @@ struct Layout {
     int64_t ncells;                    // grid cell capacity (all frames)
     size_t hdr, frame, fgrid, offsets, rowtab, zlin, cfr, cell, slot, cstart, scan, sc, yzp;
     size_t upr, dnr, up, dn, starts;
+    size_t pbuf, pstart;        // binning: plane-ordered records (aliases the links), plane starts
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, ownmask, segoff, segrank, t_state;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2;
@@ -121,7 +127,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     const int64_t N = std::max<int64_t>(n, 1);
     const int64_t T = L.ntcap;
     const int64_t mcells = (int64_t)nframes * L.ns * L.mnzmax;
-    int64_t scan_max = std::max({L.ncells + 1, N + 1, T + 1, mcells + 1});
+    int64_t scan_max = std::max({L.ncells + 1, N + 1, T + 1, mcells + 1, (int64_t)nframes * L.np * PSPLIT + 1});
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1), 256); return r; };
     L.hdr = take(sizeof(Layout));
@@ -137,10 +143,14 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.scan = take(4 * scan_aux_elems(scan_max));
     L.sc = take(16 * N);        // sorted clusters: y, z, input index, plane
     L.yzp = p->packed_links ? take(4 * N) : 0;
-    L.upr = take(4 * N);
-    L.dnr = take(4 * N);
-    L.up = take(4 * N);
-    L.dn = take(4 * N);
+    // the four link arrays, one 16-byte-per-cluster block: before the links
+    // exist it holds the plane-ordered cluster records of the binning
+    L.upr = take(16 * N);
+    L.dnr = L.upr + 4 * N;
+    L.up = L.dnr + 4 * N;
+    L.dn = L.up + 4 * N;
+    L.pbuf = L.upr;
+    L.pstart = take(4 * ((size_t)nframes * L.np * PSPLIT + 1));
     L.starts = take(4 * T);
     L.t_start = take(4 * T);
     L.t_id = take(4 * T);
@@ -296,10 +306,13 @@ __global__ void k_init_frame(Frame* f, FrameGrid* fg, int nframes)
 __device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
 
 // blockIdx.y = frame; the blocks of one frame stride over its cluster range
+__device__ __forceinline__ uint32_t plane_bucket(uint32_t pg, int i) { return pg * PSPLIT + ((uint32_t)i & (PSPLIT - 1)); }
+
 __global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
                        const uint8_t* __restrict__ row, const float* __restrict__ y, const float* __restrict__ zt,
                        int ns, int nr, int continuous, float zmax, float vdrift, float* __restrict__ zlin,
-                       uint16_t* __restrict__ cfr, Frame* f, FrameGrid* fg)
+                       uint16_t* __restrict__ cfr, Frame* f, FrameGrid* fg, int np, uint32_t* __restrict__ pcount,
+                       uint32_t* __restrict__ prank)
 {
     const int fr = blockIdx.y;
     const int b = offsets[fr], e = offsets[fr + 1];
@@ -322,6 +335,8 @@ __global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __res
         const unsigned k = fkey(fold(z, s, ns));
         kmin = min(kmin, k);
         kmax = max(kmax, k);
+        // rank of the cluster in its share of its plane (order of the atomics: any)
+        if (pcount) prank[i] = atomicAdd(&pcount[plane_bucket((uint32_t)fr * (uint32_t)np + (uint32_t)(s * nr + r), i)], 1u);
     }
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -454,6 +469,136 @@ __global__ void k_scatter(int n, const uint8_t* __restrict__ sector, const uint8
     }
 }
 
+
+// Binning in two steps.  (1) k_prep ranks every cluster among the clusters
+// of its plane (frame, sector, row) and k_pscatter moves its record into the
+// plane's range of the plane-ordered buffer.  (2) k_plane_sort, one block per
+// plane, counts the plane's clusters per cell (z-cell, y-bin) in shared
+// memory, writes the plane's cell starts and moves the records into cell
+// order.  Nothing of the size of the grid is zeroed, updated atomically or
+// scanned in global memory, so finer grids cost little here.  The order of
+// the clusters inside a cell depends on the atomics; no search depends on it.
+__global__ void k_pscatter(int n, const uint8_t* __restrict__ sector, const uint8_t* __restrict__ row,
+                           const float* __restrict__ y, const float* __restrict__ zlin, const uint16_t* __restrict__ cfr,
+                           int nr, int np, const uint32_t* __restrict__ pstart, const uint32_t* __restrict__ prank,
+                           float4* __restrict__ pbuf, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t pg = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
+        pbuf[pstart[plane_bucket(pg, i)] + prank[i]] = make_float4(y[i], zlin[i], __int_as_float(i), __uint_as_float(pg));
+    }
+}
+
+constexpr int PS_BLOCK = 256;
+constexpr int PS_ITEMS = 8;
+constexpr int PS_SMEM_CELLS = 16384;    // larger planes count in their global cell range
+
+// a[i] = base + a[0] + ... + a[i-1] for i < n (shared or global memory), by
+// one block: warp w scans 32 * PS_ITEMS consecutive entries of each chunk, a
+// row of 32 at a time.  Ends with a barrier.
+__device__ void block_excl_scan(uint32_t* a, int n, uint32_t base)
+{
+    __shared__ uint32_t wtot[PS_BLOCK / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int SEG = 32 * PS_ITEMS, CHUNK = PS_BLOCK * PS_ITEMS;
+    uint32_t carry = base;
+    for (int k0 = 0; k0 < n; k0 += CHUNK) {
+        const int s0 = k0 + w * SEG;
+        uint32_t v[PS_ITEMS];
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < PS_ITEMS; j++) {
+            const int i = s0 + j * 32 + lane;
+            const uint32_t x = i < n ? a[i] : 0u;
+            uint32_t inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            v[j] = run + inc - x;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) wtot[w] = run;
+        __syncthreads();
+        uint32_t off = carry, tot = 0;
+#pragma unroll
+        for (int k = 0; k < PS_BLOCK / 32; k++) {
+            const uint32_t t = wtot[k];
+            if (k < w) off += t;
+            tot += t;
+        }
+#pragma unroll
+        for (int j = 0; j < PS_ITEMS; j++) {
+            const int i = s0 + j * 32 + lane;
+            if (i < n) a[i] = off + v[j];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(PS_BLOCK) k_plane_sort(int nplanes, int np, int nr, int ns,
+                                                         const uint32_t* __restrict__ pstart,
+                                                         const float4* __restrict__ pbuf, uint32_t* __restrict__ rank,
+                                                         const float* __restrict__ rowtab, const Frame* __restrict__ f,
+                                                         const FrameGrid* __restrict__ fg, int smem_cells,
+                                                         uint32_t* __restrict__ cstart, float4* __restrict__ sc,
+                                                         uint32_t* __restrict__ yzp)
+{
+    extern __shared__ uint32_t cnt_sh[];
+    if (f->err) return;
+    const int ny = f->ny;
+    for (int p = blockIdx.x; p < nplanes; p += gridDim.x) {
+        const int fr = p / np, lpl = p - fr * np;
+        const int s = lpl / nr, r = lpl - s * nr;
+        const FrameGrid G = fg[fr];
+        const int nc = G.nz * ny;
+        const uint32_t cbase = G.cell_base + (uint32_t)lpl * (uint32_t)nc;
+        const uint32_t a = pstart[(size_t)p * PSPLIT], b = pstart[(size_t)(p + 1) * PSPLIT];
+        const bool in_sh = nc <= smem_cells;
+        uint32_t* cnt = in_sh ? cnt_sh : cstart + cbase;
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) cnt[c] = 0u;
+        __syncthreads();
+        // the cell of a record: the functions the window searches use
+        auto cell_of = [&](const float4& q) -> int {
+            const int zc = grid_cell(fold(q.y, s, ns), G.zmin, G.inv_cs, G.nz);
+            return zc * ny + ybin(q.x, rowtab, r, ny);
+        };
+        for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) rank[i] = atomicAdd(&cnt[cell_of(pbuf[i])], 1u);
+        __syncthreads();
+        block_excl_scan(cnt, nc, a);          // cnt[c]: sorted index of cell c's first cluster
+        if (in_sh)
+            for (int c = threadIdx.x; c < nc; c += blockDim.x) cstart[cbase + c] = cnt[c];
+        if (p == nplanes - 1 && threadIdx.x == 0) cstart[cbase + nc] = b;
+        for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+            const float4 q = pbuf[i];
+            const uint32_t d = cnt[cell_of(q)] + rank[i];
+            sc[d] = q;
+            if (yzp) yzp[d] = pack_yz(q.x, q.y);
+        }
+        __syncthreads();                      // cnt is reused by the block's next plane
+    }
+}
+
+// Shared-memory cells of k_plane_sort for planes of up to `want` cells: up
+// to PS_SMEM_CELLS once the kernel may use more than 48 KB, which is set
+// outside stream capture (once per device); 48 KB before that.
+int plane_sort_smem_cells(int64_t want, cudaStream_t st)
+{
+    static int done_dev[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (dev >= 0 && dev < 64 && !done_dev[dev] && cs == cudaStreamCaptureStatusNone &&
+        cudaFuncSetAttribute(k_plane_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(uint32_t) * PS_SMEM_CELLS)) == cudaSuccess)
+        done_dev[dev] = 1;
+    const int64_t cap = (dev >= 0 && dev < 64 && done_dev[dev]) ? PS_SMEM_CELLS : 48 * 1024 / (int)sizeof(uint32_t);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+}
 
 // The cells a search window overlaps: the z-cells c0..c1 of
 // [zp - wz, zp + wz] and, in each, the contiguous y-bins y0..y1 of
@@ -659,10 +804,11 @@ struct TrkArgs {
 // are scanned, so that the lane waits for one round of grid loads, not one
 // per z-cell.
 constexpr int NZR = 2;
-__device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G, int lplane, int r, int s, float yp,
-                                            float zp, float wy, float wz, int ny, unsigned& ncand)
+__device__ __forceinline__ int find_nearest(const TrkArgs& A, const float* rt, const FrameGrid& G, int lplane, int r,
+                                            int s, float yp,
+                                            float zp, float wy, float wz, int ny, unsigned& ncand, float& by, float& bz)
 {
-    const WinCells W = window_cells(G, lplane, s, A.ns, A.rowtab, r, ny, yp, zp, wy, wz);
+    const WinCells W = window_cells(G, lplane, s, A.ns, rt, r, ny, yp, zp, wy, wz);
     int best = -1, bid = 0;
     float bd = 0.0f;
     for (int k0 = 0; k0 < W.nzc; k0 += NZR) {
@@ -676,17 +822,23 @@ __device__ __forceinline__ int find_nearest(const TrkArgs& A, const FrameGrid& G
 #pragma unroll
         for (int j = 0; j < NZR; j++) {
             ncand += (unsigned)(qe[j] - qb[j]);
-            for (int q = qb[j]; q < qe[j]; q++) {
-                const float4 pq = A.sc[q];
+            auto cand = [&](const float4& pq, int q) {
                 const float dy = pq.x - yp;
                 const float dz = pq.y - zp;
-                if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) continue;
+                if (!(fabsf(dy) <= wy) || !(fabsf(dz) <= wz)) return;
                 const float d2 = __fmaf_rn(dy, dy, dz * dz);
                 const int id = sc_id(pq);
                 if (best < 0 || d2 < bd || (d2 == bd && id < bid)) {
-                    best = q; bd = d2; bid = id;
+                    best = q; bd = d2; bid = id; by = pq.x; bz = pq.y;
                 }
+            };
+            int q = qb[j];
+            for (; q + 1 < qe[j]; q += 2) {
+                const float4 p0 = A.sc[q], p1 = A.sc[q + 1];
+                cand(p0, q);
+                cand(p1, q + 1);
             }
+            if (q < qe[j]) cand(A.sc[q], q);
         }
     }
     return best;
@@ -724,6 +876,10 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
     // the last accepted state of each lane (outer-end / inner-end candidate) lives
     // in shared memory, element-major so that the lanes of a warp hit distinct banks
     __shared__ float keep_sh[NST][TRK_BLOCK];
+    // the row table (x, y-bin origin and scale are read at every step)
+    __shared__ float rt[ROWTAB * 256];
+    for (int i = threadIdx.x; i < ROWTAB * A.nr; i += blockDim.x) rt[i] = A.rowtab[i];
+    __syncthreads();
     if (A.f->err) return;
     const int ny = A.f->ny;
     const int nt = min(A.f->n_starts, A.cap);
@@ -817,7 +973,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
                 A.t_id[t] = sc_id(c1);
             }
             const int h2 = A.up[h1];
-            const float x1 = A.rowtab[r1 * ROWTAB], x2 = A.rowtab[(r1 + 1) * ROWTAB];
+            const float x1 = rt[r1 * ROWTAB], x2 = rt[(r1 + 1) * ROWTAB];
             const float dx12 = x2 - x1;
             const float4 c2 = A.sc[h2];
             const float2 p1 = make_float2(c1.x, c1.y), p2 = make_float2(c2.x, c2.y);
@@ -886,7 +1042,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
         }
         if (target < 0) continue;
         // ---- propagation (one call site)
-        if (!prop32(st, A.rowtab[target * ROWTAB], A.kb)) {
+        if (!prop32(st, rt[target * ROWTAB], A.kb)) {
             if (phase == PH_BACK && jump > 1) jump >>= 1;
             else phase = (phase == PH_C || phase == PH_BACK) ? PH_DONE : PH_CSTART;
             continue;
@@ -923,11 +1079,8 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             // ---- window search (one call site)
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            c = find_nearest(A, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand);
+            c = find_nearest(A, rt, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand, my, mz);
             if (c >= 0) {
-                const float4 pc = A.sc[c];
-                my = pc.x;
-                mz = pc.y;
                 cmax = A.chi2cut;
                 upd = true;
             }
@@ -1598,27 +1751,32 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     auto mark = [&](int k) -> cudaError_t { return prof ? cudaEventRecord(g_events.ev[k], st) : cudaSuccess; };
     g_launches = 0;
 
+    const int nplanes = NF * L.np;
+    uint32_t* pstart = at<uint32_t>(ws, L.pstart);
     CK(mark(0));
+    CK(cudaMemsetAsync(pstart, 0, sizeof(uint32_t) * ((size_t)nplanes * PSPLIT + 1), st));
     k_init_frame<<<std::max(1, (NF + 255) / 256), 256, 0, st>>>(f, fg, NF);
     {
         const int gx = std::max(1, std::min(grid_for(n, B), (148 * 16 + NF - 1) / NF));
         k_prep<<<dim3(gx, NF), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
-                                          g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
+                                          g->continuous, g->z_max, v_drift, zlin, cfr, f, fg, L.np, pstart, cell);
     }
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, NF, L.np, L.ny, p->z_cell, L.nzmax, (long long)L.ncells,
                                    0.25f * p->merge_dz, L.mnzmax, p->packed_links);
     g_launches += 3;
     CK(mark(1));
-    // a2: counting sort of the clusters into (frame, sector, row, z-cell, y-bin) order
-    k_zero_cells<<<grid_for(L.ncells + 1, B), B, 0, st>>>(cstart, f);
-    k_hist<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, rowtab, g->n_rows, g->n_sectors, f, fg, cstart,
-                             cell, slot);
-    g_launches += 2;
-    scan_u32(cstart, L.ncells, aux, st, &f->total_cells);
+    // a2: clusters into (frame, sector, row, z-cell, y-bin) order, a plane at a time
+    scan_u32(pstart, (int64_t)nplanes * PSPLIT, aux, st);
+    k_pscatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, pstart, cell,
+                                 at<float4>(ws, L.pbuf), f);
     uint32_t* yzp = p->packed_links ? at<uint32_t>(ws, L.yzp) : nullptr;
-    k_scatter<<<gN, B, 0, st>>>(n, cl->sector, cl->row, cl->y, zlin, cfr, g->n_rows, L.np, cstart, cell, slot, sc, f,
-                                yzp);
-    g_launches++;
+    {
+        const int smem_cells = plane_sort_smem_cells((int64_t)L.nzmax * L.ny, st);
+        k_plane_sort<<<std::max(1, std::min(nplanes, 148 * 8)), PS_BLOCK, sizeof(uint32_t) * smem_cells, st>>>(
+            nplanes, L.np, g->n_rows, g->n_sectors, pstart, at<float4>(ws, L.pbuf), slot, rowtab, f, fg, smem_cells,
+            cstart, sc, yzp);
+    }
+    g_launches += 2;
     CK(mark(2));
     if (yzp)
         k_neighbours<true><<<gN, B, 0, st>>>(n, g->n_rows, g->n_sectors, L.np, rowtab, sc, cstart, f, fg,
@@ -1750,7 +1908,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
 // tables and offsets a call reads from the workspace (pageable uploads)
 int upload(const tpc_geometry* g, const Layout& L, const int32_t* offsets, void* ws, cudaStream_t st)
 {
-    static_assert(sizeof(Layout) <= 512, "layout header");
+    static_assert(sizeof(Layout) <= 1024, "layout header");
     float tab[ROWTAB * 256];
     fill_rowtab(tab, g, L.ny);
     CK(cudaMemcpyAsync(at<float>(ws, L.rowtab), tab, sizeof(tab), cudaMemcpyHostToDevice, st));
@@ -1851,8 +2009,8 @@ int tpc_params_default(tpc_params* p)
     p->merge_chi2 = 50.0f;
     p->refit_passes = 3;
     p->refit_inflate = 100.0f;
-    p->z_cell = 3.5f;
-    p->y_bins = 8;
+    p->z_cell = 5.0f;
+    p->y_bins = 16;
     p->max_z_cells = 1024;
     p->tracklets_per_1k = 125;
     p->queue_blocks_per_sm = 0;
@@ -1909,7 +2067,7 @@ int tpc_prepare(const tpc_params* p, const tpc_geometry* g, int32_t n_clusters, 
 }
 
 // staging: the layout header (512 bytes), the row table, the frame offsets
-constexpr size_t STAGE_HDR = 512;
+constexpr size_t STAGE_HDR = 1024;
 constexpr size_t STAGE_TAB = sizeof(float) * ROWTAB * 256;
 
 int tpc_prepare_staging_size(int32_t n_frames, size_t* bytes)
@@ -2058,7 +2216,7 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     const int gN = grid_for(n, B);
     k_init_frame<<<1, 32, 0, st>>>(f, fg, 1);
     k_prep<<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
-                                      g->continuous, g->z_max, v_drift, zlin, cfr, f, fg);
+                                      g->continuous, g->z_max, v_drift, zlin, cfr, f, fg, np, nullptr, nullptr);
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, 0.25f * p->merge_dz,
                                    MAX_MERGE_CELLS, 0);
     // the histogram must start at zero: the scratch keeps the previous call's contents
