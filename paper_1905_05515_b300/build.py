@@ -20,8 +20,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
           "--expt-relaxed-constexpr"]
 UNITS = {
     "tpc_track.cu": ["-fmad=false"],
-    "tpc_refit.cu": ["-fmad=true"],
-    "tpc_calib.cu": ["-fmad=true"],
+    "tpc_refit.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
+    "tpc_calib.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
 }
 
 

@@ -15,7 +15,8 @@
 // binary32, or -- with fp64_final -- binary64 during the final pass with a
 // Joseph-form update and a binary64 chi2 sum.  This is the tolerance path
 // (compared with a binary64 fit within 1e-4 relative), so it uses the exact
-// arcsine and lets the compiler contract multiply-adds.
+// arcsine, lets the compiler contract multiply-adds, and is built with the
+// approximate division and square root (a few ulp).
 #include "tpc_dev.cuh"
 #include "tpc_fit.cuh"
 #include "tpc_track.h"
@@ -238,7 +239,11 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
             R.out.chi2_64[r] = chi2;
         }
     }
-    if (R.prof) atomicAdd(&f->w_refit_prop, (unsigned long long)nprop);
+    if (R.prof) {
+        // one atomic per warp (every thread of the block gets here)
+        nprop = __reduce_add_sync(0xffffffffu, nprop);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&f->w_refit_prop, (unsigned long long)nprop);
+    }
 }
 
 }  // namespace

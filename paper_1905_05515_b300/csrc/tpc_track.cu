@@ -1114,9 +1114,15 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
         }
     }
     if (A.prof) {
-        atomicAdd(&A.fw->w_prop, (unsigned long long)nprop);
-        atomicAdd(&A.fw->w_upd, (unsigned long long)nupd);
-        atomicAdd(&A.fw->w_cand, (unsigned long long)ncand);
+        // work counters: one atomic per warp (every lane of the warp gets here)
+        nprop = __reduce_add_sync(0xffffffffu, nprop);
+        nupd = __reduce_add_sync(0xffffffffu, nupd);
+        ncand = __reduce_add_sync(0xffffffffu, ncand);
+        if (lane == 0) {
+            atomicAdd(&A.fw->w_prop, (unsigned long long)nprop);
+            atomicAdd(&A.fw->w_upd, (unsigned long long)nupd);
+            atomicAdd(&A.fw->w_cand, (unsigned long long)ncand);
+        }
     }
 }
 
@@ -1355,7 +1361,10 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
         b.warp_reduce();
         if (lane == 0) M.bnext[a] = b.q < 0 ? -1 : M.byb[b.q];
     }
-    if (M.prof && nchi) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
+    if (M.prof) {
+        nchi = __reduce_add_sync(0xffffffffu, nchi);
+        if (lane == 0 && nchi) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
+    }
 }
 
 // best A (inner piece) for every B
