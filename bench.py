@@ -698,7 +698,7 @@ def roofline(stage, per_step, w, n, pk):
         if stage == "tracklets":
             flops = w["trk_prop"] * FLOPS_PROP + w["trk_upd"] * FLOPS_UPDATE + w["trk_cand"] * FLOPS_CAND
         elif stage == "merge":
-            flops = w["merge_chi2"] * FLOPS_MERGE * 2      # both directions evaluate the chi2
+            flops = w["merge_chi2"] * FLOPS_MERGE          # one chi2 per screened pair
         else:
             flops = w["refit_prop"] * (FLOPS_PROP + FLOPS_UPDATE)
         ach = flops / t / 1e12

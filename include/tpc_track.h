@@ -92,6 +92,10 @@ typedef struct {
                                     coordinate with step 2^-8 cm (decoded relative to the middle hit), i.e.
                                     it sees both rounded to the nearest 1/256 cm; other stages see full
                                     precision.  Needs z-cells under 60 cm (TPC_ERR_CAPACITY otherwise). */
+    int32_t merge_pairs_per_1k;  /* merger: capacity of the list of screened candidate pairs, per 1000
+                                    tracklet slots (default 4000; >= 0).  Beyond it the merger evaluates
+                                    the pairs of each segment end directly (same result, slower); 0
+                                    always does. */
 } tpc_params;
 
 /* Detector geometry (host memory). */

@@ -31,7 +31,7 @@ class TpcParams(C.Structure):
                 ("z_cell", C.c_float),
                 ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32),
                 ("queue_blocks_per_sm", C.c_int32), ("fp64_final", C.c_int32),
-                ("profile", C.c_int32), ("packed_links", C.c_int32)]
+                ("profile", C.c_int32), ("packed_links", C.c_int32), ("merge_pairs_per_1k", C.c_int32)]
 
 
 class TpcGeometry(C.Structure):

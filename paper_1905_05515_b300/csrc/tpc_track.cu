@@ -58,7 +58,8 @@ struct Layout {
     size_t pbuf, pstart;        // binning: plane-ordered records (aliases the links), plane starts
     size_t t_start, t_id, t_nhits, t_nup, t_hits, t_top, t_bot, hitw, t_kept, t_own, ownmask, segoff, segrank, t_state;
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
-    size_t bnext, bprev, snext, sprev, bad, next2, prev2;
+    size_t bnext, bprev, snext, sprev, bad, next2, prev2, mpair, mpc2, bestA, bestB;
+    int64_t mpcap;              // merger pair list capacity
     size_t headmark, tcount, thead, ttail, tcl, lencnt, order;
     size_t total;
 };
@@ -177,6 +178,11 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.byt = take(4 * T);
     L.recb = take(32 * T);      // merge-grid order: inner-end (z, tan lambda, q/pT, their variances, id)
     L.rect = take(32 * T);      // merge-grid order: outer-end record
+    L.mpcap = T * (int64_t)p->merge_pairs_per_1k / 1000;   // screened merge pairs (about T / 3 measured)
+    L.mpair = take(8 * L.mpcap);
+    L.mpc2 = take(4 * L.mpcap);
+    L.bestA = take(8 * T);
+    L.bestB = take(8 * T);
     L.bnext = take(4 * T);
     L.bprev = take(4 * T);
     L.snext = take(4 * T);
@@ -1287,6 +1293,11 @@ struct MergeArgs {
     const MergeRec* rect;   // merge-grid order, as byt
     int prof;
     Frame* fw;
+    int2* pairs;            // screened pairs: segment a, inner-end record q (bit 31: direction -1)
+    float* pc2;             // their chi2
+    unsigned long long* bestA;   // per segment: min (chi2 bits, partner id) as outer piece
+    unsigned long long* bestB;   // per segment: the same as inner piece
+    int pcap;
 };
 
 // Merge screen: tan(lambda), q/pT and their variances are unchanged by the
@@ -1322,12 +1333,108 @@ struct MergeBest {
     }
 };
 
-// One warp per segment end: the lanes read 32 consecutive candidate records
-// of the window at a time, screen them, and evaluate the chi2 of those left.
+// The window test, the screen and the chi2 of a pair (outer end of A, inner
+// end of B in the neighbouring sector) are symmetric in A and B, so the best
+// partner of every outer end and of every inner end come from one list of the
+// screened pairs: k_merge_pairs (a warp per outer end, 32 candidate records
+// at a time) lists them, k_merge_chi2 (a thread per pair) evaluates each chi2
+// once and keeps, per end, the minimum of (chi2 bits, partner id) -- chi2 >= +0
+// orders as its bits, so this is the smallest chi2, ties to the smaller id --
+// and k_merge_resolve writes the winners.  If the list overflows its capacity,
+// k_merge_next / k_merge_prev (one warp per end, chi2 inline) do it instead.
+__global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
+{
+    const int nseg = M.f->n_seg, mnz = M.f->mnz;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int a = blockIdx.x * wpb + (threadIdx.x >> 5); a < nseg; a += gridDim.x * wpb) {
+        const int ta = M.seg[a];
+        const int gsa = seg_gsector(M.sc, M.t_start, M.seg, a, M.nr);
+        const int fr = gsa / M.ns, sa = gsa - fr * M.ns;
+        const float* tp = M.t_top + (int64_t)ta * NST;
+        MergeRec ra;
+        ra.a = make_float4(tp[2], tp[4], tp[5], tp[6 + 9]);
+        ra.b = make_float4(tp[6 + 14], 0.0f, 0.0f, 0.0f);
+        for (int dir = 1; dir >= -1; dir -= 2) {
+            const int sb = neighbour_sector(sa, dir, M.ns);
+            if (sb < 0) continue;
+            const int gsb = fr * M.ns + sb;
+            int lo, hi;
+            merge_window(ra.a.x, M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
+            const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
+            for (int q0 = qb; q0 < qe; q0 += 32) {
+                const int q = q0 + lane;
+                bool pass = false;
+                if (q < qe) {
+                    const MergeRec rb = M.recb[q];
+                    pass = fabsf(rb.a.x - ra.a.x) <= M.dz && !merge_screened(ra, rb, 2.0f * M.chi2cut);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, pass);
+                if (!m) continue;
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&M.fw->n_mpairs, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (pass) {
+                    const int k = base + __popc(m & ((1u << lane) - 1u));
+                    if (k < M.pcap) M.pairs[k] = make_int2(a, q | (dir < 0 ? (int)0x80000000 : 0));
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long merge_key(float c2, int id)
+{
+    return ((unsigned long long)__float_as_uint(c2) << 32) | (unsigned long long)(uint32_t)id;
+}
+
+__global__ void k_merge_chi2(MergeArgs M)
+{
+    const int np_ = M.f->n_mpairs;
+    if (np_ > M.pcap) return;
+    unsigned nchi = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np_; i += gridDim.x * blockDim.x) {
+        const int2 pr = M.pairs[i];
+        const int a = pr.x, q = pr.y & 0x7fffffff;
+        const MergeRec rb = M.recb[q];
+        const int ta = M.seg[a], tb = __float_as_int(rb.b.z);
+        const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, M.t_bot + (int64_t)tb * NST, COS20,
+                                    pr.y < 0 ? -SIN20 : SIN20, M.kb);
+        nchi++;
+        M.pc2[i] = c2;
+        if (c2 < M.chi2cut) {
+            atomicMin(&M.bestA[a], merge_key(c2, __float_as_int(rb.b.y)));
+            atomicMin(&M.bestB[M.byb[q]], merge_key(c2, M.t_id[ta]));
+        }
+    }
+    if (M.prof) {
+        nchi = __reduce_add_sync(0xffffffffu, nchi);
+        if ((threadIdx.x & 31) == 0 && nchi) atomicAdd(&M.fw->w_merge, (unsigned long long)nchi);
+    }
+}
+
+__global__ void k_merge_resolve(MergeArgs M)
+{
+    const int np_ = M.f->n_mpairs;
+    if (np_ > M.pcap) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np_; i += gridDim.x * blockDim.x) {
+        const float c2 = M.pc2[i];
+        if (!(c2 < M.chi2cut)) continue;
+        const int2 pr = M.pairs[i];
+        const int a = pr.x, q = pr.y & 0x7fffffff;
+        const int b = M.byb[q];
+        if (M.bestA[a] == merge_key(c2, __float_as_int(M.recb[q].b.y))) M.bnext[a] = b;
+        if (M.bestB[b] == merge_key(c2, M.t_id[M.seg[a]])) M.bprev[b] = a;
+    }
+}
+
+// Fallback: one warp per segment end: the lanes read 32 consecutive candidate
+// records of the window at a time, screen them, and evaluate the chi2 of
+// those left.
 
 // best B (outer piece) for every A: A's outer end against B's inner end
 __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 {
+    if (M.f->n_mpairs <= M.pcap) return;      // the pair list held every screened pair
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     unsigned nchi = 0;
@@ -1370,6 +1477,7 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
 // best A (inner piece) for every B
 __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
 {
+    if (M.f->n_mpairs <= M.pcap) return;
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < nseg; b += gridDim.x * wpb) {
@@ -1691,7 +1799,7 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (!(g->n_sectors == 36 || g->n_sectors == 1)) return TPC_ERR_ARG;
     if (g->n_rows < 3 || g->n_rows > 255) return TPC_ERR_ARG;
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
-    if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0) return TPC_ERR_ARG;
+    if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0 || p->merge_pairs_per_1k < 0) return TPC_ERR_ARG;
     if (!(p->z_cell >= 0.25f) || p->y_bins < 1 || p->y_bins > MAX_YBINS) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
@@ -1849,18 +1957,28 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
     M.recb = at<MergeRec>(ws, L.recb); M.rect = at<MergeRec>(ws, L.rect);
     M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
+    M.pairs = at<int2>(ws, L.mpair); M.pc2 = at<float>(ws, L.mpc2);
+    M.bestA = at<unsigned long long>(ws, L.bestA); M.bestB = at<unsigned long long>(ws, L.bestB);
+    M.pcap = (int)std::min<int64_t>(L.mpcap, INT32_MAX);
+    CK(cudaMemsetAsync(M.bestA, 0xFF, 8 * (size_t)ntcap, st));
+    CK(cudaMemsetAsync(M.bestB, 0xFF, 8 * (size_t)ntcap, st));
+    CK(cudaMemsetAsync(M.bnext, 0xFF, 4 * (size_t)ntcap, st));
+    CK(cudaMemsetAsync(M.bprev, 0xFF, 4 * (size_t)ntcap, st));
     k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
                                      at<int32_t>(ws, L.byt), seg, TA.t_id, TA.t_top, TA.t_bot,
                                      at<MergeRec>(ws, L.recb), at<MergeRec>(ws, L.rect));
     const int gTw = grid_for((int64_t)ntcap * 32, 128);    // one warp per segment end
-    k_merge_next<<<gTw, 128, 0, st>>>(M);
+    k_merge_pairs<<<gTw, 128, 0, st>>>(M);
+    k_merge_chi2<<<grid_for(L.mpcap, 128), 128, 0, st>>>(M);
+    k_merge_resolve<<<grid_for(L.mpcap, B), B, 0, st>>>(M);
+    k_merge_next<<<gTw, 128, 0, st>>>(M);      // only if the pair list overflowed
     k_merge_prev<<<gTw, 128, 0, st>>>(M);
     k_merge_link<<<gt2, B, 0, st>>>(f, M.bnext, M.bprev, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev));
     k_merge_cycles<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad));
     k_merge_fix<<<gt2, B, 0, st>>>(f, at<int32_t>(ws, L.snext), at<int32_t>(ws, L.sprev), at<uint8_t>(ws, L.bad),
                                    at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
-    g_launches += 6;
+    g_launches += 9;
     scan_u32(headmark, n, aux, st);
     CK(mark(7));
     // merged cluster lists and assignments
@@ -2026,6 +2144,7 @@ int tpc_params_default(tpc_params* p)
     p->fp64_final = 0;
     p->profile = 0;
     p->packed_links = 0;
+    p->merge_pairs_per_1k = 4000;
     return TPC_OK;
 }
 

@@ -110,6 +110,17 @@ def test_packed_link_coordinates(orc, make):
     assert changed < 2e-3
 
 
+@pytest.mark.parametrize("cap", [0, 1])
+def test_merger_without_pair_list(orc, cap):
+    """A pair list too small for the screened candidate pairs (none, or one
+    per 1000 tracklet slots): the merger's direct path gives the same merges
+    and tracks, bit-exact with the oracle."""
+    import paper_1905_05515_b300 as tpc
+    ev = tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False)
+    g, r = _check(ev, orc, params=tpc.tpc_params_default(merge_pairs_per_1k=cap))
+    assert np.count_nonzero(np.asarray(r.seg_next) >= 0) > 10          # the event has merges to find
+
+
 @pytest.mark.slow
 def test_time_frame_full(orc):
     """The 50-collision continuous read-out frame (16 M clusters), whole-chain
