@@ -44,7 +44,7 @@ FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky so
 # tracklet passes), from the committed ncu capture of the same kernel build
 # (profiles/k_tracklets_frame20.md, 20-collision frame, scaled by clusters);
 # None once the kernel changes
-NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 207.5}
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 195.4}
 
 
 def parse():
@@ -258,39 +258,59 @@ def run_ours(args, ws, rank, local, pg):
     rg = run.result()
     same_as_sync = bool(rg.n_tracks == n_tracks and np.array_equal(rg.param[:n_tracks].cpu().numpy(), p_sync))
 
-    # ---- end to end through the same API with host buffers
+    # ---- end to end from host memory: the public streaming API, FramePipeline
+    # (per frame: host->device copies of the clusters, tracking, device->host
+    # copies of the filled outputs; a frame's copies run beside the tracking of
+    # the next one), and the synchronous tpc_track call with the same copies
+    pipe = tpc.FramePipeline(n, ev.row_x, depth=2, n_sectors=36, z_max=ev.z_max, continuous=True, bz=ev.bz,
+                             v_drift=ev.v_drift, device=dev)
+    hin = (host["sector"], host["row"], host["y"], host["zt"])
+    for _ in range(2):
+        pipe.push(*hin)
+    pipe.flush()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h_list, h2d = [], 0
+    for _ in range(args.steps):
+        r = pipe.push(*hin)
+        if r is not None:
+            d2h_list.append(r.d2h_bytes)
+            h2d = r.h2d_bytes
+    for r in pipe.flush():
+        d2h_list.append(r.d2h_bytes)
+        h2d = r.h2d_bytes
+    e2e_s = time.perf_counter() - t0
+    pipe_same = bool(r.n_tracks == n_tracks and np.array_equal(r.param.numpy(), p_sync))
+    del pipe
+    torch.cuda.empty_cache()
+    barrier()
+
     T_cap = trk.capacity_tracks
     outs = {"param": (T_cap, 5), "cov": (T_cap, 15), "chi2": (T_cap,), "ndf": (T_cap,), "nclus": (T_cap,),
             "clus_offset": (T_cap + 1,)}
     h_out = {k: torch.empty(sh, dtype=trk.buf[k].dtype).pin_memory() for k, sh in outs.items()}
     h_clus = torch.empty(trk.capacity_clusters, dtype=torch.int32).pin_memory()
     h_assign = torch.empty(n, dtype=torch.int32).pin_memory()
-    h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
-    d2h_list = []
-    barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for k in dv:
             dv[k].copy_(host[k], non_blocking=True)
-        r = trk.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
-        T = r.n_tracks
-        nb = 0
+        rs = trk.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+        T = rs.n_tracks
         for k in outs:
             m = T + 1 if k == "clus_offset" else T
             h_out[k][:m].copy_(trk.buf[k][:m], non_blocking=True)
-            nb += m * trk.buf[k][0].numel() * trk.buf[k].element_size()
-        nc = int(r.clus_offset[-1].item()) if T else 0
+        nc = int(rs.clus_offset[-1].item()) if T else 0
         h_clus[:nc].copy_(trk.buf["clus_index"][:nc], non_blocking=True)
-        h_assign.copy_(r.assign, non_blocking=True)
-        nb += 4 * nc + 4 * n + 4
+        h_assign.copy_(rs.assign, non_blocking=True)
         torch.cuda.synchronize()
-        d2h_list.append(nb)
-    e2e_s = time.perf_counter() - t0
+    sync_s = time.perf_counter() - t0
     barrier()
 
     # ---- max over ranks, totals
-    (ms_max, e2e_max), (n_total,) = over_ranks(pg, dev, (ms, e2e_s), (float(n),))
+    (ms_max, e2e_max, sync_max), (n_total,) = over_ranks(pg, dev, (ms, e2e_s, sync_s), (float(n),))
     if rank != 0:
         return
     value = n_total * args.steps / (ms_max / 1e3)
@@ -307,7 +327,10 @@ def run_ours(args, ws, rank, local, pg):
                    "ms_per_frame": ms_max / args.steps,
                    "l2": "inputs (10 B/cluster, 160 MB) and workspace exceed the 126 MB L2; no flush",
                    "replicas": ws, "step": "one replay of the frame's captured CUDA graph (all stages)",
-                   "graph_identical_to_sync_call": same_as_sync},
+                   "graph_identical_to_sync_call": same_as_sync,
+                   "e2e_api": "FramePipeline, depth 2 (copies of a frame beside the tracking of the next)",
+                   "e2e_pipeline_identical_to_sync_call": pipe_same,
+                   "e2e_sync_call_clusters_per_s": n_total * args.steps / sync_max},
         "roofline": roof,
         "stage_ms": {k: round(v, 4) for k, v in per_step.items()},
         "work_per_step": w,

@@ -22,6 +22,7 @@
 #include "tpc_track.h"
 
 #include <cmath>
+#include <type_traits>
 
 using namespace tpc;
 using namespace tpc::fit;
@@ -47,9 +48,24 @@ __device__ __forceinline__ bool rot(float& x, float* p, float* pl, CT* c, float 
     return true;
 }
 
+// chi2 of a binary32 pass: a compensated binary32 sum (TwoSum), far inside
+// the 1e-3 the pass's chi2 is held to, without a binary64 add per step (the
+// FP64 pipe of this GPU is narrow)
+struct Chi2Sum {
+    float s, e;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float t = s + v, bp = t - s;
+        e += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+};
+__device__ __forceinline__ double chi2_value(const Chi2Sum& a) { return (double)a.s + (double)a.e; }
+__device__ __forceinline__ double chi2_value(double a) { return a; }
+
 // standard-form update (binary32 covariance)
 __device__ __forceinline__ bool update(float* p, float* pl, float* c, float my, float mz, float vy, float vz,
-                                       double& chi2)
+                                       Chi2Sum& chi2)
 {
     const float r0 = (my - p[0]) - pl[0], r1 = (mz - p[1]) - pl[1];
     const float s00 = c[0] + vy, s01 = c[1], s11 = c[2] + vz;
@@ -57,7 +73,7 @@ __device__ __forceinline__ bool update(float* p, float* pl, float* c, float my, 
     if (!(det > 0.0f)) return false;
     const float idet = 1.0f / det;
     const float i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
-    chi2 += (double)(r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1));
+    chi2.add(r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1));
     float K0[5], K1[5], row0[5], row1[5];
 #pragma unroll
     for (int i = 0; i < 5; i++) {
@@ -141,11 +157,10 @@ struct RefitArgs {
     tpc_tracks out;
 };
 
-template <typename CT>
-__device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p, float* pl,
-                         CT* c, double& chi2, unsigned& nprop, float zref)
+template <typename CT, typename ACC>
+__device__ __forceinline__ bool run_steps(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p,
+                                          float* pl, CT* c, ACC& chi2, unsigned& nprop, float zref)
 {
-    chi2 = 0.0;
     for (int q = 0; q < n; q++) {
         const int i = inward ? n - 1 - q : q;
         const float4 cl = R.tcl[off + i];
@@ -181,6 +196,17 @@ __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& s
         }
     }
     return true;
+}
+
+template <typename CT>
+__device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p, float* pl,
+                         CT* c, double& chi2, unsigned& nprop, float zref)
+{
+    // binary32 passes: compensated binary32 chi2; the binary64 pass: binary64
+    typename std::conditional<std::is_same<CT, float>::value, Chi2Sum, double>::type acc{};
+    const bool ok = run_steps<CT>(R, off, n, inward, sec, x, p, pl, c, acc, nprop, zref);
+    chi2 = chi2_value(acc);
+    return ok;
 }
 
 // FP64: the final pass in binary64 (a separate instance, so that the
