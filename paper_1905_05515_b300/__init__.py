@@ -10,8 +10,9 @@ from .abi import (TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_CUDA, TPC_ERR_DATA, TPC
 from . import autotune, batch, calib
 from .batch import GroupedBatch
 from .calib import CalibRefit, calib_chi2
+from .pipeline import FramePipeline, HostTracks
 from .tracker import GraphRun, Tracker, TrackResult, tpc_track
 
-__all__ = ["Tracker", "TrackResult", "GraphRun", "GroupedBatch", "autotune", "batch", "calib", "CalibRefit", "calib_chi2", "tpc_track", "tpc_params_default", "tpc_workspace_size", "tpc_error_string",
+__all__ = ["Tracker", "TrackResult", "GraphRun", "GroupedBatch", "FramePipeline", "HostTracks", "autotune", "batch", "calib", "CalibRefit", "calib_chi2", "tpc_track", "tpc_params_default", "tpc_workspace_size", "tpc_error_string",
            "lib", "TpcError", "TPC_OK", "TPC_ERR_ARG", "TPC_ERR_CAPACITY", "TPC_ERR_TIMEOUT", "TPC_ERR_CUDA",
            "TPC_ERR_DATA"]
