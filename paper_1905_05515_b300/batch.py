@@ -86,6 +86,16 @@ class _Group:
             raise abi.TpcError(rc, "tpc_prepare_staging_size")
         self.staging = torch.empty(int(sz.value), dtype=torch.uint8).pin_memory()
         self.ws_bytes = abi.tpc_workspace_size(gb.params, gb.geometry, self.n, self.nf)
+        self.cap_t = cap_t
+        self.host = None                 # page-locked results of a host-I/O capture
+
+    def host_buffers(self):
+        if self.host is None:
+            self.host = dict(param=torch.empty(self.cap_t, 5, dtype=torch.float32).pin_memory(),
+                             chi2=torch.empty(self.cap_t, dtype=torch.float32).pin_memory(),
+                             assign=torch.empty(max(1, self.n), dtype=torch.int32).pin_memory(),
+                             counts=torch.zeros(8, dtype=torch.int32).pin_memory())
+        return self.host
 
 
 class GroupedBatch:
@@ -126,8 +136,12 @@ class GroupedBatch:
             self.ws.append((torch.empty(need, dtype=torch.uint8, device=self.device), need))
         self.graph = None
 
-    def _enqueue(self):
-        """All groups, each on its stream; the caller's stream waits for all."""
+    def _enqueue(self, host_in=None):
+        """All groups, each on its stream; the caller's stream waits for all.
+        With host_in (page-locked CPU tensors of the whole batch), every group
+        first copies its clusters from there and afterwards copies its
+        parameters, chi2 (whole capacity), counts and assignments to its
+        page-locked host buffers, on its own stream."""
         main = torch.cuda.current_stream(self.device)
         for st in self.streams:
             st.wait_stream(main)
@@ -135,6 +149,10 @@ class GroupedBatch:
             s = i % self.n_streams
             ws, wsb = self.ws[s]
             h = C.c_void_p(self.streams[s].cuda_stream)
+            if host_in is not None:
+                with torch.cuda.stream(self.streams[s]):
+                    for dst, src in zip(self._ins, host_in):
+                        dst[g.a:g.b].copy_(src[g.a:g.b], non_blocking=True)
             rc = self.lib.tpc_prepare_async(C.byref(self.params), C.byref(self.geometry), g.n, g.nf,
                                             g.local_off.ctypes.data_as(C.POINTER(C.c_int32)),
                                             C.c_void_p(g.staging.data_ptr()), g.staging.numel(),
@@ -146,6 +164,13 @@ class GroupedBatch:
                                           C.c_void_p(g.counts.data_ptr()), h)
             if rc:
                 raise abi.TpcError(rc, "tpc_track_async")
+            if host_in is not None:
+                hb = g.host_buffers()
+                with torch.cuda.stream(self.streams[s]):
+                    hb["param"].copy_(g.buf["param"], non_blocking=True)
+                    hb["chi2"].copy_(g.buf["chi2"], non_blocking=True)
+                    hb["counts"].copy_(g.counts, non_blocking=True)
+                    hb["assign"][:g.n].copy_(g.buf["assign"][:g.n], non_blocking=True)
         for st in self.streams:
             main.wait_stream(st)
 
@@ -153,17 +178,44 @@ class GroupedBatch:
         """Enqueue the batch eagerly (no graph)."""
         self._enqueue()
 
-    def capture(self):
+    def capture(self, host_in=None):
         """Capture the batch as a CUDA graph (after one eager run, which
-        loads the kernels)."""
-        self._enqueue()
+        loads the kernels).  host_in: page-locked CPU tensors (sector, row,
+        y, zt) of the whole batch to copy from at every replay, with the
+        results copied back (host_results); they must stay alive."""
+        for a, b in zip(host_in or (), self._ins):
+            if a.device.type != "cpu" or not a.is_pinned() or a.dtype != b.dtype or a.shape != b.shape:
+                raise ValueError("host_in: page-locked CPU tensors shaped like the device inputs")
+        self._host_in = host_in
+        self._enqueue(host_in)
         torch.cuda.synchronize(self.device)
         cap = torch.cuda.Stream(self.device)
         cap.wait_stream(torch.cuda.current_stream(self.device))
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=cap):
-            self._enqueue()
+            self._enqueue(host_in)
         return self
+
+    def host_results(self):
+        """Per group (after a replay of a host-I/O capture; synchronises):
+        (n_tracks, parameters [T, 5], chi2 [T], assignments [n]) as views of
+        the group's page-locked buffers."""
+        torch.cuda.synchronize(self.device)
+        out = []
+        for g in self.groups:
+            hb = g.host
+            c = hb["counts"].tolist()
+            if c[3]:
+                raise abi.TpcError(c[3], f"frames {g.f0}..{g.f1 - 1}")
+            T = int(c[0])
+            out.append((T, hb["param"][:T], hb["chi2"][:T], hb["assign"][:g.n]))
+        return out
+
+    def host_io_bytes(self):
+        """(host-to-device, device-to-host) bytes one host-I/O replay copies."""
+        h2d = sum(g.n * 10 for g in self.groups)
+        d2h = sum(g.cap_t * 24 + 32 + 4 * g.n for g in self.groups)
+        return h2d, d2h
 
     def replay(self):
         if self.graph is None:

@@ -159,3 +159,28 @@ def test_grouped_graph_equals_per_frame(frames, group_clusters, n_streams):
                 t0 += T
     assert gb.n_launches > 0
     torch.cuda.synchronize()
+
+
+def test_host_io_capture_equals_device_graph(frames):
+    """A capture with per-group host input copies and result copies gives the
+    device-resident graph's parameters, chi2 and assignments in host memory."""
+    import paper_1905_05515_b300 as tpc
+    cat, off = _concat(frames)
+    ins = _dev(cat)
+    ev0 = frames[0]
+    gb = tpc.GroupedBatch(*ins, off, ev0.row_x, bz=ev0.bz, v_drift=ev0.v_drift, group_clusters=1, n_streams=2)
+    gb.capture()
+    gb.replay()
+    want = gb.results()
+    host = tuple(t.cpu().pin_memory() for t in ins)
+    gb.capture(host_in=host)
+    for t in ins:
+        t.zero_()                      # the replay must take the clusters from host memory
+    gb.replay()
+    got = gb.host_results()
+    assert len(got) == len(want)
+    for (T, p, c2, a), w in zip(got, want):
+        assert T == w.n_tracks
+        assert np.array_equal(p.numpy(), w.param.cpu().numpy())
+        assert np.array_equal(c2.numpy(), w.chi2.cpu().numpy())
+        assert np.array_equal(a.numpy(), w.assign.cpu().numpy())
