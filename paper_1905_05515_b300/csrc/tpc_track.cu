@@ -810,6 +810,7 @@ struct TrkArgs {
 // are scanned, so that the lane waits for one round of grid loads, not one
 // per z-cell.
 constexpr int NZR = 2;
+template <bool PROF>
 __device__ __forceinline__ int find_nearest(const TrkArgs& A, const float* rt, const FrameGrid& G, int lplane, int r,
                                             int s, float yp,
                                             float zp, float wy, float wz, int ny, unsigned& ncand, float& by, float& bz)
@@ -827,7 +828,7 @@ __device__ __forceinline__ int find_nearest(const TrkArgs& A, const float* rt, c
         }
 #pragma unroll
         for (int j = 0; j < NZR; j++) {
-            ncand += (unsigned)(qe[j] - qb[j]);
+            if (PROF) ncand += (unsigned)(qe[j] - qb[j]);
             auto cand = [&](const float4& pq, int q) {
                 const float dy = pq.x - yp;
                 const float dz = pq.y - zp;
@@ -876,7 +877,7 @@ constexpr int TRK_BLOCK = 128;
 constexpr int TSAVE = NST + 4;
 // 8 blocks of 128 threads per SM (64 registers) measured best for both passes
 // (against 6 to 16 blocks for pass 1 and 6 to 8 for pass 2)
-template <int PASS>
+template <int PASS, bool PROF>
 __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
 {
     // the last accepted state of each lane (outer-end / inner-end candidate) lives
@@ -1053,7 +1054,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             else phase = (phase == PH_C || phase == PH_BACK) ? PH_DONE : PH_CSTART;
             continue;
         }
-        nprop++;
+        if (PROF) nprop++;
         if (phase == PH_BACK) {
             rc = target;
             if (rc == r1) {
@@ -1070,7 +1071,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             my = pn.x;
             mz = pn.y;
             upd = true;
-            nupd++;
+            if (PROF) nupd++;
         } else if (phase == PH_B) {
             rc = target;
             search = true;
@@ -1085,7 +1086,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             // ---- window search (one call site)
             const float wy = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 0] + A.vy), A.wmin), A.wmax);
             const float wz = fminf(fmaxf(A.nsig * __fsqrt_rn(st[6 + 2] + A.vz), A.wmin), A.wmax);
-            c = find_nearest(A, rt, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand, my, mz);
+            c = find_nearest<PROF>(A, rt, G, lbase + target, target, s, st[1], st[2], wy, wz, ny, ncand, my, mz);
             if (c >= 0) {
                 cmax = A.chi2cut;
                 upd = true;
@@ -1098,7 +1099,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             save_keep();
         } else if (phase == PH_B) {
             if (took) {
-                nupd++;
+                if (PROF) nupd++;
                 slot[nu++] = c;
                 save_keep();
                 miss = 0;
@@ -1107,7 +1108,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             }
         } else {
             if (took) {
-                nupd++;
+                if (PROF) nupd++;
                 nd++;
                 slot[NR - nd] = c;
                 save_keep();
@@ -1119,7 +1120,7 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             r--;
         }
     }
-    if (A.prof) {
+    if (PROF) {
         // work counters: one atomic per warp (every lane of the warp gets here)
         nprop = __reduce_add_sync(0xffffffffu, nprop);
         nupd = __reduce_add_sync(0xffffffffu, nupd);
@@ -1142,24 +1143,40 @@ __device__ __forceinline__ int trk_hit(const int32_t* slot, int nr, int nhits, i
 // ---------------------------------------------------------------------------
 // a7: TrackletSelector
 // ---------------------------------------------------------------------------
+// Selector weight of a tracklet: more hits first, then the smaller start-hit
+// id.  64 bits in general; 32 bits ((hits << 24) | (2^24 - 1 - id)) when every
+// id of the call is below 2^24 (hits <= 255 always): the same order, half the
+// memory and atomic payload.
+template <typename W> __device__ __forceinline__ W sel_weight(int nh, int id);
+template <> __device__ __forceinline__ unsigned long long sel_weight<unsigned long long>(int nh, int id)
+{
+    return tracklet_weight(nh, id);
+}
+template <> __device__ __forceinline__ unsigned sel_weight<unsigned>(int nh, int id)
+{
+    return ((unsigned)nh << 24) | (0xFFFFFFu - (unsigned)id);
+}
+
+template <typename W>
 __global__ void k_sel_weight(const Frame* __restrict__ f, int cap, int nr, int min_hits, const int32_t* __restrict__ t_id,
                              const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
-                             const int32_t* __restrict__ t_hits, unsigned long long* __restrict__ hitw)
+                             const int32_t* __restrict__ t_hits, W* __restrict__ hitw)
 {
     const int nt = min(f->n_starts, cap);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const int nh = t_nhits[t];
         if (nh < min_hits) continue;
-        const unsigned long long w = tracklet_weight(nh, t_id[t]);
+        const W w = sel_weight<W>(nh, t_id[t]);
         const int32_t* slot = t_hits + (int64_t)t * nr;
         const int nup = t_nup[t];
         for (int k = 0; k < nh; k++) atomicMax(&hitw[trk_hit(slot, nr, nh, nup, k)], w);
     }
 }
 
+template <typename W>
 __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned, const int32_t* __restrict__ t_id,
                           const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
-                          const int32_t* __restrict__ t_hits, const unsigned long long* __restrict__ hitw,
+                          const int32_t* __restrict__ t_hits, const W* __restrict__ hitw,
                           uint8_t* __restrict__ kept, int32_t* __restrict__ seg, int32_t* __restrict__ t_own,
                           uint32_t* __restrict__ ownmask)
 {
@@ -1169,7 +1186,7 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
         uint8_t k = 0;
         int own = 0;
         if (nh >= min_hits) {
-            const unsigned long long w = tracklet_weight(nh, t_id[t]);
+            const W w = sel_weight<W>(nh, t_id[t]);
             const int32_t* slot = t_hits + (int64_t)t * nr;
             const int nup = t_nup[t];
             // owned hits in ascending row order, as bits of words [q / 32][t]
@@ -1920,19 +1937,33 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     const int gT = grid_for(ntcap, TRK_BLOCK);
     const int gQ = p->queue_blocks_per_sm > 0 ? std::min(gT, 148 * p->queue_blocks_per_sm) : gT;
     TA.t_state = at<float>(ws, L.t_state);
-    k_tracklets<1><<<gQ, TRK_BLOCK, 0, st>>>(TA);
-    k_tracklets<2><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    if (prof) k_tracklets<1, true><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    else k_tracklets<1, false><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    if (prof) k_tracklets<2, true><<<gQ, TRK_BLOCK, 0, st>>>(TA);
+    else k_tracklets<2, false><<<gQ, TRK_BLOCK, 0, st>>>(TA);
     g_launches += 2;
     CK(mark(5));
     // a7: selector
-    CK(cudaMemsetAsync(hitw, 0, 8 * (size_t)n, st));
+    const bool w32 = n <= (1 << 24);   // every start-hit id below 2^24: 32-bit weights
+    CK(cudaMemsetAsync(hitw, 0, (w32 ? 4 : 8) * (size_t)n, st));
     const int gt2 = grid_for(ntcap, B);
     uint8_t* kept = at<uint8_t>(ws, L.t_kept);
     int32_t* seg = at<int32_t>(ws, L.seg);
     const int gt2w = grid_for((int64_t)ntcap * 32, B);      // one warp per tracklet
-    k_sel_weight<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup, TA.t_hits, hitw);
-    k_sel_own<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits, TA.t_nup,
-                                 TA.t_hits, hitw, kept, seg, at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
+    if (w32) {
+        unsigned* hw = reinterpret_cast<unsigned*>(hitw);
+        k_sel_weight<unsigned><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup,
+                                                  TA.t_hits, hw);
+        k_sel_own<unsigned><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits,
+                                               TA.t_nup, TA.t_hits, hw, kept, seg, at<int32_t>(ws, L.t_own),
+                                               at<uint32_t>(ws, L.ownmask));
+    } else {
+        k_sel_weight<unsigned long long><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits,
+                                                            TA.t_nup, TA.t_hits, hitw);
+        k_sel_own<unsigned long long><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id,
+                                                         TA.t_nhits, TA.t_nup, TA.t_hits, hitw, kept, seg,
+                                                         at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
+    }
     g_launches += 2;
     CK(mark(6));
     // a8: merger
