@@ -184,3 +184,31 @@ def test_host_io_capture_equals_device_graph(frames):
         assert np.array_equal(p.numpy(), w.param.cpu().numpy())
         assert np.array_equal(c2.numpy(), w.chi2.cpu().numpy())
         assert np.array_equal(a.numpy(), w.assign.cpu().numpy())
+
+
+@pytest.mark.slow
+def test_batched_call_above_2pow24_clusters():
+    """A call of more than 2^24 clusters (the 50-collision frame and an
+    8-collision frame, 19 M clusters) ranks the selector's tracklets with
+    64-bit weights; per-frame calls (below 2^24) with 32-bit ones.  Both give
+    the same tracks."""
+    import paper_1905_05515_b300 as tpc
+    evs = [tpcgen.time_frame(seed=3, with_truth=False), tpcgen.time_frame(seed=4, n_collisions=8, with_truth=False)]
+    cat, off = _concat(evs)
+    assert off[-1] > (1 << 24) and all(e.n <= (1 << 24) for e in evs)
+    ev0 = evs[0]
+    trk = tpc.Tracker(int(off[-1]), ev0.row_x, continuous=True, n_frames=2)
+    rb = trk.track_batched(*_dev(cat), off, bz=ev0.bz, v_drift=ev0.v_drift)
+    pb, ab = rb.param.cpu().numpy(), rb.assign.cpu().numpy()
+    del trk
+    t = 0
+    for f, ev in enumerate(evs):
+        one = tpc.Tracker(ev.n, ev.row_x, continuous=True)
+        r1 = one.track(*_dev({k: getattr(ev, k) for k in ("sector", "row", "y", "zt")}), bz=ev.bz, v_drift=ev.v_drift)
+        T = r1.n_tracks
+        np.testing.assert_array_equal(pb[t:t + T], r1.param.cpu().numpy())
+        a1 = r1.assign.cpu().numpy()
+        np.testing.assert_array_equal(ab[off[f]:off[f + 1]], np.where(a1 >= 0, a1 + t, -1))
+        t += T
+        del one
+    assert t == rb.n_tracks
