@@ -40,11 +40,18 @@ FLOPS_PROP = 181      # prop32: 71 for the state and Jacobian terms + 110 for F 
 FLOPS_UPDATE = 130    # update32: innovation, 2x2 inverse, chi2, gain, state, covariance
 FLOPS_CAND = 5        # one grid candidate in the following window: 2 sub + fused distance
 FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky solve (~250)
+# binary64 flops of one step of the binary64 final refit pass, counted from its
+# operation lists in tpc_fit.cuh / tpc_refit.cu: covariance transport F C F^T
+# (64 FMA) + Joseph update (gain 30, (I - KH)C 64, V K 10, C+ 120, residual,
+# S, 1/det, chi2 24)
+FLOPS_REFIT64 = 376
+# nominal B300 binary64 rate (no measured FP64 peak is available)
+FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per cluster of the frame of one stage (both
 # tracklet passes), from the committed ncu capture of the same kernel build
 # (profiles/k_tracklets_frame20.md, 20-collision frame, scaled by clusters);
 # None once the kernel changes
-NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 195.4}
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 194.8}
 
 
 def parse():
@@ -486,10 +493,14 @@ def run_batch(args, ws, rank, local, pg):
     p_frame = torch.cat(per_frame()).cpu().numpy()
     one.params.profile = 1
     pf_stage_ms = {k: 0.0 for k in tpc.abi.STAGES}
+    pf_work = {}
     for i in range(nstf):
         a, b = int(off[i]), int(off[i + 1])
-        for k, v in one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd).stage_ms.items():
+        r1 = one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd)
+        for k, v in r1.stage_ms.items():
             pf_stage_ms[k] += v
+        for k, v in r1.work.items():
+            pf_work[k] = pf_work.get(k, 0) + v
     one.params.profile = 0
     del one
     torch.cuda.empty_cache()
@@ -534,6 +545,17 @@ def run_batch(args, ws, rank, local, pg):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_same = bool(np.array_equal(torch.cat([h[1] for h in hres]).numpy(), p_graph))
     h2d, d2h = gb.host_io_bytes()
+    # roofline of the dominant stage of the per-frame calls (stage events)
+    dom = max(pf_stage_ms, key=pf_stage_ms.get)
+    if dom == "refit" and fp64:
+        fl = pf_work["refit_prop"] / params.refit_passes * FLOPS_REFIT64
+        ach = fl / (pf_stage_ms["refit"] / 1e3) / 1e12
+        roof = {"bound": "fp64", "stage": "refit", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "peak_note": "nominal B300 FP64 rate (no measured FP64 peak); the stage time includes the two "
+                             "binary32 passes"}
+    else:
+        roof = roofline(dom, pf_stage_ms, pf_work, n, peaks())
     (ms_graph, e2e_s), (n_all,) = over_ranks(pg, dev, (ms_graph, e2e_s), (float(n),))
     if rank != 0:
         return
@@ -555,6 +577,7 @@ def run_batch(args, ws, rank, local, pg):
                    "final_refit": "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32",
                    "link_coordinates": "16-bit packed (1/256 cm)" if packed else "fp32",
                    "l2": "inputs (10 B/cluster) exceed the 126 MB L2; no flush"},
+        "roofline": roof,
         "e2e": {"value": n_all / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": gb.n_launches * args.steps,
         "clocks": clk.summary(),
