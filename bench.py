@@ -77,7 +77,9 @@ def parse():
     ap.add_argument("--no-packed", action="store_true",
                     help="stf_batch: full-precision link pass (default: 16-bit packed link coordinates)")
     ap.add_argument("--no-fp64-final", action="store_true",
-                    help="stf_batch: binary32 final refit (default: FP64 Joseph covariance and chi2 in the last pass)")
+                    help="stf_batch: binary32 final refit (default: binary64 Joseph update of the loopers, binary64 chi2)")
+    ap.add_argument("--fp64-all", action="store_true",
+                    help="stf_batch: binary64 Joseph covariance update of every track in the final refit pass")
     return ap.parse_args()
 
 
@@ -380,52 +382,89 @@ def make_stf_batch(n_stf, max_coll, mult, seed0=1000):
     return cat, off, ncoll
 
 
-def batch_cpu_baseline(cat, off, k, res, fp64, base=0, packed=False):
-    """cpu_baseline of the batch: the oracle, single-threaded, on sub-time-frame
-    k alone (the smallest of the batch), and the error of the batch's results
-    for that frame against it (decisions exact, fit relative to the FP64
-    oracle refit).  res: the result holding frame k, whose cluster indices
-    count from cluster `base` of the batch."""
-    import numpy as np
-
+def _oracle_stf(job):
+    """One sub-time-frame through the oracle (process-pool worker)."""
     import oracle
     import tpcgen
-    a, b = int(off[k]), int(off[k + 1])
+    sector, row, y, zt, packed = job
     t0 = time.perf_counter()
-    r = oracle.track(cat["sector"][a:b], cat["row"][a:b], cat["y"][a:b], cat["zt"][a:b], tpcgen.row_x_f32(),
-                     n_sectors=36, z_max=250.0, continuous=True, bz=0.5, v_drift=tpcgen.V_DRIFT,
-                     params={"packed_links": int(packed)})
+    r = oracle.track(sector, row, y, zt, tpcgen.row_x_f32(), n_sectors=36, z_max=250.0, continuous=True, bz=0.5,
+                     v_drift=tpcgen.V_DRIFT, params={"packed_links": int(packed)})
     dt = time.perf_counter() - t0
+    return dict(dt=dt, n_tracks=r.n_tracks, tr_clus=r.tr_clus, assign=r.assign, tr_status=r.tr_status, tr_p=r.tr_p,
+                tr_chi2=r.tr_chi2, tr_ndf=r.tr_ndf, tr_c=r.tr_c)
+
+
+def _stf_errors(k, a, b, r, res, base, fp64):
+    """Errors of frame k of the batch's results against the oracle's run of it
+    (decisions exact; fit relative to the binary64 oracle refit on the tracks
+    that are fits of one helix, chi2/ndf < 100 in the oracle, the others
+    counted)."""
+    import numpy as np
     fr = res.frame.cpu().numpy()
     idx = np.nonzero(fr == k)[0]
-    err = {"frame": int(k), "clusters": b - a, "tracks_gpu": int(idx.size), "tracks_oracle": r.n_tracks}
-    if idx.size == r.n_tracks and idx.size > 0:
+    err = {"frame": int(k), "clusters": b - a, "tracks_gpu": int(idx.size), "tracks_oracle": int(r["n_tracks"])}
+    if idx.size == r["n_tracks"] and idx.size > 0:
         t_lo, t_hi = int(idx[0]), int(idx[-1]) + 1
         co = res.clus_offset.cpu().numpy()
         ci = res.clus_index[int(co[t_lo]):int(co[t_hi])].cpu().numpy() - (a - base)
         asg = res.assign[a - base:b - base].cpu().numpy()
         asg = np.where(asg >= 0, asg - t_lo, -1)
-        err["clusters_mismatch"] = int(ci.size != r.tr_clus.size or (ci != r.tr_clus).sum())
-        err["assign_mismatch"] = int((asg != r.assign).sum())
+        err["clusters_mismatch"] = int(ci.size != r["tr_clus"].size or (ci != r["tr_clus"]).sum())
+        err["assign_mismatch"] = int((asg != r["assign"]).sum())
         st = res.status[t_lo:t_hi].cpu().numpy()
-        ok = (st == 0) & (r.tr_status == 0)
-        err["status_mismatch"] = int((st != r.tr_status).sum())
+        both = (st == 0) & (r["tr_status"] == 0)
+        helix = r["tr_chi2"] < 100.0 * np.maximum(r["tr_ndf"], 1)
+        ok = both & helix
+        err["status_mismatch"] = int((st != r["tr_status"]).sum())
+        err["not_helix"] = int((both & ~helix).sum())
         p = res.param[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
         floor = np.array([1.0, 1.0, 1e-2, 1e-2, 1e-2])
-        pe = np.abs(p - r.tr_p[ok]) / np.maximum(np.abs(r.tr_p[ok]), floor)
+        pe = np.abs(p - r["tr_p"][ok]) / np.maximum(np.abs(r["tr_p"][ok]), floor)
+        # the parity bar of the tests: 1e-4 relative, or 1e-3 of the parameter's sigma
+        sig = np.sqrt(np.abs(r["tr_c"][ok][:, [0, 2, 5, 9, 14]]))
+        err["param_bar_violations"] = int(((pe > 1e-4) & (np.abs(p - r["tr_p"][ok]) > 1e-3 * sig)).sum())
         chi = (res.chi2_64 if fp64 else res.chi2)[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
-        ce = np.abs(chi - r.tr_chi2[ok]) / np.maximum(r.tr_chi2[ok], 1.0)
+        ce = np.abs(chi - r["tr_chi2"][ok]) / np.maximum(r["tr_chi2"][ok], 1.0)
         cov = (res.cov64 if fp64 else res.cov)[t_lo:t_hi].cpu().numpy().astype(np.float64)[ok]
         dg = [0, 2, 5, 9, 14]
-        ve = np.abs(cov[:, dg] - r.tr_c[ok][:, dg]) / np.abs(r.tr_c[ok][:, dg])
+        ve = np.abs(cov[:, dg] - r["tr_c"][ok][:, dg]) / np.abs(r["tr_c"][ok][:, dg])
         err.update(param_rel_max=pe.max(axis=0).tolist() if pe.size else None,
                    param_rel_p99=np.percentile(pe, 99, axis=0).tolist() if pe.size else None,
                    chi2_rel_max=float(ce.max()) if ce.size else None,
                    cov_diag_rel_max=float(ve.max()) if ve.size else None)
-    return {"value": (b - a) / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
-            "sample": f"sub-time-frame {k} of the batch alone ({b - a} clusters, the smallest), "
-                      f"{dt:.1f} s wall, single thread",
-            "error_vs_oracle": err}
+    return err
+
+
+def batch_cpu_baseline(pool, jobs, picks, wall, off, results, fp64):
+    """cpu_baseline of the batch: the oracle as it stands on a seeded sample
+    of sub-time-frames (the smallest, the largest and six random ones), one
+    process per frame on the host cores, and the batch's errors against it
+    on every sampled frame.  jobs: the pool's pending results; results(k) ->
+    (result holding frame k, its first cluster index)."""
+    out = [j.get() for j in jobs]
+    wall = time.perf_counter() - wall
+    errs, n_tot, t_tot = [], 0, 0.0
+    for k, r in zip(picks, out):
+        a, b = int(off[k]), int(off[k + 1])
+        res, base = results(k)
+        errs.append(_stf_errors(k, a, b, r, res, base, fp64))
+        n_tot += b - a
+        t_tot += r["dt"]
+    pool.close()
+    worst = {key: sum((e.get(key) or 0) for e in errs) for key in ("clusters_mismatch", "assign_mismatch",
+                                                                  "status_mismatch", "not_helix",
+                                                                  "param_bar_violations")}
+    pmax = [max((e["param_rel_max"] or [0] * 5)[i] for e in errs) for i in range(5)]
+    return {"value": n_tot / wall, "unit": "clusters/s", "cores": len(picks), "kind": "oracle",
+            "single_thread_clusters_per_s": n_tot / t_tot,
+            "sample": f"{len(picks)} sub-time-frames of the batch (the smallest and 7 seeded random ones of at most "
+                      f"8 M clusters: the largest, 42 M, takes the oracle minutes; {n_tot} clusters), one oracle "
+                      f"process each on the host cores, {wall:.1f} s wall",
+            "error_vs_oracle": {"frames": [int(k) for k in picks], **worst, "param_rel_max": pmax,
+                                "chi2_rel_max": max((e.get("chi2_rel_max") or 0) for e in errs),
+                                "cov_diag_rel_max": max((e.get("cov_diag_rel_max") or 0) for e in errs),
+                                "tracks_match": all(e["tracks_gpu"] == e["tracks_oracle"] for e in errs)}}
 
 
 def run_batch(args, ws, rank, local, pg):
@@ -447,9 +486,10 @@ def run_batch(args, ws, rank, local, pg):
     ins = (dv["sector"], dv["row"], dv["y"], dv["zt"])
     row_x = tpcgen.row_x_f32()
     off32 = off.astype(np.int32)
-    fp64 = not args.no_fp64_final
+    fp64_mode = 0 if args.no_fp64_final else (1 if args.fp64_all else 2)
+    fp64 = fp64_mode > 0
     packed = not args.no_packed
-    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=int(fp64), packed_links=int(packed))
+    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=fp64_mode, packed_links=int(packed))
     nstf = len(ncoll)
     vd, bz = tpcgen.V_DRIFT, 0.5
     log = lambda m: print(m, file=sys.stderr)  # noqa: E731
@@ -494,9 +534,11 @@ def run_batch(args, ws, rank, local, pg):
     one.params.profile = 1
     pf_stage_ms = {k: 0.0 for k in tpc.abi.STAGES}
     pf_work = {}
+    pf_sizes = []                    # (clusters, ms) of every frame: time against size
     for i in range(nstf):
         a, b = int(off[i]), int(off[i + 1])
         r1 = one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd)
+        pf_sizes.append((b - a, sum(r1.stage_ms.values())))
         for k, v in r1.stage_ms.items():
             pf_stage_ms[k] += v
         for k, v in r1.work.items():
@@ -545,9 +587,19 @@ def run_batch(args, ws, rank, local, pg):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_same = bool(np.array_equal(torch.cat([h[1] for h in hres]).numpy(), p_graph))
     h2d, d2h = gb.host_io_bytes()
+    # time against frame size: a linear fit over the frames, and ns per cluster
+    # of the smallest and the largest third
+    nz = np.array(pf_sizes, dtype=np.float64)
+    order = np.argsort(nz[:, 0])
+    third = max(1, len(order) // 3)
+    fit = np.polyfit(nz[:, 0] / 1e6, nz[:, 1], 1)
+    scaling = {"frames": len(order), "clusters_min": int(nz[:, 0].min()), "clusters_max": int(nz[:, 0].max()),
+               "fit_ms_per_M_clusters": float(fit[0]), "fit_intercept_ms": float(fit[1]),
+               "ns_per_cluster_smallest_third": float(1e6 * nz[order[:third], 1].sum() / nz[order[:third], 0].sum()),
+               "ns_per_cluster_largest_third": float(1e6 * nz[order[-third:], 1].sum() / nz[order[-third:], 0].sum())}
     # roofline of the dominant stage of the per-frame calls (stage events)
     dom = max(pf_stage_ms, key=pf_stage_ms.get)
-    if dom == "refit" and fp64:
+    if dom == "refit" and fp64_mode == 1:
         fl = pf_work["refit_prop"] / params.refit_passes * FLOPS_REFIT64
         ach = fl / (pf_stage_ms["refit"] / 1e3) / 1e12
         roof = {"bound": "fp64", "stage": "refit", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -574,7 +626,10 @@ def run_batch(args, ws, rank, local, pg):
                    "single_call_identical": same_batch, "tuned": tuned or None,
                    "single_call_stage_ms": {k: round(v, 3) for k, v in stage_ms.items()} if stage_ms else None,
                    "per_frame_stage_ms": {k: round(v, 3) for k, v in pf_stage_ms.items()},
-                   "final_refit": "fp64 Joseph covariance + fp64 chi2" if fp64 else "fp32",
+                   "per_frame_scaling": scaling,
+                   "final_refit": {0: "fp32", 1: "fp64 Joseph covariance of every track + fp64 chi2",
+                                   2: "fp64 Joseph covariance of the loopers (|q/pT| >= 5 or more clusters than "
+                                      "rows), fp32 update of the others, fp64 chi2"}[fp64_mode],
                    "link_coordinates": "16-bit packed (1/256 cm)" if packed else "fp32",
                    "l2": "inputs (10 B/cluster) exceed the 126 MB L2; no flush"},
         "roofline": roof,
@@ -583,9 +638,24 @@ def run_batch(args, ws, rank, local, pg):
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
-        k = int(np.argmin(np.diff(off)))
-        gi = next(i for i, g in enumerate(gb.groups) if g.f0 <= k < g.f1)
-        line["cpu_baseline"] = batch_cpu_baseline(cat, off, k, res[gi], fp64, base=gb.groups[gi].a, packed=packed)
+        import multiprocessing as mp
+        sizes = np.diff(off)
+        rng = np.random.default_rng(7)
+        rest = [k for k in range(nstf) if k != int(np.argmin(sizes)) and sizes[k] <= 8_000_000]
+        picks = [int(np.argmin(sizes))] + sorted(rng.choice(rest, min(7, len(rest)), replace=False).tolist())
+        pool = mp.get_context("spawn").Pool(len(picks))
+        wall = time.perf_counter()
+        jobs = [pool.apply_async(_oracle_stf, ((cat["sector"][int(off[k]):int(off[k + 1])],
+                                                cat["row"][int(off[k]):int(off[k + 1])],
+                                                cat["y"][int(off[k]):int(off[k + 1])],
+                                                cat["zt"][int(off[k]):int(off[k + 1])], packed),))
+                for k in picks]
+
+        def holding(k):
+            gi = next(i for i, g in enumerate(gb.groups) if g.f0 <= k < g.f1)
+            return res[gi], gb.groups[gi].a
+
+        line["cpu_baseline"] = batch_cpu_baseline(pool, jobs, picks, wall, off, holding, fp64)
     print(json.dumps(line), flush=True)
 
 

@@ -86,7 +86,11 @@ typedef struct {
     int32_t tracklets_per_1k;    /* tracklet capacity per 1000 clusters (minimum 4096 total) */
     int32_t queue_blocks_per_sm; /* TrackletConstructor work-queue width: blocks per SM taking start
                                     hits from the queue (0: as many as the capacity needs, up to 16) */
-    int32_t fp64_final;          /* 1: final refit pass updates covariance (Joseph form) and chi2 in binary64 */
+    int32_t fp64_final;          /* final refit pass in binary64: 0 off; 1 covariance (Joseph form) and chi2 of
+                                    every track in binary64; 2 the binary64 Joseph update for long looping
+                                    low-pT tracks only (|q/pT| >= 5 c/GeV after the earlier passes, or more
+                                    clusters than pad rows), the binary32 update for the others, chi2 of
+                                    every track in binary64.  cov64 holds the final covariance either way. */
     int32_t profile;             /* 1: record CUDA events on the stream at stage boundaries (tpc_tracks.stage_ms) */
     int32_t packed_links;        /* 1: the link pass reads y, z as 16-bit packed fields of a fixed-point
                                     coordinate with step 2^-8 cm (decoded relative to the middle hit), i.e.

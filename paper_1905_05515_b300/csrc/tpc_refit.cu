@@ -95,6 +95,16 @@ __device__ __forceinline__ bool update(float* p, float* pl, float* c, float my, 
     return true;
 }
 
+// standard-form update (binary32 covariance), chi2 summed in binary64
+__device__ __forceinline__ bool update(float* p, float* pl, float* c, float my, float mz, float vy, float vz,
+                                       double& chi2)
+{
+    Chi2Sum d{0.0f, 0.0f};
+    if (!update(p, pl, c, my, mz, vy, vz, d)) return false;
+    chi2 += (double)d.s;
+    return true;
+}
+
 // Joseph-form update with a binary64 covariance and chi2:
 // C+ = (I - K H) C (I - K H)^T + K V K^T
 __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my, float mz, float vy, float vz,
@@ -146,13 +156,17 @@ __device__ __forceinline__ bool update(float* p, float* pl, double* c, float my,
 }
 
 
+// |q/pT| (c/GeV) from which the binary64 mode 2 treats a track as a looper
+// (pT below 0.2 GeV/c)
+constexpr float LOOPER_QPT = 5.0f;
+
 struct RefitArgs {
     const void* frame;
     const float4* tcl;      // track clusters in track order: y, z, row x, sector (int bits)
     const int32_t* order;   // tracks by decreasing cluster count (nullable)
     const int32_t* ttail;
     const float* t_top;
-    int ns, passes, fp64, max_tracks, prof;
+    int ns, nr, passes, fp64, max_tracks, prof;
     float kb, vy, vz, inflate;
     tpc_tracks out;
 };
@@ -198,12 +212,13 @@ __device__ __forceinline__ bool run_steps(const RefitArgs& R, int off, int n, bo
     return true;
 }
 
-template <typename CT>
+// ACC: the chi2 accumulator -- a compensated binary32 sum for the binary32
+// passes, binary64 for the final pass of the binary64 modes
+template <typename CT, typename ACC = typename std::conditional<std::is_same<CT, float>::value, Chi2Sum, double>::type>
 __device__ bool run_pass(const RefitArgs& R, int off, int n, bool inward, int& sec, float& x, float* p, float* pl,
                          CT* c, double& chi2, unsigned& nprop, float zref)
 {
-    // binary32 passes: compensated binary32 chi2; the binary64 pass: binary64
-    typename std::conditional<std::is_same<CT, float>::value, Chi2Sum, double>::type acc{};
+    ACC acc{};
     const bool ok = run_steps<CT>(R, off, n, inward, sec, x, p, pl, c, acc, nprop, zref);
     chi2 = chi2_value(acc);
     return ok;
@@ -241,11 +256,23 @@ __global__ void __launch_bounds__(128) k_refit(RefitArgs R)
         for (int pass = 0; pass < nfloat && ok; pass++) ok = run_pass<float>(R, off, n, (pass % 2) == 0, sec, x, p, pl, c, chi2, nprop, zref);
         double c64[15];
         if (FP64) {
+            // mode 1: the binary64 Joseph update for every track; mode 2: for
+            // long looping low-pT tracks only (|q/pT| >= LOOPER_QPT after the
+            // earlier passes, or more clusters than pad rows), the binary32
+            // update for the others; the final pass's chi2 in binary64 always
+            const bool inward_last = ((R.passes - 1) % 2) == 0;
+            const bool joseph = R.fp64 == 1 || fabsf(p[4] + pl[4]) >= LOOPER_QPT || n > R.nr;
+            if (joseph) {
 #pragma unroll
-            for (int k = 0; k < 15; k++) c64[k] = c[k];
-            if (ok) ok = run_pass<double>(R, off, n, ((R.passes - 1) % 2) == 0, sec, x, p, pl, c64, chi2, nprop, zref);
+                for (int k = 0; k < 15; k++) c64[k] = c[k];
+                if (ok) ok = run_pass<double>(R, off, n, inward_last, sec, x, p, pl, c64, chi2, nprop, zref);
 #pragma unroll
-            for (int k = 0; k < 15; k++) c[k] = (float)c64[k];
+                for (int k = 0; k < 15; k++) c[k] = (float)c64[k];
+            } else {
+                if (ok) ok = run_pass<float, double>(R, off, n, inward_last, sec, x, p, pl, c, chi2, nprop, zref);
+#pragma unroll
+                for (int k = 0; k < 15; k++) c64[k] = c[k];
+            }
         }
 #pragma unroll
         for (int k = 0; k < 5; k++) p[k] = p[k] + pl[k];
@@ -285,6 +312,7 @@ int tpc_launch_refit(const tpc_params* p, const tpc_geometry* g, float bz, const
     R.ttail = ttail;
     R.t_top = t_top;
     R.ns = g->n_sectors;
+    R.nr = g->n_rows;
     R.passes = p->refit_passes;
     R.fp64 = p->fp64_final;
     R.max_tracks = max_tracks;

@@ -1838,6 +1838,7 @@ int out_args(const tpc_params* p, const tpc_tracks* out)
         !out->nclus || !out->clus_offset || !out->clus_index || !out->assign)
         return TPC_ERR_ARG;
     if (out->capacity_tracks < 0 || out->capacity_clusters < 0) return TPC_ERR_ARG;
+    if (p->fp64_final < 0 || p->fp64_final > 2) return TPC_ERR_ARG;
     if (p->fp64_final && (!out->cov64 || !out->chi2_64)) return TPC_ERR_ARG;
     return TPC_OK;
 }

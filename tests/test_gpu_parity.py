@@ -79,11 +79,16 @@ def test_noise_only_and_tiny_inputs(orc):
     _check(ev, orc)
 
 
-def test_fp64_final_refit(orc):
-    """Binary64 covariance (Joseph form) and chi2 in the final pass."""
+@pytest.mark.parametrize("mode, make", [(1, lambda: tpcgen.central_event(seed=2, n_tracks=1500, with_truth=False)),
+                                        (1, lambda: tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False)),
+                                        (2, lambda: tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False))])
+def test_fp64_final_refit(orc, mode, make):
+    """Binary64 covariance (Joseph form) and chi2 in the final pass: of every
+    track (mode 1) or, with binary64 chi2 for every track, of the loopers only
+    (mode 2)."""
     import paper_1905_05515_b300 as tpc
-    ev = tpcgen.central_event(seed=2, n_tracks=1500, with_truth=False)
-    g = run_gpu(ev, params=tpc.tpc_params_default(fp64_final=1))
+    ev = make()
+    g = run_gpu(ev, params=tpc.tpc_params_default(fp64_final=mode))
     r = orc.track_event(ev)
     bad = compare_decisions(ev, g, r)
     assert all(v == 0 for v in bad.values()), bad
@@ -93,6 +98,26 @@ def test_fp64_final_refit(orc):
     cov_rel = np.abs(g["cov64"][ok] - r.tr_c[ok]) / np.maximum(np.abs(r.tr_c[ok]), 1e-12)
     diag = [0, 2, 5, 9, 14]
     assert np.median(cov_rel[:, diag]) < 1e-4
+
+
+def test_fp64_loopers_only_mode():
+    """Mode 2 takes the binary64 Joseph update exactly for the loopers: their
+    covariance equals mode 1's bit for bit; the other tracks' final covariance
+    is the binary32 update's (binary32-representable), their chi2 binary64."""
+    import paper_1905_05515_b300 as tpc
+    ev = tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False)
+    g1 = run_gpu(ev, params=tpc.tpc_params_default(fp64_final=1))
+    g2 = run_gpu(ev, params=tpc.tpc_params_default(fp64_final=2))
+    np.testing.assert_array_equal(g1["assign"], g2["assign"])
+    qpt = np.abs(g2["param"][:, 4])
+    nrow = ev.row_x.shape[0]
+    loop = ((qpt >= 5.5) | (g2["nclus"] > nrow)) & (g2["status"] == 0)
+    plain = (qpt <= 4.5) & (g2["nclus"] <= nrow) & (g2["status"] == 0)
+    assert loop.sum() > 10 and plain.sum() > 100
+    np.testing.assert_array_equal(g2["cov64"][loop], g1["cov64"][loop])
+    c = g2["cov64"][plain]
+    np.testing.assert_array_equal(c, c.astype(np.float32).astype(np.float64))
+    assert np.all(np.isfinite(g2["chi2_64"][plain]))
 
 
 @pytest.mark.parametrize("make", [lambda: tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False),
