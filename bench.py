@@ -326,7 +326,14 @@ def run_ours(args, ws, rank, local, pg):
     per_step = {k: v / args.steps for k, v in stage_sum.items()}
     w = {k: v / args.steps for k, v in work_sum.items()}
     dom = max(per_step, key=per_step.get)
-    roof = roofline(dom, per_step, w, n, peaks())
+    pk_all = peaks()
+    roof = roofline(dom, per_step, w, n, pk_all)
+    n_assigned = int(rs.clus_offset[-1].item()) if rs.n_tracks else 0
+    stage_roofs = {}
+    for st_ in per_step:
+        rf = roofline(st_, per_step, w, n, pk_all, n_assigned)
+        stage_roofs[st_] = {"bound": rf["bound"], "achieved": round(rf["achieved"], 3), "unit": rf["unit"],
+                            "frac": round(rf["frac"], 4)}
     line = {
         "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -342,6 +349,7 @@ def run_ours(args, ws, rank, local, pg):
                    "e2e_sync_call_clusters_per_s": n_total * args.steps / sync_max},
         "roofline": roof,
         "stage_ms": {k: round(v, 4) for k, v in per_step.items()},
+        "stage_rooflines": stage_roofs,
         "work_per_step": w,
         "e2e": {"value": n_total * args.steps / e2e_max, "unit": "clusters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(sum(d2h_list) / len(d2h_list))},
@@ -809,9 +817,10 @@ def run_calib(args, ws, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
-def roofline(stage, per_step, w, n, pk):
-    """Roofline of the dominant stage: algorithmic work of one launch / its
-    event-timed duration."""
+def roofline(stage, per_step, w, n, pk, n_assigned=None):
+    """Roofline of a stage: algorithmic work of one call / its event-timed
+    duration (binary32 flops for the Kalman stages, bytes for the others).
+    n_assigned: clusters in tracks (the assembly's unit)."""
     t = per_step[stage] / 1e3
     if stage in ("tracklets", "merge", "refit"):
         if stage == "tracklets":
@@ -828,6 +837,10 @@ def roofline(stage, per_step, w, n, pk):
     bytes_per = {"prep": 18, "bin": 40, "neighbours": 22, "clean_start": 28}.get(stage, 0)
     hbm = pk.get("hbm_gbs", 6400.0)
     ach = bytes_per * n / t / 1e9
+    if stage == "select":        # 24 B per tracklet hit: slot, weight atomic, ownership read
+        ach = 24.0 * w.get("trk_upd", 0) / t / 1e9
+    elif stage == "assemble" and n_assigned is not None:   # 44 B per assigned cluster
+        ach = 44.0 * n_assigned / t / 1e9
     return {"bound": "hbm", "stage": stage, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": None, "peak_note": "measured" if "hbm_gbs" in pk else "fallback"}
 

@@ -760,16 +760,27 @@ __global__ void k_clean(int n, const int32_t* __restrict__ upr, const int32_t* _
     }
 }
 
-__global__ void k_starts(int n, const int32_t* __restrict__ up, const int32_t* __restrict__ dn,
-                         int32_t* __restrict__ starts, int cap, Frame* f)
+// NeighboursCleaner and StartHitsFinder in one pass: the cleaned links of h,
+// and of its up neighbour, come from the raw links directly (a link is kept
+// when the neighbour links back)
+__global__ void k_clean_starts(int n, const int32_t* __restrict__ upr, const int32_t* __restrict__ dnr,
+                               int32_t* __restrict__ up, int32_t* __restrict__ dn, int32_t* __restrict__ starts,
+                               int cap, Frame* f)
 {
     if (f->err) return;
     for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const int h = base + threadIdx.x;
         bool is = false;
         if (h < n) {
-            const int u = up[h];
-            is = u >= 0 && dn[h] < 0 && up[u] >= 0;
+            const int u = upr[h], d = dnr[h];
+            const int uc = (u >= 0 && dnr[u] == h) ? u : -1;
+            const int dc = (d >= 0 && upr[d] == h) ? d : -1;
+            up[h] = uc;
+            dn[h] = dc;
+            if (uc >= 0 && dc < 0) {
+                const int uu = upr[uc];
+                is = uu >= 0 && dnr[uu] == uc;      // the up neighbour keeps its up link
+            }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, is);
         int pos0 = 0;
@@ -1921,9 +1932,8 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                               fg, p->dy_link, p->dz_link, p->s_max_link, upr, dnr, nullptr);
     g_launches++;
     CK(mark(3));
-    k_clean<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, f);
-    k_starts<<<gN, B, 0, st>>>(n, up, dn, starts, ntcap, f);
-    g_launches += 2;
+    k_clean_starts<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, starts, ntcap, f);
+    g_launches += 1;
     CK(mark(4));
     // a6: tracklets
     TrkArgs TA;
