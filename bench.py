@@ -446,9 +446,9 @@ def _stf_errors(k, a, b, r, res, base, fp64):
 
 def batch_cpu_baseline(pool, jobs, picks, wall, off, results, fp64):
     """cpu_baseline of the batch: the oracle as it stands on a seeded sample
-    of sub-time-frames (the smallest, the largest and six random ones), one
-    process per frame on the host cores, and the batch's errors against it
-    on every sampled frame.  jobs: the pool's pending results; results(k) ->
+    of sub-time-frames (the smallest and seven random ones of at most 8 M
+    clusters), one process per frame on the host cores, and the batch's
+    errors against it on every sampled frame.  jobs: the pool's pending results; results(k) ->
     (result holding frame k, its first cluster index)."""
     out = [j.get() for j in jobs]
     wall = time.perf_counter() - wall
