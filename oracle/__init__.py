@@ -80,6 +80,9 @@ def lib():
                                         C.c_int32, _PD, _PD, _PD, _PD, _PD]
         L.orc_bspline_all.argtypes = [C.c_double, _PD, _PD]
         L.orc_bspline_all.restype = None
+        L.orc_step_pos32.argtypes = [_PF, C.c_float, C.c_float]
+        L.orc_attach.argtypes = [C.POINTER(OrcGeom), C.c_float, C.c_int32, _PU8, _PU8, _PF, _PF, C.c_int32, _P32,
+                                 _P32, _P32, _P32, _P32, _PF, _P32, C.c_float, C.c_float, _P32, _PU8]
         _lib = L
     return _lib
 
@@ -196,6 +199,50 @@ def track(sector, row, y, zt, row_x, n_sectors=36, z_max=250.0, continuous=False
     finally:
         L.orc_free(C.byref(R))
     return out
+
+
+# ---- track-based cluster attachment ---------------------------------------------
+CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
+
+
+def attach(sector, row, y, r: OracleResult, row_x, n_sectors=36, bz=0.5, radius=1.5, pt_min=0.05):
+    """Cluster attachment of an oracle tracking result: (adjacent track per
+    cluster or -1, flags CL_*) -- tubes of ``radius`` cm, tracks below
+    ``pt_min`` GeV/c not good (tpc_oracle_attach.c)."""
+    L = lib()
+    sector = np.ascontiguousarray(sector, np.uint8)
+    row = np.ascontiguousarray(row, np.uint8)
+    y = np.ascontiguousarray(y, np.float32)
+    z = np.ascontiguousarray(r.z, np.float32)
+    row_x = np.ascontiguousarray(row_x, np.float32)
+    n = int(y.shape[0])
+    G = OrcGeom(n_sectors, row_x.shape[0], _ptr(row_x, _PF), 250.0, 0)
+    i32 = lambda a: np.ascontiguousarray(a, np.int32)  # noqa: E731
+    seg_trk, seg_next, seg_prev = i32(r.seg_trk), i32(r.seg_next), i32(r.seg_prev)
+    trk_off, trk_hits, assign = i32(r.trk_off), i32(r.trk_hits), i32(r.assign)
+    bot = np.ascontiguousarray(r.trk_bot, np.float32)
+    adj = np.empty(max(n, 1), np.int32)
+    fl = np.empty(max(n, 1), np.uint8)
+    rc = L.orc_attach(C.byref(G), bz, n, _ptr(sector, _PU8), _ptr(row, _PU8), _ptr(y, _PF), _ptr(z, _PF),
+                      int(seg_trk.shape[0]), _ptr(seg_trk, _P32), _ptr(seg_next, _P32), _ptr(seg_prev, _P32),
+                      _ptr(trk_off, _P32), _ptr(trk_hits, _P32), _ptr(bot, _PF), _ptr(assign, _P32), radius, pt_min,
+                      _ptr(adj, _P32), _ptr(fl, _PU8))
+    if rc != 0:
+        raise ValueError(f"oracle attachment rejected the input (code {rc})")
+    return adj[:n], fl[:n]
+
+
+def attach_event(ev, r: OracleResult, radius=1.5, pt_min=0.05):
+    """attach() on a tpcgen.Event and the oracle's result for it."""
+    return attach(ev.sector, ev.row, ev.y, r, ev.row_x, n_sectors=ev.n_sectors, bz=ev.bz, radius=radius,
+                  pt_min=pt_min)
+
+
+def step_pos32(p, x2, kb):
+    """One binary32 helix step of (x, y, z, sin phi, tan lambda, q/pT)."""
+    s = np.ascontiguousarray(p, np.float32).copy()
+    ok = lib().orc_step_pos32(_ptr(s, _PF), x2, kb)
+    return bool(ok), s
 
 
 def track_event(ev, params: dict | None = None) -> OracleResult:

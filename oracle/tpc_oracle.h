@@ -92,6 +92,22 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
               orc_result *out);
 void orc_free(orc_result *r);
 
+/* Track-based cluster attachment (tpc_oracle_attach.c).  Inputs: the clusters
+ * (sector, row, y, z after time -> z) and the tracker's segments as
+ * orc_track returns them (seg_trk/next/prev, the tracklet hit lists and
+ * inner-end states, assign).  Outputs per cluster: the adjacent track (-1
+ * none) and flags ORC_CL_*. */
+#define ORC_CL_ATTACHED  1
+#define ORC_CL_ADJACENT  2
+#define ORC_CL_PROTECTED 4
+#define ORC_CL_REMOVE    8
+int orc_step_pos32(float *p, float x2, float kb);
+int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, const uint8_t *row,
+               const float *y, const float *z, int32_t n_seg, const int32_t *seg_trk,
+               const int32_t *seg_next, const int32_t *seg_prev, const int32_t *trk_off,
+               const int32_t *trk_hits, const float *trk_bot, const int32_t *assign, float radius,
+               float pt_min, int32_t *adjacent, uint8_t *flags);
+
 /* single Kalman steps, exposed for the pins */
 int orc_prop32(float *st21, float x2, float kb);
 int orc_rot32(float *st21, float cs, float sn, float kb);
