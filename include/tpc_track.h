@@ -54,7 +54,15 @@ extern "C" {
 #define TPC_STAGE_MERGE 6       /* cross-sector merger */
 #define TPC_STAGE_ASSEMBLE 7    /* merged cluster lists and assignments */
 #define TPC_STAGE_REFIT 8       /* Kalman refit */
+#define TPC_STAGE_ATTACH 9      /* track-based cluster attachment (when tpc_tracks.cl_flags is set) */
 #define TPC_N_STAGES 10
+
+/* Cluster attachment flags (tpc_tracks.cl_flags), paper section "TPC Data
+ * Compression", cluster rejection: */
+#define TPC_CL_ATTACHED 1   /* attached to a track (assign >= 0) */
+#define TPC_CL_ADJACENT 2   /* not attached, inside the tube of a track (tpc_tracks.adjacent) */
+#define TPC_CL_PROTECTED 4  /* attached to a good track or inside the tube of one */
+#define TPC_CL_REMOVE 8     /* attached or adjacent and not protected: to be removed */
 
 /* Method parameters.  tpc_params_default() fills the values of the reading
  * used throughout (seeding windows, straightness cut, cluster errors,
@@ -100,6 +108,18 @@ typedef struct {
                                     tracklet slots (default 4000; >= 0).  Beyond it the merger evaluates
                                     the pairs of each segment end directly (same result, slower); 0
                                     always does. */
+    float tube_radius;           /* cluster attachment: tube radius around each track (cm, 0..20; default
+                                    1.5).  The tube follows each sector piece of a track: its
+                                    TrackletConstructor state at its innermost hit (binary32, after all
+                                    of its hits) is propagated row by row through the rows of the
+                                    piece's hits, stopping at the first refused step; a cluster of the
+                                    piece's sector on a traced row lies in the tube when
+                                    dy^2 + dz^2 < R^2 from the traced point. */
+    float pt_min_physics;        /* cluster attachment: tracks with pT below this (GeV/c; default 0.05)
+                                    are not good (not used for physics).  A track's pT, here and for
+                                    the adjacency order, is 1 / |q/pT| of the inner-end state of its
+                                    innermost piece: good when |q/pT| <= 1 / pt_min_physics (binary32;
+                                    0: every track is good). */
 } tpc_params;
 
 /* Detector geometry (host memory). */
@@ -146,6 +166,11 @@ typedef struct {
     int32_t *link_up_raw, *link_dn_raw;   /* [n] NeighboursFinder best pair (input index or -1) */
     int32_t *link_up, *link_dn;           /* [n] after NeighboursCleaner */
     uint8_t *is_start;                    /* [n] StartHitsFinder flag */
+    /* nullable cluster attachment (paper, section "TPC Data Compression"); the stage runs when
+     * cl_flags is set.  A cluster attached to no track is adjacent to the track of highest pT
+     * (smallest |q/pT|, then the smaller track index) whose tube holds it. */
+    uint8_t *cl_flags;                    /* [n] TPC_CL_* flags */
+    int32_t *adjacent;                    /* [n] adjacent track index, -1 if not adjacent (nullable) */
     /* filled on return (host-visible fields of this struct) */
     int32_t n_tracks;
     int32_t n_tracklets;

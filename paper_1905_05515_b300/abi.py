@@ -31,7 +31,8 @@ class TpcParams(C.Structure):
                 ("z_cell", C.c_float),
                 ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32),
                 ("queue_blocks_per_sm", C.c_int32), ("fp64_final", C.c_int32),
-                ("profile", C.c_int32), ("packed_links", C.c_int32), ("merge_pairs_per_1k", C.c_int32)]
+                ("profile", C.c_int32), ("packed_links", C.c_int32), ("merge_pairs_per_1k", C.c_int32),
+                ("tube_radius", C.c_float), ("pt_min_physics", C.c_float)]
 
 
 class TpcGeometry(C.Structure):
@@ -53,6 +54,7 @@ class TpcTracks(C.Structure):
                 ("cov64", C.c_void_p), ("chi2_64", C.c_void_p),
                 ("z", C.c_void_p), ("link_up_raw", C.c_void_p), ("link_dn_raw", C.c_void_p),
                 ("link_up", C.c_void_p), ("link_dn", C.c_void_p), ("is_start", C.c_void_p),
+                ("cl_flags", C.c_void_p), ("adjacent", C.c_void_p),
                 ("n_tracks", C.c_int32), ("n_tracklets", C.c_int32), ("n_segments", C.c_int32),
                 ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64),
                 ("n_launches", C.c_int32), ("stage_ms", C.c_float * 10), ("work", C.c_int64 * 5)]
@@ -73,6 +75,8 @@ def calib_n_theta(n_sectors: int) -> int:
 
 
 STAGES = ("prep", "bin", "neighbours", "clean_start", "tracklets", "select", "merge", "assemble", "refit")
+ATTACH_STAGE = 9            # tpc_tracks.stage_ms index of the cluster attachment (when requested)
+CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
 
 
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",

@@ -60,7 +60,7 @@ struct Layout {
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2, mpair, mpc2, bestA, bestB;
     int64_t mpcap;              // merger pair list capacity
-    size_t headmark, tcount, thead, ttail, tcl, lencnt, order;
+    size_t headmark, tcount, thead, ttail, tcl, lencnt, order, aprot;
     size_t total;
 };
 
@@ -197,6 +197,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.tcl = take(16 * N);       // track clusters in track order: y, z, row x, sector
     L.lencnt = take(4 * (LEN_BUCKETS + 1));
     L.order = take(4 * T);      // refit order
+    L.aprot = take(N);          // cluster attachment: inside a good track's tube
     L.total = o;
     return L;
 }
@@ -1695,6 +1696,157 @@ __global__ void k_seg_fill(AsmArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Track-based cluster attachment (paper, section "TPC Data Compression":
+// tubes around the tracks, adjacency to the highest-pT track, protection by
+// good tracks, removal of the rest of the attached or adjacent clusters).
+// The tube follows each sector piece: its TrackletConstructor state at its
+// innermost hit (after all of its hits) is propagated row by row through the
+// rows its hits span; all of it is binary32 on the decision path, so the
+// flags are the same on any hardware that rounds each operation.
+// ---------------------------------------------------------------------------
+struct AttachArgs {
+    const Frame* f;
+    const FrameGrid* fg;
+    int nr, np, ns, n;
+    float kb, R, R2, qmax;
+    const int32_t* seg;
+    const int32_t* segrank;     // track of each segment (-1: none)
+    const int32_t* thead;       // innermost segment of each track
+    const int32_t* t_nhits;
+    const int32_t* t_nup;
+    const int32_t* t_hits;
+    const float* t_bot;         // [slot][NST] state at the innermost hit
+    const float4* sc;
+    const uint32_t* cstart;
+    const float* rowtab;
+    const int32_t* assign;
+    unsigned long long* akey;   // [n] best adjacency key (0: none)
+    uint8_t* aprot;             // [n] inside the tube of a good track
+    uint8_t* flags;
+    int32_t* adjacent;
+};
+
+// One helix step of the position (x, y, z, sin phi; tan lambda and q/pT
+// constant) to the plane x2: sin phi linear in x, dy = dx (s1 + s2) / (c1 +
+// c2), arc = signed chord * asin(u)/u (series to u^6), dz = tan(lambda) arc.
+// false (state unchanged) when |sin phi| reaches SNP_MAX or |u| > U_MAX.
+__device__ __forceinline__ bool step_pos32(float* p, float x2, float kb)
+{
+    const float dx = x2 - p[0];
+    if (dx == 0.0f) return true;
+    const float k = kb * p[5];
+    const float s1 = p[3];
+    const float s2 = __fmaf_rn(k, dx, s1);
+    if (!(fabsf(s1) < SNP_MAX) || !(fabsf(s2) < SNP_MAX)) return false;
+    const float c1 = __fsqrt_rn((1.0f - s1) * (1.0f + s1));
+    const float c2 = __fsqrt_rn((1.0f - s2) * (1.0f + s2));
+    const float dy = dx * __fdiv_rn(s1 + s2, c1 + c2);
+    float chord = __fsqrt_rn(__fmaf_rn(dx, dx, dy * dy));
+    if (dx < 0.0f) chord = -chord;
+    const float u = (0.5f * k) * chord;
+    if (!(fabsf(u) <= U_MAX)) return false;
+    const float u2 = u * u;
+    const float arc = chord * __fmaf_rn(u2, __fmaf_rn(u2, __fmaf_rn(u2, AS3, AS2), AS1), 1.0f);
+    p[0] = x2;
+    p[1] = p[1] + dy;
+    p[2] = p[2] + arc * p[4];
+    p[3] = s2;
+    return true;
+}
+
+__device__ __forceinline__ float track_abs_qpt(const AttachArgs& A, int tr)
+{
+    return fabsf(A.t_bot[(int64_t)A.seg[A.thead[tr]] * NST + 5]);
+}
+
+// the clusters of the traced point's row inside the tube disc
+__device__ __forceinline__ void tube_visit(const AttachArgs& A, const FrameGrid& G, int s, int r, float yp, float zp,
+                                           unsigned long long key, bool good)
+{
+    const WinCells W = window_cells(G, s * A.nr + r, s, A.ns, A.rowtab, r, A.f->ny, yp, zp, A.R, A.R);
+    for (int k = 0; k < W.nzc; k++) {
+        int qb, qe;
+        W.range(A.cstart, k, qb, qe);
+        for (int q = qb; q < qe; q++) {
+            const float4 c = A.sc[q];
+            const float dy = c.x - yp;
+            const float dz = c.y - zp;
+            if (!(fabsf(dy) <= A.R) || !(fabsf(dz) <= A.R)) continue;
+            const float d2 = __fmaf_rn(dy, dy, dz * dz);
+            if (!(d2 < A.R2)) continue;
+            const int id = sc_id(c);
+            if (good) A.aprot[id] = 1;     // every writer stores 1
+            if (A.assign[id] < 0) atomicMax(&A.akey[id], key);
+        }
+    }
+}
+
+// one thread per segment: trace its tube
+__global__ void __launch_bounds__(128) k_attach_tube(AttachArgs A)
+{
+    if (A.f->err) return;
+    const int nseg = A.f->n_seg;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+        const int tr = A.segrank[b];
+        if (tr < 0) continue;
+        const int t = A.seg[b];
+        const int nh = A.t_nhits[t], nup = A.t_nup[t];
+        if (nh <= 0) continue;
+        const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
+        const uint32_t pg = sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, 0)]);
+        const int fr = (int)(pg / (uint32_t)A.np);
+        const int pl = (int)(pg - (uint32_t)fr * A.np);
+        const int s = pl / A.nr;
+        const int r_lo = pl - s * A.nr;
+        const int r_hi = (int)(sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, nh - 1)]) % (uint32_t)A.np) - s * A.nr;
+        const float aq = track_abs_qpt(A, tr);
+        const bool good = aq <= A.qmax;
+        const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(aq)) << 32) |
+                                       (unsigned long long)(0xFFFFFFFFu - (uint32_t)tr);
+        const float* bs = A.t_bot + (int64_t)t * NST;
+        float b0[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) b0[i] = bs[i];
+        int r_b = -1;
+        for (int r = 0; r < A.nr; r++)
+            if (A.rowtab[r * ROWTAB] == b0[0]) { r_b = r; break; }
+        if (r_b < 0) continue;
+        const FrameGrid G = A.fg[fr];
+        if (r_b >= r_lo && r_b <= r_hi) tube_visit(A, G, s, r_b, b0[1], b0[2], key, good);
+        float p[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) p[i] = b0[i];
+        for (int r = r_b + 1; r <= r_hi; r++) {
+            if (!step_pos32(p, A.rowtab[r * ROWTAB], A.kb)) break;
+            if (r >= r_lo) tube_visit(A, G, s, r, p[1], p[2], key, good);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; i++) p[i] = b0[i];
+        for (int r = r_b - 1; r >= r_lo; r--) {
+            if (!step_pos32(p, A.rowtab[r * ROWTAB], A.kb)) break;
+            if (r <= r_hi) tube_visit(A, G, s, r, p[1], p[2], key, good);
+        }
+    }
+}
+
+// one thread per cluster: the flags
+__global__ void k_attach_flags(AttachArgs A)
+{
+    if (A.f->err) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.n; c += gridDim.x * blockDim.x) {
+        const int a = A.assign[c];
+        const unsigned long long key = A.akey[c];
+        const bool att = a >= 0;
+        const bool adj = !att && key != 0ull;
+        const bool prot = A.aprot[c] != 0 || (att && track_abs_qpt(A, a) <= A.qmax);
+        const bool rem = (att || adj) && !prot;
+        A.flags[c] = (uint8_t)((att ? TPC_CL_ATTACHED : 0) | (adj ? TPC_CL_ADJACENT : 0) |
+                               (prot ? TPC_CL_PROTECTED : 0) | (rem ? TPC_CL_REMOVE : 0));
+        if (A.adjacent) A.adjacent[c] = adj ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+    }
+}
+
 // Longest-first order of the tracks for the refit (one thread per track: a
 // warp then holds tracks of similar length).  Bucket = LEN_BUCKETS-1 -
 // min(n, LEN_BUCKETS-1).  Only the schedule depends on this order (each
@@ -1829,6 +1981,8 @@ int check_args(const tpc_params* p, const tpc_geometry* g)
     if (p->max_z_cells < 2 || p->tracklets_per_1k < 1 || p->refit_passes < 1) return TPC_ERR_ARG;
     if (!(p->refit_inflate >= 1.0f) || p->queue_blocks_per_sm < 0 || p->merge_pairs_per_1k < 0) return TPC_ERR_ARG;
     if (!(p->z_cell >= 0.25f) || p->y_bins < 1 || p->y_bins > MAX_YBINS) return TPC_ERR_ARG;
+    if (!(p->tube_radius >= 0.0f && p->tube_radius <= 20.0f)) return TPC_ERR_ARG;
+    if (!(p->pt_min_physics >= 0.0f && p->pt_min_physics <= 1e30f)) return TPC_ERR_ARG;
     for (int r = 0; r + 1 < g->n_rows; r++)
         if (!(g->row_x[r + 1] > g->row_x[r]) || !(g->row_x[r] > 0.0f)) return TPC_ERR_ARG;
     return TPC_OK;
@@ -2059,6 +2213,29 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     if (rr) return rr;
     g_launches++;
     CK(mark(9));
+    // optional: track-based cluster attachment
+    if (out->cl_flags) {
+        AttachArgs AT;
+        AT.f = f; AT.fg = fg; AT.nr = g->n_rows; AT.np = L.np; AT.ns = g->n_sectors; AT.n = n;
+        AT.kb = kb; AT.R = p->tube_radius;
+        AT.R2 = p->tube_radius * p->tube_radius;
+        {
+            volatile float one = 1.0f, pm = p->pt_min_physics;
+            AT.qmax = p->pt_min_physics > 0.0f ? one / pm : INFINITY;
+        }
+        AT.seg = seg; AT.segrank = AA.segrank; AT.thead = AA.thead; AT.t_nhits = TA.t_nhits; AT.t_nup = TA.t_nup;
+        AT.t_hits = TA.t_hits; AT.t_bot = TA.t_bot; AT.sc = sc; AT.cstart = cstart; AT.rowtab = rowtab;
+        AT.assign = out->assign;
+        AT.akey = at<unsigned long long>(ws, L.hitw);     // the selector's hit weights are dead by now
+        AT.aprot = at<uint8_t>(ws, L.aprot);
+        AT.flags = out->cl_flags; AT.adjacent = out->adjacent;
+        CK(cudaMemsetAsync(AT.akey, 0, 8 * (size_t)n, st));
+        CK(cudaMemsetAsync(AT.aprot, 0, (size_t)n, st));
+        k_attach_tube<<<grid_for(ntcap, 128), 128, 0, st>>>(AT);
+        k_attach_flags<<<gN, B, 0, st>>>(AT);
+        g_launches += 2;
+    }
+    CK(mark(10));
     // optional intermediate outputs
     if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
     if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
@@ -2133,7 +2310,8 @@ int run_sync(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift
     out->work[3] = (int64_t)hf.w_refit_prop;
     out->work[4] = (int64_t)hf.w_merge;
     if (prof)
-        for (int k = 0; k < 9; k++) CK(cudaEventElapsedTime(&out->stage_ms[k], g_events.ev[k], g_events.ev[k + 1]));
+        for (int k = 0; k < TPC_N_STAGES; k++)
+            CK(cudaEventElapsedTime(&out->stage_ms[k], g_events.ev[k], g_events.ev[k + 1]));
     out->n_tracklets = std::min(hf.n_starts, ntcap);
     out->n_segments = hf.n_seg;
     out->n_tracks = hf.n_tracks;
@@ -2187,6 +2365,8 @@ int tpc_params_default(tpc_params* p)
     p->profile = 0;
     p->packed_links = 0;
     p->merge_pairs_per_1k = 4000;
+    p->tube_radius = 1.5f;
+    p->pt_min_physics = 0.05f;
     return TPC_OK;
 }
 

@@ -38,6 +38,8 @@ class TrackResult:
     link_up: torch.Tensor | None = None
     link_dn: torch.Tensor | None = None
     is_start: torch.Tensor | None = None
+    cl_flags: torch.Tensor | None = None      # [n] uint8 CL_* flags (attach=True)
+    adjacent: torch.Tensor | None = None      # [n] int32 adjacent track or -1 (attach=True)
     n_tracklets: int = 0
     n_segments: int = 0
     n_launches: int = 0
@@ -50,7 +52,7 @@ class Tracker:
 
     def __init__(self, n_max: int, row_x, n_sectors: int = 36, z_max: float = 250.0, continuous: bool = False,
                  params: abi.TpcParams | None = None, device="cuda", capacity_tracks: int | None = None,
-                 debug: bool = False, n_frames: int = 1):
+                 debug: bool = False, n_frames: int = 1, attach: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("the TPC tracker needs a CUDA device")
         self.lib = abi.lib()
@@ -87,9 +89,13 @@ class Tracker:
             for k in ("link_up_raw", "link_dn_raw", "link_up", "link_dn"):
                 self.buf[k] = torch.empty(n1, dtype=torch.int32, device=d)
             self.buf["is_start"] = torch.empty(n1, dtype=torch.uint8, device=d)
+        if attach:      # track-based cluster attachment (params.tube_radius, params.pt_min_physics)
+            self.buf["cl_flags"] = torch.empty(n1, dtype=torch.uint8, device=d)
+            self.buf["adjacent"] = torch.empty(n1, dtype=torch.int32, device=d)
         self.capacity_tracks = cap_t
         self.capacity_clusters = cap_c
         self.debug = debug
+        self.attach = attach
 
     def _tracks_struct(self) -> abi.TpcTracks:
         b = self.buf
@@ -98,7 +104,7 @@ class Tracker:
         t.capacity_clusters = self.capacity_clusters
         for k in ("sector", "x", "param", "cov", "chi2", "ndf", "status", "nclus", "clus_offset", "clus_index",
                   "assign", "frame", "cov64", "chi2_64", "z", "link_up_raw", "link_dn_raw", "link_up", "link_dn",
-                  "is_start"):
+                  "is_start", "cl_flags", "adjacent"):
             setattr(t, k, b[k].data_ptr() if k in b else None)
         return t
 
@@ -121,10 +127,14 @@ class Tracker:
         if out is not None:
             res.n_tracklets, res.n_segments, res.n_launches = out.n_tracklets, out.n_segments, out.n_launches
             res.stage_ms = {k: float(out.stage_ms[i]) for i, k in enumerate(abi.STAGES)}
+            if self.attach:
+                res.stage_ms["attach"] = float(out.stage_ms[abi.ATTACH_STAGE])
             res.work = dict(zip(("trk_prop", "trk_upd", "trk_cand", "refit_prop", "merge_chi2"),
                                 (int(v) for v in out.work)))
         if "cov64" in b:
             res.cov64, res.chi2_64 = b["cov64"][:T], b["chi2_64"][:T]
+        if self.attach:
+            res.cl_flags, res.adjacent = b["cl_flags"][:n], b["adjacent"][:n]
         if self.debug:
             res.z = b["z"][:n]
             res.link_up_raw, res.link_dn_raw = b["link_up_raw"][:n], b["link_dn_raw"][:n]

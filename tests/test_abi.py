@@ -94,7 +94,11 @@ def test_grid_parameter_limits_and_packed_workspace():
     import paper_1905_05515_b300 as tpc
     import tpcgen
     g = tpc.abi.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
-    for bad in (dict(z_cell=0.1), dict(y_bins=0), dict(y_bins=65), dict(merge_pairs_per_1k=-1)):
+    d = tpc.tpc_params_default()
+    assert d.tube_radius == np.float32(1.5) and d.pt_min_physics == np.float32(0.05)
+    for bad in (dict(z_cell=0.1), dict(y_bins=0), dict(y_bins=65), dict(merge_pairs_per_1k=-1),
+                dict(tube_radius=-0.5), dict(tube_radius=25.0), dict(tube_radius=float("nan")),
+                dict(pt_min_physics=-1.0), dict(pt_min_physics=float("inf"))):
         with pytest.raises(tpc.TpcError):
             tpc.tpc_workspace_size(tpc.tpc_params_default(**bad), g, 1000)
     # any cell size at or above 0.25 cm works: searches visit the cells a window overlaps
