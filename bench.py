@@ -51,6 +51,11 @@ FP64_NOMINAL_TFLOPS = 1.25
 # tracklet passes), from the committed ncu capture of the same kernel build
 # (profiles/k_tracklets_frame20.md, 20-collision frame, scaled by clusters);
 # None once the kernel changes
+# Cluster attachment, algorithmic bytes per input cluster: clearing its
+# adjacency key and tube mark (8 + 1), one read of its sorted record by the
+# tube scan (16), the flag pass reading assignment, key and mark (4 + 8 + 1)
+# and writing flags and adjacent track (1 + 4).
+ATTACH_B_PER_CLUSTER = 43
 NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 194.8}
 
 
@@ -63,6 +68,8 @@ def parse():
     ap.add_argument("--collisions", type=int, default=50)
     ap.add_argument("--cpu-sample-collisions", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-attach", action="store_true",
+                    help="frame: skip the timing of the optional cluster attachment stage")
     ap.add_argument("--workload", choices=("frame", "stf_batch", "calib"), default="frame",
                     help="frame: the 50-collision frame; stf_batch: sub-time-frames of 1..max-coll collisions")
     ap.add_argument("--n-stf", type=int, default=64)
@@ -318,6 +325,40 @@ def run_ours(args, ws, rank, local, pg):
     sync_s = time.perf_counter() - t0
     barrier()
 
+    # ---- the optional track-based cluster attachment (not part of the step
+    # above): its stage time from profiled synchronous calls of a tracker with
+    # the attachment outputs, its flag counts and its roofline
+    attach = None
+    if not args.no_attach:
+        trk_a = tpc.Tracker(n, ev.row_x, n_sectors=36, z_max=ev.z_max, continuous=True,
+                            params=tpc.tpc_params_default(profile=1), device=dev, attach=True)
+        for _ in range(args.warmup):
+            trk_a.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+        a_ms = []
+        for _ in range(args.steps):
+            ra = trk_a.track(*args_t, bz=ev.bz, v_drift=ev.v_drift)
+            a_ms.append(ra.stage_ms["attach"])
+        fl = ra.cl_flags
+        counts = {k: int(((fl & b) != 0).sum().item()) for k, b in (("attached", tpc.abi.CL_ATTACHED),
+                                                                    ("adjacent", tpc.abi.CL_ADJACENT),
+                                                                    ("protected", tpc.abi.CL_PROTECTED),
+                                                                    ("remove", tpc.abi.CL_REMOVE))}
+        same_assign = bool(torch.equal(ra.assign, rs.assign))
+        t_att = sum(a_ms) / len(a_ms)
+        hbm = peaks().get("hbm_gbs")
+        ach = ATTACH_B_PER_CLUSTER * n / (t_att / 1e3) / 1e9
+        attach = {"ms": round(t_att, 4), "tube_radius_cm": float(trk_a.params.tube_radius),
+                  "pt_min_gev": float(trk_a.params.pt_min_physics), "counts": counts,
+                  "tracks_identical_to_step": same_assign,
+                  "roofline": {"bound": "hbm", "achieved": round(ach, 1), "unit": "GB/s",
+                               "peak": hbm if hbm else 6400.0,
+                               "frac": round(ach / (hbm if hbm else 6400.0), 4),
+                               "bytes_per_cluster": ATTACH_B_PER_CLUSTER,
+                               "peak_note": "measured" if hbm else "fallback"}}
+        del trk_a, ra, fl
+        torch.cuda.empty_cache()
+    barrier()
+
     # ---- max over ranks, totals
     (ms_max, e2e_max, sync_max), (n_total,) = over_ranks(pg, dev, (ms, e2e_s, sync_s), (float(n),))
     if rank != 0:
@@ -356,6 +397,8 @@ def run_ours(args, ws, rank, local, pg):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if attach is not None:
+        line["attach"] = attach
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_collisions, seed=3)
     print(json.dumps(line), flush=True)

@@ -1782,29 +1782,97 @@ __device__ __forceinline__ void tube_visit(const AttachArgs& A, const FrameGrid&
     }
 }
 
-// one thread per segment: trace its tube
-__global__ void __launch_bounds__(128) k_attach_tube(AttachArgs A)
+// The tube's points of a segment come from a chain of helix steps
+// (sequential, cheap); each point's cell scan is a few dependent loads of its
+// plane's cells and clusters.  Scanned in segment order those loads jump
+// between planes and miss the L2, so the points are first bucketed by plane
+// (a counting sort: one pass of the chains counts the points per plane, a
+// scan gives the bucket starts, a second pass stores each point -- y, z and
+// its track's adjacency key -- in its bucket) and then scanned one thread
+// per point in plane order.  Points beyond the buffers' capacity are scanned
+// by the tracing thread itself.  The marks are order-free (atomicMax, stores
+// of 1), so none of this changes a result.
+struct SegInfo {
+    int s, fr, r_lo, r_hi;
+    unsigned long long key;
+    bool good;
+};
+
+__device__ __forceinline__ bool seg_info(const AttachArgs& A, int b, SegInfo& I)
+{
+    const int tr = A.segrank[b];
+    if (tr < 0) return false;
+    const int t = A.seg[b];
+    const int nh = A.t_nhits[t], nup = A.t_nup[t];
+    if (nh <= 0) return false;
+    const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
+    const uint32_t pg = sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, 0)]);
+    I.fr = (int)(pg / (uint32_t)A.np);
+    const int pl = (int)(pg - (uint32_t)I.fr * A.np);
+    I.s = pl / A.nr;
+    I.r_lo = pl - I.s * A.nr;
+    I.r_hi = (int)(sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, nh - 1)]) % (uint32_t)A.np) - I.s * A.nr;
+    const float aq = track_abs_qpt(A, tr);
+    I.good = aq <= A.qmax;
+    I.key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(aq)) << 32) |
+            (unsigned long long)(0xFFFFFFFFu - (uint32_t)tr);
+    return true;
+}
+
+__device__ __forceinline__ bool key_good(unsigned long long key, float qmax)
+{
+    return __uint_as_float(0xFFFFFFFFu - (uint32_t)(key >> 32)) <= qmax;
+}
+
+// per segment: +1 at the plane of its lowest row, -1 past its highest (a
+// difference array over the rows of each sector; k_attach_rowsum turns it
+// into the number of segments spanning each plane: the bucket sizes)
+__global__ void k_attach_span(AttachArgs A, uint32_t* __restrict__ dcnt)
 {
     if (A.f->err) return;
     const int nseg = A.f->n_seg;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
-        const int tr = A.segrank[b];
-        if (tr < 0) continue;
-        const int t = A.seg[b];
-        const int nh = A.t_nhits[t], nup = A.t_nup[t];
-        if (nh <= 0) continue;
-        const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
-        const uint32_t pg = sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, 0)]);
-        const int fr = (int)(pg / (uint32_t)A.np);
-        const int pl = (int)(pg - (uint32_t)fr * A.np);
-        const int s = pl / A.nr;
-        const int r_lo = pl - s * A.nr;
-        const int r_hi = (int)(sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, nh - 1)]) % (uint32_t)A.np) - s * A.nr;
-        const float aq = track_abs_qpt(A, tr);
-        const bool good = aq <= A.qmax;
-        const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(aq)) << 32) |
-                                       (unsigned long long)(0xFFFFFFFFu - (uint32_t)tr);
-        const float* bs = A.t_bot + (int64_t)t * NST;
+        SegInfo I;
+        if (!seg_info(A, b, I)) continue;
+        const uint32_t base = (uint32_t)I.fr * (uint32_t)A.np + (uint32_t)(I.s * A.nr);
+        atomicAdd(&dcnt[base + (uint32_t)I.r_lo], 1u);
+        if (I.r_hi + 1 < A.nr) atomicAdd(&dcnt[base + (uint32_t)(I.r_hi + 1)], 0xFFFFFFFFu);
+    }
+}
+
+// one thread per (frame, sector): running sum over its rows
+__global__ void k_attach_rowsum(uint32_t* __restrict__ dcnt, int nseq, int nr, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nseq; q += gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        for (int r = 0; r < nr; r++) {
+            c += dcnt[(int64_t)q * nr + r];
+            dcnt[(int64_t)q * nr + r] = c;
+        }
+    }
+}
+
+// One thread per segment: the chain of points from the inner-end state, each
+// stored in its plane's bucket (cursor[plane]: the bucket's next free
+// position) or scanned here when the buffers are full (cap == 0: always).
+// The chain runs in blocks of ATT_U rows: the loop-carried quantities (x,
+// sin phi) first, then the ATT_U steps' square roots and divisions side by
+// side, then the checks and the y, z sums in row order -- every quantity is
+// the operation sequence of step_pos32, so the points are those of the
+// row-by-row chain.
+constexpr int ATT_U = 4;
+
+__global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t* __restrict__ cursor,
+                                                         float2* __restrict__ pts,
+                                                         unsigned long long* __restrict__ pkey, uint32_t cap)
+{
+    if (A.f->err) return;
+    const int nseg = A.f->n_seg;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+        SegInfo I;
+        if (!seg_info(A, b, I)) continue;
+        const float* bs = A.t_bot + (int64_t)A.seg[b] * NST;
         float b0[6];
 #pragma unroll
         for (int i = 0; i < 6; i++) b0[i] = bs[i];
@@ -1812,21 +1880,97 @@ __global__ void __launch_bounds__(128) k_attach_tube(AttachArgs A)
         for (int r = 0; r < A.nr; r++)
             if (A.rowtab[r * ROWTAB] == b0[0]) { r_b = r; break; }
         if (r_b < 0) continue;
-        const FrameGrid G = A.fg[fr];
-        if (r_b >= r_lo && r_b <= r_hi) tube_visit(A, G, s, r_b, b0[1], b0[2], key, good);
-        float p[6];
+        const uint32_t pbase = (uint32_t)I.fr * (uint32_t)A.np + (uint32_t)(I.s * A.nr);
+        const FrameGrid G = A.fg[I.fr];
+        auto point = [&](int r, float y, float z) {
+            if (r < I.r_lo || r > I.r_hi) return;
+            const uint32_t q = cap ? atomicAdd(&cursor[pbase + (uint32_t)r], 1u) : 0xFFFFFFFFu;
+            if (q < cap) {
+                pts[q] = make_float2(y, z);
+                pkey[q] = I.key;
+            } else {
+                tube_visit(A, G, I.s, r, y, z, I.key, I.good);
+            }
+        };
+        point(r_b, b0[1], b0[2]);
+        const float k = A.kb * b0[5];
+        const float hk = 0.5f * k;
+        const float t = b0[4];
+#pragma unroll 1
+        for (int dir = 1; dir >= -1; dir -= 2) {
+            const int rlast = dir > 0 ? I.r_hi : I.r_lo;     // inclusive
+            float x = b0[0], y = b0[1], z = b0[2], sn = b0[3];
+            int r = r_b;
+            while (dir > 0 ? r < rlast : r > rlast) {
+                float xs[ATT_U], sv[ATT_U + 1], cv[ATT_U + 1], dxv[ATT_U];
+                sv[0] = sn;
+                float xc = x;
 #pragma unroll
-        for (int i = 0; i < 6; i++) p[i] = b0[i];
-        for (int r = r_b + 1; r <= r_hi; r++) {
-            if (!step_pos32(p, A.rowtab[r * ROWTAB], A.kb)) break;
-            if (r >= r_lo) tube_visit(A, G, s, r, p[1], p[2], key, good);
-        }
+                for (int i = 0; i < ATT_U; i++) {
+                    int rr = r + dir * (i + 1);
+                    rr = dir > 0 ? min(rr, rlast) : max(rr, rlast);      // rows past the end: computed, not used
+                    xs[i] = A.rowtab[rr * ROWTAB];
+                    dxv[i] = xs[i] - xc;
+                    sv[i + 1] = __fmaf_rn(k, dxv[i], sv[i]);
+                    xc = xs[i];
+                }
 #pragma unroll
-        for (int i = 0; i < 6; i++) p[i] = b0[i];
-        for (int r = r_b - 1; r >= r_lo; r--) {
-            if (!step_pos32(p, A.rowtab[r * ROWTAB], A.kb)) break;
-            if (r <= r_hi) tube_visit(A, G, s, r, p[1], p[2], key, good);
+                for (int i = 0; i <= ATT_U; i++) cv[i] = __fsqrt_rn((1.0f - sv[i]) * (1.0f + sv[i]));
+                bool stop = false;
+#pragma unroll
+                for (int i = 0; i < ATT_U; i++) {
+                    const int rr = r + dir * (i + 1);
+                    if (stop || (dir > 0 ? rr > rlast : rr < rlast)) {
+                        stop = true;
+                        continue;
+                    }
+                    const float dx = dxv[i];
+                    const float dy = dx * __fdiv_rn(sv[i] + sv[i + 1], cv[i] + cv[i + 1]);
+                    float chord = __fsqrt_rn(__fmaf_rn(dx, dx, dy * dy));
+                    if (dx < 0.0f) chord = -chord;
+                    const float u = hk * chord;
+                    if (!(fabsf(sv[i]) < SNP_MAX) || !(fabsf(sv[i + 1]) < SNP_MAX) || !(fabsf(u) <= U_MAX)) {
+                        stop = true;
+                        r = rlast;                       // the chain ends here
+                        continue;
+                    }
+                    const float u2 = u * u;
+                    const float arc = chord * __fmaf_rn(u2, __fmaf_rn(u2, __fmaf_rn(u2, AS3, AS2), AS1), 1.0f);
+                    y = y + dy;
+                    z = z + arc * t;
+                    point(rr, y, z);
+                }
+                if (r == rlast) break;
+                r += dir * ATT_U;
+                x = xs[ATT_U - 1];
+                sn = sv[ATT_U];
+            }
         }
+    }
+}
+
+// One thread per bucket position, in plane order: start[plane] is the
+// bucket's first position (start[P]: their total), cursor[plane] the end of
+// what the chains stored in it.
+__global__ void k_attach_visit(AttachArgs A, const uint32_t* __restrict__ start, const uint32_t* __restrict__ cursor,
+                               int P, const float2* __restrict__ pts, const unsigned long long* __restrict__ pkey,
+                               uint32_t cap)
+{
+    if (A.f->err) return;
+    const uint32_t total = min(start[P], cap);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int lo = 0, hi = P - 1;          // the last plane whose bucket starts at or before q
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        if (q >= cursor[lo]) continue;   // a row the chain did not reach
+        const int fr = lo / A.np;
+        const int pl = lo - fr * A.np;
+        const int s = pl / A.nr;
+        const float2 pt = pts[q];
+        const unsigned long long key = pkey[q];
+        tube_visit(A, A.fg[fr], s, pl - s * A.nr, pt.x, pt.y, key, key_good(key, A.qmax));
     }
 }
 
@@ -2213,7 +2357,15 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     if (rr) return rr;
     g_launches++;
     CK(mark(9));
-    // optional: track-based cluster attachment
+    // optional intermediate outputs
+    if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
+        k_export_links<<<gN, B, 0, st>>>(n, sc, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
+                                         out->link_dn, out->is_start, f);
+        g_launches++;
+    }
+    // optional: track-based cluster attachment (after the exports above: it
+    // reuses the link arrays and the refit's cluster buffer)
     if (out->cl_flags) {
         AttachArgs AT;
         AT.f = f; AT.fg = fg; AT.nr = g->n_rows; AT.np = L.np; AT.ns = g->n_sectors; AT.n = n;
@@ -2231,18 +2383,35 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
         AT.flags = out->cl_flags; AT.adjacent = out->adjacent;
         CK(cudaMemsetAsync(AT.akey, 0, 8 * (size_t)n, st));
         CK(cudaMemsetAsync(AT.aprot, 0, (size_t)n, st));
-        k_attach_tube<<<grid_for(ntcap, 128), 128, 0, st>>>(AT);
+        // plane buckets: counts in the binning's plane starts (free by now),
+        // points (y, z) in the refit's cluster buffer, their keys in the link
+        // arrays -- 2n points each.  32-bit positions: with 2^32 or more
+        // possible points every point is scanned by its tracing thread.
+        const int P = nplanes;
+        uint32_t* pcnt = pstart;                 // bucket starts, then (P + 1 entries on) the fill cursors
+        uint32_t* cursor = pstart + (P + 1);
+        float2* pts = at<float2>(ws, L.tcl);
+        unsigned long long* pkey = at<unsigned long long>(ws, L.upr);
+        const bool use_pts = (int64_t)ntcap * g->n_rows < (int64_t)UINT32_MAX;
+        const uint32_t cap = use_pts ? (uint32_t)std::min<int64_t>(2 * (int64_t)std::max(n, 1), UINT32_MAX) : 0u;
+        if (use_pts) {
+            CK(cudaMemsetAsync(pcnt, 0, 4 * ((size_t)P + 1), st));
+            k_attach_span<<<gt2, B, 0, st>>>(AT, pcnt);
+            const int nseq = NF * g->n_sectors;
+            k_attach_rowsum<<<std::max(1, (nseq + 127) / 128), 128, 0, st>>>(pcnt, nseq, g->n_rows, f);
+            scan_u32(pcnt, P, aux, st);
+            CK(cudaMemcpyAsync(cursor, pcnt, 4 * ((size_t)P + 1), cudaMemcpyDeviceToDevice, st));
+            g_launches += 2;
+        }
+        k_attach_trace<<<grid_for(ntcap, 128), 128, 0, st>>>(AT, cursor, pts, pkey, cap);
+        if (use_pts) {
+            k_attach_visit<<<grid_for(cap, B), B, 0, st>>>(AT, pcnt, cursor, P, pts, pkey, cap);
+            g_launches++;
+        }
         k_attach_flags<<<gN, B, 0, st>>>(AT);
         g_launches += 2;
     }
     CK(mark(10));
-    // optional intermediate outputs
-    if (out->z) CK(cudaMemcpyAsync(out->z, zlin, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (out->link_up_raw || out->link_dn_raw || out->link_up || out->link_dn || out->is_start) {
-        k_export_links<<<gN, B, 0, st>>>(n, sc, upr, dnr, up, dn, out->link_up_raw, out->link_dn_raw, out->link_up,
-                                         out->link_dn, out->is_start, f);
-        g_launches++;
-    }
     if (dev_counts) {
         k_publish<<<1, 32, 0, st>>>(f, ntcap, dev_counts);
         g_launches++;
