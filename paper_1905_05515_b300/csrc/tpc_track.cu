@@ -60,7 +60,7 @@ struct Layout {
     size_t seg, keyb, keyt, slotb, slott, cntb, cntt, byb, byt, recb, rect;
     size_t bnext, bprev, snext, sprev, bad, next2, prev2, mpair, mpc2, bestA, bestB;
     int64_t mpcap;              // merger pair list capacity
-    size_t headmark, tcount, thead, ttail, tcl, lencnt, order, aprot;
+    size_t headmark, tcount, thead, ttail, tcl, lencnt, order, aprot, acur;
     size_t total;
 };
 
@@ -198,6 +198,7 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.lencnt = take(4 * (LEN_BUCKETS + 1));
     L.order = take(4 * T);      // refit order
     L.aprot = take(N);          // cluster attachment: inside a good track's tube
+    L.acur = take(4 * ((size_t)nframes * L.np * PSPLIT + 1));   // cluster attachment: bucket fill cursors
     L.total = o;
     return L;
 }
@@ -1722,6 +1723,7 @@ struct AttachArgs {
     const float* rowtab;
     const int32_t* assign;
     unsigned long long* akey;   // [n] best adjacency key (0: none)
+    unsigned long long* tkey;   // [tracks] adjacency key of each track
     uint8_t* aprot;             // [n] inside the tube of a good track
     uint8_t* flags;
     int32_t* adjacent;
@@ -1793,7 +1795,7 @@ __device__ __forceinline__ void tube_visit(const AttachArgs& A, const FrameGrid&
 // by the tracing thread itself.  The marks are order-free (atomicMax, stores
 // of 1), so none of this changes a result.
 struct SegInfo {
-    int s, fr, r_lo, r_hi;
+    int s, fr, r_lo, r_hi, tr;
     unsigned long long key;
     bool good;
 };
@@ -1805,6 +1807,7 @@ __device__ __forceinline__ bool seg_info(const AttachArgs& A, int b, SegInfo& I)
     const int t = A.seg[b];
     const int nh = A.t_nhits[t], nup = A.t_nup[t];
     if (nh <= 0) return false;
+    I.tr = tr;
     const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
     const uint32_t pg = sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, 0)]);
     I.fr = (int)(pg / (uint32_t)A.np);
@@ -1826,7 +1829,11 @@ __device__ __forceinline__ bool key_good(unsigned long long key, float qmax)
 
 // per segment: +1 at the plane of its lowest row, -1 past its highest (a
 // difference array over the rows of each sector; k_attach_rowsum turns it
-// into the number of segments spanning each plane: the bucket sizes)
+// into the number of segments spanning each plane: the bucket sizes).  Each
+// plane's bucket is split in PSPLIT sub-buckets, segment b filling sub-bucket
+// b mod PSPLIT, so that the bucket reservations of the segments crossing a
+// plane spread over PSPLIT counters; the sub-buckets of a plane are adjacent,
+// so the scan still visits the points in plane order.
 __global__ void k_attach_span(AttachArgs A, uint32_t* __restrict__ dcnt)
 {
     if (A.f->err) return;
@@ -1834,21 +1841,25 @@ __global__ void k_attach_span(AttachArgs A, uint32_t* __restrict__ dcnt)
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
         SegInfo I;
         if (!seg_info(A, b, I)) continue;
+        if (A.thead[I.tr] == b) A.tkey[I.tr] = I.key;     // written by the track's innermost segment
         const uint32_t base = (uint32_t)I.fr * (uint32_t)A.np + (uint32_t)(I.s * A.nr);
-        atomicAdd(&dcnt[base + (uint32_t)I.r_lo], 1u);
-        if (I.r_hi + 1 < A.nr) atomicAdd(&dcnt[base + (uint32_t)(I.r_hi + 1)], 0xFFFFFFFFu);
+        const uint32_t k = (uint32_t)b % PSPLIT;
+        atomicAdd(&dcnt[(base + (uint32_t)I.r_lo) * PSPLIT + k], 1u);
+        if (I.r_hi + 1 < A.nr) atomicAdd(&dcnt[(base + (uint32_t)(I.r_hi + 1)) * PSPLIT + k], 0xFFFFFFFFu);
     }
 }
 
-// one thread per (frame, sector): running sum over its rows
+// one thread per (frame, sector, sub-bucket): running sum over its rows
 __global__ void k_attach_rowsum(uint32_t* __restrict__ dcnt, int nseq, int nr, const Frame* __restrict__ f)
 {
     if (f->err) return;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nseq; q += gridDim.x * blockDim.x) {
+        const int64_t fs = q / PSPLIT, k = q % PSPLIT;
         uint32_t c = 0;
         for (int r = 0; r < nr; r++) {
-            c += dcnt[(int64_t)q * nr + r];
-            dcnt[(int64_t)q * nr + r] = c;
+            const int64_t e = (fs * nr + r) * PSPLIT + k;
+            c += dcnt[e];
+            dcnt[e] = c;
         }
     }
 }
@@ -1863,9 +1874,15 @@ __global__ void k_attach_rowsum(uint32_t* __restrict__ dcnt, int nseq, int nr, c
 // row-by-row chain.
 constexpr int ATT_U = 4;
 
+// bucket record of a point: its plane and its track
+__device__ __forceinline__ unsigned long long point_meta(uint32_t plane, int tr)
+{
+    return ((unsigned long long)plane << 32) | (unsigned long long)(uint32_t)tr;
+}
+
 __global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t* __restrict__ cursor,
                                                          float2* __restrict__ pts,
-                                                         unsigned long long* __restrict__ pkey, uint32_t cap)
+                                                         unsigned long long* __restrict__ pmeta, uint32_t cap)
 {
     if (A.f->err) return;
     const int nseg = A.f->n_seg;
@@ -1881,18 +1898,36 @@ __global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t*
             if (A.rowtab[r * ROWTAB] == b0[0]) { r_b = r; break; }
         if (r_b < 0) continue;
         const uint32_t pbase = (uint32_t)I.fr * (uint32_t)A.np + (uint32_t)(I.s * A.nr);
+        const uint32_t sub = (uint32_t)b % PSPLIT;
         const FrameGrid G = A.fg[I.fr];
-        auto point = [&](int r, float y, float z) {
-            if (r < I.r_lo || r > I.r_hi) return;
-            const uint32_t q = cap ? atomicAdd(&cursor[pbase + (uint32_t)r], 1u) : 0xFFFFFFFFu;
-            if (q < cap) {
-                pts[q] = make_float2(y, z);
-                pkey[q] = I.key;
-            } else {
-                tube_visit(A, G, I.s, r, y, z, I.key, I.good);
+        // store the points of rows rv[] (-1: none) in their buckets, the
+        // ATT_U bucket reservations in flight together; past the capacity the
+        // point is scanned here
+        auto emit = [&](const int* rv, const float* yv, const float* zv) {
+            uint32_t qv[ATT_U];
+#pragma unroll
+            for (int i = 0; i < ATT_U; i++)
+                qv[i] = (cap && rv[i] >= I.r_lo && rv[i] <= I.r_hi)
+                            ? atomicAdd(&cursor[(pbase + (uint32_t)rv[i]) * PSPLIT + sub], 1u) : 0xFFFFFFFFu;
+#pragma unroll
+            for (int i = 0; i < ATT_U; i++) {
+                if (rv[i] < I.r_lo || rv[i] > I.r_hi) continue;
+                if (qv[i] < cap) {
+                    pts[qv[i]] = make_float2(yv[i], zv[i]);
+                    pmeta[qv[i]] = point_meta(pbase + (uint32_t)rv[i], I.tr);
+                } else {
+                    tube_visit(A, G, I.s, rv[i], yv[i], zv[i], I.key, I.good);
+                }
             }
         };
-        point(r_b, b0[1], b0[2]);
+        {
+            int rv[ATT_U];
+            float yv[ATT_U], zv[ATT_U];
+#pragma unroll
+            for (int i = 0; i < ATT_U; i++) { rv[i] = -1; yv[i] = 0.0f; zv[i] = 0.0f; }
+            rv[0] = r_b; yv[0] = b0[1]; zv[0] = b0[2];
+            emit(rv, yv, zv);
+        }
         const float k = A.kb * b0[5];
         const float hk = 0.5f * k;
         const float t = b0[4];
@@ -1916,9 +1951,14 @@ __global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t*
                 }
 #pragma unroll
                 for (int i = 0; i <= ATT_U; i++) cv[i] = __fsqrt_rn((1.0f - sv[i]) * (1.0f + sv[i]));
+                int rv[ATT_U];
+                float yv[ATT_U], zv[ATT_U];
                 bool stop = false;
 #pragma unroll
                 for (int i = 0; i < ATT_U; i++) {
+                    rv[i] = -1;
+                    yv[i] = 0.0f;
+                    zv[i] = 0.0f;
                     const int rr = r + dir * (i + 1);
                     if (stop || (dir > 0 ? rr > rlast : rr < rlast)) {
                         stop = true;
@@ -1938,8 +1978,11 @@ __global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t*
                     const float arc = chord * __fmaf_rn(u2, __fmaf_rn(u2, __fmaf_rn(u2, AS3, AS2), AS1), 1.0f);
                     y = y + dy;
                     z = z + arc * t;
-                    point(rr, y, z);
+                    rv[i] = rr;
+                    yv[i] = y;
+                    zv[i] = z;
                 }
+                emit(rv, yv, zv);
                 if (r == rlast) break;
                 r += dir * ATT_U;
                 x = xs[ATT_U - 1];
@@ -1949,27 +1992,35 @@ __global__ void __launch_bounds__(128, 8) k_attach_trace(AttachArgs A, uint32_t*
     }
 }
 
-// One thread per bucket position, in plane order: start[plane] is the
-// bucket's first position (start[P]: their total), cursor[plane] the end of
-// what the chains stored in it.
-__global__ void k_attach_visit(AttachArgs A, const uint32_t* __restrict__ start, const uint32_t* __restrict__ cursor,
-                               int P, const float2* __restrict__ pts, const unsigned long long* __restrict__ pkey,
+// per (plane, sub-bucket): mark the positions that no point filled (rows the
+// chains did not reach)
+__global__ void k_attach_holes(const uint32_t* __restrict__ start, const uint32_t* __restrict__ cursor, int P,
+                               unsigned long long* __restrict__ pmeta, uint32_t cap, const Frame* __restrict__ f)
+{
+    if (f->err) return;
+    for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < P; gp += gridDim.x * blockDim.x) {
+        const uint32_t e = min(start[gp + 1], cap);
+        for (uint32_t q = cursor[gp]; q < e; q++) pmeta[q] = ~0ull;
+    }
+}
+
+// One thread per bucket position, in plane order (start[P]: the positions
+// in use).
+__global__ void k_attach_visit(AttachArgs A, const uint32_t* __restrict__ start, int P,
+                               const float2* __restrict__ pts, const unsigned long long* __restrict__ pmeta,
                                uint32_t cap)
 {
     if (A.f->err) return;
     const uint32_t total = min(start[P], cap);
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        int lo = 0, hi = P - 1;          // the last plane whose bucket starts at or before q
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (start[mid] <= q) lo = mid; else hi = mid - 1;
-        }
-        if (q >= cursor[lo]) continue;   // a row the chain did not reach
-        const int fr = lo / A.np;
-        const int pl = lo - fr * A.np;
+        const unsigned long long meta = pmeta[q];
+        if (meta == ~0ull) continue;     // a row the chain did not reach
+        const uint32_t gp = (uint32_t)(meta >> 32);
+        const unsigned long long key = A.tkey[(uint32_t)meta];
+        const int fr = (int)(gp / (uint32_t)A.np);
+        const int pl = (int)(gp - (uint32_t)fr * A.np);
         const int s = pl / A.nr;
         const float2 pt = pts[q];
-        const unsigned long long key = pkey[q];
         tube_visit(A, A.fg[fr], s, pl - s * A.nr, pt.x, pt.y, key, key_good(key, A.qmax));
     }
 }
@@ -2388,25 +2439,28 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
         // arrays -- 2n points each.  32-bit positions: with 2^32 or more
         // possible points every point is scanned by its tracing thread.
         const int P = nplanes;
-        uint32_t* pcnt = pstart;                 // bucket starts, then (P + 1 entries on) the fill cursors
-        uint32_t* cursor = pstart + (P + 1);
+        const int PB = P * PSPLIT;               // sub-buckets
+        uint32_t* pcnt = pstart;                 // sub-bucket starts (the binning's plane starts are free)
+        uint32_t* cursor = at<uint32_t>(ws, L.acur);
         float2* pts = at<float2>(ws, L.tcl);
-        unsigned long long* pkey = at<unsigned long long>(ws, L.upr);
+        unsigned long long* pmeta = at<unsigned long long>(ws, L.upr);
+        AT.tkey = at<unsigned long long>(ws, L.bestA);      // the merger's best-pair keys are dead by now
         const bool use_pts = (int64_t)ntcap * g->n_rows < (int64_t)UINT32_MAX;
         const uint32_t cap = use_pts ? (uint32_t)std::min<int64_t>(2 * (int64_t)std::max(n, 1), UINT32_MAX) : 0u;
         if (use_pts) {
-            CK(cudaMemsetAsync(pcnt, 0, 4 * ((size_t)P + 1), st));
+            CK(cudaMemsetAsync(pcnt, 0, 4 * ((size_t)PB + 1), st));
             k_attach_span<<<gt2, B, 0, st>>>(AT, pcnt);
-            const int nseq = NF * g->n_sectors;
+            const int nseq = NF * g->n_sectors * PSPLIT;
             k_attach_rowsum<<<std::max(1, (nseq + 127) / 128), 128, 0, st>>>(pcnt, nseq, g->n_rows, f);
-            scan_u32(pcnt, P, aux, st);
-            CK(cudaMemcpyAsync(cursor, pcnt, 4 * ((size_t)P + 1), cudaMemcpyDeviceToDevice, st));
+            scan_u32(pcnt, PB, aux, st);
+            CK(cudaMemcpyAsync(cursor, pcnt, 4 * ((size_t)PB + 1), cudaMemcpyDeviceToDevice, st));
             g_launches += 2;
         }
-        k_attach_trace<<<grid_for(ntcap, 128), 128, 0, st>>>(AT, cursor, pts, pkey, cap);
+        k_attach_trace<<<grid_for(ntcap, 128), 128, 0, st>>>(AT, cursor, pts, pmeta, cap);
         if (use_pts) {
-            k_attach_visit<<<grid_for(cap, B), B, 0, st>>>(AT, pcnt, cursor, P, pts, pkey, cap);
-            g_launches++;
+            k_attach_holes<<<grid_for(PB, B), B, 0, st>>>(pcnt, cursor, PB, pmeta, cap, f);
+            k_attach_visit<<<grid_for(cap, B), B, 0, st>>>(AT, pcnt, PB, pts, pmeta, cap);
+            g_launches += 2;
         }
         k_attach_flags<<<gN, B, 0, st>>>(AT);
         g_launches += 2;
