@@ -56,6 +56,10 @@ FP64_NOMINAL_TFLOPS = 1.25
 # tube scan (16), the flag pass reading assignment, key and mark (4 + 8 + 1)
 # and writing flags and adjacent track (1 + 4).
 ATTACH_B_PER_CLUSTER = 43
+# DRAM bytes per input cluster of the three main attachment kernels (trace,
+# visit, flags) in an ncu capture of the 35-collision frame (26.5 + 78.8 + 15.9),
+# scaled to a launch by the cluster count
+NCU_ATTACH_TRAFFIC_B_PER_CLUSTER = 121.2
 NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 194.8}
 
 
@@ -354,6 +358,7 @@ def run_ours(args, ws, rank, local, pg):
                                "peak": hbm if hbm else 6400.0,
                                "frac": round(ach / (hbm if hbm else 6400.0), 4),
                                "bytes_per_cluster": ATTACH_B_PER_CLUSTER,
+                               "traffic": NCU_ATTACH_TRAFFIC_B_PER_CLUSTER * n,
                                "peak_note": "measured" if hbm else "fallback"}}
         del trk_a, ra, fl
         torch.cuda.empty_cache()
