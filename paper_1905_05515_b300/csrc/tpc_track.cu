@@ -1372,6 +1372,8 @@ struct MergeBest {
 // orders as its bits, so this is the smallest chi2, ties to the smaller id --
 // and k_merge_resolve writes the winners.  If the list overflows its capacity,
 // k_merge_next / k_merge_prev (one warp per end, chi2 inline) do it instead.
+constexpr int MP_U = 4;
+
 __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
 {
     const int nseg = M.f->n_seg, mnz = M.f->mnz;
@@ -1391,21 +1393,35 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
             int lo, hi;
             merge_window(ra.a.x, M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
-            for (int q0 = qb; q0 < qe; q0 += 32) {
-                const int q = q0 + lane;
-                bool pass = false;
-                if (q < qe) {
-                    const MergeRec rb = M.recb[q];
-                    pass = fabsf(rb.a.x - ra.a.x) <= M.dz && !merge_screened(ra, rb, 2.0f * M.chi2cut);
+            // MP_U rounds of 32 records per iteration: their loads are in
+            // flight together before any is tested (the pair list is order-free)
+            for (int q0 = qb; q0 < qe; q0 += 32 * MP_U) {
+                MergeRec rr[MP_U];
+#pragma unroll
+                for (int u = 0; u < MP_U; u++)
+                    if (q0 + 32 * u + lane < qe) rr[u] = M.recb[q0 + 32 * u + lane];
+                unsigned m[MP_U];
+                int tot = 0;
+#pragma unroll
+                for (int u = 0; u < MP_U; u++) {
+                    const int q = q0 + 32 * u + lane;
+                    const bool pass = q < qe && fabsf(rr[u].a.x - ra.a.x) <= M.dz &&
+                                      !merge_screened(ra, rr[u], 2.0f * M.chi2cut);
+                    m[u] = __ballot_sync(0xffffffffu, pass);
+                    tot += __popc(m[u]);
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, pass);
-                if (!m) continue;
+                if (!tot) continue;
                 int base = 0;
-                if (lane == 0) base = atomicAdd(&M.fw->n_mpairs, __popc(m));
+                if (lane == 0) base = atomicAdd(&M.fw->n_mpairs, tot);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (pass) {
-                    const int k = base + __popc(m & ((1u << lane) - 1u));
-                    if (k < M.pcap) M.pairs[k] = make_int2(a, q | (dir < 0 ? (int)0x80000000 : 0));
+                const int flag = dir < 0 ? (int)0x80000000 : 0;
+#pragma unroll
+                for (int u = 0; u < MP_U; u++) {
+                    if ((m[u] >> lane) & 1u) {
+                        const int k = base + __popc(m[u] & ((1u << lane) - 1u));
+                        if (k < M.pcap) M.pairs[k] = make_int2(a, (q0 + 32 * u + lane) | flag);
+                    }
+                    base += __popc(m[u]);
                 }
             }
         }
