@@ -1170,22 +1170,31 @@ template <> __device__ __forceinline__ unsigned sel_weight<unsigned>(int nh, int
     return ((unsigned)nh << 24) | (0xFFFFFFu - (unsigned)id);
 }
 
+// SEL_G lanes per tracklet: the hits of one tracklet are adjacent in its hit
+// slot, so the group's slot loads are coalesced and its weight updates (or
+// reads) go out together.
+constexpr int SEL_G = 8;
+
 template <typename W>
 __global__ void k_sel_weight(const Frame* __restrict__ f, int cap, int nr, int min_hits, const int32_t* __restrict__ t_id,
                              const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
                              const int32_t* __restrict__ t_hits, W* __restrict__ hitw)
 {
     const int nt = min(f->n_starts, cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int j = threadIdx.x % SEL_G;
+    const int ngroups = (gridDim.x * blockDim.x) / SEL_G;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) / SEL_G; t < nt; t += ngroups) {
         const int nh = t_nhits[t];
         if (nh < min_hits) continue;
         const W w = sel_weight<W>(nh, t_id[t]);
         const int32_t* slot = t_hits + (int64_t)t * nr;
         const int nup = t_nup[t];
-        for (int k = 0; k < nh; k++) atomicMax(&hitw[trk_hit(slot, nr, nh, nup, k)], w);
+        for (int k = j; k < nh; k += SEL_G) atomicMax(&hitw[trk_hit(slot, nr, nh, nup, k)], w);
     }
 }
 
+// The loops are warp-uniform (every lane runs the warp's largest trip count)
+// so that the group's OR and sum shuffles have all lanes present.
 template <typename W>
 __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned, const int32_t* __restrict__ t_id,
                           const int32_t* __restrict__ t_nhits, const int32_t* __restrict__ t_nup,
@@ -1194,32 +1203,54 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
                           uint32_t* __restrict__ ownmask)
 {
     const int nt = min(f->n_starts, cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        const int nh = t_nhits[t];
-        uint8_t k = 0;
+    const int lane = threadIdx.x & 31;
+    const int j = lane % SEL_G;
+    constexpr int GPW = 32 / SEL_G;     // groups per warp
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t0 = warp * GPW; t0 < nt; t0 += nwarps * GPW) {
+        const int t = t0 + lane / SEL_G;
+        const bool valid = t < nt;
+        const int nh = valid ? t_nhits[t] : 0;
+        const bool act = valid && nh >= min_hits;
+        W w = 0;
+        const int32_t* slot = t_hits;
+        int nup = 0;
+        if (act) {
+            w = sel_weight<W>(nh, t_id[t]);
+            slot = t_hits + (int64_t)t * nr;
+            nup = t_nup[t];
+        }
+        const int rounds = act ? (nh + 31) >> 5 : 0;
+        const int rmax = __reduce_max_sync(0xffffffffu, rounds);
         int own = 0;
-        if (nh >= min_hits) {
-            const W w = sel_weight<W>(nh, t_id[t]);
-            const int32_t* slot = t_hits + (int64_t)t * nr;
-            const int nup = t_nup[t];
-            // owned hits in ascending row order, as bits of words [q / 32][t]
-            uint32_t word = 0u;
-            for (int q = 0; q < nh; q++) {
-                const bool o = hitw[trk_hit(slot, nr, nh, nup, q)] == w;
-                own += o;
-                word |= (uint32_t)o << (q & 31);
-                if ((q & 31) == 31 || q == nh - 1) {
-                    ownmask[(int64_t)(q >> 5) * cap + t] = word;
-                    word = 0u;
+        for (int rd = 0; rd < rmax; rd++) {
+            // owned hits in ascending row order, as bits of words [rd][t]
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int i = 0; i < 32 / SEL_G; i++) {
+                const int k = (rd << 5) + j + SEL_G * i;
+                if (act && k < nh) {
+                    const bool o = hitw[trk_hit(slot, nr, nh, nup, k)] == w;
+                    own += o;
+                    bits |= (uint32_t)o << (k & 31);
                 }
             }
-            if (own >= min_owned && 2 * own >= nh) {
+#pragma unroll
+            for (int d = SEL_G / 2; d > 0; d >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, d);
+            if (j == 0 && rd < rounds) ownmask[(int64_t)rd * cap + t] = bits;
+        }
+#pragma unroll
+        for (int d = SEL_G / 2; d > 0; d >>= 1) own += __shfl_xor_sync(0xffffffffu, own, d);
+        if (j == 0 && valid) {
+            uint8_t k = 0;
+            if (act && own >= min_owned && 2 * own >= nh) {
                 k = 1;
                 seg[atomicAdd(&f->n_seg, 1)] = t;
             }
+            kept[t] = k;
+            t_own[t] = act ? own : 0;
         }
-        kept[t] = k;
-        t_own[t] = own;
     }
 }
 
@@ -2326,17 +2357,18 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     uint8_t* kept = at<uint8_t>(ws, L.t_kept);
     int32_t* seg = at<int32_t>(ws, L.seg);
     const int gt2w = grid_for((int64_t)ntcap * 32, B);      // one warp per tracklet
+    const int gsel = grid_for((int64_t)ntcap * SEL_G, B);     // SEL_G lanes per tracklet
     if (w32) {
         unsigned* hw = reinterpret_cast<unsigned*>(hitw);
-        k_sel_weight<unsigned><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup,
+        k_sel_weight<unsigned><<<gsel, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits, TA.t_nup,
                                                   TA.t_hits, hw);
-        k_sel_own<unsigned><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits,
+        k_sel_own<unsigned><<<gsel, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id, TA.t_nhits,
                                                TA.t_nup, TA.t_hits, hw, kept, seg, at<int32_t>(ws, L.t_own),
                                                at<uint32_t>(ws, L.ownmask));
     } else {
-        k_sel_weight<unsigned long long><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits,
+        k_sel_weight<unsigned long long><<<gsel, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, TA.t_id, TA.t_nhits,
                                                             TA.t_nup, TA.t_hits, hitw);
-        k_sel_own<unsigned long long><<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id,
+        k_sel_own<unsigned long long><<<gsel, B, 0, st>>>(f, ntcap, g->n_rows, p->min_hits, p->min_owned, TA.t_id,
                                                          TA.t_nhits, TA.t_nup, TA.t_hits, hitw, kept, seg,
                                                          at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
     }
