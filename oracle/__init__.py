@@ -81,6 +81,18 @@ def lib():
         L.orc_bspline_all.argtypes = [C.c_double, _PD, _PD]
         L.orc_bspline_all.restype = None
         L.orc_step_pos32.argtypes = [_PF, C.c_float, C.c_float]
+        _PU32 = C.POINTER(C.c_uint32)
+        L.orc_rans_normalise.argtypes = [_PU32, _PU32]
+        L.orc_rans_encode.argtypes = [_PU8, C.c_int32, _PU32, _PU8, _P32]
+        L.orc_rans_decode.argtypes = [_PU8, C.c_int32, _PU32, C.c_int32, _PU8]
+        L.orc_compress_fields.argtypes = [C.c_int32, C.c_int32, C.c_int32, _PU8, _PU8, _PF, _PF, C.c_int32,
+                                          C.c_int32, C.c_int32, _P32, _P32, _P32, C.POINTER(_PU32),
+                                          C.POINTER(C.c_int64)]
+        L.orc_decompress_fields.argtypes = [C.c_int32, C.c_int32, C.POINTER(_PU32), C.POINTER(C.c_int64),
+                                            C.c_int32, C.c_int32, _PU8, _PU8, _P32, _P32]
+        L.orc_code_stream.argtypes = [_PU32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), _P32]
+        L.orc_free_ptr.argtypes = [C.c_void_p]
+        L.orc_free_ptr.restype = None
         L.orc_attach.argtypes = [C.POINTER(OrcGeom), C.c_float, C.c_int32, _PU8, _PU8, _PF, _PF, C.c_int32, _P32,
                                  _P32, _P32, _P32, _P32, _PF, _P32, C.c_float, C.c_float, _P32, _PU8]
         _lib = L
@@ -243,6 +255,97 @@ def step_pos32(p, x2, kb):
     s = np.ascontiguousarray(p, np.float32).copy()
     ok = lib().orc_step_pos32(_ptr(s, _PF), x2, kb)
     return bool(ok), s
+
+
+# ---- cluster compression -----------------------------------------------------------
+COMPRESS_STREAMS = ("n_track", "head_sector", "head_row", "head_y", "head_t", "d_sector", "d_row", "res_y",
+                    "res_t", "u_count", "u_dt", "u_y")
+_PU32 = C.POINTER(C.c_uint32)
+
+
+def rans_normalise(hist):
+    h = np.ascontiguousarray(hist, np.uint32)
+    f = np.zeros(256, np.uint32)
+    rc = lib().orc_rans_normalise(_ptr(h, _PU32), _ptr(f, _PU32))
+    if rc:
+        raise ValueError(f"empty histogram ({rc})")
+    return f
+
+
+def rans_encode(sym, freq):
+    sym = np.ascontiguousarray(sym, np.uint8)
+    freq = np.ascontiguousarray(freq, np.uint32)
+    out = np.zeros(4 + 2 * sym.size, np.uint8)
+    nb = C.c_int32(0)
+    rc = lib().orc_rans_encode(_ptr(sym, _PU8), sym.size, _ptr(freq, _PU32), _ptr(out, _PU8), C.byref(nb))
+    if rc:
+        raise ValueError(f"rANS encode failed ({rc})")
+    return out[:nb.value].copy()
+
+
+def rans_decode(data, freq, n):
+    data = np.ascontiguousarray(data, np.uint8)
+    freq = np.ascontiguousarray(freq, np.uint32)
+    sym = np.zeros(max(n, 1), np.uint8)
+    rc = lib().orc_rans_decode(_ptr(data, _PU8), data.size, _ptr(freq, _PU32), n, _ptr(sym, _PU8))
+    if rc:
+        raise ValueError(f"rANS decode failed ({rc})")
+    return sym[:n]
+
+
+def compress_fields(sector, row, y, zt, r: OracleResult, n_sectors=36, n_rows=152, ey=5, et=6) -> dict:
+    """The integer streams of the compressed format (before entropy coding)
+    of a frame and the oracle's tracking result for it."""
+    L = lib()
+    sector = np.ascontiguousarray(sector, np.uint8)
+    row = np.ascontiguousarray(row, np.uint8)
+    y = np.ascontiguousarray(y, np.float32)
+    zt = np.ascontiguousarray(zt, np.float32)
+    off = np.ascontiguousarray(r.tr_off, np.int32)
+    clus = np.ascontiguousarray(r.tr_clus, np.int32)
+    assign = np.ascontiguousarray(r.assign, np.int32)
+    vals = (_PU32 * 12)()
+    counts = (C.c_int64 * 12)()
+    rc = L.orc_compress_fields(n_sectors, n_rows, y.size, _ptr(sector, _PU8), _ptr(row, _PU8), _ptr(y, _PF),
+                               _ptr(zt, _PF), ey, et, r.n_tracks, _ptr(off, _P32), _ptr(clus, _P32),
+                               _ptr(assign, _P32), vals, counts)
+    if rc:
+        raise ValueError(f"compress_fields failed ({rc})")
+    out = {}
+    for k, name in enumerate(COMPRESS_STREAMS):
+        m = int(counts[k])
+        out[name] = np.ctypeslib.as_array(vals[k], shape=(max(m, 1),))[:m].copy()
+        L.orc_free_ptr(C.cast(vals[k], C.c_void_p))
+    return out
+
+
+def decompress_fields(fields: dict, n_tracks, n, n_sectors=36, n_rows=152):
+    """Quantised clusters (sector, row, qy, qt) back from the streams:
+    attached clusters in track order, then the others plane by plane."""
+    arrs = [np.ascontiguousarray(fields[k], np.uint32) for k in COMPRESS_STREAMS]
+    vals = (_PU32 * 12)(*[_ptr(a, _PU32) for a in arrs])
+    counts = (C.c_int64 * 12)(*[a.size for a in arrs])
+    sector = np.zeros(max(n, 1), np.uint8)
+    row = np.zeros(max(n, 1), np.uint8)
+    qy = np.zeros(max(n, 1), np.int32)
+    qt = np.zeros(max(n, 1), np.int32)
+    rc = lib().orc_decompress_fields(n_sectors, n_rows, vals, counts, n_tracks, n, _ptr(sector, _PU8),
+                                     _ptr(row, _PU8), _ptr(qy, _P32), _ptr(qt, _P32))
+    if rc:
+        raise ValueError(f"decompress_fields failed ({rc})")
+    return sector[:n], row[:n], qy[:n], qt[:n]
+
+
+def code_stream(v, chunk=4096, roundtrip=True):
+    """Coded bytes of one integer stream (table, chunk sizes, rANS chunks,
+    escapes) and whether every chunk decodes back exactly."""
+    v = np.ascontiguousarray(v, np.uint32)
+    nb = C.c_int64(0)
+    ok = C.c_int32(0)
+    rc = lib().orc_code_stream(_ptr(v, _PU32), v.size, chunk, C.byref(nb), C.byref(ok) if roundtrip else None)
+    if rc:
+        raise ValueError(f"code_stream failed ({rc})")
+    return int(nb.value), bool(ok.value) if roundtrip else None
 
 
 def track_event(ev, params: dict | None = None) -> OracleResult:

@@ -108,6 +108,23 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
                const int32_t *trk_hits, const float *trk_bot, const int32_t *assign, float radius,
                float pt_min, int32_t *adjacent, uint8_t *flags);
 
+/* Cluster compression (tpc_oracle_compress.c): rANS coder of byte symbols,
+ * the integer fields of the format (12 streams), their inverse, and the
+ * coded size of one stream. */
+int orc_rans_normalise(const uint32_t *hist, uint32_t *freq);
+int orc_rans_encode(const uint8_t *sym, int32_t n, const uint32_t *freq, uint8_t *out, int32_t *nbytes);
+int orc_rans_decode(const uint8_t *in, int32_t nbytes, const uint32_t *freq, int32_t n, uint8_t *sym);
+int orc_compress_fields(int32_t n_sectors, int32_t n_rows, int32_t n, const uint8_t *sector, const uint8_t *row,
+                        const float *y, const float *zt, int32_t ey, int32_t et, int32_t n_tracks,
+                        const int32_t *clus_offset, const int32_t *clus_index, const int32_t *assign,
+                        uint32_t **vals, int64_t *counts);
+int orc_decompress_fields(int32_t n_sectors, int32_t n_rows, const uint32_t *const *vals, const int64_t *counts,
+                          int32_t n_tracks, int32_t n, uint8_t *sector, uint8_t *row, int32_t *qy, int32_t *qt);
+int64_t orc_symbolise(const uint32_t *v, int64_t n, uint8_t *sym, uint8_t *raw, int64_t *nraw);
+int orc_desymbolise(const uint8_t *sym, int64_t n, const uint8_t *raw, int64_t nraw, uint32_t *v);
+int orc_code_stream(const uint32_t *v, int64_t n, int32_t chunk, int64_t *bytes, int32_t *roundtrip_ok);
+void orc_free_ptr(void *p);
+
 /* single Kalman steps, exposed for the pins */
 int orc_prop32(float *st21, float x2, float kb);
 int orc_rot32(float *st21, float cs, float sn, float kb);
