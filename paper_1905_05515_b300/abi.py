@@ -82,7 +82,7 @@ CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
             "tpc_track_batched", "tpc_prepare", "tpc_prepare_staging_size", "tpc_prepare_async", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
             "tpc_error_string", "tpc_calib_workspace_size", "tpc_calib_forward", "tpc_calib_backward",
-            "tpc_calib_status")
+            "tpc_calib_status", "tpc_rans_workspace_size", "tpc_rans_max_bytes", "tpc_rans_encode")
 
 _lib = None
 
@@ -100,6 +100,10 @@ def lib(build_if_missing: bool = True):
             raise OSError(f"CUDA tracker library missing: {path}")
         L = C.CDLL(path)
         L.tpc_params_default.argtypes = [C.POINTER(TpcParams)]
+        L.tpc_rans_workspace_size.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
+        L.tpc_rans_max_bytes.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]
+        L.tpc_rans_encode.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
         L.tpc_workspace_size.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int64,
                                          C.POINTER(C.c_size_t)]
         L.tpc_track.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,

@@ -22,6 +22,7 @@ UNITS = {
     "tpc_track.cu": ["-fmad=false"],
     "tpc_refit.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
     "tpc_calib.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
+    "tpc_compress.cu": [],
 }
 
 
@@ -34,7 +35,7 @@ def _nvcc():
 
 def sources():
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    out.extend(os.path.join(INCLUDE, h) for h in ("tpc_track.h", "tpc_calib.h"))
+    out.extend(os.path.join(INCLUDE, h) for h in ("tpc_track.h", "tpc_calib.h", "tpc_compress.h"))
     out.append(os.path.abspath(__file__))
     return out
 

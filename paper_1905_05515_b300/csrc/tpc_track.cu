@@ -1776,34 +1776,6 @@ struct AttachArgs {
     int32_t* adjacent;
 };
 
-// One helix step of the position (x, y, z, sin phi; tan lambda and q/pT
-// constant) to the plane x2: sin phi linear in x, dy = dx (s1 + s2) / (c1 +
-// c2), arc = signed chord * asin(u)/u (series to u^6), dz = tan(lambda) arc.
-// false (state unchanged) when |sin phi| reaches SNP_MAX or |u| > U_MAX.
-__device__ __forceinline__ bool step_pos32(float* p, float x2, float kb)
-{
-    const float dx = x2 - p[0];
-    if (dx == 0.0f) return true;
-    const float k = kb * p[5];
-    const float s1 = p[3];
-    const float s2 = __fmaf_rn(k, dx, s1);
-    if (!(fabsf(s1) < SNP_MAX) || !(fabsf(s2) < SNP_MAX)) return false;
-    const float c1 = __fsqrt_rn((1.0f - s1) * (1.0f + s1));
-    const float c2 = __fsqrt_rn((1.0f - s2) * (1.0f + s2));
-    const float dy = dx * __fdiv_rn(s1 + s2, c1 + c2);
-    float chord = __fsqrt_rn(__fmaf_rn(dx, dx, dy * dy));
-    if (dx < 0.0f) chord = -chord;
-    const float u = (0.5f * k) * chord;
-    if (!(fabsf(u) <= U_MAX)) return false;
-    const float u2 = u * u;
-    const float arc = chord * __fmaf_rn(u2, __fmaf_rn(u2, __fmaf_rn(u2, AS3, AS2), AS1), 1.0f);
-    p[0] = x2;
-    p[1] = p[1] + dy;
-    p[2] = p[2] + arc * p[4];
-    p[3] = s2;
-    return true;
-}
-
 __device__ __forceinline__ float track_abs_qpt(const AttachArgs& A, int tr)
 {
     return fabsf(A.t_bot[(int64_t)A.seg[A.thead[tr]] * NST + 5]);
@@ -1916,9 +1888,12 @@ __global__ void k_attach_rowsum(uint32_t* __restrict__ dcnt, int nseq, int nr, c
 // position) or scanned here when the buffers are full (cap == 0: always).
 // The chain runs in blocks of ATT_U rows: the loop-carried quantities (x,
 // sin phi) first, then the ATT_U steps' square roots and divisions side by
-// side, then the checks and the y, z sums in row order -- every quantity is
-// the operation sequence of step_pos32, so the points are those of the
-// row-by-row chain.
+// side, then the checks and the y, z sums in row order.  Each step is the
+// helix step of the position -- sin phi linear in x, dy = dx (s1 + s2) / (c1 +
+// c2), arc = signed chord * asin(u)/u by its series to u^6 with u = k chord
+// / 2, dz = tan(lambda) arc, refused when |sin phi| reaches SNP_MAX or |u| >
+// U_MAX -- with the operations of a row-by-row chain in the same order, so
+// the points are that chain's.
 constexpr int ATT_U = 4;
 
 // bucket record of a point: its plane and its track
