@@ -106,3 +106,27 @@ def test_grid_parameter_limits_and_packed_workspace():
     plain = tpc.tpc_workspace_size(tpc.tpc_params_default(z_cell=3.5), g, 1000)
     packed = tpc.tpc_workspace_size(tpc.tpc_params_default(packed_links=1, z_cell=3.5), g, 1000)
     assert packed >= plain + 4 * 1000          # the 4-byte packed words
+
+
+def test_rans_sizes_host_only():
+    """The entropy coder's size queries (no device needed): the worst case is
+    4 bytes per chunk plus 2 per symbol, the workspace grows with the stream,
+    and out-of-range sizes are rejected."""
+    import ctypes as C
+
+    import paper_1905_05515_b300 as tpc
+    L = tpc.lib()
+    mb = C.c_int64(0)
+    assert L.tpc_rans_max_bytes(10000, 4096, C.byref(mb)) == 0 and mb.value == 4 * 3 + 2 * 10000
+    assert L.tpc_rans_max_bytes(0, 4096, C.byref(mb)) == 0 and mb.value == 0
+    ws_small, ws_big = C.c_size_t(0), C.c_size_t(0)
+    assert L.tpc_rans_workspace_size(1000, 4096, C.byref(ws_small)) == 0
+    assert L.tpc_rans_workspace_size(10_000_000, 4096, C.byref(ws_big)) == 0
+    assert 0 < ws_small.value < ws_big.value
+    for n, chunk in ((-1, 4096), (1 << 31, 4096), (1000, 0), (1000, 65537)):
+        assert L.tpc_rans_workspace_size(n, chunk, C.byref(ws_small)) == tpc.TPC_ERR_ARG
+        assert L.tpc_rans_max_bytes(n, chunk, C.byref(mb)) == tpc.TPC_ERR_ARG
+    # the binding refuses host tensors before any device work
+    import torch
+    with pytest.raises(ValueError):
+        tpc.rans_encode(torch.zeros(10, dtype=torch.uint8))
