@@ -91,6 +91,10 @@ def lib():
         L.orc_decompress_fields.argtypes = [C.c_int32, C.c_int32, C.POINTER(_PU32), C.POINTER(C.c_int64),
                                             C.c_int32, C.c_int32, _PU8, _PU8, _P32, _P32]
         L.orc_code_stream.argtypes = [_PU32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), _P32]
+        L.orc_pack_stream.argtypes = [_PU32, C.c_int64, C.c_int32, _PU8]
+        L.orc_pack_stream.restype = C.c_int64
+        L.orc_unpack_stream.argtypes = [_PU8, C.c_int64, _PU32, C.c_int64, C.POINTER(C.c_int64)]
+        L.orc_unpack_stream.restype = C.c_int64
         L.orc_free_ptr.argtypes = [C.c_void_p]
         L.orc_free_ptr.restype = None
         L.orc_attach.argtypes = [C.POINTER(OrcGeom), C.c_float, C.c_int32, _PU8, _PU8, _PF, _PF, C.c_int32, _P32,
@@ -346,6 +350,32 @@ def code_stream(v, chunk=4096, roundtrip=True):
     if rc:
         raise ValueError(f"code_stream failed ({rc})")
     return int(nb.value), bool(ok.value) if roundtrip else None
+
+
+def pack_stream(v, chunk=4096) -> np.ndarray:
+    """One integer stream as a self-contained coded container (format stated
+    at orc_pack_stream in tpc_oracle_compress.c)."""
+    v = np.ascontiguousarray(v, np.uint32)
+    L = lib()
+    size = L.orc_pack_stream(_ptr(v, _PU32), v.size, chunk, None)
+    if size < 0:
+        raise ValueError("pack_stream failed")
+    out = np.zeros(size, np.uint8)
+    if L.orc_pack_stream(_ptr(v, _PU32), v.size, chunk, _ptr(out, _PU8)) != size:
+        raise ValueError("pack_stream failed")
+    return out
+
+
+def unpack_stream(data, vcap=None) -> np.ndarray:
+    """The values of a container written by pack_stream."""
+    data = np.ascontiguousarray(data, np.uint8)
+    vcap = int(vcap if vcap is not None else max(1, data.size))
+    v = np.zeros(max(vcap, 1), np.uint32)
+    n = C.c_int64(0)
+    used = lib().orc_unpack_stream(_ptr(data, _PU8), data.size, _ptr(v, _PU32), vcap, C.byref(n))
+    if used < 0 or used != data.size:
+        raise ValueError("malformed container")
+    return v[:n.value]
 
 
 def track_event(ev, params: dict | None = None) -> OracleResult:

@@ -123,6 +123,8 @@ int orc_decompress_fields(int32_t n_sectors, int32_t n_rows, const uint32_t *con
 int64_t orc_symbolise(const uint32_t *v, int64_t n, uint8_t *sym, uint8_t *raw, int64_t *nraw);
 int orc_desymbolise(const uint8_t *sym, int64_t n, const uint8_t *raw, int64_t nraw, uint32_t *v);
 int orc_code_stream(const uint32_t *v, int64_t n, int32_t chunk, int64_t *bytes, int32_t *roundtrip_ok);
+int64_t orc_pack_stream(const uint32_t *v, int64_t n, int32_t chunk, uint8_t *out);
+int64_t orc_unpack_stream(const uint8_t *in, int64_t nbytes, uint32_t *v, int64_t vcap, int64_t *n_out);
 void orc_free_ptr(void *p);
 
 /* single Kalman steps, exposed for the pins */

@@ -412,3 +412,90 @@ int orc_code_stream(const uint32_t *v, int64_t n, int32_t chunk, int64_t *bytes,
 }
 
 void orc_free_ptr(void *p) { free(p); }
+
+/* --------------------------------------------------- stream container */
+/* One coded stream as bytes (all integers little-endian):
+ *   u32 n (values), u32 chunk, u32 nraw (escape bytes),
+ *   u16 freq[256] (the table; all 0 when n = 0),
+ *   u32 chunk_bytes[ceil(n / chunk)], the chunks back to back, the escape
+ *   bytes.
+ * orc_pack_stream writes it to out (NULL: size only) and returns its size,
+ * or -1 on error. */
+static void put32(uint8_t *o, int64_t *p, uint32_t v)
+{
+    if (o) for (int b = 0; b < 4; b++) o[*p + b] = (uint8_t)(v >> (8 * b));
+    *p += 4;
+}
+
+static uint32_t get32(const uint8_t *in, int64_t p)
+{
+    return (uint32_t)in[p] | ((uint32_t)in[p + 1] << 8) | ((uint32_t)in[p + 2] << 16) | ((uint32_t)in[p + 3] << 24);
+}
+
+int64_t orc_pack_stream(const uint32_t *v, int64_t n, int32_t chunk, uint8_t *out)
+{
+    if (n < 0 || n > 0xFFFFFFFFLL || chunk < 1) return -1;
+    uint8_t *sym = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    uint8_t *raw = (uint8_t *)malloc(4 * (size_t)(n > 0 ? n : 1));
+    int64_t nraw = 0;
+    orc_symbolise(v, n, sym, raw, &nraw);
+    uint32_t hist[256] = {0}, freq[256] = {0};
+    for (int64_t i = 0; i < n; i++) hist[sym[i]]++;
+    if (n > 0 && orc_rans_normalise(hist, freq)) { free(sym); free(raw); return -1; }
+    const int64_t nch = n > 0 ? (n + chunk - 1) / chunk : 0;
+    int64_t p = 0;
+    put32(out, &p, (uint32_t)n);
+    put32(out, &p, (uint32_t)chunk);
+    put32(out, &p, (uint32_t)nraw);
+    for (int s = 0; s < 256; s++) {
+        if (out) { out[p] = (uint8_t)(freq[s] & 0xFF); out[p + 1] = (uint8_t)(freq[s] >> 8); }
+        p += 2;
+    }
+    int64_t sizes_at = p;
+    p += 4 * nch;
+    uint8_t *buf = (uint8_t *)malloc(4 + 2 * (size_t)chunk);
+    for (int64_t c = 0; c < nch; c++) {
+        const int32_t m = (int32_t)(n - c * chunk < chunk ? n - c * chunk : chunk);
+        int32_t nb = 0;
+        if (orc_rans_encode(sym + c * chunk, m, freq, buf, &nb)) { free(buf); free(sym); free(raw); return -1; }
+        int64_t q = sizes_at + 4 * c;
+        put32(out, &q, (uint32_t)nb);
+        if (out) memcpy(out + p, buf, (size_t)nb);
+        p += nb;
+    }
+    if (out) memcpy(out + p, raw, (size_t)nraw);
+    p += nraw;
+    free(buf); free(sym); free(raw);
+    return p;
+}
+
+/* Inverse of orc_pack_stream: the n values (n read from the container,
+ * returned through *n_out; v holds at least that many).  Returns the bytes
+ * consumed, or -1 when the container is malformed. */
+int64_t orc_unpack_stream(const uint8_t *in, int64_t nbytes, uint32_t *v, int64_t vcap, int64_t *n_out)
+{
+    if (nbytes < 12 + 512) return -1;
+    const int64_t n = get32(in, 0);
+    const int32_t chunk = (int32_t)get32(in, 4);
+    const int64_t nraw = get32(in, 8);
+    if (chunk < 1 || n > vcap) return -1;
+    uint32_t freq[256];
+    int64_t p = 12;
+    for (int s = 0; s < 256; s++, p += 2) freq[s] = (uint32_t)in[p] | ((uint32_t)in[p + 1] << 8);
+    const int64_t nch = n > 0 ? (n + chunk - 1) / chunk : 0;
+    if (p + 4 * nch > nbytes) return -1;
+    const int64_t sizes_at = p;
+    p += 4 * nch;
+    uint8_t *sym = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < nch; c++) {
+        const int32_t m = (int32_t)(n - c * chunk < chunk ? n - c * chunk : chunk);
+        const int64_t nb = get32(in, sizes_at + 4 * c);
+        if (p + nb > nbytes || orc_rans_decode(in + p, (int32_t)nb, freq, m, sym + c * chunk)) { free(sym); return -1; }
+        p += nb;
+    }
+    if (p + nraw > nbytes || orc_desymbolise(sym, n, in + p, nraw, v)) { free(sym); return -1; }
+    p += nraw;
+    free(sym);
+    *n_out = n;
+    return p;
+}

@@ -156,3 +156,22 @@ def test_residual_streams_cost_less_than_positions():
     total = sum(oracle.code_stream(v)[0] for v in f.values())
     factor = 10.0 * ev.n / total
     assert factor > 2.5, factor
+
+
+def test_stream_containers_round_trip():
+    """Every field stream of a frame, packed into its container and unpacked,
+    comes back exactly; the container is the coded size plus its 12-byte
+    header; a truncated container is refused."""
+    ev = tpcgen.time_frame(seed=3, n_collisions=2, with_truth=False)
+    r = oracle.track_event(ev)
+    f = oracle.compress_fields(ev.sector, ev.row, ev.y, ev.zt, r)
+    for name, v in f.items():
+        data = oracle.pack_stream(v, chunk=1024)
+        back = oracle.unpack_stream(data, vcap=max(v.size, 1))
+        assert np.array_equal(back, v), name
+        nb, _ = oracle.code_stream(v, chunk=1024, roundtrip=False)
+        assert data.size == nb + 12, name
+        with pytest.raises(ValueError):
+            oracle.unpack_stream(data[:-1], vcap=max(v.size, 1))
+    empty = oracle.pack_stream(np.zeros(0, np.uint32))
+    assert empty.size == 12 + 512 and oracle.unpack_stream(empty).size == 0
