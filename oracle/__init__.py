@@ -24,7 +24,7 @@ class OrcParams(C.Structure):
                 ("chi2_cut", C.c_float), ("max_miss", C.c_int32), ("min_hits", C.c_int32),
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float),
                 ("merge_dz", C.c_float), ("merge_chi2", C.c_float), ("refit_passes", C.c_int32),
-                ("refit_inflate", C.c_float), ("packed_links", C.c_int32)]
+                ("refit_inflate", C.c_float), ("packed_links", C.c_int32), ("back_jump", C.c_int32)]
 
 
 class OrcGeom(C.Structure):
@@ -367,9 +367,19 @@ def pack_stream(v, chunk=4096) -> np.ndarray:
 
 
 def unpack_stream(data, vcap=None) -> np.ndarray:
-    """The values of a container written by pack_stream."""
+    """The values of a container written by pack_stream.  Without vcap the
+    capacity is the value count of the container's header (its first four
+    bytes, little-endian); a very compressible stream holds more values than
+    bytes."""
     data = np.ascontiguousarray(data, np.uint8)
-    vcap = int(vcap if vcap is not None else max(1, data.size))
+    if vcap is None:
+        if data.size < 12 + 512:
+            raise ValueError("malformed container")
+        vcap, chunk = (int(v) for v in data[:8].view("<u4"))
+        # sanity bound: every chunk of `chunk` values carries at least its 4-byte size entry
+        if vcap > chunk * max(1, (data.size - 12 - 512) // 4):
+            raise ValueError("malformed container")
+    vcap = int(vcap)
     v = np.zeros(max(vcap, 1), np.uint32)
     n = C.c_int64(0)
     used = lib().orc_unpack_stream(_ptr(data, _PU8), data.size, _ptr(v, _PU32), vcap, C.byref(n))

@@ -18,12 +18,19 @@
  * helix crossings (forward and backward), Jacobians against finite
  * differences, the update against the information form, the B = 0 fit
  * against closed-form least squares, exact recovery of noise-free helices,
- * pulls and chi2/ndf, the NeighboursFinder against an exhaustive search with
- * exact binary32 emulation, hand-built link cases, efficiency / clone / fake
- * rates against generator truth.  The exact decisions of the tracklet
- * constructor, selector and merger have no worked example in the paper:
- * beyond those statistical bars and structural invariants their parity is
- * unpinned.
+ * the refit passes' fixed point against a batch least-squares helix fit and
+ * their contraction against 1/(1 + refit_inflate), pulls and chi2/ndf, the
+ * NeighboursFinder against an exhaustive search with exact binary32
+ * emulation, hand-built link cases, the merger's chi2 against noise-free
+ * split helices (zero), a closed form (d^T C^-1 d) and the chi2
+ * distribution with five degrees of freedom, hand-built straight-line
+ * tracklet cases with hand-derived tracklets and tracks (the selector's
+ * tie-break in both input orders, following across an empty row, the state
+ * against numpy's least-squares line), efficiency / clone / fake rates
+ * against generator truth.  The paper prints no worked example of the
+ * tracklet constructor, selector or merger: on real events their exact
+ * decisions are pinned only by those hand-built cases, the statistical bars
+ * and the structural invariants.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math (see build.py);
  * x86-64 evaluates float in binary32 (FLT_EVAL_METHOD 0), so every float
@@ -39,7 +46,6 @@
 /* ---------------------------------------------------------------- constants */
 #define SNP_MAX   0.999f
 #define U_MAX     0.1f
-#define BACK_JUMP 32      /* rows per back-propagation jump of the TrackletConstructor's phase C */
 /* arcsine series asin(u)/u = 1 + u^2/6 + 3u^4/40 + 5u^6/112 + ... and its derivative */
 #define AS1 0.16666666666666666667f
 #define AS2 0.075f
@@ -70,6 +76,7 @@ void orc_params_default(orc_params *p)
     p->refit_passes = 3;
     p->refit_inflate = 100.0f;
     p->packed_links = 0;
+    p->back_jump = 32;
 }
 
 /* ===================================================================== *
@@ -735,14 +742,14 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
                 }
             }
         }
-        /* phase C: back to the start row in jumps of at most BACK_JUMP rows
+        /* phase C: back to the start row in jumps of at most back_jump rows
          * (a refused jump -- |u| or |sin(phi)| out of range -- is retried
          * with half as many rows; a refused single-row step ends the
          * tracklet), then follow row by row below the start */
         memcpy(bot, top, sizeof(st));
         if (rc == r1) memcpy(bot, st, sizeof(st));
         int back_ok = 1;
-        for (int jump = BACK_JUMP; rc > r1;) {
+        for (int jump = P->back_jump > 0 ? P->back_jump : 1; rc > r1;) {
             int tgt = rc - jump > r1 ? rc - jump : r1;
             if (orc_prop32(st, X[tgt], kb)) {
                 rc = tgt;

@@ -40,6 +40,7 @@ typedef struct {
     int32_t refit_passes;                 /* Kalman refit passes, alternating direction */
     float refit_inflate;                  /* factor on the previous angular covariance at each pass start */
     int32_t packed_links;                 /* 1: the link pass sees y, z rounded to 1/256 cm (16-bit packed) */
+    int32_t back_jump;                    /* TrackletConstructor phase C: rows per return jump (1: row by row) */
 } orc_params;
 
 typedef struct {

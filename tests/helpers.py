@@ -74,3 +74,30 @@ def is_spd(c15) -> bool:
         return True
     except np.linalg.LinAlgError:
         return False
+
+
+def golden_line_cases(path):
+    """The hand-built straight-line cases of tests/golden/tracklets_b0.json as
+    (case, sector, row, y, z) cluster arrays (one sector, Bz = 0, z given)."""
+    import json
+
+    import tpcgen
+    X = tpcgen.row_x_f32().astype(np.float64)
+    with open(path) as f:
+        spec = json.load(f)
+    for case in spec["cases"]:
+        rows, ys, zs = [], [], []
+        for part in case["parts"]:
+            r = np.array([q for q in range(*part["rows"]) if q not in part.get("skip", [])])
+            dx = X[r] - X[0]
+            rows.append(r)
+            ys.append(part["y0"] + part["a"] * dx)
+            zs.append(part["z0"] + part["b"] * dx + part["dz"])
+        row = np.concatenate(rows).astype(np.uint8)
+        y = np.concatenate(ys)
+        z = np.concatenate(zs)
+        if case.get("noise_cm", 0.0) > 0:
+            rng = np.random.default_rng(case["noise_seed"])
+            y = y + rng.normal(0, case["noise_cm"], y.size)
+            z = z + rng.normal(0, case["noise_cm"], z.size)
+        yield case, np.zeros(row.size, np.uint8), row, y.astype(np.float32), z.astype(np.float32)

@@ -175,3 +175,15 @@ def test_stream_containers_round_trip():
             oracle.unpack_stream(data[:-1], vcap=max(v.size, 1))
     empty = oracle.pack_stream(np.zeros(0, np.uint32))
     assert empty.size == 12 + 512 and oracle.unpack_stream(empty).size == 0
+
+
+def test_container_capacity_from_its_header():
+    """Without a given capacity the unpacker sizes its output from the value
+    count in the container's header: a stream of 100,000 equal values codes
+    into far fewer bytes than values and still comes back."""
+    v = np.zeros(100_000, np.uint32)
+    data = oracle.pack_stream(v)
+    assert data.size < v.size // 50
+    assert np.array_equal(oracle.unpack_stream(data), v)
+    w = np.concatenate([v, np.arange(300, dtype=np.uint32)])      # with escapes
+    assert np.array_equal(oracle.unpack_stream(oracle.pack_stream(w, chunk=1024)), w)

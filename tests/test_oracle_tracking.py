@@ -122,3 +122,43 @@ def test_links_independent_of_input_order(orc, sector_ev):
     sets1 = {tuple(sorted(r.track_clusters(t))) for t in range(r.n_tracks)}
     sets2 = {tuple(sorted(perm[r2.track_clusters(t)])) for t in range(r2.n_tracks)}
     assert len(sets1 & sets2) >= 0.9 * len(sets1)
+
+
+def _same_hits(r_a, r_b):
+    assert np.array_equal(r_a.trk_start, r_b.trk_start)
+    return np.array([t for t in range(r_a.trk_start.size)
+                     if np.array_equal(r_a.tracklet_hits(t), r_b.tracklet_hits(t))], int)
+
+
+def test_phase_c_jumps_agree_with_row_by_row_return(orc, central_ev, frame_ev):
+    """Phase C returns to the start row in jumps of up to 32 rows; the
+    earlier reading stepped back row by row (back_jump = 1).  A helix step is
+    exact, so the two differ only in binary32 rounding: the hit lists agree
+    (>= 99.9 % of tracklets), the outer-end states are identical, and the
+    inner-end states agree within 0.02 sigma + 64 ulp where |z| <= 250 cm.
+    On a continuous frame z carries the drift offset of the collision
+    (|z| up to ~2500 cm, one binary32 ulp = 0.01 sigma of a fitted z): there
+    the states agree within 1 sigma, 99 % of them within 0.3 sigma and
+    half of them within 0.01 sigma."""
+    diag = 6 + np.array([0, 2, 5, 9, 14])
+    for ev, continuous in ((central_ev, False), (frame_ev, True)):
+        r32 = orc.track_event(ev)
+        r1 = orc.track_event(ev, params={"back_jump": 1})
+        same = _same_hits(r32, r1)
+        assert same.size >= 0.999 * r32.trk_start.size
+        np.testing.assert_array_equal(r32.trk_top[same], r1.trk_top[same])
+        b32 = r32.trk_bot[same].astype(np.float64)
+        b1 = r1.trk_bot[same].astype(np.float64)
+        sig = np.sqrt(b1[:, diag])
+        dp = np.abs(b32[:, 1:6] - b1[:, 1:6])
+        if continuous:
+            worst = (dp / sig).max(axis=1)
+            assert worst.max() < 1.0 and np.percentile(worst, 99) < 0.3 and np.median(worst) < 0.01
+        else:
+            ulp = np.spacing(np.abs(r1.trk_bot[same][:, 1:6])).astype(np.float64)
+            assert (dp / (0.02 * sig + 64 * ulp)).max() < 1.0
+        # covariances in correlation units
+        ii = [i for i in range(5) for j in range(i + 1)]
+        jj = [j for i in range(5) for j in range(i + 1)]
+        assert (np.abs(b32[:, 6:] - b1[:, 6:]) / (sig[:, ii] * sig[:, jj])).max() < 1e-3
+        assert np.mean(r32.assign != r1.assign) < 1e-3
