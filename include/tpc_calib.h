@@ -104,6 +104,22 @@ int tpc_calib_backward(const tpc_params *p, const tpc_geometry *g, float bz, flo
                        const tpc_calib_tracks *tr, const float *theta, const float *dchi2, const uint8_t *used,
                        const void *workspace, size_t ws_bytes, double *grad, void *stream);
 
+/* Calibration track selection (the rule of this library's reading of the
+ * online calibration, sections "Tracking" and "TPC Tracking": tracks from the
+ * primary vertex whose collision time is known): t_sel[r] = t_coll[r] when
+ * the track's refit succeeded (status[r] == 0) and |q/pT| <= qpt_max
+ * (binary32, on param[r][4]); NaN otherwise, which tpc_calib_forward reads as
+ * "not used".  Low-pT loopers (|q/pT| above TPC_CALIB_QPT_MAX, pT below
+ * 0.2 GeV/c) are left out because their later legs do not point to the
+ * vertex.  t_coll[r] may itself be NaN (no matched time).  Device arrays
+ * owned by the caller: t_coll [n_tracks], status [n_tracks], param
+ * [n_tracks][5] (as tpc_tracks), t_sel [n_tracks] (may alias t_coll).
+ * Enqueues one kernel on `stream`.  Errors: TPC_ERR_ARG (n_tracks < 0, a
+ * null array with n_tracks > 0, qpt_max not a number), TPC_ERR_CUDA. */
+#define TPC_CALIB_QPT_MAX 5.0f
+int tpc_calib_select(int32_t n_tracks, const float *t_coll, const int32_t *status, const float *param,
+                     float qpt_max, float *t_sel, void *stream);
+
 /* Synchronises `stream` and writes the workspace's error flag to *err
  * (0: none; 1: invalid track data seen).  Errors: TPC_ERR_ARG, TPC_ERR_CUDA. */
 int tpc_calib_status(const void *workspace, int32_t *err, void *stream);

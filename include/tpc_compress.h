@@ -53,7 +53,12 @@ int tpc_rans_max_bytes(int64_t n, int32_t chunk, int64_t *bytes);
  *   chunk_bytes [ceil(n / chunk)] device: coded bytes of each chunk.
  *   out         device, out_cap bytes (>= tpc_rans_max_bytes): the chunks.
  *   total       host: total coded bytes (the call synchronises `stream` to
- *               read it), may be NULL (then nothing waits).
+ *               read it and the device-side error flag), may be NULL: then
+ *               nothing waits and a device-side failure (a table that does
+ *               not normalise, a chunk that overflows its slot) is not
+ *               reported -- freq, chunk_bytes and out are then unspecified.
+ *               Callers that cannot wait should call once with total set
+ *               to validate a stream shape, or check the outputs themselves.
  * workspace: device, tpc_rans_workspace_size bytes, caller-owned; its
  * contents need not be initialised.  n = 0 codes nothing (all tables 0).
  * Errors: TPC_ERR_ARG (sizes, null pointers, out_cap too small),

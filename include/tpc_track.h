@@ -285,11 +285,16 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
  * NeighboursFinder and NeighboursCleaner for at most
  * TPC_LINKS_STATIC_MAX_CLUSTERS clusters, with all scratch memory in a fixed
  * device array inside the library.  The paper has no counterpart; this entry
- * point exists for callers that cannot allocate device memory: code running
- * inside a CUDA graph being captured or replayed, a host thread that must
- * not block on the allocator while other streams run, or an embedding that
- * forbids cudaMalloc after start-up.  They still pass their own device inputs
- * and outputs; nothing else is allocated, by them or by the library.
+ * point exists for callers that cannot allocate device memory: a host thread
+ * that must not block on the allocator (cudaMalloc can synchronise the
+ * device) while other streams run, or an embedding that forbids cudaMalloc
+ * after start-up (a plug-in inside a host framework that owns all device
+ * memory).  They still pass their own device inputs and outputs; nothing else
+ * is allocated, by them or by the library.
+ *   - The call copies the row table and plane offsets from host memory,
+ *     reads the data-error flag back and ends by synchronising `stream`: it
+ *     must not be made while `stream` (or the legacy stream) is being
+ *     captured into a CUDA graph.
  *   - Outputs (device, indexed by input cluster): link_up, link_dn (cleaned
  *     links, input index or -1), is_start (nullable, 0/1).  They equal the
  *     link_up / link_dn / is_start outputs of tpc_track on the same input.
@@ -302,7 +307,6 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
  *   - Every call uses the same array and leaves its contents behind (the
  *     call clears what must start at zero).  Calls that overlap on the GPU --
  *     on two streams, or from two host threads -- race on it: serialise them.
- *   - Enqueues on `stream`, then waits for it (to read the data-error flag).
  * Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_DATA, TPC_ERR_CUDA. */
 #define TPC_LINKS_STATIC_MAX_CLUSTERS 262144
 #define TPC_LINKS_STATIC_SCRATCH_BYTES 14416896

@@ -78,6 +78,8 @@ def lib():
         L.orc_calib_explain.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcGeom), C.c_double, C.c_double,
                                         C.c_double, _P32, _PF, _PF, _P32, _P32, _PU8, _PU8, _PF, _PF, _PF, _PD,
                                         C.c_int32, _PD, _PD, _PD, _PD, _PD]
+        L.orc_calib_select.argtypes = [C.c_int32, _PF, _P32, _PF, C.c_float, _PF]
+        L.orc_calib_select.restype = None
         L.orc_bspline_all.argtypes = [C.c_double, _PD, _PD]
         L.orc_bspline_all.restype = None
         L.orc_step_pos32.argtypes = [_PF, C.c_float, C.c_float]
@@ -542,6 +544,34 @@ def calib(tr: CalibTracks, theta, weight=None, grad=True, params: dict | None = 
     if rc:
         raise ValueError(f"orc_calib failed ({rc})")
     return chi2, used.astype(bool), g
+
+
+CALIB_QPT_MAX = 5.0     # loopers below pT = 0.2 GeV/c are left out of the calibration
+
+
+def calib_select(t_coll, status, param, qpt_max=CALIB_QPT_MAX):
+    """Collision times with NaN for the tracks the calibration leaves out
+    (failed refit, or |q/pT| > qpt_max on the binary32 parameters)."""
+    t = np.ascontiguousarray(t_coll, np.float32)
+    st = np.ascontiguousarray(status, np.int32)
+    p = np.ascontiguousarray(param, np.float32).reshape(-1, 5)
+    out = np.zeros(max(t.size, 1), np.float32)
+    lib().orc_calib_select(t.size, _ptr(t, _PF), _ptr(st, _P32), _ptr(p, _PF), qpt_max, _ptr(out, _PF))
+    return out[:t.size]
+
+
+def calib_tracks_of(ev, r: OracleResult, t_coll=None, qpt_max=CALIB_QPT_MAX) -> CalibTracks:
+    """The calibration problem of an oracle tracking result: the oracle's own
+    tracks (binary32 parameters, as the calibration pass consumes them), the
+    collision time of each (given, e.g. from generator truth) and the
+    oracle's selection."""
+    if t_coll is None:
+        raise ValueError("t_coll (collision time per track) is needed")
+    p32 = r.tr_p.astype(np.float32)
+    tc = calib_select(t_coll, r.tr_status, p32, qpt_max)
+    return CalibTracks(r.tr_sector, r.tr_x.astype(np.float32), p32, r.tr_off.astype(np.int32),
+                       r.tr_clus.astype(np.int32), tc, ev.sector, ev.row, ev.y, ev.zt, ev.row_x,
+                       n_sectors=ev.n_sectors, z_max=ev.z_max, bz=ev.bz, v_nom=ev.v_drift)
 
 
 def calib_measure(tr: CalibTracks, theta, idx, tc):

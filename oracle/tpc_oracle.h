@@ -161,6 +161,10 @@ int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, d
               const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y, const float *t,
               const float *tcoll, const double *theta, const double *weight, double *chi2_out, uint8_t *used,
               double *grad);
+/* calibration track selection: t_sel[r] = t_coll[r] if status[r] == 0 and
+ * |param[r][4]| <= qpt_max (binary32), else NaN */
+void orc_calib_select(int32_t n, const float *t_coll, const int32_t *status, const float *param, float qpt_max,
+                      float *t_sel);
 /* the calibrated measurement of each cluster (for the pins) */
 void orc_calib_measure(const orc_geom *G, const double *theta, int32_t n, const uint8_t *sector,
                        const uint8_t *row, const float *y, const float *t, const float *tc, double *my, double *mz);

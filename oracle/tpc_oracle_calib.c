@@ -424,3 +424,18 @@ int orc_calib_explain(const orc_params *P, const orc_geom *G, double bz, double 
     free(S);
     return ok ? 0 : 1;
 }
+
+/* Calibration track selection (the reading: tracks from the primary vertex
+ * whose collision time is known): a track is used when its refit succeeded
+ * and |q/pT| <= qpt_max, decided in binary32 on the binary32 parameter the
+ * calibration pass consumes; t_sel = t_coll for a used track, NaN otherwise
+ * (low-pT loopers: their later legs do not point to the vertex). */
+void orc_calib_select(int32_t n, const float *t_coll, const int32_t *status, const float *param, float qpt_max,
+                      float *t_sel)
+{
+    for (int32_t r = 0; r < n; r++) {
+        float q = param[5 * (int64_t)r + 4];
+        int keep = status[r] == 0 && fabsf(q) <= qpt_max;
+        t_sel[r] = keep ? t_coll[r] : NAN;
+    }
+}

@@ -19,15 +19,28 @@ import torch
 from . import abi
 
 VERTEX_VAR = 0.01          # primary-vertex pseudo-measurement variance (cm^2)
-QPT_MAX = 5.0              # tracks below pT = 0.2 GeV/c (loopers) are left out
+QPT_MAX = 5.0              # TPC_CALIB_QPT_MAX: tracks below pT = 0.2 GeV/c (loopers) are left out
 
 
 def select_tracks(t_coll: torch.Tensor, status: torch.Tensor, param: torch.Tensor, qpt_max: float = QPT_MAX):
-    """Collision times with NaN for tracks the calibration leaves out: failed
-    refits and |q/pT| > qpt_max (low-pT loopers, whose later legs do not come
-    from the vertex)."""
-    keep = (status == 0) & (param[:, 4].abs() <= qpt_max)
-    return torch.where(keep, t_coll, torch.full_like(t_coll, float("nan")))
+    """Collision times with NaN for the tracks the calibration leaves out
+    (tpc_calib_select: failed refits and |q/pT| > qpt_max, the low-pT loopers
+    whose later legs do not come from the vertex)."""
+    T = int(t_coll.shape[0])
+    dev = t_coll.device
+    if dev.type != "cuda":
+        raise RuntimeError("tpc_calib_select needs CUDA tensors")
+    t_coll = t_coll.to(dtype=torch.float32).contiguous()
+    status = status[:T].to(device=dev, dtype=torch.int32).contiguous()
+    param = param[:T].to(device=dev, dtype=torch.float32).contiguous()
+    out = torch.empty_like(t_coll)
+    st = torch.cuda.current_stream(dev)
+    rc = abi.lib().tpc_calib_select(T, C.c_void_p(t_coll.data_ptr()), C.c_void_p(status.data_ptr()),
+                                    C.c_void_p(param.data_ptr()), float(qpt_max), C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(st.cuda_stream))
+    if rc:
+        raise abi.TpcError(rc, "tpc_calib_select")
+    return out
 
 
 def nominal_theta(v_drift: float, n_sectors: int = 36, device="cuda") -> torch.Tensor:

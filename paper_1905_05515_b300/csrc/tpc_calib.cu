@@ -648,6 +648,17 @@ __global__ void __launch_bounds__(ORDER_BUCKETS) k_calib_order(CalibArgs A)
     for (int r = threadIdx.x; r < A.T; r += blockDim.x) A.order[atomicAdd(&cnt[bucket(r)], 1u)] = r;
 }
 
+// Calibration track selection: one thread per track, NaN marks a track the
+// calibration passes leave out (failed refit or |q/pT| > qpt_max).
+__global__ void k_calib_select(int T, const float* t_coll, const int32_t* __restrict__ status,
+                               const float* __restrict__ param, float qpt_max, float* t_sel)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const bool keep = status[r] == 0 && fabsf(param[5 * r + 4]) <= qpt_max;
+        t_sel[r] = keep ? t_coll[r] : __int_as_float(0x7fc00000);
+    }
+}
+
 int fill_args(const tpc_params* p, const tpc_geometry* g, float bz, float v_nominal, float vertex_var,
               const tpc_calib_tracks* tr, const float* theta, CalibArgs& A)
 {
@@ -768,6 +779,17 @@ int tpc_calib_backward(const tpc_params* p, const tpc_geometry* g, float bz, flo
     if (cudaFuncSetAttribute(k_calib_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return TPC_ERR_CUDA;
     k_calib_bwd<<<calib_grid(A.T), CALIB_BLOCK, smem, st>>>(A);
+    return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
+
+int tpc_calib_select(int32_t n_tracks, const float* t_coll, const int32_t* status, const float* param,
+                     float qpt_max, float* t_sel, void* stream)
+{
+    if (n_tracks < 0 || qpt_max != qpt_max) return TPC_ERR_ARG;
+    if (n_tracks == 0) return TPC_OK;
+    if (!t_coll || !status || !param || !t_sel) return TPC_ERR_ARG;
+    const int grid = calib_grid(n_tracks);
+    k_calib_select<<<grid, CALIB_BLOCK, 0, (cudaStream_t)stream>>>(n_tracks, t_coll, status, param, qpt_max, t_sel);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }
 

@@ -130,3 +130,12 @@ def test_rans_sizes_host_only():
     import torch
     with pytest.raises(ValueError):
         tpc.rans_encode(torch.zeros(10, dtype=torch.uint8))
+
+
+def test_calib_select_rejects_bad_arguments_without_touching_the_gpu():
+    import paper_1905_05515_b300 as tpc
+    L = tpc.lib()
+    assert L.tpc_calib_select(-1, None, None, None, 5.0, None, None) == tpc.TPC_ERR_ARG
+    assert L.tpc_calib_select(3, None, None, None, 5.0, None, None) == tpc.TPC_ERR_ARG
+    assert L.tpc_calib_select(3, 8, 8, 8, float("nan"), 8, None) == tpc.TPC_ERR_ARG
+    assert L.tpc_calib_select(0, None, None, None, 5.0, None, None) == tpc.TPC_OK

@@ -1,6 +1,9 @@
 """GPU parity of the calibration chi2 and its adjoint (tpc_calib_forward /
-tpc_calib_backward) against the binary64 oracle, on tracks the CUDA tracker
-found in a miscalibrated continuous frame.
+tpc_calib_backward) against the binary64 oracle, on a miscalibrated
+continuous frame.  The calibration problem is the oracle's own: the tracks of
+oracle.track_event, their generator-truth collision times and the oracle's
+track selection (oracle.calib_select); the GPU's selection
+(tpc_calib_select, through the C ABI) must equal it on the same tracks.
 
 Bars: per-track chi2 within 1e-3 relative (floor 1); gradient components
 within 1e-3 of max(|g_i|, 1e-2 |g|_inf); directional derivatives within
@@ -19,22 +22,24 @@ REL = 1e-3
 
 
 def _problem(n_collisions=3, mult=600, seed=5):
+    """The oracle's calibration problem of a calibration frame, and the
+    cluster tensors on the device."""
     import torch
 
+    import oracle
     import paper_1905_05515_b300 as tpc
     ev = tpcgen.calib_frame(seed=seed, n_collisions=n_collisions, mult_mean=mult)
     dev = torch.device("cuda:0")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     cl = (t(ev.sector), t(ev.row), t(ev.y), t(ev.zt))
-    trk = tpc.Tracker(ev.n, ev.row_x, continuous=True)
-    res = trk.track(*cl, bz=ev.bz, v_drift=ev.v_drift)
-    T = res.n_tracks
-    off = res.clus_offset[:T + 1].cpu().numpy()
-    clus = res.clus_index[:int(off[-1])].cpu().numpy()
-    tc_truth = tpcgen.track_collision_time(ev, off, clus)
-    tc = tpc.calib.select_tracks(t(tc_truth), res.status[:T], res.param[:T]).cpu().numpy()
-    h = dict(sector=res.sector[:T].cpu().numpy(), x=res.x[:T].cpu().numpy(), param=res.param[:T].cpu().numpy(),
-             off=off, clus=clus, tc=tc)
+    r = oracle.track_event(ev)
+    tc_truth = tpcgen.track_collision_time(ev, r.tr_off, r.tr_clus)
+    ot = oracle.calib_tracks_of(ev, r, tc_truth)
+    # the library's selection of the same tracks is the oracle's, NaN for NaN
+    tc_gpu = tpc.calib.select_tracks(t(tc_truth), t(r.tr_status.astype(np.int32)), t(ot.param)).cpu().numpy()
+    assert np.array_equal(np.isnan(tc_gpu), np.isnan(ot.tcoll))
+    assert np.array_equal(tc_gpu[~np.isnan(tc_gpu)], ot.tcoll[~np.isnan(ot.tcoll)])
+    h = dict(sector=ot.sector, x=ot.x, param=ot.param, off=ot.off, clus=ot.clus, tc=ot.tcoll)
     return ev, cl, h
 
 

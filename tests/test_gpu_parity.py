@@ -1,21 +1,21 @@
 """Parity of the CUDA tracker (called through the C ABI) with the CPU oracle
 on the same seeded inputs.  Decisions -- z after time->z, raw and cleaned
 links, start hits, tracklet hit lists and end states, selector verdicts,
-merged cluster lists, assignments -- are bit-exact; refitted parameters agree
-within 1e-4 relative (floors 1 cm, 1 cm, 0.01, 0.01, 0.01 GeV^-1 for y, z,
-sin phi, tan lambda, q/pT, or within 1e-3 of the parameter's standard
-deviation) and chi2 within 1e-3 relative of the binary64 oracle fit, on the
-tracks that are fits of one helix (chi2/ndf < 100)."""
+merged cluster lists, assignments -- are bit-exact.  Refitted parameters
+agree within 1e-4 relative (measured against max(|p|, scale) with the scales
+1 cm, 1 cm, 0.01, 0.01, 0.01 GeV^-1 of y, z, sin phi, tan lambda, q/pT) and
+chi2 within 1e-3 relative of the binary64 oracle fit, on every track both
+sides fit that is a fit of one helix (oracle chi2/ndf < 100).  What falls
+outside that set is reported and bounded as its own number: tracks that are
+not helix fits (their errors within 1e-3), refit status mismatches, and
+tracks whose refit failed on both sides."""
 import numpy as np
 import pytest
 
 import tpcgen
-from gpu_helpers import compare_decisions, compare_fit, run_gpu
+from gpu_helpers import CHI2_TOL, PARAM_TOL, compare_decisions, compare_fit, fit_summary, run_gpu
 
 pytestmark = pytest.mark.gpu
-
-PARAM_TOL = 1e-4
-CHI2_TOL = 1e-3
 
 
 def _check(ev, orc, params=None, fit=True, orc_params=None):
@@ -25,13 +25,17 @@ def _check(ev, orc, params=None, fit=True, orc_params=None):
     assert all(v == 0 for v in bad.values()), bad
     if fit:
         f = compare_fit(g, r)
-        assert f["status_mismatch"] <= max(2, r.n_tracks // 1000), f
-        assert f["n_not_helix"] <= max(5, r.n_tracks // 500), f
-        print(f"fit parity: {f['n_ok']} tracks, {f['n_not_helix']} not helix fits, max param err "
-              f"{f['param_max'].max():.2e}, max chi2 err {f['chi2_max']:.2e}")
-        assert f["param_max"].max() < PARAM_TOL, f
-        assert f["chi2_max"] < CHI2_TOL, f
+        print(fit_summary(f))
+        T = r.n_tracks
+        # the spec bar on every covered track: parameters 1e-4, chi2 1e-3 relative
+        assert f["n_param_over"] == 0 and f["param_max"].max() < PARAM_TOL, f
+        assert f["n_chi2_over"] == 0 and f["chi2_max"] < CHI2_TOL, f
         assert f["x_max"] < 1e-3, f
+        # not helix fits (mis-merged looper legs): few, their errors bounded on their own
+        assert f["n_not_helix"] <= max(5, T // 500), f
+        assert f["not_helix_param_max"] < 1e-3 and f["not_helix_chi2_max"] < CHI2_TOL, f
+        # refit status (one side's propagation left the helix domain): few
+        assert f["status_mismatch"] <= max(2, T // 1000), f
     return g, r
 
 
@@ -93,11 +97,20 @@ def test_fp64_final_refit(orc, mode, make):
     bad = compare_decisions(ev, g, r)
     assert all(v == 0 for v in bad.values()), bad
     ok = (g["status"] == 0) & (r.tr_status == 0)
-    ce = np.abs(g["chi2_64"][ok] - r.tr_chi2[ok]) / np.maximum(r.tr_chi2[ok], 1.0)
-    assert ce.max() < CHI2_TOL
-    cov_rel = np.abs(g["cov64"][ok] - r.tr_c[ok]) / np.maximum(np.abs(r.tr_c[ok]), 1e-12)
+    ce = np.abs(g["chi2_64"][ok] - r.tr_chi2[ok]) / r.tr_chi2[ok]
     diag = [0, 2, 5, 9, 14]
-    assert np.median(cov_rel[:, diag]) < 1e-4
+    cov_rel = (np.abs(g["cov64"][ok] - r.tr_c[ok]) / np.abs(r.tr_c[ok]))[:, diag]
+    # the tracks the binary64 Joseph update is for: long looping low-pT tracks
+    loop = ((np.abs(r.tr_p[ok, 4]) >= 5.0) | (r.tr_nclus[ok] > ev.row_x.shape[0]))
+    helix = (r.tr_chi2[ok] / np.maximum(r.tr_ndf[ok], 1)) < 100.0
+    print(f"binary64 mode {mode}: chi2 max rel {ce.max():.2e}; covariance diagonal max rel {cov_rel.max():.2e} "
+          f"(loopers: {int(loop.sum())}, max {cov_rel[loop].max() if loop.any() else 0:.2e}; helix-fit loopers "
+          f"max {cov_rel[loop & helix].max() if (loop & helix).any() else 0:.2e})")
+    assert ce.max() < CHI2_TOL
+    if ev.continuous:                         # the frames carry loopers, the central event none
+        assert loop.sum() >= 5
+        assert cov_rel[loop & helix].max() < 1e-4
+    assert cov_rel[helix].max() < 1e-4
 
 
 def test_fp64_loopers_only_mode():
@@ -151,3 +164,24 @@ def test_time_frame_full(orc):
     """The 50-collision continuous read-out frame (16 M clusters), whole-chain
     parity with the oracle (the oracle takes a few minutes here)."""
     _check(tpcgen.time_frame(seed=3, with_truth=False), orc)
+
+
+def test_golden_line_cases(orc):
+    """The hand-built straight-line cases (tests/golden/tracklets_b0.json):
+    the GPU's tracklets, selector verdicts and tracks equal the hand-derived
+    ones and the oracle's, bit for bit."""
+    import os
+    import types
+
+    from helpers import golden_line_cases
+    from test_oracle_golden_tracks import GOLDEN, check_golden_case
+    X = tpcgen.row_x_f32()
+    for case, sector, row, y, z in golden_line_cases(GOLDEN):
+        ev = types.SimpleNamespace(n=y.size, row_x=X, n_sectors=1, z_max=250.0, continuous=False, sector=sector,
+                                   row=row, y=y, zt=z, bz=0.0, v_drift=2.58)
+        g, r = _check(ev, orc, fit=False)
+        tk = g["tracklets"]
+        off = g["clus_offset"]
+        tracks = [g["clus_index"][off[t]:off[t + 1]] for t in range(int(g["n_tracks"]))]
+        check_golden_case(case, y.size, tk["start"], tk["nhits"], tk["kept"], tracks)
+    assert os.path.exists(GOLDEN)

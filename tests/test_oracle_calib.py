@@ -225,3 +225,19 @@ def test_measurement_derivative_is_twice_the_weighted_smoothed_residual(orc, pro
             yp, ym = np.float32(tr.cl_y[c] + 1e-2), np.float32(tr.cl_y[c] - 1e-2)   # the binary32 inputs
             fd = (f(yp) - f(ym)) / (float(yp) - float(ym))
             assert a_y == pytest.approx(fd, rel=1e-5, abs=1e-6), (t, k)
+
+
+def test_track_selection_cases():
+    """The calibration's track selection on hand-made cases: refit status 0
+    and |q/pT| <= 5 (binary32, the edge included) keep the collision time;
+    a failed refit, |q/pT| just above 5 or a NaN parameter give NaN; a NaN
+    collision time stays NaN."""
+    import oracle
+    q = np.array([0.0, 5.0, -5.0, np.nextafter(np.float32(5), np.float32(6)), np.nan, 1.0, 1.0], np.float32)
+    param = np.zeros((q.size, 5), np.float32)
+    param[:, 4] = q
+    status = np.array([0, 0, 0, 0, 0, 1, 0], np.int32)
+    tc = np.array([10, 20, 30, 40, 50, 60, np.nan], np.float32)
+    out = oracle.calib_select(tc, status, param)
+    exp = np.array([10, 20, 30, np.nan, np.nan, np.nan, np.nan], np.float32)
+    np.testing.assert_array_equal(out, exp)

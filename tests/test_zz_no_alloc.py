@@ -1,9 +1,9 @@
 """tpc_links_static: seeding with no allocation at all.
 
-Some callers cannot allocate device memory when they need the links: a CUDA
-graph being captured or replayed, a host thread that must not block in the
-allocator while other streams run, an embedding that forbids cudaMalloc after
-start-up.  This entry point keeps its scratch in a fixed device array inside
+Some callers cannot allocate device memory when they need the links: a host
+thread that must not block in the allocator (which can synchronise the
+device) while other streams run, or an embedding that forbids cudaMalloc
+after start-up.  This entry point keeps its scratch in a fixed device array inside
 the library; the caller passes only its inputs and outputs.  The test calls
 it through the C ABI on consecutive, different events and checks that its
 links and start flags equal those of tpc_track (bit for bit, as every link
