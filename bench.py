@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-attach", action="store_true",
                     help="frame: skip the timing of the optional cluster attachment stage")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="frame workload: skip the bounded sub-time-frame batch object (graph vs per-frame loop)")
+    ap.add_argument("--batch-stf", type=int, default=16, help="frame workload: sub-time-frames of the batch object")
+    ap.add_argument("--batch-max-coll", type=int, default=40,
+                    help="frame workload: batch object frames of U{1..N} collisions")
     ap.add_argument("--workload", choices=("frame", "stf_batch", "calib"), default="frame",
                     help="frame: the 50-collision frame; stf_batch: sub-time-frames of 1..max-coll collisions")
     ap.add_argument("--n-stf", type=int, default=64)
@@ -172,6 +177,50 @@ def peaks():
         return {}
 
 
+_FMA_PEAK = {}
+
+
+def fma_peak(dev, precision=32):
+    """Fused multiply-add throughput of this GPU (TFLOP/s) from the library's
+    probe kernel (tpc_probe_fma: 8 independent chains per thread, 148 x 8
+    blocks of 256 threads), timed with CUDA events on the launching stream
+    after warm-up launches; the best of the timed launches."""
+    import ctypes as C
+
+    import torch
+
+    import paper_1905_05515_b300 as tpc
+    key = (str(dev), precision)
+    if key in _FMA_PEAK:
+        return _FMA_PEAK[key]
+    L = tpc.lib()
+    blocks, threads = 148 * 8, 256
+    iters = (1 << 14) if precision == 32 else (1 << 7)
+    out = torch.empty(blocks, dtype=torch.float32 if precision == 32 else torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    flops = C.c_int64(0)
+
+    def launch():
+        rc = L.tpc_probe_fma(precision, blocks, threads, iters, C.c_void_p(out.data_ptr()), C.byref(flops),
+                             C.c_void_p(st.cuda_stream))
+        if rc:
+            raise tpc.TpcError(rc, "tpc_probe_fma")
+
+    for _ in range(3):
+        launch()
+    best = None
+    for _ in range(10 if precision == 32 else 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        launch()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    _FMA_PEAK[key] = flops.value / best / 1e12
+    return _FMA_PEAK[key]
+
+
 def cpu_baseline(n_coll: int, seed: int):
     """The oracle as it stands, single-threaded, on a bounded frame of the same generator."""
     import oracle
@@ -217,12 +266,88 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def batch_object(cat, off, ncoll, dev, steps, warmup, max_coll):
+    """Batched mode at bounded size: the same sub-time-frames tracked by a
+    loop of synchronous tpc_track calls (one per frame) and by one replay of
+    a captured GroupedBatch graph (frame groups on two streams), in the
+    configuration of the batched workload (binary64 final refit of the
+    loopers, 16-bit packed link coordinates); both timed with CUDA events,
+    outputs compared bit for bit."""
+    import numpy as np
+    import torch
+
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in cat.items()}
+    dv = {k: v.to(dev) for k, v in host.items()}
+    ins = (dv["sector"], dv["row"], dv["y"], dv["zt"])
+    row_x = tpcgen.row_x_f32()
+    params = tpc.tpc_params_default(tracklets_per_1k=60, fp64_final=2, packed_links=1)
+    nstf = len(ncoll)
+    vd, bz = tpcgen.V_DRIFT, 0.5
+    big = int(np.max(np.diff(off)))
+    one = tpc.Tracker(big, row_x, continuous=True, params=params, device=dev)
+
+    def per_frame():
+        ps = []
+        for i in range(nstf):
+            a, b = int(off[i]), int(off[i + 1])
+            ps.append(one.track(*(t[a:b] for t in ins), bz=bz, v_drift=vd).param.clone())
+        return ps
+
+    def timed(fn, k):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    for _ in range(max(1, warmup)):
+        per_frame()
+    ms_frame = timed(per_frame, steps)
+    p_frame = torch.cat(per_frame()).cpu().numpy()
+    launches_frame = sum(one.track(*(t[int(off[i]):int(off[i + 1])] for t in ins), bz=bz, v_drift=vd).n_launches
+                         for i in range(nstf))
+    del one
+    torch.cuda.empty_cache()
+    gb = tpc.GroupedBatch(*ins, off, row_x, params=params, bz=bz, v_drift=vd, group_clusters=32_000_000,
+                          n_streams=2)
+    gb.capture()
+    for _ in range(max(1, warmup)):
+        gb.replay()
+    ms_graph = timed(gb.replay, steps)
+    res = gb.results()
+    p_graph = torch.cat([r.param for r in res]).cpu().numpy()
+    n_tracks = sum(r.n_tracks for r in res)
+    same = bool(np.array_equal(p_graph, p_frame))
+    out = {"workload": f"{nstf} sub-time-frames of U{{1..{max_coll}}} collisions "
+                       f"(multiplicity Exp(2000), 50 kHz), binary64 final refit of the loopers, packed link "
+                       f"coordinates", "clusters": int(off[-1]), "collisions": int(ncoll.sum()),
+           "tracks": int(n_tracks), "groups": len(gb.groups), "graph_ms": ms_graph, "per_frame_ms": ms_frame,
+           "speedup_vs_per_frame": ms_frame / ms_graph, "identical_to_per_frame": same,
+           "graph_clusters_per_s": int(off[-1]) / (ms_graph / 1e3),
+           "per_frame_clusters_per_s": int(off[-1]) / (ms_frame / 1e3),
+           "graph_launches": gb.n_launches, "per_frame_launches": launches_frame,
+           "timing": "CUDA events around one replay (graph) or one loop of synchronous calls (per frame), "
+                     f"mean of {steps}"}
+    del gb, res, dv
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank, local, pg):
     import numpy as np
     import torch
 
     import paper_1905_05515_b300 as tpc
     import tpcgen
+    batch_in = None
+    if not args.no_batch:
+        # generated in a spawned process pool before this process uses CUDA
+        batch_in = make_stf_batch(args.batch_stf, args.batch_max_coll, 2000.0, seed0=2000 + 100 * rank)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ev = tpcgen.time_frame(seed=3 + rank, n_collisions=args.collisions, with_truth=False)
@@ -364,6 +489,14 @@ def run_ours(args, ws, rank, local, pg):
         torch.cuda.empty_cache()
     barrier()
 
+    # ---- the bounded batch object: graph-captured frame groups against the per-frame loop
+    batch = None
+    if batch_in is not None:
+        batch = batch_object(*batch_in, dev, max(3, args.steps // 2), args.warmup, args.batch_max_coll)
+    barrier()
+    # ---- measured FMA rates (roofline denominators of the Kalman stages)
+    fp32_peak, fp64_peak = fma_peak(dev, 32), fma_peak(dev, 64)
+
     # ---- max over ranks, totals
     (ms_max, e2e_max, sync_max), (n_total,) = over_ranks(pg, dev, (ms, e2e_s, sync_s), (float(n),))
     if rank != 0:
@@ -372,9 +505,9 @@ def run_ours(args, ws, rank, local, pg):
     per_step = {k: v / args.steps for k, v in stage_sum.items()}
     w = {k: v / args.steps for k, v in work_sum.items()}
     dom = max(per_step, key=per_step.get)
-    pk_all = peaks()
-    roof = roofline(dom, per_step, w, n, pk_all)
+    pk_all = dict(peaks(), fp32_tflops_measured=fp32_peak)
     n_assigned = int(rs.clus_offset[-1].item()) if rs.n_tracks else 0
+    roof = roofline(dom, per_step, w, n, pk_all, n_assigned)
     stage_roofs = {}
     for st_ in per_step:
         rf = roofline(st_, per_step, w, n, pk_all, n_assigned)
@@ -402,8 +535,13 @@ def run_ours(args, ws, rank, local, pg):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    line["measured_peaks"] = {"fp32_tflops": round(fp32_peak, 2), "fp64_tflops": round(fp64_peak, 3),
+                              "how": "tpc_probe_fma: 148 x 8 blocks x 256 threads x 8 independent FMA chains, "
+                                     "best of the CUDA-event-timed launches after warm-up"}
     if attach is not None:
         line["attach"] = attach
+    if batch is not None:
+        line["batch"] = batch
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_collisions, seed=3)
     print(json.dumps(line), flush=True)
@@ -876,16 +1014,26 @@ def roofline(stage, per_step, w, n, pk, n_assigned=None):
     t = per_step[stage] / 1e3
     if stage in ("tracklets", "merge", "refit"):
         if stage == "tracklets":
+            # algorithmic: one propagation and one update per input cluster
+            # (one tracklet pass); executed: the counted steps, back-jumps,
+            # empty rows and window candidates included
+            algo = n * (FLOPS_PROP + FLOPS_UPDATE)
             flops = w["trk_prop"] * FLOPS_PROP + w["trk_upd"] * FLOPS_UPDATE + w["trk_cand"] * FLOPS_CAND
         elif stage == "merge":
-            flops = w["merge_chi2"] * FLOPS_MERGE          # one chi2 per screened pair
+            flops = algo = w["merge_chi2"] * FLOPS_MERGE          # one chi2 per screened pair
         else:
+            # three passes of one propagation and one update per track cluster
             flops = w["refit_prop"] * (FLOPS_PROP + FLOPS_UPDATE)
-        ach = flops / t / 1e12
+            algo = 3 * (n_assigned if n_assigned is not None else n) * (FLOPS_PROP + FLOPS_UPDATE)
+        ach = algo / t / 1e12
         tb = NCU_TRAFFIC_B_PER_CLUSTER.get(stage)
-        return {"bound": "alu", "stage": stage, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": tb * n if tb is not None else None,
-                "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"}
+        pk32 = pk.get("fp32_tflops_measured")
+        peak = pk32 if pk32 else FP32_PEAK_TFLOPS
+        return {"bound": "alu", "stage": stage, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "executed_tflops": flops / t / 1e12, "executed_frac": flops / t / 1e12 / peak,
+                "algorithmic_flops_per_launch": algo, "traffic": tb * n if tb is not None else None,
+                "peak_note": ("measured binary32 FMA rate (tpc_probe_fma, CUDA events)" if pk32 else
+                              "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)")}
     bytes_per = {"prep": 18, "bin": 40, "neighbours": 22, "clean_start": 28}.get(stage, 0)
     hbm = pk.get("hbm_gbs", 6400.0)
     ach = bytes_per * n / t / 1e9

@@ -82,7 +82,8 @@ CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
             "tpc_track_batched", "tpc_prepare", "tpc_prepare_staging_size", "tpc_prepare_async", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
             "tpc_error_string", "tpc_calib_workspace_size", "tpc_calib_forward", "tpc_calib_backward",
-            "tpc_calib_status", "tpc_calib_select", "tpc_rans_workspace_size", "tpc_rans_max_bytes", "tpc_rans_encode")
+            "tpc_calib_status", "tpc_calib_select", "tpc_rans_workspace_size", "tpc_rans_max_bytes", "tpc_rans_encode",
+            "tpc_probe_fma")
 
 _lib = None
 
@@ -134,6 +135,8 @@ def lib(build_if_missing: bool = True):
         L.tpc_calib_status.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
         L.tpc_calib_select.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p,
                                        C.c_void_p]
+        L.tpc_probe_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int64),
+                                    C.c_void_p]
         L.tpc_error_string.argtypes = [C.c_int]
         L.tpc_error_string.restype = C.c_char_p
         _lib = L

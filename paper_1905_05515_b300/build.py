@@ -23,6 +23,7 @@ UNITS = {
     "tpc_refit.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
     "tpc_calib.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"],
     "tpc_compress.cu": [],
+    "tpc_probe.cu": ["-fmad=true"],
 }
 
 
@@ -35,7 +36,7 @@ def _nvcc():
 
 def sources():
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    out.extend(os.path.join(INCLUDE, h) for h in ("tpc_track.h", "tpc_calib.h", "tpc_compress.h"))
+    out.extend(os.path.join(INCLUDE, h) for h in ("tpc_track.h", "tpc_calib.h", "tpc_compress.h", "tpc_probe.h"))
     out.append(os.path.abspath(__file__))
     return out
 
