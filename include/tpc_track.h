@@ -120,6 +120,15 @@ typedef struct {
                                     the adjacency order, is 1 / |q/pT| of the inner-end state of its
                                     innermost piece: good when |q/pT| <= 1 / pt_min_physics (binary32;
                                     0: every track is good). */
+    float outlier_chi2;          /* cluster rejection before the refit (section "TPC Tracking": the fit
+                                    rejects clusters; default 25, 0: off).  Each kept tracklet's state at
+                                    its innermost hit (binary32, after all of its hits) is carried with the
+                                    decision-path helix step up through the rows of its hits; an owned hit
+                                    with dy^2/sigma_y^2 + dz^2/sigma_z^2 > outlier_chi2 to it leaves the
+                                    track's cluster list, the refit and the assignment (assign = -1),
+                                    unless fewer than 5 owned hits of the tracklet would remain.  A refused
+                                    step ends the check of that tracklet.  Bit-exact on any hardware that
+                                    rounds each operation. */
 } tpc_params;
 
 /* Detector geometry (host memory). */
@@ -183,6 +192,8 @@ typedef struct {
     int64_t work[5];             /* with params.profile: tracklet propagations, tracklet updates, grid
                                     candidates examined while following, refit propagations, merger
                                     chi2 evaluations */
+    int32_t n_rejected;          /* clusters the rejection before the refit took out of their tracks
+                                    (tpc_track, tpc_track_batched) */
 } tpc_tracks;
 
 #define TPC_MAX_CLUSTERS 2145386495LL   /* INT32_MAX - 2^21 */

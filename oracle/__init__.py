@@ -24,7 +24,8 @@ class OrcParams(C.Structure):
                 ("chi2_cut", C.c_float), ("max_miss", C.c_int32), ("min_hits", C.c_int32),
                 ("min_owned", C.c_int32), ("edge_margin", C.c_float),
                 ("merge_dz", C.c_float), ("merge_chi2", C.c_float), ("refit_passes", C.c_int32),
-                ("refit_inflate", C.c_float), ("packed_links", C.c_int32), ("back_jump", C.c_int32)]
+                ("refit_inflate", C.c_float), ("packed_links", C.c_int32), ("back_jump", C.c_int32),
+                ("outlier_chi2", C.c_float)]
 
 
 class OrcGeom(C.Structure):
@@ -46,7 +47,7 @@ class OrcResult(C.Structure):
                 ("n_seg", C.c_int32), ("seg_trk", _P32), ("seg_next", _P32), ("seg_prev", _P32),
                 ("n_tracks", C.c_int32), ("tr_sector", _P32), ("tr_x", _PD), ("tr_p", _PD), ("tr_c", _PD),
                 ("tr_chi2", _PD), ("tr_ndf", _P32), ("tr_status", _P32), ("tr_nclus", _P32),
-                ("tr_off", _P32), ("tr_clus", _P32), ("assign", _P32),
+                ("tr_off", _P32), ("tr_clus", _P32), ("assign", _P32), ("rejected", _PU8), ("n_rejected", C.c_int32),
                 ("row_qup", C.c_float * 256), ("row_qdn", C.c_float * 256), ("row_w", C.c_float * 256)]
 
 
@@ -83,6 +84,9 @@ def lib():
         L.orc_bspline_all.argtypes = [C.c_double, _PD, _PD]
         L.orc_bspline_all.restype = None
         L.orc_step_pos32.argtypes = [_PF, C.c_float, C.c_float]
+        L.orc_loopers.argtypes = [C.c_int32, C.c_float, C.c_float, C.c_float, C.c_int32, _P32, _P32, _PF, _P32, _P32]
+        L.orc_atan2_own.argtypes = [C.c_float, C.c_float]
+        L.orc_atan2_own.restype = C.c_float
         _PU32 = C.POINTER(C.c_uint32)
         L.orc_rans_normalise.argtypes = [_PU32, _PU32]
         L.orc_rans_encode.argtypes = [_PU8, C.c_int32, _PU32, _PU8, _P32]
@@ -152,6 +156,7 @@ class OracleResult:
     tr_off: np.ndarray
     tr_clus: np.ndarray
     assign: np.ndarray
+    rejected: np.ndarray
     row_qup: np.ndarray
     row_qdn: np.ndarray
     row_w: np.ndarray
@@ -211,7 +216,7 @@ def track(sector, row, y, zt, row_x, n_sectors=36, z_max=250.0, continuous=False
             tr_chi2=_copy(R.tr_chi2, T, np.float64), tr_ndf=_copy(R.tr_ndf, T, np.int32),
             tr_status=_copy(R.tr_status, T, np.int32), tr_nclus=_copy(R.tr_nclus, T, np.int32),
             tr_off=tr_off, tr_clus=_copy(R.tr_clus, int(tr_off[-1]), np.int32),
-            assign=_copy(R.assign, n, np.int32),
+            assign=_copy(R.assign, n, np.int32), rejected=_copy(R.rejected, n, np.uint8),
             row_qup=np.array(R.row_qup[:], np.float32), row_qdn=np.array(R.row_qdn[:], np.float32),
             row_w=np.array(R.row_w[:], np.float32))
     finally:
@@ -254,6 +259,37 @@ def attach_event(ev, r: OracleResult, radius=1.5, pt_min=0.05):
     """attach() on a tpcgen.Event and the oracle's result for it."""
     return attach(ev.sector, ev.row, ev.y, r, ev.row_x, n_sectors=ev.n_sectors, bz=ev.bz, radius=radius,
                   pt_min=pt_min)
+
+
+LOOPER_QPT_MIN = 5.0     # |q/pT| (c/GeV) of a looper-leg candidate: pT below 200 MeV/c
+
+
+def track_heads(r: OracleResult):
+    """Per track: the tracklet index of its innermost piece (tracks are in the
+    order of their innermost pieces' start indices)."""
+    return r.seg_trk[r.seg_prev < 0]
+
+
+def loopers(sector, r: OracleResult, n_sectors=36, bz=0.5, qpt_min=LOOPER_QPT_MIN, frame=None, z_max=250.0):
+    """Looper-leg groups and leg numbers of an oracle tracking result
+    (tpc_oracle_loopers.c): group[t] = smallest track of the legs of one
+    particle (-1 alone), leg[t] = 0 for the earliest leg in drift."""
+    heads = track_heads(r)
+    T = r.n_tracks
+    sec = np.ascontiguousarray(np.asarray(sector)[r.trk_start[heads]], np.int32)
+    st = np.ascontiguousarray(r.trk_bot[heads], np.float32)
+    fr = None if frame is None else np.ascontiguousarray(frame, np.int32)
+    g = np.zeros(max(T, 1), np.int32)
+    lg = np.zeros(max(T, 1), np.int32)
+    rc = lib().orc_loopers(n_sectors, z_max, bz, qpt_min, T, _ptr(sec, _P32), None if fr is None else _ptr(fr, _P32),
+                           _ptr(st, _PF), _ptr(g, _P32), _ptr(lg, _P32))
+    if rc:
+        raise ValueError(f"orc_loopers failed ({rc})")
+    return g[:T], lg[:T]
+
+
+def atan2_own(y, x):
+    return float(lib().orc_atan2_own(np.float32(y), np.float32(x)))
 
 
 def step_pos32(p, x2, kb):

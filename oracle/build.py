@@ -5,7 +5,8 @@ IEEE-strict flags (no contraction of a*b+c, no fast-math) so that its binary32
 decision path is exactly the operation sequence written in tpc_oracle.c
 (tpc_oracle_calib.c: the calibration chi2 and its gradient, binary64;
 tpc_oracle_attach.c: the track-based cluster attachment;
-tpc_oracle_compress.c: the cluster compression).
+tpc_oracle_compress.c: the cluster compression; tpc_oracle_loopers.c: the
+looper-leg identification).
 """
 import os
 import subprocess
@@ -13,7 +14,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRCS = [os.path.join(HERE, "tpc_oracle.c"), os.path.join(HERE, "tpc_oracle_calib.c"),
-        os.path.join(HERE, "tpc_oracle_attach.c"), os.path.join(HERE, "tpc_oracle_compress.c")]
+        os.path.join(HERE, "tpc_oracle_attach.c"), os.path.join(HERE, "tpc_oracle_compress.c"),
+        os.path.join(HERE, "tpc_oracle_loopers.c")]
 LIB = os.path.join(HERE, "liboracle.so")
 FLAGS = ["-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-ffp-contract=off",
          "-fno-fast-math", "-fexcess-precision=standard", "-Wall"]

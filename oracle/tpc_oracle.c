@@ -59,6 +59,7 @@
 #define KB_C  (-2.99792458e-3f)    /* d sin(phi)/dx = KB_C * Bz[T] * q/pT[1/GeV] (cm^-1) */
 
 #define NST 21   /* x, p[5], c[15] */
+#define MIN_KEEP 5  /* cluster rejection leaves a tracklet at least this many owned hits */
 
 static inline size_t nz(int n) { return n > 0 ? (size_t)n : 1; }
 static inline int ci(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
@@ -77,6 +78,7 @@ void orc_params_default(orc_params *p)
     p->refit_inflate = 100.0f;
     p->packed_links = 0;
     p->back_jump = 32;
+    p->outlier_chi2 = 25.0f;
 }
 
 /* ===================================================================== *
@@ -812,6 +814,41 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
         if (own >= P->min_owned && 2 * own >= R->trk_nhits[q]) { R->trk_kept[q] = 1; ns++; }
     }
 
+    /* ---- cluster rejection before the refit (section "TPC Tracking": the
+     * track fit rejects clusters).  Reading: each kept tracklet's inner-end
+     * state -- binary32, after all of its hits -- is carried row by row with
+     * the decision-path propagation up through the rows of its hits; an
+     * owned hit whose residual to it passes dy^2/vy + dz^2/vz > outlier_chi2
+     * is rejected: it leaves the track's cluster list, the refit and the
+     * assignment.  A refused step ends the check of that tracklet.  A
+     * tracklet that would keep fewer than MIN_KEEP owned hits rejects none. */
+    R->rejected = (uint8_t *)calloc(nz(n), 1);
+    R->n_rejected = 0;
+    if (P->outlier_chi2 > 0.0f) {
+        const float ivy = 1.0f / vy, ivz = 1.0f / vz;
+        int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)NR);
+        for (int q = 0; q < nt; q++) {
+            if (!R->trk_kept[q]) continue;
+            uint64_t w = tracklet_weight(R->trk_nhits[q], R->trk_start[q]);
+            int own = 0, nc = 0;
+            for (int k = R->trk_off[q]; k < R->trk_off[q + 1]; k++) own += hitw[R->trk_hits[k]] == w;
+            float st[NST];
+            memcpy(st, R->trk_bot + (size_t)q * NST, sizeof(st));
+            for (int k = R->trk_off[q]; k < R->trk_off[q + 1]; k++) {
+                int c = R->trk_hits[k];
+                if (!orc_prop32(st, X[row[c]], kb)) break;
+                float dy = y[c] - st[1];
+                float dz = R->z[c] - st[2];
+                float q2 = fmaf(dy * dy, ivy, (dz * dz) * ivz);
+                if (hitw[c] == w && q2 > P->outlier_chi2) cand[nc++] = c;
+            }
+            if (own - nc < MIN_KEEP) continue;
+            for (int k = 0; k < nc; k++) R->rejected[cand[k]] = 1;
+            R->n_rejected += nc;
+        }
+        free(cand);
+    }
+
     /* ---- a8: cross-sector merger (adjacent sectors, same side) */
     R->n_seg = ns;
     R->seg_trk = (int32_t *)malloc(sizeof(int32_t) * nz(ns));
@@ -932,7 +969,7 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
             uint64_t w = tracklet_weight(R->trk_nhits[tq], R->trk_start[tq]);
             for (int k = R->trk_off[tq]; k < R->trk_off[tq + 1]; k++) {
                 int c = R->trk_hits[k];
-                if (hitw[c] == w) iv_push(&cl, c);
+                if (hitw[c] == w && !R->rejected[c]) iv_push(&cl, c);
             }
             tail = b;
         }
@@ -983,6 +1020,6 @@ void orc_free(orc_result *R)
     free(R->trk_top); free(R->trk_bot);
     free(R->seg_trk); free(R->seg_next); free(R->seg_prev);
     free(R->tr_sector); free(R->tr_x); free(R->tr_p); free(R->tr_c); free(R->tr_chi2); free(R->tr_ndf);
-    free(R->tr_status); free(R->tr_nclus); free(R->tr_off); free(R->tr_clus); free(R->assign);
+    free(R->tr_status); free(R->tr_nclus); free(R->tr_off); free(R->tr_clus); free(R->assign); free(R->rejected);
     memset(R, 0, sizeof(*R));
 }

@@ -41,6 +41,7 @@ typedef struct {
     float refit_inflate;                  /* factor on the previous angular covariance at each pass start */
     int32_t packed_links;                 /* 1: the link pass sees y, z rounded to 1/256 cm (16-bit packed) */
     int32_t back_jump;                    /* TrackletConstructor phase C: rows per return jump (1: row by row) */
+    float outlier_chi2;                   /* cluster rejection before the refit: dy^2/vy + dz^2/vz cut (0: off) */
 } orc_params;
 
 typedef struct {
@@ -84,6 +85,8 @@ typedef struct {
     int32_t *tr_off;          /* [T+1] */
     int32_t *tr_clus;         /* cluster indices inner -> outer */
     int32_t *assign;          /* [n] track index or -1 */
+    uint8_t *rejected;        /* [n] 1: owned by a kept tracklet but rejected before the refit */
+    int32_t n_rejected;
     float row_qup[256], row_qdn[256], row_w[256];
 } orc_result;
 
@@ -108,6 +111,15 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
                const int32_t *seg_next, const int32_t *seg_prev, const int32_t *trk_off,
                const int32_t *trk_hits, const float *trk_bot, const int32_t *assign, float radius,
                float pt_min, int32_t *adjacent, uint8_t *flags);
+
+/* Looper-leg identification (tpc_oracle_loopers.c).  Per track: sector and
+ * time frame (frame may be NULL) of its innermost piece and that piece's
+ * inner-end state (21 floats: x, y, z, sin(phi), tan(lambda), q/pT, cov);
+ * outputs group (smallest track index of the legs of one particle, -1 alone)
+ * and leg (0 = the earliest in drift, -1 alone). */
+int orc_loopers(int32_t n_sectors, float z_max, float bz, float qpt_min, int32_t n_tracks, const int32_t *sector,
+                const int32_t *frame, const float *state, int32_t *group, int32_t *leg);
+float orc_atan2_own(float y, float x);
 
 /* Cluster compression (tpc_oracle_compress.c): rANS coder of byte symbols,
  * the integer fields of the format (12 streams), their inverse, and the

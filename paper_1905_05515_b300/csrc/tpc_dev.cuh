@@ -250,6 +250,7 @@ struct Frame {
     int trk_next;                  // work queue heads of the tracklet constructor's two passes
     int trk_next2;
     int n_mpairs;                  // merger: candidate pairs that passed the screen
+    int n_rejected;                // clusters rejected before the refit
     // work counters (params.profile): tracklet propagations, updates, window
     // candidates examined; refit propagations; merger chi2 evaluations
     unsigned long long w_prop, w_upd, w_cand, w_refit_prop, w_merge;

@@ -1255,6 +1255,60 @@ __global__ void k_sel_own(Frame* f, int cap, int nr, int min_hits, int min_owned
 }
 
 // ---------------------------------------------------------------------------
+// Cluster rejection before the refit (section "TPC Tracking": the track fit
+// rejects clusters).  One thread per kept tracklet carries its state at the
+// innermost hit (after all of its hits) with the decision-path helix step up
+// through the rows of its hits; an owned hit whose residual passes
+// dy^2/vy + dz^2/vz > cut loses its owned bit, so that the assembly leaves it
+// out of the track, the refit and the assignment -- unless fewer than
+// REJ_MIN_KEEP owned hits of the tracklet would remain.  A refused step ends
+// the check of that tracklet.
+// ---------------------------------------------------------------------------
+constexpr int REJ_MIN_KEEP = 5;
+constexpr int REJ_WORDS = 8;            // hits per tracklet <= rows <= 255
+
+__global__ void k_reject(Frame* f, int cap, int nr, int np, float kb, float ivy, float ivz, float cut,
+                         const int32_t* __restrict__ seg, const int32_t* __restrict__ t_nhits,
+                         const int32_t* __restrict__ t_nup, const int32_t* __restrict__ t_hits,
+                         const float* __restrict__ t_bot, const float4* __restrict__ sc,
+                         const float* __restrict__ rowtab, uint32_t* __restrict__ ownmask, int32_t* __restrict__ t_own)
+{
+    if (f->err) return;
+    const int nseg = f->n_seg;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+        const int t = seg[b];
+        const int nh = min(t_nhits[t], REJ_WORDS * 32), nup = t_nup[t];
+        const int32_t* slot = t_hits + (int64_t)t * nr;
+        float st[NST];
+#pragma unroll
+        for (int i = 0; i < NST; i++) st[i] = t_bot[(int64_t)t * NST + i];
+        uint32_t rej[REJ_WORDS];
+#pragma unroll
+        for (int w = 0; w < REJ_WORDS; w++) rej[w] = 0u;
+        int nc = 0;
+        uint32_t m = 0u;
+        for (int k = 0; k < nh; k++) {
+            if ((k & 31) == 0) m = ownmask[(int64_t)(k >> 5) * cap + t];
+            const float4 c = sc[trk_hit(slot, nr, nh, nup, k)];
+            const int r = (int)(sc_plane(c) % (uint32_t)np) % nr;
+            if (!prop32(st, rowtab[r * ROWTAB], kb)) break;
+            const float dy = c.x - st[1];
+            const float dz = c.y - st[2];
+            const float q2 = __fmaf_rn(dy * dy, ivy, (dz * dz) * ivz);
+            if (((m >> (k & 31)) & 1u) && q2 > cut) {
+                rej[k >> 5] |= 1u << (k & 31);
+                nc++;
+            }
+        }
+        if (nc == 0 || t_own[t] - nc < REJ_MIN_KEEP) continue;
+        for (int w = 0; w < REJ_WORDS; w++)
+            if (rej[w]) ownmask[(int64_t)w * cap + t] &= ~rej[w];
+        t_own[t] -= nc;
+        atomicAdd(&f->n_rejected, nc);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a8: cross-sector merger (adjacent sectors of one side, inside one frame)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
@@ -2348,6 +2402,13 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                                          at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
     }
     g_launches += 2;
+    if (p->outlier_chi2 > 0.0f) {
+        volatile float ivyv = 1.0f / vy, ivzv = 1.0f / vz;
+        k_reject<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, L.np, kb, ivyv, ivzv, p->outlier_chi2, seg, TA.t_nhits,
+                                    TA.t_nup, TA.t_hits, TA.t_bot, sc, rowtab, at<uint32_t>(ws, L.ownmask),
+                                    at<int32_t>(ws, L.t_own));
+        g_launches++;
+    }
     CK(mark(6));
     // a8: merger
     const int64_t mcells = (int64_t)NF * g->n_sectors * L.mnzmax;
@@ -2524,7 +2585,7 @@ int run_sync(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift
     const Layout L = make_layout(p, g, n, nframes);
     if (ws_bytes < L.total) return TPC_ERR_CAPACITY;
     cudaStream_t st = (cudaStream_t)stream;
-    out->n_tracks = out->n_tracklets = out->n_segments = 0;
+    out->n_tracks = out->n_tracklets = out->n_segments = out->n_rejected = 0;
     out->tracklets_needed = out->tracks_needed = out->clusters_needed = 0;
     out->n_launches = 0;
     for (int k = 0; k < TPC_N_STAGES; k++) out->stage_ms[k] = 0.0f;
@@ -2561,6 +2622,7 @@ int run_sync(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift
     out->n_tracklets = std::min(hf.n_starts, ntcap);
     out->n_segments = hf.n_seg;
     out->n_tracks = hf.n_tracks;
+    out->n_rejected = hf.n_rejected;
     if (hf.err == TPC_ERR_DATA) return TPC_ERR_DATA;
     if (hf.n_starts > ntcap) {
         out->tracklets_needed = hf.n_starts;
@@ -2613,6 +2675,7 @@ int tpc_params_default(tpc_params* p)
     p->merge_pairs_per_1k = 4000;
     p->tube_radius = 1.5f;
     p->pt_min_physics = 0.05f;
+    p->outlier_chi2 = 25.0f;
     return TPC_OK;
 }
 

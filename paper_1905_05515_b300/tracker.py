@@ -43,6 +43,7 @@ class TrackResult:
     n_tracklets: int = 0
     n_segments: int = 0
     n_launches: int = 0
+    n_rejected: int = 0                        # clusters the rejection before the refit took out
     stage_ms: dict | None = None
     work: dict | None = None
 
@@ -126,6 +127,7 @@ class Tracker:
         res.frame = b["frame"][:T]
         if out is not None:
             res.n_tracklets, res.n_segments, res.n_launches = out.n_tracklets, out.n_segments, out.n_launches
+            res.n_rejected = out.n_rejected
             res.stage_ms = {k: float(out.stage_ms[i]) for i, k in enumerate(abi.STAGES)}
             if self.attach:
                 res.stage_ms["attach"] = float(out.stage_ms[abi.ATTACH_STAGE])

@@ -59,6 +59,7 @@ def compare_decisions(ev, g, r):
             bad["clus_index"] = -1
         bad["sector"] = int((g["sector"] != r.tr_sector).sum())
     bad["assign"] = int((g["assign"] != r.assign).sum())
+    bad["n_rejected"] = abs(int(g["n_rejected"]) - int(r.rejected.sum()))
     return bad
 
 
@@ -79,7 +80,7 @@ def compare_fit(g, r):
       |dchi2| / chi2.
     * n_param_over / param_over_sigma: covered tracks with a parameter above
       PARAM_TOL and the largest of those errors in units of the parameter's
-      standard deviation (diagnostic; the bar allows none).
+      standard deviation (reported and bounded apart by the tests).
     * n_not_helix and its errors: fitted tracks with chi2/ndf >= CHI2NDF_FIT
       (mis-merged looper legs, where least squares amplifies rounding).
     * status_mismatch: tracks one side fitted and the other did not;

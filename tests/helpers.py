@@ -91,7 +91,10 @@ def golden_line_cases(path):
             r = np.array([q for q in range(*part["rows"]) if q not in part.get("skip", [])])
             dx = X[r] - X[0]
             rows.append(r)
-            ys.append(part["y0"] + part["a"] * dx)
+            yy = part["y0"] + part["a"] * dx
+            for rr, d in part.get("displace", []):
+                yy[r == rr] += d
+            ys.append(yy)
             zs.append(part["z0"] + part["b"] * dx + part["dz"])
         row = np.concatenate(rows).astype(np.uint8)
         y = np.concatenate(ys)

@@ -21,7 +21,11 @@ def check_golden_case(case, n, trk_start, trk_nhits, trk_kept, tracks):
     np.testing.assert_array_equal(trk_start, exp["start"], err_msg=case["name"])
     np.testing.assert_array_equal(trk_nhits, exp["nhits"], err_msg=case["name"])
     np.testing.assert_array_equal(trk_kept, exp["kept"], err_msg=case["name"])
-    want = [list(range(n))] if case["expect_tracks"] == "all" else case["expect_tracks"]
+    want = case["expect_tracks"]
+    if want == "all":
+        want = [list(range(n))]
+    elif isinstance(want, dict):
+        want = [[i for i in range(n) if i not in want["all_but"]]]
     assert [list(map(int, t)) for t in tracks] == want, case["name"]
 
 
@@ -47,6 +51,8 @@ def test_golden_line_cases(orc):
         r = orc.track(sector, row, y, z, X, n_sectors=1, bz=0.0)
         tracks = [r.track_clusters(t) for t in range(r.n_tracks)]
         check_golden_case(case, y.size, r.trk_start, r.trk_nhits, r.trk_kept, tracks)
+        if "expect_rejected" in case:
+            assert np.nonzero(r.rejected)[0].tolist() == case["expect_rejected"], case["name"]
         if case.get("check_lstsq"):
             top = r.trk_top[0].astype(np.float64)
             assert top[0] == X[151]
