@@ -129,6 +129,8 @@ typedef struct {
                                     unless fewer than 5 owned hits of the tracklet would remain.  A refused
                                     step ends the check of that tracklet.  Bit-exact on any hardware that
                                     rounds each operation. */
+    float looper_qpt_min;        /* looper legs: tracks with |q/pT| >= this (c/GeV, default 5: pT below
+                                    200 MeV/c) are looper-leg candidates (see tpc_tracks.looper_group) */
 } tpc_params;
 
 /* Detector geometry (host memory). */
@@ -180,6 +182,19 @@ typedef struct {
      * (smallest |q/pT|, then the smaller track index) whose tube holds it. */
     uint8_t *cl_flags;                    /* [n] TPC_CL_* flags */
     int32_t *adjacent;                    /* [n] adjacent track index, -1 if not adjacent (nullable) */
+    /* nullable looper legs (paper, sections "Introduction" and "TPC Data Compression": a low-pT particle
+     * leaves several legs; the stage runs when either array, or cl_flags, is set).  Tracks whose
+     * innermost piece has |q/pT| >= looper_qpt_min are candidates; two candidates of one time frame are
+     * legs of one particle when their circles in the transverse plane agree (centre within
+     * 2 s + 2 cm, radius within 2 s + 1 cm, s the combined radius uncertainty from the q/pT variance;
+     * legs known to worse than 5 cm are not grouped), |tan(lambda)| within 0.05, and their z
+     * difference is the helix's z advance over the turning angle between them plus whole turns
+     * (at most 10) within 3 cm + the radius uncertainty's share; all binary32 on the decision path.
+     * With cl_flags, a secondary leg (looper_leg >= 1) is not a good track (the paper's removal
+     * category of secondary legs of loopers below 200 MeV/c). */
+    int32_t *looper_group;                /* [T] smallest track of the legs of one particle, -1 alone */
+    int32_t *looper_leg;                  /* [T] leg number in ascending s z (0 = the earliest leg of the
+                                             drift, s = +1 on the A side, -1 on the C side), -1 alone */
     /* filled on return (host-visible fields of this struct) */
     int32_t n_tracks;
     int32_t n_tracklets;

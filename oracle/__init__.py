@@ -104,7 +104,7 @@ def lib():
         L.orc_free_ptr.argtypes = [C.c_void_p]
         L.orc_free_ptr.restype = None
         L.orc_attach.argtypes = [C.POINTER(OrcGeom), C.c_float, C.c_int32, _PU8, _PU8, _PF, _PF, C.c_int32, _P32,
-                                 _P32, _P32, _P32, _P32, _PF, _P32, C.c_float, C.c_float, _P32, _PU8]
+                                 _P32, _P32, _P32, _P32, _PF, _P32, C.c_float, C.c_float, _P32, _P32, _PU8]
         _lib = L
     return _lib
 
@@ -228,10 +228,12 @@ def track(sector, row, y, zt, row_x, n_sectors=36, z_max=250.0, continuous=False
 CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
 
 
-def attach(sector, row, y, r: OracleResult, row_x, n_sectors=36, bz=0.5, radius=1.5, pt_min=0.05):
+def attach(sector, row, y, r: OracleResult, row_x, n_sectors=36, bz=0.5, radius=1.5, pt_min=0.05,
+           loopers_first=True, frame=None):
     """Cluster attachment of an oracle tracking result: (adjacent track per
     cluster or -1, flags CL_*) -- tubes of ``radius`` cm, tracks below
-    ``pt_min`` GeV/c not good (tpc_oracle_attach.c)."""
+    ``pt_min`` GeV/c not good, nor (loopers_first) the secondary legs of
+    loopers (tpc_oracle_attach.c, tpc_oracle_loopers.c)."""
     L = lib()
     sector = np.ascontiguousarray(sector, np.uint8)
     row = np.ascontiguousarray(row, np.uint8)
@@ -246,19 +248,22 @@ def attach(sector, row, y, r: OracleResult, row_x, n_sectors=36, bz=0.5, radius=
     bot = np.ascontiguousarray(r.trk_bot, np.float32)
     adj = np.empty(max(n, 1), np.int32)
     fl = np.empty(max(n, 1), np.uint8)
+    legs = None
+    if loopers_first:
+        legs = np.ascontiguousarray(loopers(sector, r, n_sectors=n_sectors, bz=bz, frame=frame)[1], np.int32)
     rc = L.orc_attach(C.byref(G), bz, n, _ptr(sector, _PU8), _ptr(row, _PU8), _ptr(y, _PF), _ptr(z, _PF),
                       int(seg_trk.shape[0]), _ptr(seg_trk, _P32), _ptr(seg_next, _P32), _ptr(seg_prev, _P32),
                       _ptr(trk_off, _P32), _ptr(trk_hits, _P32), _ptr(bot, _PF), _ptr(assign, _P32), radius, pt_min,
-                      _ptr(adj, _P32), _ptr(fl, _PU8))
+                      None if legs is None else _ptr(legs, _P32), _ptr(adj, _P32), _ptr(fl, _PU8))
     if rc != 0:
         raise ValueError(f"oracle attachment rejected the input (code {rc})")
     return adj[:n], fl[:n]
 
 
-def attach_event(ev, r: OracleResult, radius=1.5, pt_min=0.05):
+def attach_event(ev, r: OracleResult, radius=1.5, pt_min=0.05, loopers_first=True):
     """attach() on a tpcgen.Event and the oracle's result for it."""
     return attach(ev.sector, ev.row, ev.y, r, ev.row_x, n_sectors=ev.n_sectors, bz=ev.bz, radius=radius,
-                  pt_min=pt_min)
+                  pt_min=pt_min, loopers_first=loopers_first)
 
 
 LOOPER_QPT_MIN = 5.0     # |q/pT| (c/GeV) of a looper-leg candidate: pT below 200 MeV/c

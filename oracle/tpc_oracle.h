@@ -99,8 +99,9 @@ void orc_free(orc_result *r);
 /* Track-based cluster attachment (tpc_oracle_attach.c).  Inputs: the clusters
  * (sector, row, y, z after time -> z) and the tracker's segments as
  * orc_track returns them (seg_trk/next/prev, the tracklet hit lists and
- * inner-end states, assign).  Outputs per cluster: the adjacent track (-1
- * none) and flags ORC_CL_*. */
+ * inner-end states, assign) and optionally (tr_leg, NULL: none) the looper
+ * leg number of each track (orc_loopers).  Outputs per cluster: the adjacent
+ * track (-1 none) and flags ORC_CL_*. */
 #define ORC_CL_ATTACHED  1
 #define ORC_CL_ADJACENT  2
 #define ORC_CL_PROTECTED 4
@@ -110,7 +111,7 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
                const float *y, const float *z, int32_t n_seg, const int32_t *seg_trk,
                const int32_t *seg_next, const int32_t *seg_prev, const int32_t *trk_off,
                const int32_t *trk_hits, const float *trk_bot, const int32_t *assign, float radius,
-               float pt_min, int32_t *adjacent, uint8_t *flags);
+               float pt_min, const int32_t *tr_leg, int32_t *adjacent, uint8_t *flags);
 
 /* Looper-leg identification (tpc_oracle_loopers.c).  Per track: sector and
  * time frame (frame may be NULL) of its innermost piece and that piece's

@@ -30,9 +30,13 @@
  *     to the smaller track index;
  *   - the clusters attached to a good track are protected (they are used for
  *     physics) as well as the clusters in its tube.
- * The other removal categories of the paper (secondary legs of low-pT loopers,
- * high-inclination segments left out of the fit, noise) need looper-leg
- * identification or cluster shapes that this tracker does not produce.
+ *   - a secondary leg of a looper (tr_leg >= 1: a later leg of a particle
+ *     below 200 MeV/c, tpc_oracle_loopers.c) is not a good track: its
+ *     clusters are removed unless a good track protects them (the paper's
+ *     category of secondary legs of low-pT loopers).
+ * The remaining categories of the paper (high-inclination segments left out
+ * of the fit, noise and broken pads) need cluster shapes and pad data that the
+ * inputs do not carry.
  *
  * Pins (tests/test_oracle_attach.py): the traced points against the closed-
  * form helix in binary64, the tube membership and the adjacency against a
@@ -152,7 +156,7 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
                const float *y, const float *z, int32_t n_seg, const int32_t *seg_trk,
                const int32_t *seg_next, const int32_t *seg_prev, const int32_t *trk_off,
                const int32_t *trk_hits, const float *trk_bot, const int32_t *assign, float radius,
-               float pt_min, int32_t *adjacent, uint8_t *flags)
+               float pt_min, const int32_t *tr_leg, int32_t *adjacent, uint8_t *flags)
 {
     const int NR = G->n_rows, NP = G->n_sectors * G->n_rows;
     const float *Xr = G->row_x;
@@ -173,8 +177,10 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
     }
     /* pT of each track: |q/pT| of its innermost piece's inner-end state */
     float *tr_aq = (float *)malloc(sizeof(float) * (size_t)(n_tracks > 0 ? n_tracks : 1));
+    uint8_t *tr_good = (uint8_t *)malloc((size_t)(n_tracks > 0 ? n_tracks : 1));
     for (int a = 0; a < n_seg; a++)
         if (seg_prev[a] < 0) tr_aq[seg_track[a]] = fabsf(trk_bot[(size_t)seg_trk[a] * A_NST + 5]);
+    for (int t = 0; t < n_tracks; t++) tr_good[t] = tr_aq[t] <= qmax && !(tr_leg && tr_leg[t] >= 1);
 
     /* clusters of each (sector, row) plane sorted by z */
     plane_index X;
@@ -206,7 +212,7 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
         int s = sector[hits[0]];
         int r_lo = row[hits[0]], r_hi = row[hits[nh - 1]];   /* hits ascend in row */
         float aq = tr_aq[tr];
-        int good = aq <= qmax;
+        int good = tr_good[tr];
         uint64_t key = ((uint64_t)(0xFFFFFFFFu - fbits(aq)) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)tr);
         const float *b = trk_bot + (size_t)t * A_NST;
         /* the row of the inner-end state */
@@ -232,13 +238,13 @@ int orc_attach(const orc_geom *G, float bz, int32_t n, const uint8_t *sector, co
     for (int c = 0; c < n; c++) {
         int att = assign[c] >= 0;
         int adj = !att && T.key[c] != 0;
-        int prot = T.prot[c] || (att && tr_aq[assign[c]] <= qmax);
+        int prot = T.prot[c] || (att && tr_good[assign[c]]);
         int rem = (att || adj) && !prot;
         flags[c] = (uint8_t)(att | (adj << 1) | (prot << 2) | (rem << 3));
         adjacent[c] = adj ? (int32_t)(0xFFFFFFFFu - (uint32_t)(T.key[c] & 0xFFFFFFFFu)) : -1;
     }
     free(T.key); free(T.prot);
     free(X.ord); free(X.pstart); free(X.zs); free(pl);
-    free(tr_aq); free(seg_track); free(seg_head);
+    free(tr_aq); free(tr_good); free(seg_track); free(seg_head);
     return 0;
 }

@@ -27,9 +27,18 @@
  *       |R_i - R_j| < 2 s + 1 cm, |C_i - C_j|^2 < (2 s + 2 cm)^2,
  *       | |tl_i| - |tl_j| | < 0.05, |z_j - z_i| <= z_max,
  *     and, with the turning angle dpsi = atan2(cross, dot) of P_i - C_i
- *     and P_j - C_i and a = (a_i + a_j)/2, for sigma = +1 or -1:
+ *     and P_j - C_i (counter-clockwise positive), a = (a_i + a_j)/2 and
+ *     the sense sigma of the z advance (below):
  *       w = sigma (z_j - z_i) - a dpsi,  m = clamp(rint(w / (2 pi a)), -10, 10),
- *       |w - 2 pi a m| < 3 cm + |tl| (|dpsi| + 2 pi |m|) 2 s
+ *       |w - 2 pi a m| < 3 cm + |tl| (|dpsi| + 2 pi |m|) 2 s;
+ *   - the sense: along the motion z advances by tan(lambda) R per radian
+ *     the particle turns, and the turning sense is the sign of the
+ *     curvature, so z advances by sigma a per radian of counter-clockwise
+ *     turning with sigma = sign(k tan(lambda)); the tracker fits an inward
+ *     leg in the direction of increasing x, which flips both k and
+ *     tan(lambda), so sigma is the same on every leg of a particle.  Two
+ *     candidates need the same sigma when both |tan(lambda)| >= 0.02; below
+ *     that (z nearly constant along the helix) either sense is tried;
  *     (legs of one helix differ in z by the advance over the turning angle
  *     between them, plus whole turns; a looper makes at most 10 turns, its
  *     legs lie on one side of the drift volume);
@@ -55,6 +64,7 @@
 #define LOOP_SRMAX 5.0f     /* legs with a radius uncertainty above this are not grouped (cm) */
 #define LOOP_DTGL 0.05f
 #define LOOP_DZ 3.0f
+#define LOOP_TLSENSE 0.02f  /* both |tan(lambda)| above this: the z-advance senses must agree */
 #define LOOP_TURNS 10.0f
 #define PI_F 3.14159265358979323846f
 #define TWO_PI_F 6.28318530717958647692f
@@ -107,7 +117,7 @@ float orc_atan2_own(float y, float x) { return atan2_own(y, x); }
 typedef struct {
     int idx;
     float R, sr, cx, cy, px, py, z, tl, a, sz;
-    int frame;
+    int frame, sense;
 } cand_t;
 
 static int find_root(int32_t *par, int i)
@@ -161,6 +171,7 @@ int orc_loopers(int32_t n_sectors, float z_max, float bz, float qpt_min, int32_t
         e->py = fmaf(s[0], sn, s[1] * cs);
         e->z = s[2];
         e->tl = fabsf(s[4]);
+        e->sense = k * s[4] >= 0.0f ? 1 : -1;
         e->a = e->tl * e->R;
         float side = (n_sectors == 36 && sector[t] >= 18) ? -1.0f : 1.0f;
         e->sz = side * s[2];
@@ -187,10 +198,14 @@ int orc_loopers(int32_t n_sectors, float z_max, float bz, float qpt_min, int32_t
             float a = 0.5f * (A->a + B->a);
             float tl = 0.5f * (A->tl + B->tl);
             float tpa = TWO_PI_F * a;
+            int steep = A->tl >= LOOP_TLSENSE && B->tl >= LOOP_TLSENSE;
+            if (steep && A->sense != B->sense) continue;
             int ok = 0;
             for (int sg = 0; sg < 2 && !ok; sg++) {
+                int sense = sg == 0 ? A->sense : -A->sense;
+                if (steep && sg == 1) break;
                 float dz = B->z - A->z;
-                float w = (sg == 0 ? dz : -dz) - a * dpsi;
+                float w = (sense > 0 ? dz : -dz) - a * dpsi;
                 float m = tpa > 0.0f ? rintf(w / tpa) : 0.0f;
                 m = fminf(fmaxf(m, -LOOP_TURNS), LOOP_TURNS);
                 float res = fmaf(-tpa, m, w);

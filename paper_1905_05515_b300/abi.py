@@ -32,7 +32,8 @@ class TpcParams(C.Structure):
                 ("max_z_cells", C.c_int32), ("y_bins", C.c_int32), ("tracklets_per_1k", C.c_int32),
                 ("queue_blocks_per_sm", C.c_int32), ("fp64_final", C.c_int32),
                 ("profile", C.c_int32), ("packed_links", C.c_int32), ("merge_pairs_per_1k", C.c_int32),
-                ("tube_radius", C.c_float), ("pt_min_physics", C.c_float), ("outlier_chi2", C.c_float)]
+                ("tube_radius", C.c_float), ("pt_min_physics", C.c_float), ("outlier_chi2", C.c_float),
+                ("looper_qpt_min", C.c_float)]
 
 
 class TpcGeometry(C.Structure):
@@ -55,6 +56,7 @@ class TpcTracks(C.Structure):
                 ("z", C.c_void_p), ("link_up_raw", C.c_void_p), ("link_dn_raw", C.c_void_p),
                 ("link_up", C.c_void_p), ("link_dn", C.c_void_p), ("is_start", C.c_void_p),
                 ("cl_flags", C.c_void_p), ("adjacent", C.c_void_p),
+                ("looper_group", C.c_void_p), ("looper_leg", C.c_void_p),
                 ("n_tracks", C.c_int32), ("n_tracklets", C.c_int32), ("n_segments", C.c_int32),
                 ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64),
                 ("n_launches", C.c_int32), ("stage_ms", C.c_float * 10), ("work", C.c_int64 * 5),

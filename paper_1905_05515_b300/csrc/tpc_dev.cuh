@@ -251,6 +251,7 @@ struct Frame {
     int trk_next2;
     int n_mpairs;                  // merger: candidate pairs that passed the screen
     int n_rejected;                // clusters rejected before the refit
+    int n_loop_err;                // looper legs: a bounded union-find walk gave up (never expected)
     // work counters (params.profile): tracklet propagations, updates, window
     // candidates examined; refit propagations; merger chi2 evaluations
     unsigned long long w_prop, w_upd, w_cand, w_refit_prop, w_merge;

@@ -61,6 +61,7 @@ struct Layout {
     size_t bnext, bprev, snext, sprev, bad, next2, prev2, mpair, mpc2, bestA, bestB;
     int64_t mpcap;              // merger pair list capacity
     size_t headmark, tcount, thead, ttail, tcl, lencnt, order, aprot, acur;
+    size_t lcand, lpar, lcnt, llist, lgrp, lleg, lbin, lsorted, lcur, tgood;   // looper legs, track goodness
     size_t total;
 };
 
@@ -77,6 +78,7 @@ int64_t scan_aux_elems(int64_t n)
 // y-bins per z-cell (the searches visit whatever bins a window overlaps, so
 // any count works; the grid grows with it)
 constexpr int MAX_YBINS = 64;
+constexpr int LOOP_NBIN = 256;          // looper candidates: radius bins of LOOP_BINW cm per frame
 int effective_ybins(const tpc_params* p, const tpc_geometry*) { return std::max(1, std::min(p->y_bins, MAX_YBINS)); }
 
 // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r],
@@ -199,6 +201,18 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
     L.order = take(4 * T);      // refit order
     L.aprot = take(N);          // cluster attachment: inside a good track's tube
     L.acur = take(4 * ((size_t)nframes * L.np * PSPLIT + 1));   // cluster attachment: bucket fill cursors
+    // looper legs: candidate records, union-find parents, group counts and
+    // member lists, group / leg scratch, radius-bin counts and order
+    L.lcand = take(48 * T);
+    L.lpar = take(4 * T);
+    L.lcnt = take(4 * (T + 1));
+    L.llist = take(4 * T);
+    L.lgrp = take(4 * T);
+    L.lleg = take(4 * T);
+    L.lbin = take(4 * ((size_t)nframes * LOOP_NBIN + 1));
+    L.lsorted = take(4 * T);
+    L.lcur = take(4 * (std::max<int64_t>(T, (int64_t)nframes * LOOP_NBIN) + 1));   // fill cursors
+    L.tgood = take(T);          // cluster attachment: good tracks
     L.total = o;
     return L;
 }
@@ -1828,6 +1842,7 @@ struct AttachArgs {
     uint8_t* aprot;             // [n] inside the tube of a good track
     uint8_t* flags;
     int32_t* adjacent;
+    const uint8_t* tgood;       // [tracks] good: pT cut passed and not a secondary looper leg
 };
 
 __device__ __forceinline__ float track_abs_qpt(const AttachArgs& A, int tr)
@@ -1889,15 +1904,16 @@ __device__ __forceinline__ bool seg_info(const AttachArgs& A, int b, SegInfo& I)
     I.r_lo = pl - I.s * A.nr;
     I.r_hi = (int)(sc_plane(A.sc[trk_hit(slot, A.nr, nh, nup, nh - 1)]) % (uint32_t)A.np) - I.s * A.nr;
     const float aq = track_abs_qpt(A, tr);
-    I.good = aq <= A.qmax;
+    I.good = A.tgood[tr] != 0;
     I.key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(aq)) << 32) |
             (unsigned long long)(0xFFFFFFFFu - (uint32_t)tr);
     return true;
 }
 
-__device__ __forceinline__ bool key_good(unsigned long long key, float qmax)
+// the track of an adjacency key is its low word (0xFFFFFFFF - track)
+__device__ __forceinline__ bool key_good(const AttachArgs& A, unsigned long long key)
 {
-    return __uint_as_float(0xFFFFFFFFu - (uint32_t)(key >> 32)) <= qmax;
+    return A.tgood[0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)] != 0;
 }
 
 // per segment: +1 at the plane of its lowest row, -1 past its highest (a
@@ -2097,7 +2113,307 @@ __global__ void k_attach_visit(AttachArgs A, const uint32_t* __restrict__ start,
         const int pl = (int)(gp - (uint32_t)fr * A.np);
         const int s = pl / A.nr;
         const float2 pt = pts[q];
-        tube_visit(A, A.fg[fr], s, pl - s * A.nr, pt.x, pt.y, key, key_good(key, A.qmax));
+        tube_visit(A, A.fg[fr], s, pl - s * A.nr, pt.x, pt.y, key, key_good(A, key));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Looper legs (sections "Introduction" and "TPC Data Compression": a low-pT
+// particle leaves several legs; the secondary legs of loopers below
+// 200 MeV/c are removable).  In continuous read-out every leg of a particle
+// carries the drift offset of its collision, so in the tracker's coordinates
+// its legs lie on one helix.  All binary32 on the decision path:
+//   - candidate: |q/pT| >= qmin of the inner-end state of the track's
+//     innermost piece; circle: k = kb q/pT, local centre (x - sinphi/k,
+//     y + cosphi/k) and point (x, y) rotated by the sector angle, radius
+//     R = 1/|k| known to s_R = R sqrt(C_qq)/|q/pT| (legs above LOOP_SRMAX are
+//     not grouped); a = |tanl| R, the z advance per radian; sense = sign of
+//     k tanl (the same on every leg: the tracker fits an inward leg in the
+//     direction of increasing x, which flips k and tanl together);
+//   - candidates i < j of one frame are legs of one particle when, with
+//     s = sqrt(s_Ri^2 + s_Rj^2): |R_i - R_j| < 2s + 1, |C_i - C_j| < 2s + 2,
+//     | |tanl_i| - |tanl_j| | < 0.05, |z_j - z_i| <= z_max, equal senses
+//     when both |tanl| >= 0.02 (else either sense is tried), and the z
+//     difference matches the advance over the turning angle dpsi between
+//     the points (own arctangent) plus whole turns (|m| <= 10):
+//     |w - 2 pi a m| < 3 + |tanl| (|dpsi| + 2 pi |m|) 2s, w = sense dz - a dpsi;
+//   - groups: connected components (union-find, the larger root linked under
+//     the smaller, so a group's root is its smallest track); legs numbered in
+//     ascending s z (the earliest leg of the drift first), ties by track.
+// ---------------------------------------------------------------------------
+struct LoopCand {
+    float R, sr, cx, cy, px, py, z, tl, a, sz;
+    int sense, frame;       // frame -1: not a candidate
+};
+static_assert(sizeof(LoopCand) == 48, "LoopCand layout");
+
+constexpr float LOOP_BINW = 4.0f;
+constexpr int LOOP_WBINS = 4;           // 2 sqrt(2) LOOP_SRMAX + LOOP_DR < LOOP_WBINS * LOOP_BINW
+constexpr float LOOP_SRMAX = 5.0f;
+constexpr float LOOP_DR = 1.0f;
+constexpr float LOOP_DC = 2.0f;
+constexpr float LOOP_NSIG = 2.0f;
+constexpr float LOOP_DTGL = 0.05f;
+constexpr float LOOP_DZ = 3.0f;
+constexpr float LOOP_TLSENSE = 0.02f;
+constexpr float LOOP_TURNS = 10.0f;
+constexpr float PI_F = 3.14159265358979323846f;
+constexpr float TWO_PI_F = 6.28318530717958647692f;
+constexpr float HALF_PI_F = 1.57079632679489661923f;
+constexpr int UF_MAX_STEPS = 1 << 20;
+
+// cos and sin of the sector angles (s mod 18) * 20 + 10 degrees
+__constant__ float c_sec_cos[18] = {
+    0.98480775301220805936f, 0.86602540378443864676f, 0.64278760968653932632f, 0.34202014332566873304f,
+    0.0f, -0.34202014332566873304f, -0.64278760968653932632f, -0.86602540378443864676f,
+    -0.98480775301220805936f, -0.98480775301220805936f, -0.86602540378443864676f, -0.64278760968653932632f,
+    -0.34202014332566873304f, 0.0f, 0.34202014332566873304f, 0.64278760968653932632f,
+    0.86602540378443864676f, 0.98480775301220805936f};
+__constant__ float c_sec_sin[18] = {
+    0.17364817766693034885f, 0.5f, 0.76604444311897803520f, 0.93969262078590838405f,
+    1.0f, 0.93969262078590838405f, 0.76604444311897803520f, 0.5f,
+    0.17364817766693034885f, -0.17364817766693034885f, -0.5f, -0.76604444311897803520f,
+    -0.93969262078590838405f, -1.0f, -0.93969262078590838405f, -0.76604444311897803520f,
+    -0.5f, -0.17364817766693034885f};
+
+// atan(x), |x| <= 1: two half-angle reductions atan(x) = 2 atan(x / (1 +
+// sqrt(1 + x^2))) bring the argument below tan(pi/16), where the Maclaurin
+// series of atan to x^15 is exact in binary32 (next term < 1e-13)
+__device__ __forceinline__ float atan_unit(float x)
+{
+    const float x1 = __fdiv_rn(x, 1.0f + __fsqrt_rn(__fmaf_rn(x, x, 1.0f)));
+    const float x2 = __fdiv_rn(x1, 1.0f + __fsqrt_rn(__fmaf_rn(x1, x1, 1.0f)));
+    const float t2 = x2 * x2;
+    float p = __fmaf_rn(t2, -0.066666666666666666667f, 0.076923076923076923077f);
+    p = __fmaf_rn(t2, p, -0.090909090909090909091f);
+    p = __fmaf_rn(t2, p, 0.11111111111111111111f);
+    p = __fmaf_rn(t2, p, -0.14285714285714285714f);
+    p = __fmaf_rn(t2, p, 0.2f);
+    p = __fmaf_rn(t2, p, -0.33333333333333333333f);
+    const float a = __fmaf_rn(x2 * t2, p, x2);
+    return 4.0f * a;
+}
+
+__device__ __forceinline__ float atan2_own(float y, float x)
+{
+    if (x == 0.0f && y == 0.0f) return 0.0f;
+    if (fabsf(y) <= fabsf(x)) {
+        float a = atan_unit(__fdiv_rn(y, x));
+        if (x < 0.0f) a = y >= 0.0f ? a + PI_F : a - PI_F;
+        return a;
+    }
+    const float a = atan_unit(__fdiv_rn(x, y));
+    return (y > 0.0f ? HALF_PI_F : -HALF_PI_F) - a;
+}
+
+struct LoopArgs {
+    const Frame* f;
+    int ns, nr, np, nfr, cap;
+    float kb, qmin, zmax;
+    const int32_t* seg;
+    const int32_t* thead;
+    const int32_t* t_start;
+    const float* t_bot;
+    const float4* sc;
+    LoopCand* cand;
+    int32_t* par;
+    uint32_t* bincnt;       // [nfr * LOOP_NBIN + 1]
+    int32_t* sorted;        // candidates in (frame, bin) order
+    uint32_t* gcnt;         // [cap + 1] members per root, then scanned
+    int32_t* glist;
+    int32_t* group;
+    int32_t* leg;
+    int* err;
+};
+
+__device__ __forceinline__ int loop_bin(const LoopCand& c)
+{
+    return c.frame * LOOP_NBIN + min((int)(c.R * (1.0f / LOOP_BINW)), LOOP_NBIN - 1);
+}
+
+// per track: its candidate record (or none), group and leg -1
+__global__ void k_loop_cand(LoopArgs A)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        A.group[r] = -1;
+        A.leg[r] = -1;
+        A.par[r] = r;
+        LoopCand e;
+        e.frame = -1;
+        const int t = A.seg[A.thead[r]];
+        const float* s = A.t_bot + (int64_t)t * NST;
+        const float q = s[5];
+        if (fabsf(q) >= A.qmin) {
+            const float k = A.kb * q;
+            const float sp = s[3];
+            const float cp = __fsqrt_rn((1.0f - sp) * (1.0f + sp));
+            const float ik = __fdiv_rn(1.0f, k);
+            const float lx = s[0] - sp * ik, ly = __fmaf_rn(cp, ik, s[1]);
+            const uint32_t pg = sc_plane(A.sc[A.t_start[t]]);
+            const int fr = (int)(pg / (uint32_t)A.np);
+            const int sec = (int)(pg - (uint32_t)fr * A.np) / A.nr;
+            const int w = A.ns == 1 ? 0 : sec % 18;
+            const float cs = c_sec_cos[w], sn = c_sec_sin[w];
+            e.R = fabsf(ik);
+            e.sr = e.R * __fdiv_rn(__fsqrt_rn(s[6 + 14]), fabsf(q));
+            e.cx = __fmaf_rn(lx, cs, -(ly * sn));
+            e.cy = __fmaf_rn(lx, sn, ly * cs);
+            e.px = __fmaf_rn(s[0], cs, -(s[1] * sn));
+            e.py = __fmaf_rn(s[0], sn, s[1] * cs);
+            e.z = s[2];
+            e.tl = fabsf(s[4]);
+            e.a = e.tl * e.R;
+            e.sense = k * s[4] >= 0.0f ? 1 : -1;
+            const float side = (A.ns == 36 && sec >= 18) ? -1.0f : 1.0f;
+            e.sz = side * s[2];
+            if (e.sr <= LOOP_SRMAX) {
+                e.frame = fr;
+                atomicAdd(&A.bincnt[loop_bin(e)], 1u);
+            }
+        }
+        A.cand[r] = e;
+    }
+}
+
+__global__ void k_loop_sort(LoopArgs A, uint32_t* __restrict__ cursor)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const LoopCand e = A.cand[r];
+        if (e.frame >= 0) A.sorted[atomicAdd(&cursor[loop_bin(e)], 1u)] = r;
+    }
+}
+
+__device__ __forceinline__ bool loop_pair(const LoopCand& A, const LoopCand& B, float zmax)
+{
+    const float tsg = LOOP_NSIG * __fsqrt_rn(__fmaf_rn(A.sr, A.sr, B.sr * B.sr));
+    if (!(fabsf(A.R - B.R) < tsg + LOOP_DR)) return false;
+    const float dx = B.cx - A.cx, dy = B.cy - A.cy;
+    const float dc = tsg + LOOP_DC;
+    if (!(__fmaf_rn(dx, dx, dy * dy) < dc * dc)) return false;
+    if (!(fabsf(A.tl - B.tl) < LOOP_DTGL)) return false;
+    if (!(fabsf(B.z - A.z) <= zmax)) return false;
+    const float ux = A.px - A.cx, uy = A.py - A.cy;
+    const float vx = B.px - A.cx, vy = B.py - A.cy;
+    const float cr = __fmaf_rn(ux, vy, -(uy * vx));
+    const float dt = __fmaf_rn(ux, vx, uy * vy);
+    const float dpsi = atan2_own(cr, dt);
+    const float a = 0.5f * (A.a + B.a);
+    const float tl = 0.5f * (A.tl + B.tl);
+    const float tpa = TWO_PI_F * a;
+    const bool steep = A.tl >= LOOP_TLSENSE && B.tl >= LOOP_TLSENSE;
+    if (steep && A.sense != B.sense) return false;
+    for (int sg = 0; sg < 2; sg++) {
+        if (steep && sg == 1) break;
+        const int sense = sg == 0 ? A.sense : -A.sense;
+        const float dz = B.z - A.z;
+        const float w = (sense > 0 ? dz : -dz) - a * dpsi;
+        float m = tpa > 0.0f ? rintf(__fdiv_rn(w, tpa)) : 0.0f;
+        m = fminf(fmaxf(m, -LOOP_TURNS), LOOP_TURNS);
+        const float res = __fmaf_rn(-tpa, m, w);
+        const float turn = __fmaf_rn(TWO_PI_F, fabsf(m), fabsf(dpsi));
+        const float tol = __fmaf_rn(tl * turn, tsg, LOOP_DZ);
+        if (fabsf(res) < tol) return true;
+    }
+    return false;
+}
+
+// union-find on the track indices: roots only ever move to smaller indices,
+// so every walk ends; the step counts are bounded all the same
+__device__ __forceinline__ int uf_find(int32_t* par, int x, int* err)
+{
+    for (int it = 0; it < UF_MAX_STEPS; it++) {
+        const int p = atomicAdd(&par[x], 0);
+        if (p == x) return x;
+        x = p;
+    }
+    atomicExch(err, 1);
+    return x;
+}
+
+__device__ __forceinline__ void uf_union(int32_t* par, int a, int b, int* err)
+{
+    for (int it = 0; it < UF_MAX_STEPS; it++) {
+        a = uf_find(par, a, err);
+        b = uf_find(par, b, err);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(&par[b], b, a);
+        if (old == b) return;
+        b = old;
+    }
+    atomicExch(err, 1);
+}
+
+// one thread per candidate: the candidates of its frame in the radius bins
+// within the tolerance, each unordered pair tested once (i < j)
+__global__ void k_loop_pairs(LoopArgs A)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        const LoopCand a = A.cand[i];
+        if (a.frame < 0) continue;
+        const int b0 = loop_bin(a);
+        const int lo = max(b0 - LOOP_WBINS, a.frame * LOOP_NBIN);
+        const int hi = min(b0 + LOOP_WBINS, a.frame * LOOP_NBIN + LOOP_NBIN - 1);
+        for (uint32_t q = A.bincnt[lo]; q < A.bincnt[hi + 1]; q++) {
+            const int j = A.sorted[q];
+            if (j <= i) continue;
+            if (loop_pair(a, A.cand[j], A.zmax)) uf_union(A.par, i, j, A.err);
+        }
+    }
+}
+
+__global__ void k_loop_count(LoopArgs A)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x)
+        if (A.cand[r].frame >= 0) atomicAdd(&A.gcnt[uf_find(A.par, r, A.err)], 1u);
+}
+
+// members listed by root (gcnt scanned: the root's first slot; gcnt[root + 1]
+// - gcnt[root] its size); cursor = a copy of the scanned counts
+__global__ void k_loop_list(LoopArgs A, uint32_t* __restrict__ cursor)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x)
+        if (A.cand[r].frame >= 0) A.glist[atomicAdd(&cursor[uf_find(A.par, r, A.err)], 1u)] = r;
+}
+
+__global__ void k_loop_legs(LoopArgs A)
+{
+    const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const LoopCand e = A.cand[r];
+        if (e.frame < 0) continue;
+        const int root = uf_find(A.par, r, A.err);
+        const uint32_t b = A.gcnt[root], en = A.gcnt[root + 1];
+        if (en - b < 2) continue;
+        int rank = 0;
+        for (uint32_t q = b; q < en; q++) {
+            const int j = A.glist[q];
+            const float szj = A.cand[j].sz;
+            rank += szj < e.sz || (szj == e.sz && j < r);
+        }
+        A.group[r] = root;
+        A.leg[r] = rank;
+    }
+}
+
+// good tracks of the attachment: the pT cut passed and not a secondary leg
+__global__ void k_track_good(const Frame* __restrict__ f, int cap, const int32_t* __restrict__ seg,
+                             const int32_t* __restrict__ thead, const float* __restrict__ t_bot, float qmax,
+                             const int32_t* __restrict__ leg, uint8_t* __restrict__ good)
+{
+    const int T = f->err ? 0 : min(f->n_tracks, cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const float aq = fabsf(t_bot[(int64_t)seg[thead[r]] * NST + 5]);
+        good[r] = (aq <= qmax && !(leg && leg[r] >= 1)) ? 1 : 0;
     }
 }
 
@@ -2110,7 +2426,7 @@ __global__ void k_attach_flags(AttachArgs A)
         const unsigned long long key = A.akey[c];
         const bool att = a >= 0;
         const bool adj = !att && key != 0ull;
-        const bool prot = A.aprot[c] != 0 || (att && track_abs_qpt(A, a) <= A.qmax);
+        const bool prot = A.aprot[c] != 0 || (att && A.tgood[a] != 0);
         const bool rem = (att || adj) && !prot;
         A.flags[c] = (uint8_t)((att ? TPC_CL_ATTACHED : 0) | (adj ? TPC_CL_ADJACENT : 0) |
                                (prot ? TPC_CL_PROTECTED : 0) | (rem ? TPC_CL_REMOVE : 0));
@@ -2499,6 +2815,41 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                          out->link_dn, out->is_start, f);
         g_launches++;
     }
+    // optional: looper legs (also needed by the cluster attachment)
+    int32_t* lleg = nullptr;
+    if (out->looper_group || out->looper_leg || out->cl_flags) {
+        LoopArgs LA;
+        LA.f = f; LA.ns = g->n_sectors; LA.nr = g->n_rows; LA.np = L.np; LA.nfr = NF;
+        LA.cap = std::min(out->capacity_tracks, ntcap);
+        LA.kb = kb; LA.qmin = p->looper_qpt_min; LA.zmax = g->z_max;
+        LA.seg = seg; LA.thead = AA.thead; LA.t_start = TA.t_start; LA.t_bot = TA.t_bot; LA.sc = sc;
+        LA.cand = at<LoopCand>(ws, L.lcand);
+        LA.par = at<int32_t>(ws, L.lpar);
+        LA.bincnt = at<uint32_t>(ws, L.lbin);
+        LA.sorted = at<int32_t>(ws, L.lsorted);
+        LA.gcnt = at<uint32_t>(ws, L.lcnt);
+        LA.glist = at<int32_t>(ws, L.llist);
+        LA.group = out->looper_group ? out->looper_group : at<int32_t>(ws, L.lgrp);
+        LA.leg = out->looper_leg ? out->looper_leg : at<int32_t>(ws, L.lleg);
+        LA.err = &f->n_loop_err;
+        const size_t nbins = (size_t)NF * LOOP_NBIN;
+        uint32_t* cursor = at<uint32_t>(ws, L.lcur);
+        CK(cudaMemsetAsync(LA.bincnt, 0, 4 * (nbins + 1), st));
+        CK(cudaMemsetAsync(LA.gcnt, 0, 4 * ((size_t)ntcap + 1), st));
+        const int gl = grid_for(LA.cap, B);
+        k_loop_cand<<<gl, B, 0, st>>>(LA);
+        scan_u32(LA.bincnt, (int64_t)nbins, aux, st);
+        CK(cudaMemcpyAsync(cursor, LA.bincnt, 4 * (nbins + 1), cudaMemcpyDeviceToDevice, st));
+        k_loop_sort<<<gl, B, 0, st>>>(LA, cursor);
+        k_loop_pairs<<<gl, B, 0, st>>>(LA);
+        k_loop_count<<<gl, B, 0, st>>>(LA);
+        scan_u32(LA.gcnt, ntcap, aux, st);
+        CK(cudaMemcpyAsync(cursor, LA.gcnt, 4 * ((size_t)ntcap + 1), cudaMemcpyDeviceToDevice, st));
+        k_loop_list<<<gl, B, 0, st>>>(LA, cursor);
+        k_loop_legs<<<gl, B, 0, st>>>(LA);
+        g_launches += 6;
+        lleg = LA.leg;
+    }
     // optional: track-based cluster attachment (after the exports above: it
     // reuses the link arrays and the refit's cluster buffer)
     if (out->cl_flags) {
@@ -2516,6 +2867,10 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
         AT.akey = at<unsigned long long>(ws, L.hitw);     // the selector's hit weights are dead by now
         AT.aprot = at<uint8_t>(ws, L.aprot);
         AT.flags = out->cl_flags; AT.adjacent = out->adjacent;
+        AT.tgood = at<uint8_t>(ws, L.tgood);
+        k_track_good<<<grid_for(std::min(out->capacity_tracks, ntcap), B), B, 0, st>>>(
+            f, std::min(out->capacity_tracks, ntcap), seg, AA.thead, TA.t_bot, AT.qmax, lleg, at<uint8_t>(ws, L.tgood));
+        g_launches++;
         CK(cudaMemsetAsync(AT.akey, 0, 8 * (size_t)n, st));
         CK(cudaMemsetAsync(AT.aprot, 0, (size_t)n, st));
         // plane buckets: counts in the binning's plane starts (free by now),
@@ -2676,6 +3031,7 @@ int tpc_params_default(tpc_params* p)
     p->tube_radius = 1.5f;
     p->pt_min_physics = 0.05f;
     p->outlier_chi2 = 25.0f;
+    p->looper_qpt_min = 5.0f;
     return TPC_OK;
 }
 

@@ -40,6 +40,8 @@ class TrackResult:
     is_start: torch.Tensor | None = None
     cl_flags: torch.Tensor | None = None      # [n] uint8 CL_* flags (attach=True)
     adjacent: torch.Tensor | None = None      # [n] int32 adjacent track or -1 (attach=True)
+    looper_group: torch.Tensor | None = None  # [T] int32 smallest track of the legs of one particle, -1 alone
+    looper_leg: torch.Tensor | None = None    # [T] int32 leg number (0 = earliest in drift), -1 alone
     n_tracklets: int = 0
     n_segments: int = 0
     n_launches: int = 0
@@ -53,7 +55,7 @@ class Tracker:
 
     def __init__(self, n_max: int, row_x, n_sectors: int = 36, z_max: float = 250.0, continuous: bool = False,
                  params: abi.TpcParams | None = None, device="cuda", capacity_tracks: int | None = None,
-                 debug: bool = False, n_frames: int = 1, attach: bool = False):
+                 debug: bool = False, n_frames: int = 1, attach: bool = False, loopers: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("the TPC tracker needs a CUDA device")
         self.lib = abi.lib()
@@ -93,10 +95,14 @@ class Tracker:
         if attach:      # track-based cluster attachment (params.tube_radius, params.pt_min_physics)
             self.buf["cl_flags"] = torch.empty(n1, dtype=torch.uint8, device=d)
             self.buf["adjacent"] = torch.empty(n1, dtype=torch.int32, device=d)
+        if loopers:     # looper-leg groups and leg numbers per track (params.looper_qpt_min)
+            self.buf["looper_group"] = torch.empty(cap_t, dtype=torch.int32, device=d)
+            self.buf["looper_leg"] = torch.empty(cap_t, dtype=torch.int32, device=d)
         self.capacity_tracks = cap_t
         self.capacity_clusters = cap_c
         self.debug = debug
         self.attach = attach
+        self.loopers = loopers
 
     def _tracks_struct(self) -> abi.TpcTracks:
         b = self.buf
@@ -105,7 +111,7 @@ class Tracker:
         t.capacity_clusters = self.capacity_clusters
         for k in ("sector", "x", "param", "cov", "chi2", "ndf", "status", "nclus", "clus_offset", "clus_index",
                   "assign", "frame", "cov64", "chi2_64", "z", "link_up_raw", "link_dn_raw", "link_up", "link_dn",
-                  "is_start", "cl_flags", "adjacent"):
+                  "is_start", "cl_flags", "adjacent", "looper_group", "looper_leg"):
             setattr(t, k, b[k].data_ptr() if k in b else None)
         return t
 
@@ -137,6 +143,8 @@ class Tracker:
             res.cov64, res.chi2_64 = b["cov64"][:T], b["chi2_64"][:T]
         if self.attach:
             res.cl_flags, res.adjacent = b["cl_flags"][:n], b["adjacent"][:n]
+        if self.loopers:
+            res.looper_group, res.looper_leg = b["looper_group"][:T], b["looper_leg"][:T]
         if self.debug:
             res.z = b["z"][:n]
             res.link_up_raw, res.link_dn_raw = b["link_up_raw"][:n], b["link_dn_raw"][:n]

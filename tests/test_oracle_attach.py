@@ -190,21 +190,23 @@ def test_flags_follow_their_definitions():
 
 
 def test_special_cases():
+    """Without the looper-leg category (loopers_first=False) the special
+    cases of the tube radius and the momentum cut."""
     ev = tpcgen.time_frame(seed=9, n_collisions=2, mult_mean=400)
     r = oracle.track_event(ev)
     att = r.assign >= 0
     # a tube of radius 0 holds nothing: no adjacency, protection only by attachment
-    adj, fl = oracle.attach_event(ev, r, radius=0.0, pt_min=0.05)
+    adj, fl = oracle.attach_event(ev, r, radius=0.0, pt_min=0.05, loopers_first=False)
     assert (adj == -1).all() and not (fl & oracle.CL_ADJACENT).any()
     segs, head_q = _segments(ev, r)
     good_att = att & (head_q[np.maximum(r.assign, 0)] <= np.float32(1.0) / np.float32(0.05))
     assert np.array_equal((fl & oracle.CL_PROTECTED) > 0, good_att)
     # pt_min = 0: every track is good, nothing is removed, adjacent clusters are protected
-    adj, fl = oracle.attach_event(ev, r, radius=1.5, pt_min=0.0)
+    adj, fl = oracle.attach_event(ev, r, radius=1.5, pt_min=0.0, loopers_first=False)
     assert not (fl & oracle.CL_REMOVE).any()
     assert ((fl & oracle.CL_PROTECTED) > 0)[(fl & (oracle.CL_ATTACHED | oracle.CL_ADJACENT)) > 0].all()
     # an unreachable pt_min: no track is good, every attached or adjacent cluster is removed
-    adj, fl = oracle.attach_event(ev, r, radius=1.5, pt_min=1e30)
+    adj, fl = oracle.attach_event(ev, r, radius=1.5, pt_min=1e30, loopers_first=False)
     assert not (fl & oracle.CL_PROTECTED).any()
     assert np.array_equal((fl & oracle.CL_REMOVE) > 0, (fl & (oracle.CL_ATTACHED | oracle.CL_ADJACENT)) > 0)
 
@@ -233,3 +235,28 @@ def test_tubes_catch_the_clusters_tracking_missed():
                     break
         missed = np.array(missed, int)
         assert missed.size >= 5 and (adj[missed] >= 0).mean() >= 0.9, (missed.size, (adj[missed] >= 0).mean())
+
+
+def test_secondary_looper_legs_are_removed():
+    """The paper's category of secondary legs of loopers below 200 MeV/c: with
+    pt_min = 0 (every track good otherwise) exactly the clusters attached to
+    a secondary leg (leg >= 1) and in no good track's tube are removed, the
+    primary legs' clusters stay; without the looper identification nothing
+    is removed."""
+    ev = tpcgen.time_frame(seed=4, n_collisions=4)
+    r = oracle.track_event(ev)
+    g, leg = oracle.loopers(ev.sector, r)
+    assert (leg >= 1).sum() > 20
+    adj0, fl0 = oracle.attach_event(ev, r, radius=1.5, pt_min=0.0, loopers_first=False)
+    assert not (fl0 & oracle.CL_REMOVE).any()
+    adj, fl = oracle.attach_event(ev, r, radius=1.5, pt_min=0.0)
+    np.testing.assert_array_equal(adj, adj0)                  # adjacency does not depend on goodness
+    att = r.assign >= 0
+    sec = att & (leg[np.maximum(r.assign, 0)] >= 1)
+    prim = att & (leg[np.maximum(r.assign, 0)] == 0)
+    rem = (fl & oracle.CL_REMOVE) > 0
+    prot = (fl & oracle.CL_PROTECTED) > 0
+    assert rem[sec].sum() > 0.5 * sec.sum()
+    np.testing.assert_array_equal(rem[sec], ~prot[sec])
+    assert not rem[prim].any()
+    assert not rem[att & ~sec].any()
