@@ -73,7 +73,7 @@ def lib():
         L.orc_rotate64.argtypes = [_PD, _PD, C.c_double, C.c_double, C.c_double, _PD]
         L.orc_calib.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcGeom), C.c_double, C.c_double, C.c_double,
                                 C.c_int32, _P32, _PF, _PF, _P32, _P32, _PU8, _PU8, _PF, _PF, _PF, _PD, _PD, _PD,
-                                _PU8, _PD]
+                                _PU8, _PD, _PF, C.c_double]
         L.orc_calib_measure.argtypes = [C.POINTER(OrcGeom), _PD, C.c_int32, _PU8, _PU8, _PF, _PF, _PF, _PD, _PD]
         L.orc_calib_measure.restype = None
         L.orc_calib_explain.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcGeom), C.c_double, C.c_double,
@@ -519,6 +519,7 @@ def rotate64(x, p, cs, sn, kb):
 # ---- calibration chi2 and gradient ------------------------------------------------
 CALIB_NSPL = 8
 VERTEX_VAR = 0.01      # primary-vertex pseudo-measurement variance (cm^2)
+TGL_VAR = 9e-8       # dip angle of the matched inner track: variance (sigma 3e-4)
 
 
 def calib_n_theta(n_sectors=36):
@@ -565,9 +566,12 @@ class CalibTracks:
         return OrcGeom(self.n_sectors, self.row_x.shape[0], _ptr(self.row_x, _PF), self.z_max, 1)
 
 
-def calib(tr: CalibTracks, theta, weight=None, grad=True, params: dict | None = None, vtx_var=VERTEX_VAR):
+def calib(tr: CalibTracks, theta, weight=None, grad=True, params: dict | None = None, vtx_var=VERTEX_VAR,
+          tgl_ext=None, tgl_var=TGL_VAR):
     """Per-track calibration chi2, used flags and (optionally) the gradient of
-    sum_r weight[r] chi2_r with respect to theta (all binary64)."""
+    sum_r weight[r] chi2_r with respect to theta (all binary64).  tgl_ext:
+    per-track dip angle from outside the TPC (NaN: none), an update of
+    variance tgl_var after the vertex step."""
     th = np.ascontiguousarray(theta, np.float64)
     assert th.shape == (calib_n_theta(tr.n_sectors),)
     T = tr.n_tracks
@@ -575,13 +579,15 @@ def calib(tr: CalibTracks, theta, weight=None, grad=True, params: dict | None = 
     used = np.zeros(T, np.uint8)
     g = np.zeros_like(th) if grad else None
     w = None if weight is None else np.ascontiguousarray(weight, np.float64)
+    te = None if tgl_ext is None else np.ascontiguousarray(tgl_ext, np.float32)
     P = _params(params)
     G = tr.geom()
     rc = lib().orc_calib(C.byref(P), C.byref(G), tr.bz, tr.v_nom, vtx_var, T, _ptr(tr.sector, _P32),
                          _ptr(tr.x, _PF), _ptr(tr.param, _PF), _ptr(tr.off, _P32), _ptr(tr.clus, _P32),
                          _ptr(tr.cl_sector, _PU8), _ptr(tr.cl_row, _PU8), _ptr(tr.cl_y, _PF), _ptr(tr.cl_t, _PF),
                          _ptr(tr.tcoll, _PF), _ptr(th, _PD), None if w is None else _ptr(w, _PD),
-                         _ptr(chi2, _PD), _ptr(used, _PU8), None if g is None else _ptr(g, _PD))
+                         _ptr(chi2, _PD), _ptr(used, _PU8), None if g is None else _ptr(g, _PD),
+                         None if te is None else _ptr(te, _PF), tgl_var)
     if rc:
         raise ValueError(f"orc_calib failed ({rc})")
     return chi2, used.astype(bool), g

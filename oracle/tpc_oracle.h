@@ -166,14 +166,17 @@ float orc_merge_chi2(const float *top21, const float *bot21, float cs, float sn,
  * output (sector, x, 5 parameters in the tracker's z frame, cluster lists
  * inner -> outer); tcoll[r] = collision time (us), NaN = track not used.
  * chi2_out[r] / used[r] per track; grad (n_theta, may be NULL) = gradient of
- * sum_r weight[r] chi2_r (weight NULL = all 1).  Returns 0, or -1 for a
- * geometry without drift times. */
+ * sum_r weight[r] chi2_r (weight NULL = all 1).  tgl_ext (may be NULL; NaN
+ * entries: none) is a dip angle tan(lambda) of the track measured outside
+ * the TPC (the matched inner track), applied after the vertex step as one
+ * more update with variance tgl_var.  Returns 0, or -1 for a geometry
+ * without drift times. */
 #define ORC_CALIB_NSPL 8
 int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, double vtx_var, int32_t n_tracks,
               const int32_t *tr_sector, const float *tr_x, const float *tr_p, const int32_t *tr_off,
               const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y, const float *t,
               const float *tcoll, const double *theta, const double *weight, double *chi2_out, uint8_t *used,
-              double *grad);
+              double *grad, const float *tgl_ext, double tgl_var);
 /* calibration track selection: t_sel[r] = t_coll[r] if status[r] == 0 and
  * |param[r][4]| <= qpt_max (binary32), else NaN */
 void orc_calib_select(int32_t n, const float *t_coll, const int32_t *status, const float *param, float qpt_max,

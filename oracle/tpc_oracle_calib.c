@@ -224,6 +224,12 @@ static int vertex_step(double kb, double *x, double *q, double F[5][5])
     return 1;
 }
 
+/* the dip-angle update after the vertex step */
+typedef struct {
+    int on;
+    double K[5], W, r;
+} anchor_t;
+
 /* per-step record of the inward pass of one track */
 typedef struct {
     double F[5][5];     /* Jacobian from the previous step's state */
@@ -240,7 +246,8 @@ typedef struct {
 static int track_pass(const orc_params *P, const orc_geom *G, double kb, double v_nom, double vtx_var,
                       const int32_t *tr_sector, const float *tr_x, const float *tr_p, const int32_t *tr_off,
                       const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y,
-                      const float *t, const float *tcoll, const double *theta, int r, step_t *S, double *chi2o)
+                      const float *t, const float *tcoll, const double *theta, int r, step_t *S, double *chi2o,
+                      double tgl_m, double tgl_var, anchor_t *A)
 {
     const int off = tr_off[r], n = tr_off[r + 1] - tr_off[r];
     const double tc = tcoll[r];
@@ -324,6 +331,18 @@ static int track_pass(const orc_params *P, const orc_geom *G, double kb, double 
         for (int i = 0; i < 5; i++)
             for (int j = 0; j < 5; j++) C[i][j] = Cm[i][j] - (st->K[i][0] * Cm[0][j] + st->K[i][1] * Cm[1][j]);
     }
+    /* the dip-angle pseudo-measurement of the matched inner track (when
+     * given): one more update at the vertex, H selecting tan(lambda) */
+    A->on = 0;
+    if (tgl_m == tgl_m) {
+        A->on = 1;
+        A->r = tgl_m - (q[3] + dp[3]);
+        const double sv = C[3][3] + tgl_var;
+        if (!(sv > 0)) return 0;
+        A->W = 1.0 / sv;
+        chi2 += A->r * A->W * A->r;
+        for (int i = 0; i < 5; i++) A->K[i] = C[i][3] * A->W;
+    }
     *chi2o = chi2;
     return 1;
 }
@@ -332,7 +351,7 @@ int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, d
               const int32_t *tr_sector, const float *tr_x, const float *tr_p, const int32_t *tr_off,
               const int32_t *tr_clus, const uint8_t *sector, const uint8_t *row, const float *y, const float *t,
               const float *tcoll, const double *theta, const double *weight, double *chi2_out, uint8_t *used,
-              double *grad)
+              double *grad, const float *tgl_ext, double tgl_var)
 {
     if (!G->continuous || G->n_rows < 2) return -1;
     /* the field constant as the tracker forms it (binary32 product) */
@@ -352,8 +371,10 @@ int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, d
         const int n = tr_off[r + 1] - tr_off[r];
         if (n < 2 || !(tcoll[r] == tcoll[r])) continue;
         double chi2;
+        anchor_t A;
+        const double tgl_m = tgl_ext ? (double)tgl_ext[r] : NAN;
         if (!track_pass(P, G, kb, v_nom, vtx_var, tr_sector, tr_x, tr_p, tr_off, tr_clus, sector, row, y, t, tcoll,
-                        theta, r, S, &chi2))
+                        theta, r, S, &chi2, tgl_m, tgl_var, &A))
             continue;
         chi2_out[r] = chi2;
         used[r] = 1;
@@ -362,6 +383,7 @@ int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, d
         /* reverse sweep: lam = d chi2 / d(deviation after step k);
          * a = d chi2 / d(measurement of step k) */
         double lam[5] = {0, 0, 0, 0, 0};
+        if (A.on) lam[3] = -2.0 * A.W * A.r;     /* through the dip-angle update (its gain meets lam = 0) */
         for (int k = n; k >= 0; k--) {
             const step_t *st = &S[k];
             double a[2];
@@ -409,8 +431,9 @@ int orc_calib_explain(const orc_params *P, const orc_geom *G, double bz, double 
     const int n = tr_off[r + 1] - tr_off[r];
     step_t *S = (step_t *)malloc(sizeof(step_t) * (size_t)(n + 1));
     if (!S) return -2;
+    anchor_t A;
     const int ok = track_pass(P, G, kb, v_nom, vtx_var, tr_sector, tr_x, tr_p, tr_off, tr_clus, sector, row, y, t,
-                              tcoll, theta, r, S, chi2);
+                              tcoll, theta, r, S, chi2, NAN, 1.0, &A);
     if (ok)
         for (int k = 0; k <= n; k++) {
             memcpy(F + 25 * k, S[k].F, sizeof(double) * 25);

@@ -18,7 +18,8 @@
  *     its residuals to a prediction the decoder can repeat from what it has
  *     already decoded: the previous cluster of the run, or the straight line
  *     through the previous two, in row (integer arithmetic, the division
- *     truncated toward zero);
+ *     truncated toward zero; the previous value when those two share a
+ *     row);
  *   - clusters attached to no track: per (sector, row) plane, in ascending
  *     (qt, qy, input index), their number, the first qt and then qt steps,
  *     and qy;
@@ -180,10 +181,11 @@ static void us_push(ustream *s, uint32_t v)
 static uint32_t zz(int64_t v) { return v >= 0 ? (uint32_t)(2 * v) : (uint32_t)(-2 * v - 1); }
 static int64_t unzz(uint32_t u) { return (u & 1u) ? -(int64_t)(u >> 1) - 1 : (int64_t)(u >> 1); }
 
-/* prediction of a run's next value from its previous one or two clusters */
+/* prediction of a run's next value from its previous one or two clusters
+ * (the previous value when those two share a row: no line through them) */
 static int64_t predict(int nprev, int64_t v0, int r0, int64_t v1, int r1, int r)
 {
-    if (nprev < 2) return v1;
+    if (nprev < 2 || r1 == r0) return v1;
     return v1 + ((v1 - v0) * (int64_t)(r - r1)) / (int64_t)(r1 - r0);
 }
 

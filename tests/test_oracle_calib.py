@@ -73,7 +73,7 @@ def test_measurement_model_against_truth(orc, problem):
     assert (mz0 - ev.true_z[idx]).std() > 1.5 * dz.std()
 
 
-def _lsq_chi2(F, h, m, v, c0):
+def _lsq_chi2(F, h, m, v, c0, anchor=None):
     """Minimum of the batch objective equivalent to the Kalman pass: prior
     N((m0 - h0, 0, 0, 0), C0) on the deviation d at step 0, measurements
     m_k = h_k + H Phi_k d + noise(v_k), Phi_k = F_k ... F_1."""
@@ -91,6 +91,10 @@ def _lsq_chi2(F, h, m, v, c0):
         for e in range(2):
             rows.append(Phi[e] / np.sqrt(v[k, e]))
             rhs.append((m[k, e] - h[k, e]) / np.sqrt(v[k, e]))
+    if anchor is not None:                    # (tan(lambda) measured, reference tan(lambda), variance)
+        tm, q3, var = anchor
+        rows.append(Phi[3] / np.sqrt(var))
+        rhs.append((tm - q3) / np.sqrt(var))
     A, b = np.array(rows), np.array(rhs)
     d, *_ = np.linalg.lstsq(A, b, rcond=None)
     res = A @ d - b
@@ -114,6 +118,46 @@ def test_chi2_equals_batch_least_squares(orc, problem):
         assert c2 == pytest.approx(ref, rel=1e-7, abs=1e-9)
         checked += 1
     assert checked >= 20
+
+
+def test_dip_angle_anchor_equals_batch_least_squares(orc, problem):
+    """The pass with the matched inner track's dip angle: its chi2 is the
+    minimum of the batch problem with one more row, tan(lambda) at the vertex
+    (the reference's dip angle is the tracker's, constant along the helix);
+    the gradient through the extra update against central differences."""
+    ev, r, tr, th_true, th_nom = problem
+    p = orc.default_params()
+    c0 = np.array([p["sigma_y"] ** 2, p["sigma_z"] ** 2, p["c0_snp"], p["c0_tgl"], p["c0_qpt"]], np.float64)
+    c0[:2] = np.float32(p["sigma_y"]) ** 2, np.float32(p["sigma_z"]) ** 2
+    tg = tpcgen.track_dip_angle(ev, r.tr_off, r.tr_clus)
+    var = 9e-8
+    chi2, used, _ = orc.calib(tr, th_nom, grad=False, tgl_ext=tg, tgl_var=var)
+    free, _, _ = orc.calib(tr, th_nom, grad=False)
+    cand = np.nonzero(used & np.isfinite(tg))[0]
+    for t in cand[:: max(1, cand.size // 25)]:
+        F, h, m, v, c2 = orc.calib_explain(tr, th_nom, int(t))
+        assert c2 == pytest.approx(free[t], rel=1e-12)
+        ref = _lsq_chi2(F, h, m, v, c0, anchor=(float(tg[t]), float(tr.param[t, 3]), var))
+        assert chi2[t] == pytest.approx(ref, rel=1e-7, abs=1e-9)
+        assert chi2[t] >= free[t]
+    # tracks without a dip angle keep their chi2; a huge variance gives the free pass back
+    nan = np.nonzero(used & ~np.isfinite(tg))[0]
+    assert np.array_equal(chi2[nan], free[nan])
+    loose, _, _ = orc.calib(tr, th_nom, grad=False, tgl_ext=tg, tgl_var=1e12)
+    np.testing.assert_allclose(loose[used], free[used], rtol=1e-9, atol=1e-9)
+    # gradient with the anchor against central differences (v, t0, one spline coefficient)
+    sel = np.zeros(tr.n_tracks)
+    sel[cand[:60]] = 1.0
+    _, _, g = orc.calib(tr, th_true, weight=sel, tgl_ext=tg, tgl_var=var)
+
+    def f(x):
+        return float((orc.calib(tr, x, grad=False, tgl_ext=tg, tgl_var=var)[0] * sel).sum())
+
+    for i, hs in ((0, 1e-6), (1, 1e-5), (2 + int(np.argmax(np.abs(g[2:]))), 1e-5)):
+        e = np.zeros_like(th_true)
+        e[i] = 1.0
+        fd = (f(th_true + hs * e) - f(th_true - hs * e)) / (2 * hs)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(g).max())
 
 
 def test_chi2_per_dof_at_true_calibration(orc, problem):

@@ -187,3 +187,26 @@ def test_container_capacity_from_its_header():
     assert np.array_equal(oracle.unpack_stream(data), v)
     w = np.concatenate([v, np.arange(300, dtype=np.uint32)])      # with escapes
     assert np.array_equal(oracle.unpack_stream(oracle.pack_stream(w, chunk=1024)), w)
+
+
+def test_same_row_pair_predicts_the_previous_value():
+    """Two consecutive clusters of a run on one row (a looper turning inside a
+    sector) give no line to extrapolate: the next residual is taken against
+    the previous value, and the format still round-trips."""
+    rows = np.array([20, 21, 21, 22, 23], np.uint8)
+    qy = np.array([100, 104, 109, 115, 118], np.int64)
+    qt = np.array([7000, 6990, 6985, 6970, 6960], np.int64)
+    y = (qy / 32.0).astype(np.float32)
+    zt = (qt / 64.0).astype(np.float32)
+    sec = np.full(rows.size, 4, np.uint8)
+    r = types.SimpleNamespace(n_tracks=1, tr_off=np.array([0, rows.size], np.int32),
+                              tr_clus=np.arange(rows.size, dtype=np.int32), assign=np.zeros(rows.size, np.int32))
+    f = oracle.compress_fields(sec, rows, y, zt, r, n_sectors=36, n_rows=152)
+    zz = lambda v: int(2 * v) if v >= 0 else int(-2 * v - 1)  # noqa: E731
+    # residuals of clusters 1..4: previous value, line (rows 20, 21 -> 21), previous value (21, 21 share the
+    # row), line through (21, 109) and (22, 115)
+    line = lambda v0, r0, v1, r1, rr: v1 + ((v1 - v0) * (rr - r1)) // (r1 - r0)  # noqa: E731
+    exp_y = [qy[1] - qy[0], qy[2] - line(qy[0], 20, qy[1], 21, 21), qy[3] - qy[2], qy[4] - line(qy[2], 21, qy[3], 22, 23)]
+    assert f["res_y"].tolist() == [zz(v) for v in exp_y]
+    s, rw, dy, dt = oracle.decompress_fields(f, 1, rows.size, n_sectors=36, n_rows=152)
+    assert np.array_equal(rw, rows) and np.array_equal(dy, qy) and np.array_equal(dt, qt)

@@ -377,3 +377,29 @@ def track_collision_time(ev: Event, off, clus, min_frac: float = 0.5):
         if vals[k] >= 0 and cnt[k] >= min_frac * (b - a):
             out[t] = np.float32(ev.trk_tc[vals[k]])
     return out
+
+
+def track_dip_angle(ev: Event, off, clus, sigma: float = 3e-4, seed: int = 7, min_frac: float = 0.5):
+    """Generator-truth dip angle tan(lambda) = sinh(eta) of reconstructed
+    tracks (the label owning most of a track's clusters, as
+    :func:`track_collision_time`), smeared by a Gaussian of ``sigma``; NaN
+    where no label owns ``min_frac`` of the clusters.  Stands in for the dip
+    angle of the inner-detector track that matching pairs with it."""
+    off = np.asarray(off, np.int64)
+    clus = np.asarray(clus, np.int64)
+    T = off.size - 1
+    out = np.full(max(T, 0), np.nan, np.float32)
+    if T <= 0:
+        return out
+    rng = np.random.Generator(np.random.Philox(20_000 + seed))
+    noise = rng.standard_normal(T)
+    lab = ev.label[clus]
+    for t in range(T):
+        a, b = off[t], off[t + 1]
+        if b <= a:
+            continue
+        vals, cnt = np.unique(lab[a:b], return_counts=True)
+        k = int(np.argmax(cnt))
+        if vals[k] >= 0 and cnt[k] >= min_frac * (b - a):
+            out[t] = np.float32(np.sinh(ev.trk_eta[vals[k]]) + sigma * noise[t])
+    return out
