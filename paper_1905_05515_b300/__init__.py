@@ -10,10 +10,10 @@ from .abi import (TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_CUDA, TPC_ERR_DATA, TPC
 from . import autotune, batch, calib, compress
 from .batch import GroupedBatch
 from .calib import CalibRefit, calib_chi2
-from .compress import RansStream, rans_encode
+from .compress import RansStream, compress_fields, compress_frame, rans_encode
 from .pipeline import FramePipeline, HostTracks
 from .tracker import GraphRun, Tracker, TrackResult, tpc_track
 
-__all__ = ["compress", "rans_encode", "RansStream", "Tracker", "TrackResult", "GraphRun", "GroupedBatch", "FramePipeline", "HostTracks", "autotune", "batch", "calib", "CalibRefit", "calib_chi2", "tpc_track", "tpc_params_default", "tpc_workspace_size", "tpc_error_string",
+__all__ = ["compress", "rans_encode", "compress_fields", "compress_frame", "RansStream", "Tracker", "TrackResult", "GraphRun", "GroupedBatch", "FramePipeline", "HostTracks", "autotune", "batch", "calib", "CalibRefit", "calib_chi2", "tpc_track", "tpc_params_default", "tpc_workspace_size", "tpc_error_string",
            "lib", "TpcError", "TPC_OK", "TPC_ERR_ARG", "TPC_ERR_CAPACITY", "TPC_ERR_TIMEOUT", "TPC_ERR_CUDA",
            "TPC_ERR_DATA"]

@@ -66,7 +66,31 @@ class TpcCalibTracks(C.Structure):
     _fields_ = [("n_tracks", C.c_int32), ("sector", C.c_void_p), ("x", C.c_void_p), ("param", C.c_void_p),
                 ("clus_offset", C.c_void_p), ("clus_index", C.c_void_p), ("t_coll", C.c_void_p),
                 ("n_clusters", C.c_int64), ("cl_sector", C.c_void_p), ("cl_row", C.c_void_p),
-                ("cl_y", C.c_void_p), ("cl_t", C.c_void_p)]
+                ("cl_y", C.c_void_p), ("cl_t", C.c_void_p), ("tgl_ext", C.c_void_p), ("tgl_var", C.c_float)]
+
+
+class TpcCompressIn(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_sectors", C.c_int32), ("n_rows", C.c_int32), ("sector", C.c_void_p),
+                ("row", C.c_void_p), ("y", C.c_void_p), ("zt", C.c_void_p), ("n_tracks", C.c_int32),
+                ("n_attached", C.c_int64), ("clus_offset", C.c_void_p), ("clus_index", C.c_void_p),
+                ("assign", C.c_void_p)]
+
+
+# stream order of tpc_compress_fields / tpc_compress_frame
+CMP_STREAMS = ("n_track", "head_sector", "head_row", "head_y", "head_t", "d_sector", "d_row", "res_y", "res_t",
+               "u_count", "u_dt", "u_y")
+
+
+class TpcCalibFitOpts(C.Structure):
+    _fields_ = [("prior_sigma", C.c_float), ("scale_v", C.c_float), ("scale_t0", C.c_float),
+                ("max_iter", C.c_int32), ("rounds", C.c_int32), ("chi2ndf_first", C.c_float),
+                ("anchor_cut_first", C.c_float), ("chi2ndf_cut", C.c_float), ("anchor_cut", C.c_float),
+                ("ftol", C.c_double)]
+
+
+class TpcCalibFitReport(C.Structure):
+    _fields_ = [("f_start", C.c_double), ("f_final", C.c_double), ("evaluations", C.c_int32),
+                ("rounds", C.c_int32), ("tracks", C.c_int32), ("anchors", C.c_int32)]
 
 
 CALIB_NSPL = 8
@@ -85,7 +109,9 @@ CL_ATTACHED, CL_ADJACENT, CL_PROTECTED, CL_REMOVE = 1, 2, 4, 8
 EXPORTED = ("tpc_params_default", "tpc_workspace_size", "tpc_workspace_size_batched", "tpc_track",
             "tpc_track_batched", "tpc_prepare", "tpc_prepare_staging_size", "tpc_prepare_async", "tpc_track_async", "tpc_export_tracklets", "tpc_links_static",
             "tpc_error_string", "tpc_calib_workspace_size", "tpc_calib_forward", "tpc_calib_backward",
-            "tpc_calib_status", "tpc_calib_select", "tpc_rans_workspace_size", "tpc_rans_max_bytes", "tpc_rans_encode",
+            "tpc_calib_status", "tpc_calib_select", "tpc_calib_fit_defaults", "tpc_calib_fit_workspace_size",
+            "tpc_calib_fit", "tpc_rans_workspace_size", "tpc_rans_max_bytes", "tpc_rans_encode",
+            "tpc_compress_workspace_size", "tpc_compress_max_size", "tpc_compress_fields", "tpc_compress_frame",
             "tpc_probe_fma")
 
 _lib = None
@@ -108,6 +134,19 @@ def lib(build_if_missing: bool = True):
         L.tpc_rans_max_bytes.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]
         L.tpc_rans_encode.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
+        L.tpc_calib_fit_defaults.argtypes = [C.POINTER(TpcCalibFitOpts)]
+        L.tpc_calib_fit_workspace_size.argtypes = [C.POINTER(TpcGeometry), C.c_int32, C.c_int64,
+                                                   C.POINTER(C.c_size_t)]
+        L.tpc_calib_fit.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float, C.c_float,
+                                    C.POINTER(TpcCalibTracks), C.POINTER(TpcCalibFitOpts), C.c_void_p, C.c_void_p,
+                                    C.c_size_t, C.POINTER(TpcCalibFitReport), C.c_void_p]
+        L.tpc_compress_workspace_size.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.POINTER(C.c_size_t)]
+        L.tpc_compress_max_size.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.POINTER(C.c_int64),
+                                            C.POINTER(C.c_int64)]
+        L.tpc_compress_fields.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
+                                          C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
+        L.tpc_compress_frame.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                         C.c_size_t, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
         L.tpc_workspace_size.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_int64,
                                          C.POINTER(C.c_size_t)]
         L.tpc_track.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float,

@@ -12,7 +12,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "tpc_compress.h"
 #include "tpc_track.h"
@@ -262,5 +264,626 @@ extern "C" int tpc_rans_encode(const uint8_t* sym, int64_t n, int32_t chunk, voi
         *total = t;
     }
 #undef CK
+    return TPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The compressed cluster format (tpc_compress.h): integer fields, per-track
+// run streams, per-plane streams of the other clusters, then each stream
+// symbolised (escapes) and coded into its container.
+//
+// Kernels: k_cq (quantisation, plane counts of the other clusters, checks),
+// k_ct_count (per track: clusters, runs), k_scan1 (one-block exclusive scans
+// of the per-track and per-plane counts), k_ct_fill (one thread per track
+// writes its values at the scanned offsets), k_cu_scatter / k_cu_plane (the
+// other clusters by plane, then one block per plane ranks them by (qt, qy,
+// index) and writes the plane's values), k_sym_count / k_sym_write (escape
+// split), k_pack_head (container header and table).
+// ---------------------------------------------------------------------------
+namespace {
+
+enum { CS_NT, CS_HS, CS_HR, CS_HY, CS_HT, CS_DS, CS_DR, CS_RY, CS_RT, CS_UN, CS_UT, CS_UY, CS_N };
+static_assert(CS_N == TPC_CMP_N_STREAMS, "stream count");
+constexpr int CU_SMEM = 4096;           // keys of a plane's other clusters held in shared memory
+
+__device__ __forceinline__ uint32_t zz32(long long v)
+{
+    return v >= 0 ? (uint32_t)(2 * v) : (uint32_t)(-2 * v - 1);
+}
+
+struct CmpArgs {
+    int64_t n;
+    int ns, nr, np, T;
+    int64_t na;
+    const uint8_t* sector;
+    const uint8_t* row;
+    const float* y;
+    const float* zt;
+    const int32_t* off;
+    const int32_t* clus;
+    const int32_t* assign;
+    float sy, st;                 // 2^ey, 2^et
+    int32_t* qy;
+    int32_t* qt;
+    uint32_t* tcnt;               // [4][T + 1]: has clusters, runs, clusters - 1, clusters - runs (then scanned)
+    uint32_t* pcnt;               // [np + 1] other clusters per plane (then scanned)
+    uint32_t* pfill;              // [np] fill cursors
+    int32_t* uord;                // [n] other clusters by plane (arbitrary order inside)
+    int32_t* usort;               // [n] sorted inside each plane
+    uint32_t* vals;               // stream values, stream s from vbase[s]
+    int64_t vbase[CS_N + 1];
+    int* err;
+};
+
+__global__ void k_cq(CmpArgs A)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = A.sector[i], r = A.row[i];
+        if (s >= A.ns || r >= A.nr) {
+            atomicExch(A.err, 1);
+            continue;
+        }
+        A.qy[i] = __float2int_rn(A.y[i] * A.sy);
+        A.qt[i] = __float2int_rn(A.zt[i] * A.st);
+        if (A.assign[i] < 0) atomicAdd(&A.pcnt[s * A.nr + r], 1u);
+    }
+}
+
+// per track: [0] 1 if it has clusters, [1] runs, [2] clusters - 1, [3] clusters - runs
+__global__ void k_ct_count(CmpArgs A)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.T; t += gridDim.x * blockDim.x) {
+        const int a = A.off[t], b = A.off[t + 1];
+        uint32_t runs = 0;
+        if (a < 0 || b < a || (int64_t)b > A.na) {
+            atomicExch(A.err, 1);
+        } else {
+            int sec = -1;
+            for (int k = a; k < b; k++) {
+                const int c = A.clus[k];
+                if (c < 0 || (int64_t)c >= A.n) {
+                    atomicExch(A.err, 1);
+                    break;
+                }
+                const int s = A.sector[c];
+                runs += (k == a || s != sec);
+                sec = s;
+            }
+        }
+        const uint32_t m = (a >= 0 && b >= a) ? (uint32_t)(b - a) : 0u;
+        const int64_t T1 = (int64_t)A.T + 1;
+        A.tcnt[t] = m > 0;
+        A.tcnt[T1 + t] = runs;
+        A.tcnt[2 * T1 + t] = m > 0 ? m - 1 : 0;
+        A.tcnt[3 * T1 + t] = m >= runs ? m - runs : 0;
+    }
+}
+
+// one block: in[0..n) -> exclusive sums in place, in[n] = total
+__global__ void __launch_bounds__(1024) k_scan1(uint32_t* a, int64_t n)
+{
+    __shared__ uint32_t part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = threadIdx.x * per, hi = min(n, lo + per);
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; i++) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; t++) {
+            const uint32_t v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        a[n] = run;
+    }
+    __syncthreads();
+    uint32_t o = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; i++) {
+        const uint32_t v = a[i];
+        a[i] = o;
+        o += v;
+    }
+}
+
+// prediction of a run's next value from its previous one or two clusters
+__device__ __forceinline__ long long predict(int nprev, long long v0, int r0, long long v1, int r1, int r)
+{
+    if (nprev < 2 || r1 == r0) return v1;
+    return v1 + ((v1 - v0) * (long long)(r - r1)) / (long long)(r1 - r0);
+}
+
+// one thread per track: its values in the track streams
+__global__ void k_ct_fill(CmpArgs A)
+{
+    if (*A.err) return;
+    const int64_t T1 = (int64_t)A.T + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.T; t += gridDim.x * blockDim.x) {
+        const int a = A.off[t], b = A.off[t + 1];
+        A.vals[A.vbase[CS_NT] + t] = (uint32_t)(b - a);
+        if (b <= a) continue;
+        uint32_t* hs = A.vals + A.vbase[CS_HS] + A.tcnt[t];
+        uint32_t* hr = A.vals + A.vbase[CS_HR] + A.tcnt[T1 + t];
+        uint32_t* hy = A.vals + A.vbase[CS_HY] + A.tcnt[T1 + t];
+        uint32_t* ht = A.vals + A.vbase[CS_HT] + A.tcnt[T1 + t];
+        uint32_t* ds = A.vals + A.vbase[CS_DS] + A.tcnt[2 * T1 + t];
+        uint32_t* dr = A.vals + A.vbase[CS_DR] + A.tcnt[3 * T1 + t];
+        uint32_t* ry = A.vals + A.vbase[CS_RY] + A.tcnt[3 * T1 + t];
+        uint32_t* rt = A.vals + A.vbase[CS_RT] + A.tcnt[3 * T1 + t];
+        int run = 0, rp0 = 0, rp1 = 0, sec = -1, nh = 0, nr = 0;
+        long long y0 = 0, y1 = 0, t0 = 0, t1 = 0;
+        for (int k = a; k < b; k++) {
+            const int c = A.clus[k];
+            const int s = A.sector[c], r = A.row[c];
+            const long long qy = A.qy[c], qt = A.qt[c];
+            if (k > a) ds[k - a - 1] = zz32((long long)s - sec);
+            if (k == a || s != sec) {
+                if (k == a) hs[0] = (uint32_t)s;
+                hr[nh] = (uint32_t)r;
+                hy[nh] = zz32(qy);
+                ht[nh] = zz32(qt);
+                nh++;
+                run = 1;
+            } else {
+                dr[nr] = zz32((long long)r - rp1);
+                ry[nr] = zz32(qy - predict(run, y0, rp0, y1, rp1, r));
+                rt[nr] = zz32(qt - predict(run, t0, rp0, t1, rp1, r));
+                nr++;
+                run++;
+            }
+            sec = s;
+            rp0 = rp1; y0 = y1; t0 = t1;
+            rp1 = r; y1 = qy; t1 = qt;
+        }
+    }
+}
+
+// the other clusters to their plane's range (order inside: the atomics')
+__global__ void k_cu_scatter(CmpArgs A)
+{
+    if (*A.err) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (A.assign[i] >= 0) continue;
+        const int s = A.sector[i], r = A.row[i];
+        if (s >= A.ns || r >= A.nr) continue;
+        const int p = s * A.nr + r;
+        A.uord[A.pcnt[p] + atomicAdd(&A.pfill[p], 1u)] = (int32_t)i;
+    }
+}
+
+__device__ __forceinline__ bool cu_less(int32_t ta, int32_t ya, int32_t ia, int32_t tb, int32_t yb, int32_t ib)
+{
+    return ta < tb || (ta == tb && (ya < yb || (ya == yb && ia < ib)));
+}
+
+// one block per plane: its other clusters ranked by (qt, qy, index) (keys in
+// shared memory when they fit, else read from global memory), then the
+// plane's values
+__global__ void __launch_bounds__(256) k_cu_plane(CmpArgs A)
+{
+    __shared__ int32_t kt[CU_SMEM], ky[CU_SMEM], ki[CU_SMEM];
+    if (*A.err) return;
+    for (int p = blockIdx.x; p < A.np; p += gridDim.x) {
+        const uint32_t ps = A.pcnt[p];
+        const int m = (int)(A.pcnt[p + 1] - ps);
+        if (threadIdx.x == 0) A.vals[A.vbase[CS_UN] + p] = (uint32_t)m;
+        const bool sh = m <= CU_SMEM;
+        __syncthreads();                    // the previous plane is done with the keys
+        if (sh)
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                const int c = A.uord[ps + k];
+                kt[k] = A.qt[c];
+                ky[k] = A.qy[c];
+                ki[k] = c;
+            }
+        __syncthreads();
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            int32_t t, yv, iv;
+            if (sh) {
+                t = kt[k]; yv = ky[k]; iv = ki[k];
+            } else {
+                iv = A.uord[ps + k]; t = A.qt[iv]; yv = A.qy[iv];
+            }
+            int rank = 0;
+            if (sh) {
+                for (int j = 0; j < m; j++) rank += cu_less(kt[j], ky[j], ki[j], t, yv, iv);
+            } else {
+                for (int j = 0; j < m; j++) {
+                    const int c = A.uord[ps + j];
+                    rank += cu_less(A.qt[c], A.qy[c], c, t, yv, iv);
+                }
+            }
+            A.usort[ps + rank] = iv;
+        }
+        __syncthreads();                    // usort of the plane complete (global writes of this block)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int c = A.usort[ps + k];
+            const int32_t t = A.qt[c];
+            A.vals[A.vbase[CS_UT] + ps + k] = k == 0 ? zz32(t) : (uint32_t)(t - A.qt[A.usort[ps + k - 1]]);
+            A.vals[A.vbase[CS_UY] + ps + k] = zz32(A.qy[c]);
+        }
+    }
+}
+
+// ---- symbolisation: values >= 252 become an escape symbol plus raw bytes
+__device__ __forceinline__ int esc_bytes(uint32_t v)
+{
+    if (v < 252u) return 0;
+    const uint32_t w = v - 252u;
+    return w < (1u << 8) ? 1 : w < (1u << 16) ? 2 : w < (1u << 24) ? 3 : 4;
+}
+
+__global__ void k_sym_count(const uint32_t* __restrict__ v, int64_t n, uint32_t* __restrict__ rawn)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rawn[i] = (uint32_t)esc_bytes(v[i]);
+}
+
+// rawo: exclusive sums of the escape byte counts (rawo[n] = nraw)
+__global__ void k_sym_write(const uint32_t* __restrict__ v, int64_t n, const uint32_t* __restrict__ rawo,
+                            uint8_t* __restrict__ sym, uint8_t* __restrict__ raw)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = v[i];
+        const int k = esc_bytes(x);
+        if (k == 0) {
+            sym[i] = (uint8_t)x;
+            continue;
+        }
+        sym[i] = (uint8_t)(251 + k);
+        const uint32_t w = x - 252u;
+        uint8_t* o = raw + rawo[i];
+        for (int b = 0; b < k; b++) o[b] = (uint8_t)(w >> (8 * b));
+    }
+}
+
+// ---- exclusive scan of n uint32 in place (a[n] receives the total): tile
+// sums, one-block scan of the tile sums, tiles rescanned with their offsets
+constexpr int SC_BLOCK = 256, SC_ITEMS = 16, SC_TILE = SC_BLOCK * SC_ITEMS;
+
+__global__ void __launch_bounds__(SC_BLOCK) k_tile_sum(const uint32_t* __restrict__ a, int64_t n,
+                                                       uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t w[SC_BLOCK / 32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE;
+    uint32_t s = 0;
+    for (int k = threadIdx.x; k < SC_TILE; k += SC_BLOCK) {
+        const int64_t i = base + k;
+        if (i < n) s += a[i];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < SC_BLOCK / 32; k++) t += w[k];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(SC_BLOCK) k_tile_apply(uint32_t* __restrict__ a, int64_t n,
+                                                         const uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t w[SC_BLOCK / 32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; j++) {
+        const int64_t i = base + j;
+        v[j] = i < n ? a[i] : 0u;
+        run += v[j];
+    }
+    // exclusive prefix of the thread sums within the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) w[wid] = inc;
+    __syncthreads();
+    uint32_t off = sums[blockIdx.x];
+    for (int k = 0; k < wid; k++) off += w[k];
+    off += inc - run;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; j++) {
+        const int64_t i = base + j;
+        if (i < n) a[i] = off;
+        off += v[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SC_BLOCK - 1) a[n] = off;
+}
+
+// a[0..n] (n + 1 entries; a[n] overwritten with the total); tmp holds
+// ceil(n / SC_TILE) + 1 entries
+void scan_n(uint32_t* a, int64_t n, uint32_t* tmp, cudaStream_t st)
+{
+    const int64_t nt = std::max<int64_t>(1, (n + SC_TILE - 1) / SC_TILE);
+    k_tile_sum<<<(unsigned)nt, SC_BLOCK, 0, st>>>(a, n, tmp);
+    k_scan1<<<1, 1024, 0, st>>>(tmp, nt);
+    k_tile_apply<<<(unsigned)nt, SC_BLOCK, 0, st>>>(a, n, tmp);
+}
+
+int64_t scan_tmp_elems(int64_t n) { return (n + SC_TILE - 1) / SC_TILE + 2; }
+
+}  // namespace
+
+namespace {
+
+// container header of one stream: n, chunk, nraw, the table as u16, the
+// chunk sizes; the coded total goes to *coded (one block)
+__global__ void __launch_bounds__(256) k_pack_head(uint8_t* __restrict__ cont, uint32_t n, int32_t chunk,
+                                                   const uint32_t* __restrict__ nraw,
+                                                   const uint32_t* __restrict__ freq,
+                                                   const int32_t* __restrict__ chunk_bytes, int64_t nch,
+                                                   long long* __restrict__ coded)
+{
+    __shared__ long long part[256];
+    auto put32 = [&](int64_t o, uint32_t v) {
+        for (int b = 0; b < 4; b++) cont[o + b] = (uint8_t)(v >> (8 * b));
+    };
+    if (threadIdx.x == 0) {
+        put32(0, n);
+        put32(4, (uint32_t)chunk);
+        put32(8, *nraw);
+    }
+    for (int s = threadIdx.x; s < 256; s += blockDim.x) {
+        const uint32_t f = n > 0 ? freq[s] : 0u;
+        cont[12 + 2 * s] = (uint8_t)(f & 0xFF);
+        cont[13 + 2 * s] = (uint8_t)(f >> 8);
+    }
+    long long t = 0;
+    for (int64_t c = threadIdx.x; c < nch; c += blockDim.x) {
+        put32(524 + 4 * c, (uint32_t)chunk_bytes[c]);
+        t += chunk_bytes[c];
+    }
+    part[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sum = 0;
+        for (int k = 0; k < (int)blockDim.x; k++) sum += part[k];
+        *coded = sum;
+    }
+}
+
+// the coded chunks and the escape bytes after the header; *size = the
+// container's bytes
+__global__ void k_pack_copy(uint8_t* __restrict__ cont, int64_t nch, const uint8_t* __restrict__ coded_bytes,
+                            const long long* __restrict__ coded, const uint8_t* __restrict__ raw,
+                            const uint32_t* __restrict__ nraw, long long* __restrict__ size)
+{
+    const long long nc = *coded, nr = *nraw;
+    const long long o1 = 524 + 4 * nch, o2 = o1 + nc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc + nr;
+         i += (long long)gridDim.x * blockDim.x)
+        cont[o1 + i] = i < nc ? coded_bytes[i] : raw[i - nc];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *size = o2 + nr;
+}
+
+struct CmpLayout {
+    size_t err, qy, qt, tcnt, pcnt, pfill, uord, usort, stmp, sizes, coded;   // fields
+    size_t vals, rawn, sym, raw, rans, cout, cbytes, freq, stage;              // coding (frame only)
+    int64_t max_vals, max_stream, max_cont_total;
+    size_t total;
+};
+
+int64_t n_chunks(int64_t m, int32_t chunk) { return m > 0 ? (m + chunk - 1) / chunk : 0; }
+int64_t cont_max(int64_t m, int32_t chunk) { return 524 + 8 * n_chunks(m, chunk) + 6 * m; }
+
+int check_in(const tpc_compress_in* in)
+{
+    if (!in || in->n < 0 || in->n > (int64_t)INT32_MAX || in->n_tracks < 0 || in->n_attached < 0 ||
+        in->n_attached > (int64_t)INT32_MAX || in->n_sectors < 1 || in->n_sectors > 255 || in->n_rows < 1 ||
+        in->n_rows > 255)
+        return TPC_ERR_ARG;
+    if (in->n > 0 && (!in->sector || !in->row || !in->y || !in->zt || !in->assign)) return TPC_ERR_ARG;
+    if (!in->clus_offset || (in->n_attached > 0 && !in->clus_index)) return TPC_ERR_ARG;
+    return TPC_OK;
+}
+
+CmpLayout cmp_layout(const tpc_compress_in* in, int32_t chunk)
+{
+    CmpLayout L;
+    const int64_t n = in->n, T = in->n_tracks, na = in->n_attached;
+    const int64_t np = (int64_t)in->n_sectors * in->n_rows;
+    L.max_vals = 2 * T + 7 * na + np + 2 * n;
+    L.max_stream = std::max<int64_t>({T, na, np, n, 1});
+    L.max_cont_total = 0;
+    const int64_t per[CS_N] = {T, T, na, na, na, na, na, na, na, np, n, n};
+    for (int s = 0; s < CS_N; s++) L.max_cont_total += (cont_max(per[s], chunk) + 15) / 16 * 16;
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t r = o; o = al(o + std::max<size_t>(b, 1)); return r; };
+    L.err = take(4);
+    L.qy = take(4 * (size_t)n);
+    L.qt = take(4 * (size_t)n);
+    L.tcnt = take(4 * 4 * (size_t)(T + 1));
+    L.pcnt = take(4 * (size_t)(np + 1));
+    L.pfill = take(4 * (size_t)np);
+    L.uord = take(4 * (size_t)n);
+    L.usort = take(4 * (size_t)n);
+    L.stmp = take(4 * (size_t)scan_tmp_elems(std::max<int64_t>(L.max_stream, 4 * (T + 1)) + 1));
+    L.sizes = take(8 * CS_N);
+    L.coded = take(8);
+    L.vals = take(4 * (size_t)L.max_vals);
+    L.rawn = take(4 * (size_t)(L.max_stream + 1));
+    L.sym = take((size_t)L.max_stream);
+    L.raw = take(4 * (size_t)L.max_stream);
+    L.rans = take(rans_layout(L.max_stream, chunk).total);
+    L.cout = take(4 * (size_t)n_chunks(L.max_stream, chunk) + 2 * (size_t)L.max_stream);
+    L.cbytes = take(4 * (size_t)std::max<int64_t>(n_chunks(L.max_stream, chunk), 1));
+    L.freq = take(4 * 256);
+    L.stage = take((size_t)L.max_cont_total);     // containers at worst-case offsets, then packed
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+namespace {
+
+#define CCK(x) do { if ((x) != cudaSuccess) return TPC_ERR_CUDA; } while (0)
+
+// the 12 integer streams into vals (stream s from its worst-case base in
+// vbase); counts (host) read back.  Synchronises the stream.
+int run_fields(const tpc_compress_in* in, int32_t ey, int32_t et, void* ws, const CmpLayout& L, int64_t* counts,
+               int64_t* vbase, cudaStream_t st)
+{
+    CmpArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = in->n;
+    A.ns = in->n_sectors;
+    A.nr = in->n_rows;
+    A.np = A.ns * A.nr;
+    A.T = in->n_tracks;
+    A.na = in->n_attached;
+    A.sector = in->sector; A.row = in->row; A.y = in->y; A.zt = in->zt;
+    A.off = in->clus_offset; A.clus = in->clus_index; A.assign = in->assign;
+    A.sy = ldexpf(1.0f, ey);
+    A.st = ldexpf(1.0f, et);
+    A.qy = at<int32_t>(ws, L.qy);
+    A.qt = at<int32_t>(ws, L.qt);
+    A.tcnt = at<uint32_t>(ws, L.tcnt);
+    A.pcnt = at<uint32_t>(ws, L.pcnt);
+    A.pfill = at<uint32_t>(ws, L.pfill);
+    A.uord = at<int32_t>(ws, L.uord);
+    A.usort = at<int32_t>(ws, L.usort);
+    A.err = at<int>(ws, L.err);
+    A.vals = at<uint32_t>(ws, L.vals);
+    // worst-case stream bases: NT, HS: T; HR .. RT: n_attached each; UN: planes; UT, UY: n
+    const int64_t per[CS_N] = {A.T, A.T, A.na, A.na, A.na, A.na, A.na, A.na, A.na, A.np, A.n, A.n};
+    A.vbase[0] = 0;
+    for (int k = 0; k < CS_N; k++) A.vbase[k + 1] = A.vbase[k] + per[k];
+    uint32_t* stmp = at<uint32_t>(ws, L.stmp);
+    const int64_t T1 = (int64_t)A.T + 1;
+    CCK(cudaMemsetAsync(A.err, 0, 4, st));
+    CCK(cudaMemsetAsync(A.pcnt, 0, 4 * ((size_t)A.np + 1), st));
+    CCK(cudaMemsetAsync(A.pfill, 0, 4 * (size_t)A.np, st));
+    // the offset table must start at 0 and end at n_attached
+    if (A.n > 0) k_cq<<<grid_cap(A.n, 256), 256, 0, st>>>(A);
+    if (A.T > 0) k_ct_count<<<grid_cap(A.T, 128), 128, 0, st>>>(A);
+    for (int k = 0; k < 4; k++) scan_n(A.tcnt + k * T1, A.T, stmp, st);
+    scan_n(A.pcnt, A.np, stmp, st);
+    k_ct_fill<<<grid_cap(std::max(A.T, 1), 128), 128, 0, st>>>(A);
+    if (A.n > 0) k_cu_scatter<<<grid_cap(A.n, 256), 256, 0, st>>>(A);
+    k_cu_plane<<<(unsigned)std::min(A.np, 148 * 8), 256, 0, st>>>(A);
+    CCK(cudaGetLastError());
+    // read back: error flag, offset table ends, stream lengths
+    uint32_t tc[4] = {0, 0, 0, 0}, pc = 0;
+    int32_t ends[2] = {0, 0};
+    int e = 0;
+    CCK(cudaMemcpyAsync(&e, A.err, 4, cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < 4; k++) CCK(cudaMemcpyAsync(&tc[k], A.tcnt + k * T1 + A.T, 4, cudaMemcpyDeviceToHost, st));
+    CCK(cudaMemcpyAsync(&pc, A.pcnt + A.np, 4, cudaMemcpyDeviceToHost, st));
+    CCK(cudaMemcpyAsync(&ends[0], A.off, 4, cudaMemcpyDeviceToHost, st));
+    CCK(cudaMemcpyAsync(&ends[1], A.off + A.T, 4, cudaMemcpyDeviceToHost, st));
+    CCK(cudaStreamSynchronize(st));
+    if (e || ends[0] != 0 || (int64_t)ends[1] != A.na) return TPC_ERR_DATA;
+    const int64_t cnt[CS_N] = {A.T, tc[0], tc[1], tc[1], tc[1], tc[2], tc[3], tc[3], tc[3], A.np, pc, pc};
+    for (int k = 0; k < CS_N; k++) {
+        counts[k] = cnt[k];
+        vbase[k] = A.vbase[k];
+    }
+    return TPC_OK;
+}
+
+}  // namespace
+
+extern "C" int tpc_compress_workspace_size(const tpc_compress_in* in, int32_t chunk, size_t* bytes)
+{
+    if (check_in(in) || !bytes || chunk < 1 || chunk > TPC_RANS_MAX_CHUNK) return TPC_ERR_ARG;
+    *bytes = cmp_layout(in, chunk).total;
+    return TPC_OK;
+}
+
+extern "C" int tpc_compress_max_size(const tpc_compress_in* in, int32_t chunk, int64_t* max_values,
+                                     int64_t* max_bytes)
+{
+    if (check_in(in) || chunk < 1 || chunk > TPC_RANS_MAX_CHUNK) return TPC_ERR_ARG;
+    const CmpLayout L = cmp_layout(in, chunk);
+    if (max_values) *max_values = L.max_vals;
+    if (max_bytes) *max_bytes = L.max_cont_total;
+    return TPC_OK;
+}
+
+extern "C" int tpc_compress_fields(const tpc_compress_in* in, int32_t ey, int32_t et, void* workspace,
+                                   size_t ws_bytes, uint32_t* vals, int64_t vals_cap, int64_t* counts, void* stream)
+{
+    if (check_in(in) || !counts || !workspace || ey < -30 || ey > 30 || et < -30 || et > 30) return TPC_ERR_ARG;
+    const CmpLayout L = cmp_layout(in, 4096);     // the fields' regions do not depend on the chunk
+    if (ws_bytes < L.rawn || (L.max_vals > 0 && (!vals || vals_cap < L.max_vals))) return TPC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t vbase[CS_N];
+    int rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
+    if (rc) return rc;
+    int64_t o = 0;
+    for (int k = 0; k < CS_N; k++) {
+        if (counts[k] > 0)
+            CCK(cudaMemcpyAsync(vals + o, at<uint32_t>(workspace, L.vals) + vbase[k], 4 * (size_t)counts[k],
+                                cudaMemcpyDeviceToDevice, st));
+        o += counts[k];
+    }
+    CCK(cudaStreamSynchronize(st));
+    return TPC_OK;
+}
+
+extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t et, int32_t chunk, void* workspace,
+                                  size_t ws_bytes, uint8_t* out, int64_t out_cap, int64_t* bytes, void* stream)
+{
+    if (check_in(in) || !bytes || !workspace || !out || chunk < 1 || chunk > TPC_RANS_MAX_CHUNK || ey < -30 ||
+        ey > 30 || et < -30 || et > 30)
+        return TPC_ERR_ARG;
+    const CmpLayout L = cmp_layout(in, chunk);
+    if (ws_bytes < L.total || out_cap < L.max_cont_total) return TPC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t counts[CS_N], vbase[CS_N];
+    int rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
+    if (rc) return rc;
+    uint32_t* vals = at<uint32_t>(workspace, L.vals);
+    uint32_t* rawn = at<uint32_t>(workspace, L.rawn);
+    uint8_t* sym = at<uint8_t>(workspace, L.sym);
+    uint8_t* raw = at<uint8_t>(workspace, L.raw);
+    uint8_t* cout = at<uint8_t>(workspace, L.cout);
+    int32_t* cbytes = at<int32_t>(workspace, L.cbytes);
+    uint32_t* freq = at<uint32_t>(workspace, L.freq);
+    long long* sizes = at<long long>(workspace, L.sizes);
+    long long* coded = at<long long>(workspace, L.coded);
+    uint32_t* stmp = at<uint32_t>(workspace, L.stmp);
+    uint8_t* stage = at<uint8_t>(workspace, L.stage);
+    const size_t rans_ws = rans_layout(L.max_stream, chunk).total;
+    int64_t cbase[CS_N];
+    int64_t o = 0;
+    for (int k = 0; k < CS_N; k++) {
+        cbase[k] = o;
+        const int64_t m = counts[k], nch = n_chunks(m, chunk);
+        o += (cont_max(m, chunk) + 15) / 16 * 16;
+        const uint32_t* v = vals + vbase[k];
+        if (m > 0) k_sym_count<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn);
+        scan_n(rawn, m, stmp, st);          // rawn[m] = escape bytes
+        if (m > 0) k_sym_write<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn, sym, raw);
+        CCK(cudaGetLastError());
+        int64_t maxb = 0;
+        tpc_rans_max_bytes(m, chunk, &maxb);
+        rc = tpc_rans_encode(sym, m, chunk, at<void>(workspace, L.rans), rans_ws, freq, cbytes, cout,
+                             std::max<int64_t>(maxb, 1), nullptr, stream);
+        if (rc) return rc;
+        k_pack_head<<<1, 256, 0, st>>>(stage + cbase[k], (uint32_t)m, chunk,
+                                       rawn + m, freq, cbytes, nch, coded);
+        k_pack_copy<<<grid_cap(2 * m + 4 * nch + 1, 256), 256, 0, st>>>(stage + cbase[k], nch, cout, coded, raw,
+                                                                        rawn + m, sizes + k);
+        CCK(cudaGetLastError());
+    }
+    long long sz[CS_N];
+    CCK(cudaMemcpyAsync(sz, sizes, sizeof(sz), cudaMemcpyDeviceToHost, st));
+    CCK(cudaStreamSynchronize(st));
+    int64_t p = 0;
+    for (int k = 0; k < CS_N; k++) {
+        CCK(cudaMemcpyAsync(out + p, stage + cbase[k], (size_t)sz[k], cudaMemcpyDeviceToDevice, st));
+        bytes[k] = sz[k];
+        p += sz[k];
+    }
+    CCK(cudaStreamSynchronize(st));
     return TPC_OK;
 }

@@ -78,7 +78,8 @@ int64_t scan_aux_elems(int64_t n)
 // y-bins per z-cell (the searches visit whatever bins a window overlaps, so
 // any count works; the grid grows with it)
 constexpr int MAX_YBINS = 64;
-constexpr int LOOP_NBIN = 256;          // looper candidates: radius bins of LOOP_BINW cm per frame
+constexpr int LOOP_G = 48;              // looper candidates: LOOP_G x LOOP_G cells of their circle centres
+constexpr int LOOP_NBIN = LOOP_G * LOOP_G;   // per frame
 int effective_ybins(const tpc_params* p, const tpc_geometry*) { return std::max(1, std::min(p->y_bins, MAX_YBINS)); }
 
 // per-row binary32 tables: X, X[r+1]/X[r], X[r-1]/X[r],
@@ -2147,8 +2148,6 @@ struct LoopCand {
 };
 static_assert(sizeof(LoopCand) == 48, "LoopCand layout");
 
-constexpr float LOOP_BINW = 4.0f;
-constexpr int LOOP_WBINS = 4;           // 2 sqrt(2) LOOP_SRMAX + LOOP_DR < LOOP_WBINS * LOOP_BINW
 constexpr float LOOP_SRMAX = 5.0f;
 constexpr float LOOP_DR = 1.0f;
 constexpr float LOOP_DC = 2.0f;
@@ -2226,9 +2225,19 @@ struct LoopArgs {
     int* err;
 };
 
+// Centre cells of LOOP_CW cm from -LOOP_G LOOP_CW / 2 (clamped at the grid
+// edges: monotone in the coordinate).  A pair needs centres closer than
+// 2 sqrt(2) LOOP_SRMAX + LOOP_DC < LOOP_CW, so its cells are neighbours.
+constexpr float LOOP_CW = 17.0f;
+static_assert(2.0f * 1.41421357f * LOOP_SRMAX + LOOP_DC < LOOP_CW, "centre cells hold the pair tolerance");
+__device__ __forceinline__ int loop_cell(float c)
+{
+    const float t = (c + 0.5f * LOOP_G * LOOP_CW) * (1.0f / LOOP_CW);
+    return (int)fminf(fmaxf(t, 0.0f), (float)(LOOP_G - 1));   // NaN -> 0
+}
 __device__ __forceinline__ int loop_bin(const LoopCand& c)
 {
-    return c.frame * LOOP_NBIN + min((int)(c.R * (1.0f / LOOP_BINW)), LOOP_NBIN - 1);
+    return c.frame * LOOP_NBIN + loop_cell(c.cy) * LOOP_G + loop_cell(c.cx);
 }
 
 // per track: its candidate record (or none), group and leg -1
@@ -2350,21 +2359,23 @@ __device__ __forceinline__ void uf_union(int32_t* par, int a, int b, int* err)
     atomicExch(err, 1);
 }
 
-// one thread per candidate: the candidates of its frame in the radius bins
-// within the tolerance, each unordered pair tested once (i < j)
+// one thread per candidate: the candidates of its frame in the 3 x 3 centre
+// cells around its own, each unordered pair tested once (i < j)
 __global__ void k_loop_pairs(LoopArgs A)
 {
     const int T = A.f->err ? 0 : min(A.f->n_tracks, A.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
         const LoopCand a = A.cand[i];
         if (a.frame < 0) continue;
-        const int b0 = loop_bin(a);
-        const int lo = max(b0 - LOOP_WBINS, a.frame * LOOP_NBIN);
-        const int hi = min(b0 + LOOP_WBINS, a.frame * LOOP_NBIN + LOOP_NBIN - 1);
-        for (uint32_t q = A.bincnt[lo]; q < A.bincnt[hi + 1]; q++) {
-            const int j = A.sorted[q];
-            if (j <= i) continue;
-            if (loop_pair(a, A.cand[j], A.zmax)) uf_union(A.par, i, j, A.err);
+        const int gx = loop_cell(a.cx), gy = loop_cell(a.cy);
+        const int x0 = max(gx - 1, 0), x1 = min(gx + 1, LOOP_G - 1);
+        for (int yy = max(gy - 1, 0); yy <= min(gy + 1, LOOP_G - 1); yy++) {
+            const int row = a.frame * LOOP_NBIN + yy * LOOP_G;
+            for (uint32_t q = A.bincnt[row + x0]; q < A.bincnt[row + x1 + 1]; q++) {
+                const int j = A.sorted[q];
+                if (j <= i) continue;
+                if (loop_pair(a, A.cand[j], A.zmax)) uf_union(A.par, i, j, A.err);
+            }
         }
     }
 }

@@ -75,3 +75,82 @@ def test_format_fields_of_a_frame(orc):
     for name, v in f.items():
         coded += _check(orc, _symbols(v), 4096)
     assert coded > 0
+
+
+# ---------------------------------------------------------------------------
+# the whole format on the GPU (tpc_compress_fields / tpc_compress_frame)
+# against the oracle's fields and containers, on the same tracks
+# ---------------------------------------------------------------------------
+def _dev(a, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dt)).cuda()
+
+
+def _format_check(orc, sector, row, y, zt, off, clus, assign, n_sectors, n_rows, chunk=4096, ey=5, et=6):
+    import types
+
+    import paper_1905_05515_b300 as tpc
+    args = (_dev(sector, np.uint8), _dev(row, np.uint8), _dev(y, np.float32), _dev(zt, np.float32),
+            _dev(off, np.int32), _dev(clus if len(clus) else np.zeros(0), np.int32), _dev(assign, np.int32))
+    r = types.SimpleNamespace(n_tracks=len(off) - 1, tr_off=np.asarray(off, np.int32),
+                              tr_clus=np.asarray(clus, np.int32), assign=np.asarray(assign, np.int32))
+    exp = orc.compress_fields(sector, row, y, zt, r, n_sectors=n_sectors, n_rows=n_rows, ey=ey, et=et)
+    got = tpc.compress_fields(*args, n_sectors=n_sectors, n_rows=n_rows, ey=ey, et=et)
+    for name in exp:
+        np.testing.assert_array_equal(got[name].cpu().numpy().view(np.uint32), exp[name], err_msg=name)
+    data, sizes = tpc.compress_frame(*args, n_sectors=n_sectors, n_rows=n_rows, ey=ey, et=et, chunk=chunk)
+    conts = [orc.pack_stream(exp[name], chunk) for name in exp]
+    assert sizes == [c.size for c in conts]
+    np.testing.assert_array_equal(data.cpu().numpy(), np.concatenate(conts))
+    return data.numel()
+
+
+@pytest.mark.parametrize("make", [lambda: tpcgen.time_frame(seed=3, n_collisions=3, with_truth=False),
+                                  lambda: tpcgen.one_sector(seed=1, with_truth=False)])
+def test_format_matches_oracle(orc, make):
+    """Fields and containers of a frame byte-identical to the oracle's, with
+    the oracle's own tracks as the tracks of both sides."""
+    ev = make()
+    r = orc.track_event(ev)
+    nb = _format_check(orc, ev.sector, ev.row, ev.y, ev.zt, r.tr_off, r.tr_clus, r.assign, ev.n_sectors,
+                       ev.row_x.size)
+    assert nb < 10 * ev.n                  # smaller than the float clusters
+
+
+def test_format_edge_cases(orc):
+    """No tracks; one crowded plane of other clusters (more than the shared
+    memory holds); tracks with sector changes, same-row neighbours and
+    escapes; empty streams; several chunk sizes."""
+    rng = np.random.default_rng(11)
+    # a crowded plane and nothing attached
+    n = 5000
+    sec = np.full(n, 3, np.uint8)
+    row = np.full(n, 17, np.uint8)
+    y = rng.uniform(-20, 20, n).astype(np.float32)
+    zt = rng.uniform(0, 1000, n).astype(np.float32)
+    zt[:50] = zt[50]                       # ties in qt: qy and the index decide
+    _format_check(orc, sec, row, y, zt, [0], [], np.full(n, -1), 36, 152, chunk=1000)
+    # hand-made tracks over a random frame
+    n = 3000
+    sec = rng.integers(0, 36, n).astype(np.uint8)
+    row = rng.integers(0, 152, n).astype(np.uint8)
+    y = rng.uniform(-40, 40, n).astype(np.float32)
+    zt = rng.uniform(0, 2000, n).astype(np.float32)
+    perm = rng.permutation(n)[:2000]
+    lens = [0, 1, 2, 5, 150, 300, 0, 40]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    clus = perm[:off[-1]].astype(np.int32)
+    # runs with same-row neighbours inside a sector
+    a = off[4]
+    sec[clus[a:a + 150]] = 7
+    row[clus[a:a + 150]] = np.repeat(np.arange(75), 2)
+    assign = np.full(n, -1, np.int32)
+    for t in range(len(lens)):
+        assign[clus[off[t]:off[t + 1]]] = t
+    y[clus[off[5]:off[5] + 10]] = 3000.0   # large residuals: escapes
+    for chunk in (1, 64, 4096):
+        _format_check(orc, sec, row, y, zt, off, clus, assign, 36, 152, chunk=chunk)
+    # other quantisation steps
+    _format_check(orc, sec, row, y, zt, off, clus, assign, 36, 152, ey=3, et=8)
+    # no clusters at all
+    _format_check(orc, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), [0], [], np.zeros(0), 36, 152)
