@@ -23,7 +23,9 @@
  * its clusters (outermost first) ending with a primary-vertex
  * pseudo-measurement (y = z = 0 at the origin, variance vertex_var; the last
  * step rotates the frame about the origin onto the innermost reference
- * position, then follows the helix to x = 0), linearised
+ * position, then follows the helix to x = 0) and, for a track with a dip
+ * angle from the matched inner track (tgl_ext), one more update of
+ * tan(lambda) with variance tgl_var at the vertex, linearised
  * around a reference helix that does not depend on theta: the tracker's
  * output state (tpc_tracks.param etc.), its z moved from the tracker's frame
  * to absolute z by sgn v_nominal t_c, carried along the cluster planes.  Step
@@ -75,6 +77,9 @@ typedef struct {
     const uint8_t *cl_row;        /* [n] */
     const float *cl_y;            /* [n] local y (cm) */
     const float *cl_t;            /* [n] drift time (us) */
+    const float *tgl_ext;         /* [T] dip angle tan(lambda) of the matched inner track, NaN = none;
+                                     NULL: no track has one */
+    float tgl_var;                /* its variance (> 0 when tgl_ext is given) */
 } tpc_calib_tracks;
 
 /* Device workspace (bytes) for n_tracks tracks holding at most n_clusters
@@ -119,6 +124,57 @@ int tpc_calib_backward(const tpc_params *p, const tpc_geometry *g, float bz, flo
 #define TPC_CALIB_QPT_MAX 5.0f
 int tpc_calib_select(int32_t n_tracks, const float *t_coll, const int32_t *status, const float *param,
                      float qpt_max, float *t_sel, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Closed-loop calibration (section "TPC Tracking": online drift-velocity
+ * calibration; this library's reading): theta minimising
+ *   F(theta) = sum over the selected tracks of chi2_r(theta)
+ *              + sum over the spline coefficients of (c / prior_sigma)^2,
+ * by L-BFGS (memory 10, backtracking line search with the sufficient
+ * decrease condition) in the variables x = (theta - theta_start) / s with
+ * s = (scale_v, scale_t0, prior_sigma, ...), chi2 and gradient from
+ * tpc_calib_forward / tpc_calib_backward on the GPU, the L-BFGS algebra on
+ * the host in binary64.  The Gaussian prior decides between the spline map
+ * and (v, t0) where the tracks cannot: a common z offset or z scale of every
+ * sector.  Track selection: the first round uses the tracks with t_coll set
+ * whose chi2 / ndf (ndf = 2 n) at theta_start is below chi2ndf_first and the
+ * dip angles whose chi2 contribution there is below anchor_cut_first; each
+ * later round re-selects at the current theta with chi2ndf_cut and
+ * anchor_cut and continues from it.  A round ends after max_iter iterations
+ * or when an iteration lowers F by less than ftol F.
+ * -------------------------------------------------------------------- */
+typedef struct {
+    float prior_sigma;            /* spline coefficients (cm), default 0.3 */
+    float scale_v, scale_t0;      /* variable scales of v (cm/us) and t0 (us): 0.01, 0.1 */
+    int32_t max_iter;             /* L-BFGS iterations per round (300) */
+    int32_t rounds;               /* rounds after the first (2) */
+    float chi2ndf_first, anchor_cut_first;   /* first selection (10, 100) */
+    float chi2ndf_cut, anchor_cut;           /* later selections (2.5, 16) */
+    double ftol;                  /* 1e-10 */
+} tpc_calib_fit_opts;
+
+typedef struct {
+    double f_start, f_final;      /* F at theta_start (first selection) and at the result (last selection) */
+    int32_t evaluations;          /* chi2 + gradient evaluations (forward + backward pairs) */
+    int32_t rounds;               /* rounds run */
+    int32_t tracks, anchors;      /* tracks and dip angles of the last selection */
+} tpc_calib_fit_report;
+
+int tpc_calib_fit_defaults(tpc_calib_fit_opts *opt);
+
+/* Device workspace of tpc_calib_fit: the pass's workspace plus per-track
+ * selections, chi2 buffers and the gradient.  Errors: TPC_ERR_ARG. */
+int tpc_calib_fit_workspace_size(const tpc_geometry *g, int32_t n_tracks, int64_t n_clusters, size_t *bytes);
+
+/* theta (device, binary32, TPC_CALIB_N_THETA(n_sectors)): the start on entry,
+ * the result on return.  t_used / tgl_used (device [n_tracks], may be NULL):
+ * the last selection, as t_coll / tgl_ext with NaN for the tracks and dip
+ * angles left out.  rep (host) may be NULL.  Synchronises `stream` at every
+ * evaluation.  Errors: as tpc_calib_forward; TPC_ERR_DATA when a pass flags
+ * invalid track data. */
+int tpc_calib_fit(const tpc_params *p, const tpc_geometry *g, float bz, float v_nominal, float vertex_var,
+                  const tpc_calib_tracks *tr, const tpc_calib_fit_opts *opt, float *theta, void *workspace,
+                  size_t ws_bytes, float *t_used, float *tgl_used, tpc_calib_fit_report *rep, void *stream);
 
 /* Synchronises `stream` and writes the workspace's error flag to *err
  * (0: none; 1: invalid track data seen).  Errors: TPC_ERR_ARG, TPC_ERR_CUDA. */

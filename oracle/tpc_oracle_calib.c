@@ -123,10 +123,16 @@ typedef struct {
     double sgn;
     int sector, i0, j0;
     double Bu[4], Bw[4];
+    /* error scale of m_z: s = (v / v_nom) (1 - d dz / d zl at the nominal
+     * position), its derivatives: ds/dv = s / v, ds/dc[i0+a][j0n+b][1] =
+     * -(v / v_nom) Bu[a] dBn[b] */
+    double s;
+    int j0n;
+    double dBn[4];
 } meas_t;
 
-static void measure(const orc_geom *G, const double *theta, int sector, int row, double y, double t, double tc,
-                    meas_t *m)
+static void measure(const orc_geom *G, const double *theta, double v_nom, int sector, int row, double y, double t,
+                    double tc, meas_t *m)
 {
     const double v = theta[0], t0 = theta[1];
     const double x_first = G->row_x[0], x_last = G->row_x[G->n_rows - 1];
@@ -159,6 +165,17 @@ static void measure(const orc_geom *G, const double *theta, int sector, int row,
     m->dmz_dt0 = sgn * (1.0 - dz_w * dw_dzl) * dzl[1];
     m->sgn = sgn;
     m->sector = sector;
+    /* the drift-time error carried into m_z: the slope of the map is taken at
+     * the nominal position (v_nom, no t0), so that s is linear in the map */
+    const double wn = (zmax - v_nom * (t - tc)) / zmax;
+    const double dwn = (wn > 0.0 && wn < 1.0) ? 1.0 / zmax : 0.0;
+    double Bn[4], dBn[4];
+    m->j0n = bspline(wn, Bn, dBn);
+    double dzn = 0.0;
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) dzn += m->Bu[a] * dBn[b] * c[((m->i0 + a) * NSPL + (m->j0n + b)) * 2 + 1];
+    m->s = (v / v_nom) * (1.0 - dzn * dwn);
+    for (int b = 0; b < 4; b++) m->dBn[b] = dBn[b] * dwn;
 }
 
 void orc_calib_measure(const orc_geom *G, const double *theta, int32_t n, const uint8_t *sector,
@@ -166,7 +183,7 @@ void orc_calib_measure(const orc_geom *G, const double *theta, int32_t n, const 
 {
     for (int32_t i = 0; i < n; i++) {
         meas_t m;
-        measure(G, theta, sector[i], row[i], y[i], t[i], tc[i], &m);
+        measure(G, theta, theta[0], sector[i], row[i], y[i], t[i], tc[i], &m);
         my[i] = m.my;
         mz[i] = m.mz;
     }
@@ -270,11 +287,11 @@ static int track_pass(const orc_params *P, const orc_geom *G, double kb, double 
         if (k < n) {
             const int c = tr_clus[off + n - 1 - k];
             if (k > 0 && !ref_step(G, kb, &sec, &x, q, sector[c], G->row_x[row[c]], st->F)) return 0;
-            measure(G, theta, sector[c], row[c], y[c], t[c], tc, &st->m);
+            measure(G, theta, v_nom, sector[c], row[c], y[c], t[c], tc, &st->m);
             st->my = st->m.my;
             st->mz = st->m.mz;
             st->vy = vy;
-            st->vz = vz;
+            st->vz = vz * st->m.s * st->m.s;
         } else {
             if (!vertex_step(kb, &x, q, st->F)) return 0;
             st->my = 0.0;
@@ -289,7 +306,7 @@ static int track_pass(const orc_params *P, const orc_geom *G, double kb, double 
                 for (int j = 0; j < 5; j++) st->F[i][j] = 0.0;
             memset(C, 0, sizeof(C));
             C[0][0] = vy;
-            C[1][1] = vz;
+            C[1][1] = st->vz;
             C[2][2] = P->c0_snp;
             C[3][3] = P->c0_tgl;
             C[4][4] = P->c0_qpt;
@@ -405,6 +422,17 @@ int orc_calib(const orc_params *P, const orc_geom *G, double bz, double v_nom, d
             }
             if (k == n) continue;          /* the vertex does not depend on theta */
             const meas_t *m = &st->m;
+            /* through the variance of m_z: d chi2 / d vz = -(r*_z / vz)^2 with
+             * the smoothed residual r*_z = vz a_z / 2, d vz / ds = 2 vz / s */
+            const double q = -0.5 * a[1] * a[1] * st->vz / m->s;
+            grad[0] += wr * q * m->s / theta[0];
+            {
+                double *gz = grad + 2 + (size_t)m->sector * NSPL * NSPL * 2;
+                const double f = -theta[0] / v_nom;
+                for (int i = 0; i < 4; i++)
+                    for (int j = 0; j < 4; j++)
+                        gz[((m->i0 + i) * NSPL + (m->j0n + j)) * 2 + 1] += wr * q * f * m->Bu[i] * m->dBn[j];
+            }
             grad[0] += wr * (a[0] * m->dmy_dv + a[1] * m->dmz_dv);
             grad[1] += wr * (a[0] * m->dmy_dt0 + a[1] * m->dmz_dt0);
             double *g = grad + 2 + (size_t)m->sector * NSPL * NSPL * 2;

@@ -139,7 +139,7 @@ def lib(build_if_missing: bool = True):
                                                    C.POINTER(C.c_size_t)]
         L.tpc_calib_fit.argtypes = [C.POINTER(TpcParams), C.POINTER(TpcGeometry), C.c_float, C.c_float, C.c_float,
                                     C.POINTER(TpcCalibTracks), C.POINTER(TpcCalibFitOpts), C.c_void_p, C.c_void_p,
-                                    C.c_size_t, C.POINTER(TpcCalibFitReport), C.c_void_p]
+                                    C.c_size_t, C.c_void_p, C.c_void_p, C.POINTER(TpcCalibFitReport), C.c_void_p]
         L.tpc_compress_workspace_size.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.POINTER(C.c_size_t)]
         L.tpc_compress_max_size.argtypes = [C.POINTER(TpcCompressIn), C.c_int32, C.POINTER(C.c_int64),
                                             C.POINTER(C.c_int64)]

@@ -19,6 +19,7 @@ import torch
 from . import abi
 
 VERTEX_VAR = 0.01          # primary-vertex pseudo-measurement variance (cm^2)
+TGL_VAR = 9e-8             # dip angle of the matched inner track: variance (sigma 3e-4)
 QPT_MAX = 5.0              # TPC_CALIB_QPT_MAX: tracks below pT = 0.2 GeV/c (loopers) are left out
 
 
@@ -60,7 +61,8 @@ class CalibRefit:
 
     def __init__(self, sector, x, param, clus_offset, clus_index, t_coll, cl_sector, cl_row, cl_y, cl_t, row_x,
                  n_sectors: int = 36, z_max: float = 250.0, bz: float = 0.5, v_nominal: float = 2.58,
-                 params: abi.TpcParams | None = None, vertex_var: float = VERTEX_VAR):
+                 params: abi.TpcParams | None = None, vertex_var: float = VERTEX_VAR, tgl_ext=None,
+                 tgl_var: float = TGL_VAR):
         self.lib = abi.lib()
         dev = param.device
         if dev.type != "cuda":
@@ -78,6 +80,8 @@ class CalibRefit:
                       clus_index=clus_index.to(device=dev, dtype=torch.int32).contiguous(),
                       t_coll=prep(t_coll, torch.float32, T), cl_sector=cl_sector.contiguous(),
                       cl_row=cl_row.contiguous(), cl_y=cl_y.contiguous(), cl_t=cl_t.contiguous())
+        if tgl_ext is not None:
+            self.t["tgl_ext"] = prep(tgl_ext, torch.float32, T)
         for k, dt in (("cl_sector", torch.uint8), ("cl_row", torch.uint8), ("cl_y", torch.float32),
                       ("cl_t", torch.float32)):
             if self.t[k].dtype != dt or not self.t[k].is_cuda:
@@ -99,7 +103,8 @@ class CalibRefit:
         self._tracks = abi.TpcCalibTracks(T, st["sector"].data_ptr(), st["x"].data_ptr(), st["param"].data_ptr(),
                                           st["clus_offset"].data_ptr(), st["clus_index"].data_ptr(),
                                           st["t_coll"].data_ptr(), self.n_clusters, st["cl_sector"].data_ptr(),
-                                          st["cl_row"].data_ptr(), st["cl_y"].data_ptr(), st["cl_t"].data_ptr())
+                                          st["cl_row"].data_ptr(), st["cl_y"].data_ptr(), st["cl_t"].data_ptr(),
+                                          st["tgl_ext"].data_ptr() if "tgl_ext" in st else None, float(tgl_var))
 
     @classmethod
     def from_result(cls, res, t_coll, sector, row, y, zt, row_x, **kw):
@@ -149,6 +154,42 @@ class CalibRefit:
         if check:
             self.check(ws)
         return grad
+
+    def fit(self, theta: torch.Tensor, **opts):
+        """Closed-loop calibration (tpc_calib_fit): theta minimising the summed
+        chi2 of the selected tracks plus the spline prior, from ``theta`` (a
+        copy is returned with the report).  Keyword options: the fields of
+        tpc_calib_fit_opts (prior_sigma, scale_v, scale_t0, max_iter, rounds,
+        chi2ndf_first, anchor_cut_first, chi2ndf_cut, anchor_cut, ftol).  The
+        report holds the last selection too: ``t_used`` / ``tgl_used`` (CUDA
+        float32 [n_tracks], NaN where left out)."""
+        th = self._theta(theta).clone()
+        o = abi.TpcCalibFitOpts()
+        self.lib.tpc_calib_fit_defaults(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise ValueError(f"unknown fit option {k}")
+            setattr(o, k, v)
+        s = C.c_size_t(0)
+        rc = self.lib.tpc_calib_fit_workspace_size(C.byref(self.geometry), self.n_tracks, self.n_clusters,
+                                                   C.byref(s))
+        if rc:
+            raise abi.TpcError(rc, "tpc_calib_fit_workspace_size")
+        ws = torch.empty(int(s.value), dtype=torch.uint8, device=self.device)
+        rep = abi.TpcCalibFitReport()
+        st = torch.cuda.current_stream(self.device)
+        tu = torch.empty(max(self.n_tracks, 1), dtype=torch.float32, device=self.device)
+        gu = torch.empty_like(tu)
+        rc = self.lib.tpc_calib_fit(C.byref(self.params), C.byref(self.geometry), self.bz, self.v_nominal,
+                                    self.vertex_var, C.byref(self._tracks), C.byref(o), C.c_void_p(th.data_ptr()),
+                                    C.c_void_p(ws.data_ptr()), int(s.value), C.c_void_p(tu.data_ptr()),
+                                    C.c_void_p(gu.data_ptr()), C.byref(rep), C.c_void_p(st.cuda_stream))
+        if rc:
+            raise abi.TpcError(rc, "tpc_calib_fit")
+        out = {k: getattr(rep, k) for k, _ in rep._fields_}
+        out["t_used"] = tu[:self.n_tracks]
+        out["tgl_used"] = gu[:self.n_tracks]
+        return th, out
 
     def check(self, ws):
         err = C.c_int32(0)

@@ -26,6 +26,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <vector>
 
 using namespace tpc;
 using namespace tpc::fit;
@@ -59,6 +61,8 @@ struct CalibArgs {
     const float* cy;
     const float* ct;
     const float* theta;
+    const float* tgl;                   // [T] dip angle of the matched inner track (NaN: none), may be null
+    float tvar;
     float* chi2;
     uint8_t* used;
     const uint8_t* used_in;
@@ -130,6 +134,12 @@ struct Meas {
     float sgn;
     int s, i0, j0;
     float Bu[4], Bw[4];
+    // error scale of m_z (the drift-time error through the map): es = (v /
+    // v_nom) (1 - d dz / d zl at the nominal position); d es / d c[i0+a]
+    // [j0n+b][z] = -(v / v_nom) Bu[a] dBn[b]
+    float es;
+    int j0n;
+    float dBn[4];
 };
 
 // per-row u-basis table in shared memory: ub[4 r + a] the four non-zero
@@ -193,6 +203,23 @@ __device__ __forceinline__ void measure(const CalibArgs& A, const float* __restr
     m.dz_t0 = kz * v;
     m.sgn = sgn;
     m.s = s;
+    // the slope of the map at the nominal position (v_nom, no t0)
+    const float wn = (A.zmax - A.v_nom * (A.ct[c] - tc)) / A.zmax;
+    const float dwn = (wn > 0.0f && wn < 1.0f) ? 1.0f / A.zmax : 0.0f;
+    float Bn[4], dBn[4];
+    m.j0n = bspline(wn, Bn, dBn);
+    const float* cn = spl + (s * NSPL * NSPL + m.i0 * NSPL + m.j0n) * 2;
+    float dzn = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        float rz = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; b++) rz += dBn[b] * cn[(a * NSPL + b) * 2 + 1];
+        dzn += m.Bu[a] * rz;
+    }
+    m.es = (v / A.v_nom) * (1.0f - dzn * dwn);
+#pragma unroll
+    for (int b = 0; b < 4; b++) m.dBn[b] = dBn[b] * dwn;
 }
 
 // pass state: reference (x, sector, p + pl) and deviation (dp, C)
@@ -408,7 +435,7 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
 #pragma unroll
             for (int i = 0; i < 15; i++) S.C[i] = 0.0f;
             S.C[0] = A.vy;
-            S.C[2] = A.vz;
+            S.C[2] = A.vz * m.es * m.es;
             S.C[CI(2, 2)] = A.c0s;
             S.C[CI(3, 3)] = A.c0t;
             S.C[CI(4, 4)] = A.c0q;
@@ -424,7 +451,7 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
                     my = m.my;
                     mz = m.mz;
                     vy = A.vy;
-                    vz = A.vz;
+                    vz = A.vz * m.es * m.es;
                 } else {
                     ok = vertex_step(A, S, R);
                     if (!ok) break;
@@ -433,6 +460,21 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_fwd(CalibArgs A)
                 }
                 ok = filter_step(S, R, my, mz, vy, vz, chi2);
                 if (ok && k % SEG == 0 && k < n) save_ckpt(ck + (k / SEG) * (CK_FLOATS / 4), S);
+            }
+            // the dip angle of the matched inner track: one more update at the
+            // vertex (H selects tan(lambda)); no covariance is needed after it
+            const float tm = (ok && A.tgl) ? A.tgl[r] : __int_as_float(0x7fc00000);
+            if (!isnan(tm)) {
+                const float rr = ((tm - S.p[3]) - S.pl[3]) - S.dp[3];
+                const float sv = S.C[CI(3, 3)] + A.tvar;
+                if (!(sv > 0.0f)) {
+                    ok = false;
+                } else {
+                    const float w = 1.0f / sv;
+                    chi2 += rr * w * rr;
+#pragma unroll
+                    for (int i = 0; i < 5; i++) S.dp[i] += S.C[cidx(i, 3)] * w * rr;
+                }
             }
             if (ok) {
                 A.dfin[2 * (int64_t)r] = make_float4(S.dp[0], S.dp[1], S.dp[2], S.dp[3]);
@@ -468,6 +510,46 @@ __device__ __forceinline__ void flush(GradAcc& G, double* grad)
 #pragma unroll
     for (int q = 0; q < 32; q++) G.g[q] = 0.0f;
     G.key = -1;
+}
+
+// Sums of the error-scale term of the z coefficients (support of the
+// nominal-position slope), flushed like GradAcc
+struct SlopeAcc {
+    int key;
+    float g[16];         // [i * 4 + j]
+};
+
+__device__ __forceinline__ void flush(SlopeAcc& G, double* grad)
+{
+    if (G.key < 0) return;
+    const int s = G.key >> 6, i0 = (G.key >> 3) & 7, j0 = G.key & 7;
+    double* g = grad + 2 + (s * NSPL * NSPL + i0 * NSPL + j0) * 2;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) atomicAdd(&g[(i * NSPL + j) * 2 + 1], (double)G.g[i * 4 + j]);
+#pragma unroll
+    for (int q = 0; q < 16; q++) G.g[q] = 0.0f;
+    G.key = -1;
+}
+
+// the derivative through the variance of m_z: with V = vz es^2 and the
+// smoothed residual r1, d chi2 / d es = -2 r1^2 / (V es) (weight wr)
+__device__ __forceinline__ void scatter_var(const CalibArgs& A, SlopeAcc& G, const Meas& m, float wr, float r1,
+                                            float iv, float& gv, double* grad)
+{
+    const float q = -2.0f * wr * r1 * r1 * iv / m.es;
+    gv += q * m.es / A.theta[0];
+    const int key = m.s * 64 + m.i0 * 8 + m.j0n;
+    if (key != G.key) {
+        flush(G, grad);
+        G.key = key;
+    }
+    const float f = -q * A.theta[0] / A.v_nom;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) G.g[i * 4 + j] += f * m.Bu[i] * m.dBn[j];
 }
 
 // adds a0 dm_y/dtheta + a1 dm_z/dtheta of measurement m
@@ -557,6 +639,10 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
         G.key = -1;
 #pragma unroll
         for (int q = 0; q < 32; q++) G.g[q] = 0.0f;
+        SlopeAcc GS;
+        GS.key = -1;
+#pragma unroll
+        for (int q = 0; q < 16; q++) GS.g[q] = 0.0f;
         const int nseg = (n + SEG - 1) / SEG;
         bool ok = true;
         float hy = 0.0f, hyl = 0.0f, hz = 0.0f, hzl = 0.0f;
@@ -595,7 +681,9 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
                     measure(A, spl, rb, c, tc, m);
                     const float r0 = ((m.my - R.y) - R.yl) - dev[0];
                     const float r1 = ((m.mz - R.z) - R.zl) - dev[1];
-                    scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * ivz * r1, gv, gt0, A.grad);
+                    const float iv = ivz / (m.es * m.es);
+                    scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * iv * r1, gv, gt0, A.grad);
+                    scatter_var(A, GS, m, wr, r1, iv, gv, A.grad);
                 }
                 inv_step(R, dev);
             }
@@ -608,9 +696,12 @@ __global__ void __launch_bounds__(CALIB_BLOCK) k_calib_bwd(CalibArgs A)
             measure(A, spl, rb, c, tc, m);
             const float r0 = ((m.my - hy) - hyl) - dev[0];
             const float r1 = ((m.mz - hz) - hzl) - dev[1];
-            scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * ivz * r1, gv, gt0, A.grad);
+            const float iv = ivz / (m.es * m.es);
+            scatter_grad(A, spl, rb, G, m, 2.0f * wr * ivy * r0, 2.0f * wr * iv * r1, gv, gt0, A.grad);
+            scatter_var(A, GS, m, wr, r1, iv, gv, A.grad);
         }
         flush(G, A.grad);
+        flush(GS, A.grad);
         atomicAdd(&gvt[0], (double)gv);
         atomicAdd(&gvt[1], (double)gt0);
     }
@@ -701,6 +792,9 @@ int fill_args(const tpc_params* p, const tpc_geometry* g, float bz, float v_nomi
     A.cy = tr->cl_y;
     A.ct = tr->cl_t;
     A.theta = theta;
+    A.tgl = tr->tgl_ext;
+    A.tvar = tr->tgl_var;
+    if (A.tgl && !(A.tvar > 0.0f)) return TPC_ERR_ARG;
     return TPC_OK;
 }
 
@@ -800,6 +894,345 @@ int tpc_calib_status(const void* workspace, int32_t* err, void* stream)
     if (cudaMemcpyAsync(err, workspace, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return TPC_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Closed-loop calibration (tpc_calib_fit): selection kernels and the host
+// L-BFGS over theta
+// ---------------------------------------------------------------------------
+namespace {
+
+// binary64 sum of chi2 over the used tracks (one block)
+__global__ void __launch_bounds__(1024) k_fit_sum(const float* __restrict__ chi2, const uint8_t* __restrict__ used,
+                                                  int T, double* __restrict__ out)
+{
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < T; r += blockDim.x)
+        if (used[r]) s += (double)chi2[r];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += part[k];
+        *out = t;
+    }
+}
+
+__global__ void k_fit_fill(float* __restrict__ a, int n, float v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+// selection at the current theta: a track is kept when its pass without the
+// dip angle is used and chi2 / (2 n) < ndf_cut; its dip angle when given and
+// its chi2 contribution (with - without) < anchor_cut.  counts[0] tracks,
+// counts[1] dip angles kept.
+__global__ void k_fit_select(int T, const int32_t* __restrict__ off, const float* __restrict__ t_coll,
+                             const float* __restrict__ tgl, const float* __restrict__ chi2_f,
+                             const uint8_t* __restrict__ used_f, const float* __restrict__ chi2_a,
+                             const uint8_t* __restrict__ used_a, float ndf_cut, float anchor_cut,
+                             float* __restrict__ tsel, float* __restrict__ tgl_sel, int* __restrict__ counts)
+{
+    const float NaN = __int_as_float(0x7fc00000);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x) {
+        const float ndf = 2.0f * (float)(off[r + 1] - off[r]);
+        const bool keep = used_f[r] && chi2_f[r] < ndf_cut * ndf;
+        tsel[r] = keep ? t_coll[r] : NaN;
+        bool anc = false;
+        if (tgl) {
+            anc = keep && used_a[r] && !isnan(tgl[r]) && chi2_a[r] - chi2_f[r] < anchor_cut;
+            tgl_sel[r] = anc ? tgl[r] : NaN;
+        }
+        if (keep) atomicAdd(&counts[0], 1);
+        if (anc) atomicAdd(&counts[1], 1);
+    }
+}
+
+struct FitLayout {
+    size_t tsel, tgl, chi2a, chi2f, useda, usedf, ones, grad, theta, sum, counts, total;
+};
+
+FitLayout fit_layout(size_t calib_ws, int32_t T, int n_theta)
+{
+    FitLayout L;
+    size_t o = (calib_ws + 255) / 256 * 256;
+    auto take = [&](size_t b) { size_t r = o; o = (o + std::max<size_t>(b, 1) + 255) / 256 * 256; return r; };
+    L.tsel = take(4 * (size_t)T);
+    L.tgl = take(4 * (size_t)T);
+    L.chi2a = take(4 * (size_t)T);
+    L.chi2f = take(4 * (size_t)T);
+    L.useda = take((size_t)T);
+    L.usedf = take((size_t)T);
+    L.ones = take(4 * (size_t)T);
+    L.grad = take(8 * (size_t)n_theta);
+    L.theta = take(4 * (size_t)n_theta);
+    L.sum = take(8);
+    L.counts = take(8);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpc_calib_fit_defaults(tpc_calib_fit_opts* o)
+{
+    if (!o) return TPC_ERR_ARG;
+    o->prior_sigma = 0.3f;
+    o->scale_v = 0.01f;
+    o->scale_t0 = 0.1f;
+    o->max_iter = 300;
+    o->rounds = 2;
+    o->chi2ndf_first = 10.0f;
+    o->anchor_cut_first = 100.0f;
+    o->chi2ndf_cut = 2.5f;
+    o->anchor_cut = 16.0f;
+    o->ftol = 1e-10;
+    return TPC_OK;
+}
+
+int tpc_calib_fit_workspace_size(const tpc_geometry* g, int32_t n_tracks, int64_t n_clusters, size_t* bytes)
+{
+    size_t cw = 0;
+    int rc = tpc_calib_workspace_size(g, n_tracks, n_clusters, &cw);
+    if (rc) return rc;
+    *bytes = fit_layout(cw, n_tracks, TPC_CALIB_N_THETA(g->n_sectors)).total;
+    return TPC_OK;
+}
+
+int tpc_calib_fit(const tpc_params* p, const tpc_geometry* g, float bz, float v_nominal, float vertex_var,
+                  const tpc_calib_tracks* tr, const tpc_calib_fit_opts* opt, float* theta, void* workspace,
+                  size_t ws_bytes, float* t_used, float* tgl_used, tpc_calib_fit_report* rep, void* stream)
+{
+    if (!p || !g || !tr || !opt || !theta) return TPC_ERR_ARG;
+    {
+        CalibArgs A;
+        const int rc = fill_args(p, g, bz, v_nominal, vertex_var, tr, theta, A);
+        if (rc) return rc;
+    }
+    if (!(opt->prior_sigma > 0.0f) || !(opt->scale_v > 0.0f) || !(opt->scale_t0 > 0.0f) || opt->max_iter < 1 ||
+        opt->rounds < 0 || !(opt->ftol >= 0.0))
+        return TPC_ERR_ARG;
+    size_t cw = 0, need = 0;
+    int rc = tpc_calib_workspace_size(g, tr->n_tracks, tr->n_clusters, &cw);
+    if (rc) return rc;
+    const int T = tr->n_tracks, NT = TPC_CALIB_N_THETA(g->n_sectors);
+    const FitLayout L = fit_layout(cw, T, NT);
+    need = L.total;
+    if (!workspace || ws_bytes < need) return TPC_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = static_cast<char*>(workspace);
+    float* tsel = reinterpret_cast<float*>(ws + L.tsel);
+    float* tgls = reinterpret_cast<float*>(ws + L.tgl);
+    float* chi2a = reinterpret_cast<float*>(ws + L.chi2a);
+    float* chi2f = reinterpret_cast<float*>(ws + L.chi2f);
+    uint8_t* useda = reinterpret_cast<uint8_t*>(ws + L.useda);
+    uint8_t* usedf = reinterpret_cast<uint8_t*>(ws + L.usedf);
+    float* ones = reinterpret_cast<float*>(ws + L.ones);
+    double* gradd = reinterpret_cast<double*>(ws + L.grad);
+    float* thd = reinterpret_cast<float*>(ws + L.theta);
+    double* sumd = reinterpret_cast<double*>(ws + L.sum);
+    int* cnt = reinterpret_cast<int*>(ws + L.counts);
+#define FCK(x) do { if ((x) != cudaSuccess) return TPC_ERR_CUDA; } while (0)
+    const int grid = calib_grid(std::max(T, 1));
+    if (T > 0) k_fit_fill<<<grid, CALIB_BLOCK, 0, st>>>(ones, T, 1.0f);
+    // the start
+    std::vector<float> th32(NT);
+    FCK(cudaMemcpyAsync(th32.data(), theta, 4 * (size_t)NT, cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    std::vector<double> th0(th32.begin(), th32.end());
+    std::vector<double> D(NT, (double)opt->prior_sigma);
+    D[0] = opt->scale_v;
+    D[1] = opt->scale_t0;
+    const double ip2 = 1.0 / ((double)opt->prior_sigma * opt->prior_sigma);
+    tpc_calib_tracks tf = *tr;          // the fit's view: selected tracks and dip angles
+    tf.t_coll = tsel;
+    tf.tgl_ext = tr->tgl_ext ? tgls : nullptr;
+    int evals = 0;
+    // F and dF/dtheta at theta (host, binary64) with the current selection
+    auto evaluate = [&](const std::vector<double>& th, double& F, std::vector<double>& gth) -> int {
+        for (int i = 0; i < NT; i++) th32[i] = (float)th[i];
+        FCK(cudaMemcpyAsync(thd, th32.data(), 4 * (size_t)NT, cudaMemcpyHostToDevice, st));
+        int r2 = tpc_calib_forward(p, g, bz, v_nominal, vertex_var, &tf, thd, chi2a, useda, workspace, cw, stream);
+        if (r2) return r2;
+        if (T > 0) k_fit_sum<<<1, 1024, 0, st>>>(chi2a, useda, T, sumd);
+        else FCK(cudaMemsetAsync(sumd, 0, 8, st));
+        r2 = tpc_calib_backward(p, g, bz, v_nominal, vertex_var, &tf, thd, ones, useda, workspace, cw, gradd,
+                                stream);
+        if (r2) return r2;
+        double s = 0.0;
+        gth.assign(NT, 0.0);
+        FCK(cudaMemcpyAsync(&s, sumd, 8, cudaMemcpyDeviceToHost, st));
+        FCK(cudaMemcpyAsync(gth.data(), gradd, 8 * (size_t)NT, cudaMemcpyDeviceToHost, st));
+        FCK(cudaStreamSynchronize(st));
+        F = s;
+        for (int i = 2; i < NT; i++) {
+            F += th[i] * th[i] * ip2;
+            gth[i] += 2.0 * th[i] * ip2;
+        }
+        evals++;
+        return TPC_OK;
+    };
+    // selection at th
+    auto select = [&](const std::vector<double>& th, float ndf_cut, float anchor_cut, int& ntr, int& nanc) -> int {
+        for (int i = 0; i < NT; i++) th32[i] = (float)th[i];
+        FCK(cudaMemcpyAsync(thd, th32.data(), 4 * (size_t)NT, cudaMemcpyHostToDevice, st));
+        tpc_calib_tracks tfree = *tr;
+        tfree.tgl_ext = nullptr;
+        int r2 = tpc_calib_forward(p, g, bz, v_nominal, vertex_var, &tfree, thd, chi2f, usedf, workspace, cw, stream);
+        if (r2) return r2;
+        if (tr->tgl_ext) {
+            r2 = tpc_calib_forward(p, g, bz, v_nominal, vertex_var, tr, thd, chi2a, useda, workspace, cw, stream);
+            if (r2) return r2;
+        }
+        FCK(cudaMemsetAsync(cnt, 0, 8, st));
+        if (T > 0)
+            k_fit_select<<<grid, CALIB_BLOCK, 0, st>>>(T, tr->clus_offset, tr->t_coll, tr->tgl_ext, chi2f, usedf,
+                                                       chi2a, useda, ndf_cut, anchor_cut, tsel, tgls, cnt);
+        FCK(cudaGetLastError());
+        int c[2] = {0, 0};
+        FCK(cudaMemcpyAsync(c, cnt, 8, cudaMemcpyDeviceToHost, st));
+        FCK(cudaStreamSynchronize(st));
+        ntr = c[0];
+        nanc = c[1];
+        return TPC_OK;
+    };
+    std::vector<double> th = th0, gth, gx(NT), x(NT), xn(NT), gn(NT), thn(NT), d(NT);
+    int ntr = 0, nanc = 0, rounds = 0;
+    double F = 0.0, f_start = 0.0;
+    for (int round = 0; round <= opt->rounds; round++) {
+        rc = select(th, round == 0 ? opt->chi2ndf_first : opt->chi2ndf_cut,
+                    round == 0 ? opt->anchor_cut_first : opt->anchor_cut, ntr, nanc);
+        if (rc) return rc;
+        rounds++;
+        // L-BFGS in x = (theta - base) / D from x = 0
+        const std::vector<double> base = th;
+        std::fill(x.begin(), x.end(), 0.0);
+        if ((rc = evaluate(th, F, gth))) return rc;
+        if (round == 0) f_start = F;
+        for (int i = 0; i < NT; i++) gx[i] = D[i] * gth[i];
+        constexpr int M = 10;
+        std::vector<std::vector<double>> S, Y;
+        std::vector<double> rho;
+        for (int it = 0; it < opt->max_iter; it++) {
+            // two-loop recursion: d = -H gx
+            std::vector<double> q = gx, alpha(S.size());
+            for (int k = (int)S.size() - 1; k >= 0; k--) {
+                double a = 0.0;
+                for (int i = 0; i < NT; i++) a += S[k][i] * q[i];
+                a *= rho[k];
+                alpha[k] = a;
+                for (int i = 0; i < NT; i++) q[i] -= a * Y[k][i];
+            }
+            double gamma = 1.0;
+            if (!S.empty()) {
+                double sy = 0.0, yy = 0.0;
+                for (int i = 0; i < NT; i++) {
+                    sy += S.back()[i] * Y.back()[i];
+                    yy += Y.back()[i] * Y.back()[i];
+                }
+                gamma = sy / yy;
+            } else {
+                double gg = 0.0;
+                for (int i = 0; i < NT; i++) gg += gx[i] * gx[i];
+                gamma = gg > 0.0 ? 1.0 / std::sqrt(gg) : 1.0;
+            }
+            for (int i = 0; i < NT; i++) q[i] *= gamma;
+            for (int k = 0; k < (int)S.size(); k++) {
+                double b = 0.0;
+                for (int i = 0; i < NT; i++) b += Y[k][i] * q[i];
+                b *= rho[k];
+                for (int i = 0; i < NT; i++) q[i] += S[k][i] * (alpha[k] - b);
+            }
+            double dg = 0.0;
+            for (int i = 0; i < NT; i++) {
+                d[i] = -q[i];
+                dg += d[i] * gx[i];
+            }
+            if (!(dg < 0.0)) {              // not a descent direction: restart from the gradient
+                S.clear(); Y.clear(); rho.clear();
+                double gg = 0.0;
+                for (int i = 0; i < NT; i++) gg += gx[i] * gx[i];
+                const double sc = gg > 0.0 ? 1.0 / std::sqrt(gg) : 0.0;
+                dg = 0.0;
+                for (int i = 0; i < NT; i++) {
+                    d[i] = -gx[i] * sc;
+                    dg += d[i] * gx[i];
+                }
+                if (!(dg < 0.0)) break;
+            }
+            double step = 1.0, Fn = 0.0;
+            bool ok = false;
+            for (int ls = 0; ls < 40; ls++) {
+                for (int i = 0; i < NT; i++) {
+                    xn[i] = x[i] + step * d[i];
+                    thn[i] = base[i] + D[i] * xn[i];
+                }
+                std::vector<double> gthn;
+                if ((rc = evaluate(thn, Fn, gthn))) return rc;
+                if (Fn <= F + 1e-4 * step * dg) {
+                    for (int i = 0; i < NT; i++) gn[i] = D[i] * gthn[i];
+                    ok = true;
+                    break;
+                }
+                step *= 0.5;
+            }
+            if (!ok) break;
+            std::vector<double> s(NT), y(NT);
+            double sy = 0.0, ss = 0.0, yy = 0.0;
+            for (int i = 0; i < NT; i++) {
+                s[i] = xn[i] - x[i];
+                y[i] = gn[i] - gx[i];
+                sy += s[i] * y[i];
+                ss += s[i] * s[i];
+                yy += y[i] * y[i];
+            }
+            if (sy > 1e-12 * std::sqrt(ss * yy)) {
+                if ((int)S.size() == M) {
+                    S.erase(S.begin()); Y.erase(Y.begin()); rho.erase(rho.begin());
+                }
+                S.push_back(s); Y.push_back(y); rho.push_back(1.0 / sy);
+            }
+            const double dec = F - Fn;
+            x = xn;
+            gx = gn;
+            F = Fn;
+            for (int i = 0; i < NT; i++) th[i] = base[i] + D[i] * x[i];
+            if (dec < opt->ftol * std::fabs(F)) break;
+        }
+        int32_t e = 0;
+        if ((rc = tpc_calib_status(workspace, &e, stream))) return rc;
+        if (e) return TPC_ERR_DATA;
+    }
+#undef FCK
+    for (int i = 0; i < NT; i++) th32[i] = (float)th[i];
+    if (T > 0 && t_used && cudaMemcpyAsync(t_used, tsel, 4 * (size_t)T, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return TPC_ERR_CUDA;
+    if (T > 0 && tgl_used) {
+        if (tr->tgl_ext) {
+            if (cudaMemcpyAsync(tgl_used, tgls, 4 * (size_t)T, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return TPC_ERR_CUDA;
+        } else {
+            k_fit_fill<<<grid, CALIB_BLOCK, 0, st>>>(tgl_used, T, __builtin_nanf(""));
+        }
+    }
+    if (cudaMemcpyAsync(theta, th32.data(), 4 * (size_t)NT, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return TPC_ERR_CUDA;
+    if (rep) {
+        rep->f_start = f_start;
+        rep->f_final = F;
+        rep->evaluations = evals;
+        rep->rounds = rounds;
+        rep->tracks = ntr;
+        rep->anchors = nanc;
+    }
+    return TPC_OK;
 }
 
 }  // extern "C"

@@ -241,6 +241,7 @@ def test_measurement_derivative_is_twice_the_weighted_smoothed_residual(orc, pro
         n1 = F.shape[0]
         rows, rhs = [], []
         mu0 = np.array([m[0, 0] - h[0, 0], m[0, 1] - h[0, 1], 0, 0, 0])
+        c0 = np.array([v[0, 0], v[0, 1], *c0[2:]])
         for i in range(5):
             e = np.zeros(5)
             e[i] = 1 / np.sqrt(c0[i])
@@ -285,3 +286,35 @@ def test_track_selection_cases():
     out = oracle.calib_select(tc, status, param)
     exp = np.array([10, 20, 30, np.nan, np.nan, np.nan, np.nan], np.float32)
     np.testing.assert_array_equal(out, exp)
+
+
+def test_z_error_follows_the_drift_time(orc, problem):
+    """The z error of a cluster is its drift-time error carried through the
+    calibration map: variance sigma_z^2 s^2 with s = (v / v_nom) (1 - d dz /
+    d zl), the slope of the map taken at the nominal position; s = 1 at the
+    nominal calibration.  The slope here comes from tpcgen's own basis by
+    central differences."""
+    ev, r, tr, th_true, th_nom = problem
+    p = orc.default_params()
+    sz2 = float(np.float32(p["sigma_z"])) ** 2
+    used = orc.calib(tr, th_nom, grad=False)[1]
+    t = int(np.nonzero(used)[0][3])
+    F, h, m, v, c2 = orc.calib_explain(tr, th_nom, t)
+    assert np.allclose(v[:-1, 1], sz2, rtol=1e-6)
+    th = th_true.copy()
+    F, h, m, v, c2 = orc.calib_explain(tr, th, t)
+    n = tr.off[t + 1] - tr.off[t]
+    coef = th[2:].reshape(36, 8, 8, 2)
+    for k in range(n):
+        c = int(tr.clus[tr.off[t] + n - 1 - k])
+        s_ = int(tr.cl_sector[c])
+        u = (tr.row_x[tr.cl_row[c]] - tr.row_x[0]) / (tr.row_x[-1] - tr.row_x[0])
+        wn = (tr.z_max - tr.v_nom * (float(tr.cl_t[c]) - float(tr.tcoll[t]))) / tr.z_max
+        bu = tpcgen.bspline_basis(np.array([u]), 8)[0]
+
+        def dz(w):
+            return float(bu @ coef[s_, :, :, 1] @ tpcgen.bspline_basis(np.array([w]), 8)[0])
+
+        slope = (dz(wn + 1e-6) - dz(wn - 1e-6)) / 2e-6 / tr.z_max if 1e-6 < wn < 1 - 1e-6 else 0.0
+        s = th[0] / tr.v_nom * (1.0 - slope)
+        assert v[k, 1] == pytest.approx(sz2 * s * s, rel=1e-7), k
