@@ -61,6 +61,10 @@ ATTACH_B_PER_CLUSTER = 43
 # scaled to a launch by the cluster count
 NCU_ATTACH_TRAFFIC_B_PER_CLUSTER = 121.2
 NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 194.8}
+# Cluster compression, algorithmic bytes per input cluster (the coded output
+# is added per frame): one read of its sector, row, y, zt (10) and of its
+# assignment (4), one read of its entry in the track cluster lists (4).
+COMPRESS_B_PER_CLUSTER = 18
 
 
 def parse():
@@ -74,6 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-attach", action="store_true",
                     help="frame: skip the timing of the optional cluster attachment stage")
+    ap.add_argument("--no-compress", action="store_true", help="frame: skip the cluster compression object")
     ap.add_argument("--no-batch", action="store_true",
                     help="frame workload: skip the bounded sub-time-frame batch object (graph vs per-frame loop)")
     ap.add_argument("--batch-stf", type=int, default=16, help="frame workload: sub-time-frames of the batch object")
@@ -231,9 +236,40 @@ def cpu_baseline(n_coll: int, seed: int):
     r = oracle.track_event(ev)
     dt = time.perf_counter() - t0
     cpu = time.process_time() - cpu0
-    return {"value": ev.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_coll}-collision frame of the same generator (seed {seed}), {ev.n} clusters, "
-                      f"{r.n_tracks} tracks, {dt:.1f} s wall / {cpu:.1f} s CPU, single thread"}
+    out = {"value": ev.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n_coll}-collision frame of the same generator (seed {seed}), {ev.n} clusters, "
+                     f"{r.n_tracks} tracks, {dt:.1f} s wall / {cpu:.1f} s CPU, single thread"}
+    out["all_cores"] = cpu_all_cores(n_coll, seed)
+    return out
+
+
+def _oracle_frame(job):
+    import oracle
+    import tpcgen
+    seed, n_coll = job
+    ev = tpcgen.time_frame(seed=seed, n_collisions=n_coll, with_truth=False)
+    t0 = time.perf_counter()
+    oracle.track_event(ev)
+    return ev.n, time.perf_counter() - t0
+
+
+def cpu_all_cores(n_coll: int, seed: int):
+    """The oracle on every host core: one independent frame per process (frames
+    shard with no exchange), spawned processes; bounded to 32 processes."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, 32))
+    jobs = [(seed + 100 + k, n_coll) for k in range(cores)]
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_frame, jobs))
+    wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    slow = max(r[1] for r in res)
+    return {"value": n / slow, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} {n_coll}-collision frames tracked side by side, one per spawned process ({n} "
+                      f"clusters); value = all clusters over the slowest process's tracking time ({slow:.1f} s; "
+                      f"{wall:.1f} s wall with process start-up and frame generation)"}
 
 
 def run_reference(args, ws, rank, pg):
@@ -489,6 +525,45 @@ def run_ours(args, ws, rank, local, pg):
         torch.cuda.empty_cache()
     barrier()
 
+    # ---- the cluster compression of the frame (not part of the step): the
+    # compressed format of the frame's clusters with the step's tracks
+    compress = None
+    if not args.no_compress:
+        T = rs.n_tracks
+        off = rs.clus_offset[:T + 1].contiguous()
+        na = int(off[-1].item()) if T else 0
+        cargs = (dv["sector"], dv["row"], dv["y"], dv["zt"], off, rs.clus_index[:na].contiguous(),
+                 rs.assign.contiguous())
+        cw, co = tpc.compress.compress_buffers(*cargs)
+        for _ in range(args.warmup):
+            data, sizes = tpc.compress_frame(*cargs, workspace=cw, out=co)
+        first = data.clone()
+        ce = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        c_ms = []
+        for _ in range(args.steps):
+            ce[0].record(stream)
+            data, sizes = tpc.compress_frame(*cargs, workspace=cw, out=co)
+            ce[1].record(stream)
+            torch.cuda.synchronize()
+            c_ms.append(ce[0].elapsed_time(ce[1]))
+        t_c = sum(c_ms) / len(c_ms)
+        total = sum(sizes)
+        hbm = peaks().get("hbm_gbs") or 6400.0
+        alg = COMPRESS_B_PER_CLUSTER * n + total
+        compress = {"ms": round(t_c, 4), "bytes": total, "bytes_per_cluster": round(total / n, 4),
+                    "factor_vs_float_clusters": round(10.0 * n / total, 3),
+                    "input_gb_per_s": round(10.0 * n / (t_c / 1e3) / 1e9, 1),
+                    "stream_bytes": dict(zip(tpc.abi.CMP_STREAMS, sizes)),
+                    "repeat_identical": bool(torch.equal(first, data)),
+                    "roofline": {"bound": "hbm", "achieved": round(alg / (t_c / 1e3) / 1e9, 1), "unit": "GB/s",
+                                 "peak": hbm, "frac": round(alg / (t_c / 1e3) / 1e9 / hbm, 4),
+                                 "bytes_per_cluster": COMPRESS_B_PER_CLUSTER, "traffic": None,
+                                 "peak_note": "measured" if peaks().get("hbm_gbs") else "fallback"},
+                    "timing": "CUDA events around tpc_compress_frame (it synchronises twice to read stream sizes)"}
+        del cw, co, data, first
+        torch.cuda.empty_cache()
+    barrier()
+
     # ---- the bounded batch object: graph-captured frame groups against the per-frame loop
     batch = None
     if batch_in is not None:
@@ -540,6 +615,8 @@ def run_ours(args, ws, rank, local, pg):
                                      "best of the CUDA-event-timed launches after warm-up"}
     if attach is not None:
         line["attach"] = attach
+    if compress is not None:
+        line["compress"] = compress
     if batch is not None:
         line["batch"] = batch
     if not args.no_cpu_baseline:
@@ -863,9 +940,12 @@ def run_batch(args, ws, rank, local, pg):
 # (w B-spline basis 40, 4 x 4 spline sums 64, chain rule 10) 114; the backward
 # recomputes the reference step (60) and the measurement (114), forms the
 # smoothed residual (6), applies the inverse step Jacobians (16) and adds the
-# 4 x 4 x 2 gradient products (70)
-FLOPS_CALIB_FWD = 366
-FLOPS_CALIB_BWD = 266
+# 4 x 4 x 2 gradient products (70); both evaluate the map's slope at the
+# nominal position for the error scale of m_z (basis 40, 4 x 4 sums 32,
+# scale and variance 6) and the backward adds its 4 x 4 variance-term
+# products (40)
+FLOPS_CALIB_FWD = 444
+FLOPS_CALIB_BWD = 384
 
 
 def run_calib(args, ws, rank, local, pg):
@@ -890,7 +970,8 @@ def run_calib(args, ws, rank, local, pg):
     off = res.clus_offset[:T + 1].cpu().numpy()
     clus = res.clus_index[:int(off[-1])].cpu().numpy()
     tc = tpc.calib.select_tracks(t(tpcgen.track_collision_time(ev, off, clus)), res.status[:T], res.param[:T])
-    calib = tpc.CalibRefit.from_result(res, tc, *cl, ev.row_x, bz=ev.bz, v_nominal=ev.v_drift)
+    tg = t(tpcgen.track_dip_angle(ev, off, clus))
+    calib = tpc.CalibRefit.from_result(res, tc, *cl, ev.row_x, bz=ev.bz, v_nominal=ev.v_drift, tgl_ext=tg)
     theta = tpc.calib.nominal_theta(ev.v_drift, device=dev).requires_grad_(True)
 
     def step():
@@ -958,10 +1039,26 @@ def run_calib(args, ws, rank, local, pg):
         float(loss.item())
         theta.grad.cpu()
     e2e_s = (time.perf_counter() - t0) / args.steps
+    # the closed-loop fit from the nominal calibration (tpc_calib_fit)
+    cal = ev.calib
+    torch.cuda.synchronize()
+    tf0 = time.perf_counter()
+    th_fit, rep = calib.fit(tpc.calib.nominal_theta(ev.v_drift, device=dev))
+    fit_s = time.perf_counter() - tf0
+    th_fit = th_fit.cpu().numpy().astype(np.float64)
+    spl_true = np.asarray(cal["spline"]).ravel()
+    fit = {"s": round(fit_s, 3), "evaluations": rep["evaluations"], "rounds": rep["rounds"],
+           "tracks": rep["tracks"], "dip_angles": rep["anchors"], "f_start": rep["f_start"],
+           "f_final": rep["f_final"], "v_fit": th_fit[0], "v_true": cal["v_drift"],
+           "v_rel_err": th_fit[0] / cal["v_drift"] - 1.0, "t0_fit_us": th_fit[1], "t0_true_us": cal["t0"],
+           "map_rms_err_cm": float(np.sqrt(((th_fit[2:] - spl_true) ** 2).mean())),
+           "map_rms_true_cm": float(np.sqrt((spl_true ** 2).mean())),
+           "how": "L-BFGS over theta on the GPU chi2 and gradient, prior sigma 0.3 cm on the map, "
+                  "dip angles of the matched inner tracks (generator truth smeared by 3e-4)"}
+    pk = fma_peak(dev, 32)
     (ms, e2e_s), (steps_all,) = over_ranks(pg, dev, (ms, e2e_s), (float(n_steps),))
     if rank != 0:
         return
-    pk = FP32_PEAK_TFLOPS
     dom, t_dom, fl = (("calib_backward", bk_ms, FLOPS_CALIB_BWD) if bk_ms >= fk_ms
                       else ("calib_forward", fk_ms, FLOPS_CALIB_FWD))
     bw_tf = n_steps * fl / (t_dom * 1e-3) / 1e12
@@ -978,11 +1075,12 @@ def run_calib(args, ws, rank, local, pg):
                    "l2": "clusters (160 MB) and checkpoints exceed the 126 MB L2; no flush"},
         "roofline": {"bound": "alu", "stage": dom, "achieved": bw_tf, "peak": pk, "unit": "TFLOP/s",
                      "frac": bw_tf / pk, "traffic": None,
-                     "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x 2.032 GHz (derived)"},
+                     "peak_note": "measured binary32 FMA rate (tpc_probe_fma, CUDA events)"},
         "e2e": {"value": steps_all / e2e_s, "unit": "track clusters/s",
                 "h2d_bytes_per_step": 4 * theta.numel(), "d2h_bytes_per_step": 4 + 4 * theta.numel()},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
+        "fit": fit,
     }
     if not args.no_cpu_baseline:
         import oracle

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "tpc_compress.h"
 #include "tpc_track.h"
@@ -62,53 +63,104 @@ __global__ void k_rans_hist(const uint8_t* __restrict__ sym, int64_t n, uint32_t
         if (h[s]) atomicAdd(&hist[s], h[s]);
 }
 
-// one thread: the table (largest remainders), its cumulative sums
-__global__ void k_rans_table(const uint32_t* __restrict__ hist, uint32_t* __restrict__ freq,
-                             uint32_t* __restrict__ cum, int* __restrict__ err)
+// One block of 256 threads, thread s for symbol s: the table (largest
+// remainders) and its cumulative sums.  The missing units go to the present
+// symbols ranked first by (remainder descending, symbol ascending) -- the
+// order in which repeatedly taking the largest remainder, ties to the
+// smaller symbol, hands them out; the surplus after raising absent-looking
+// present symbols to 1 is taken back one unit at a time from the largest
+// frequency above 1 (ties to the smaller symbol), each by a block argmax.
+constexpr int TABLE_THREADS = 256;
+
+__global__ void __launch_bounds__(TABLE_THREADS) k_rans_table(const uint32_t* __restrict__ hist,
+                                                              uint32_t* __restrict__ freq,
+                                                              uint32_t* __restrict__ cum, int* __restrict__ err)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ unsigned long long rem_sh[256];
+    __shared__ uint32_t f_sh[256];
+    __shared__ unsigned long long red64[TABLE_THREADS / 32];
+    __shared__ uint32_t red32[TABLE_THREADS / 32];
+    const int s = threadIdx.x, lane = s & 31, w = s >> 5;
+    const uint32_t h = hist[s];
+    // total
+    unsigned long long t = h;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red64[w] = t;
+    __syncthreads();
     unsigned long long total = 0;
-    for (int s = 0; s < 256; s++) total += hist[s];
+    for (int k = 0; k < TABLE_THREADS / 32; k++) total += red64[k];
     if (total == 0) {
-        for (int s = 0; s < 256; s++) freq[s] = 0;
-        for (int s = 0; s <= 256; s++) cum[s] = 0;
+        freq[s] = 0;
+        cum[s] = 0;
+        if (s == 0) cum[256] = 0;
         return;
     }
-    unsigned long long rem[256];
-    bool got[256];
-    long long sum = 0;
-    for (int s = 0; s < 256; s++) {
-        const unsigned long long m = (unsigned long long)hist[s] * RANS_M;
-        freq[s] = (uint32_t)(m / total);
-        rem[s] = m % total;
-        got[s] = false;
-        sum += freq[s];
-    }
-    while (sum < (long long)RANS_M) {
-        int best = -1;
-        for (int s = 0; s < 256; s++) {
-            if (hist[s] == 0 || got[s]) continue;
-            if (best < 0 || rem[s] > rem[best]) best = s;
+    const unsigned long long m = (unsigned long long)h * RANS_M;
+    uint32_t f = (uint32_t)(m / total);
+    const unsigned long long rem = m % total;
+    rem_sh[s] = rem;
+    uint32_t fs = f;
+    for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(0xffffffffu, fs, o);
+    __syncthreads();                       // red64 read by every thread above
+    if (lane == 0) red32[w] = fs;
+    __syncthreads();
+    uint32_t sum = 0;
+    for (int k = 0; k < TABLE_THREADS / 32; k++) sum += red32[k];
+    const uint32_t missing = RANS_M - sum;  // fewer than the present symbols
+    if (h > 0) {
+        uint32_t rank = 0;
+        for (int q = 0; q < 256; q++) {
+            if (hist[q] == 0) continue;
+            const unsigned long long rq = rem_sh[q];
+            rank += (rq > rem || (rq == rem && q < s));
         }
-        if (best < 0) { *err = 1; return; }
-        freq[best]++;
-        got[best] = true;
-        sum++;
+        if (rank < missing) f++;
+        if (f == 0) f = 1;
     }
-    for (int s = 0; s < 256; s++)
-        if (hist[s] > 0 && freq[s] == 0) { freq[s] = 1; sum++; }
-    while (sum > (long long)RANS_M) {
-        int best = -1;
-        for (int s = 0; s < 256; s++) {
-            if (freq[s] <= 1) continue;
-            if (best < 0 || freq[s] > freq[best]) best = s;
+    f_sh[s] = f;
+    __syncthreads();
+    // the sum after the raises, then the surplus taken back
+    uint32_t fs2 = f;
+    for (int o = 16; o > 0; o >>= 1) fs2 += __shfl_xor_sync(0xffffffffu, fs2, o);
+    if (lane == 0) red32[w] = fs2;
+    __syncthreads();
+    uint32_t sum2 = 0;
+    for (int k = 0; k < TABLE_THREADS / 32; k++) sum2 += red32[k];
+    __syncthreads();
+    for (uint32_t it = 0; sum2 > RANS_M && it < 256; it++, sum2--) {
+        // argmax of (freq, -symbol) over freq > 1
+        const uint32_t fv = f_sh[s];
+        uint32_t key = fv > 1 ? (fv << 8) | (uint32_t)(255 - s) : 0u;
+        for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+        if (lane == 0) red32[w] = key;
+        __syncthreads();
+        uint32_t best = 0;
+        for (int k = 0; k < TABLE_THREADS / 32; k++) best = max(best, red32[k]);
+        if (best == 0) {
+            if (s == 0) *err = 1;
+            return;
         }
-        if (best < 0) { *err = 1; return; }
-        freq[best]--;
-        sum--;
+        if (s == 255 - (int)(best & 0xFF)) f_sh[s] = fv - 1;
+        __syncthreads();
     }
-    cum[0] = 0;
-    for (int s = 0; s < 256; s++) cum[s + 1] = cum[s] + freq[s];
+    if (sum2 > RANS_M) {
+        if (s == 0) *err = 1;
+        return;
+    }
+    // cumulative sums: an exclusive scan over the 256 frequencies
+    const uint32_t fv = f_sh[s];
+    freq[s] = fv;
+    uint32_t inc = fv;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) red32[w] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int k = 0; k < w; k++) base += red32[k];
+    cum[s] = base + inc - fv;
+    if (s == 255) cum[256] = base + inc;
 }
 
 // one thread per chunk; slot c holds 4 + 2 chunk bytes, filled from its end
@@ -118,10 +170,20 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
                                                      uint8_t* __restrict__ scratch, int32_t* __restrict__ len,
                                                      const int* __restrict__ err)
 {
-    __shared__ uint32_t freq[256], cum[256];
+    // x / f by multiplication (Granlund and Montgomery, division by invariant
+    // integers): l = ceil(log2 f), m = ceil(2^(32 + l) / f); for x < 2^32,
+    // x / f = (x m) >> (32 + l) exactly; m <= 2^33 and x < 2^31 keep x m
+    // below 2^64
+    // per symbol, one 16-byte entry (frequency, cumulative frequency, shift,
+    // renormalisation bound) and its magic multiplier
+    __shared__ uint4 tab[256];
+    __shared__ unsigned long long mag[256];
     for (int s = threadIdx.x; s < 256; s += blockDim.x) {
-        freq[s] = freq_g[s];
-        cum[s] = cum_g[s];
+        const uint32_t f = freq_g[s];
+        uint32_t l = 0;
+        while (l < 12 && (1u << l) < f) l++;
+        tab[s] = make_uint4(f, cum_g[s], 32 + l, ((RANS_L >> RANS_BITS) << 8) * f);
+        mag[s] = f ? (((1ull << (32 + l)) - 1ull) / f + 1ull) : 0ull;
     }
     __syncthreads();
     if (*err) return;
@@ -133,15 +195,18 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
         uint8_t* base = scratch + (size_t)c * cap;
         size_t p = cap;
         uint32_t x = RANS_L;
+        uint32_t sn = sym[a + m - 1];        // the next symbol, loaded a step ahead
         for (int64_t i = a + m - 1; i >= a; i--) {
-            const uint32_t s = sym[i];
-            const uint32_t f = freq[s];
-            const uint32_t xmax = ((RANS_L >> RANS_BITS) << 8) * f;
-            while (x >= xmax) {
+            const uint32_t s = sn;
+            if (i > a) sn = sym[i - 1];
+            const uint4 e = tab[s];
+            const unsigned long long mg = mag[s];
+            while (x >= e.w) {
                 base[--p] = (uint8_t)(x & 0xFF);
                 x >>= 8;
             }
-            x = ((x / f) << RANS_BITS) + (x % f) + cum[s];
+            const uint32_t q = (uint32_t)(((unsigned long long)x * mg) >> e.z);
+            x = (q << RANS_BITS) + (x - q * e.x) + e.y;
         }
         base[--p] = (uint8_t)(x & 0xFF);
         base[--p] = (uint8_t)((x >> 8) & 0xFF);
@@ -244,7 +309,7 @@ extern "C" int tpc_rans_encode(const uint8_t* sym, int64_t n, int32_t chunk, voi
     CK(cudaMemsetAsync(hist, 0, 4 * 256, st));
     CK(cudaMemsetAsync(err, 0, 4, st));
     k_rans_hist<<<grid_cap(n, 256), 256, 0, st>>>(sym, n, hist);
-    k_rans_table<<<1, 32, 0, st>>>(hist, freq, cum, err);
+    k_rans_table<<<1, TABLE_THREADS, 0, st>>>(hist, freq, cum, err);
     if (nch > 0) {
         k_rans_chunks<<<grid_cap(nch, 128), 128, 0, st>>>(sym, n, chunk, freq, cum, at<uint8_t>(workspace, L.scratch),
                                                           len, err);
@@ -663,9 +728,16 @@ __global__ void k_pack_copy(uint8_t* __restrict__ cont, int64_t nch, const uint8
     if (blockIdx.x == 0 && threadIdx.x == 0) *size = o2 + nr;
 }
 
+// per stream, its own coding regions: the streams are coded side by side
+struct StreamRegions {
+    size_t rawn, sym, raw, rans, cout, cbytes, freq, stmp, coded, cont;
+    int64_t cap;                  // values the stream can hold
+};
+
 struct CmpLayout {
-    size_t err, qy, qt, tcnt, pcnt, pfill, uord, usort, stmp, sizes, coded;   // fields
-    size_t vals, rawn, sym, raw, rans, cout, cbytes, freq, stage;              // coding (frame only)
+    size_t err, qy, qt, tcnt, pcnt, pfill, uord, usort, stmp, sizes;   // fields
+    size_t vals;                                                        // the streams' values
+    StreamRegions st[CS_N];                                             // coding (frame only)
     int64_t max_vals, max_stream, max_cont_total;
     size_t total;
 };
@@ -706,16 +778,22 @@ CmpLayout cmp_layout(const tpc_compress_in* in, int32_t chunk)
     L.usort = take(4 * (size_t)n);
     L.stmp = take(4 * (size_t)scan_tmp_elems(std::max<int64_t>(L.max_stream, 4 * (T + 1)) + 1));
     L.sizes = take(8 * CS_N);
-    L.coded = take(8);
     L.vals = take(4 * (size_t)L.max_vals);
-    L.rawn = take(4 * (size_t)(L.max_stream + 1));
-    L.sym = take((size_t)L.max_stream);
-    L.raw = take(4 * (size_t)L.max_stream);
-    L.rans = take(rans_layout(L.max_stream, chunk).total);
-    L.cout = take(4 * (size_t)n_chunks(L.max_stream, chunk) + 2 * (size_t)L.max_stream);
-    L.cbytes = take(4 * (size_t)std::max<int64_t>(n_chunks(L.max_stream, chunk), 1));
-    L.freq = take(4 * 256);
-    L.stage = take((size_t)L.max_cont_total);     // containers at worst-case offsets, then packed
+    for (int k = 0; k < CS_N; k++) {
+        StreamRegions& R = L.st[k];
+        const int64_t c = per[k];
+        R.cap = c;
+        R.rawn = take(4 * (size_t)(c + 1));
+        R.sym = take((size_t)c);
+        R.raw = take(4 * (size_t)c);
+        R.rans = take(rans_layout(c, chunk).total);
+        R.cout = take(4 * (size_t)n_chunks(c, chunk) + 2 * (size_t)c);
+        R.cbytes = take(4 * (size_t)std::max<int64_t>(n_chunks(c, chunk), 1));
+        R.freq = take(4 * 256);
+        R.stmp = take(4 * (size_t)scan_tmp_elems(c + 1));
+        R.coded = take(8);
+        R.cont = take((size_t)cont_max(c, chunk));      // the container, packed at the end
+    }
     L.total = o;
     return L;
 }
@@ -813,7 +891,8 @@ extern "C" int tpc_compress_fields(const tpc_compress_in* in, int32_t ey, int32_
 {
     if (check_in(in) || !counts || !workspace || ey < -30 || ey > 30 || et < -30 || et > 30) return TPC_ERR_ARG;
     const CmpLayout L = cmp_layout(in, 4096);     // the fields' regions do not depend on the chunk
-    if (ws_bytes < L.rawn || (L.max_vals > 0 && (!vals || vals_cap < L.max_vals))) return TPC_ERR_ARG;
+    if (ws_bytes < L.vals + 4 * (size_t)L.max_vals || (L.max_vals > 0 && (!vals || vals_cap < L.max_vals)))
+        return TPC_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int64_t vbase[CS_N];
     int rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
@@ -829,6 +908,38 @@ extern "C" int tpc_compress_fields(const tpc_compress_in* in, int32_t ey, int32_
     return TPC_OK;
 }
 
+namespace {
+
+// side streams for coding the 12 field streams concurrently: created once
+// per device (non-blocking), joined to the caller's stream with events
+struct SideStreams {
+    bool ready = false;
+    cudaStream_t s[CS_N];
+    cudaEvent_t fork, join[CS_N];
+};
+SideStreams g_side[64];
+std::mutex g_side_mu;
+
+int side_streams(SideStreams** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TPC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    SideStreams& S = g_side[dev];
+    if (!S.ready) {
+        if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess) return TPC_ERR_CUDA;
+        for (int k = 0; k < CS_N; k++)
+            if (cudaStreamCreateWithFlags(&S.s[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&S.join[k], cudaEventDisableTiming) != cudaSuccess)
+                return TPC_ERR_CUDA;
+        S.ready = true;
+    }
+    *out = &S;
+    return TPC_OK;
+}
+
+}  // namespace
+
 extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t et, int32_t chunk, void* workspace,
                                   size_t ws_bytes, uint8_t* out, int64_t out_cap, int64_t* bytes, void* stream)
 {
@@ -838,49 +949,53 @@ extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t
     const CmpLayout L = cmp_layout(in, chunk);
     if (ws_bytes < L.total || out_cap < L.max_cont_total) return TPC_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SideStreams* SS = nullptr;
+    int rc = side_streams(&SS);
+    if (rc) return rc;
     int64_t counts[CS_N], vbase[CS_N];
-    int rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
+    rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
     if (rc) return rc;
     uint32_t* vals = at<uint32_t>(workspace, L.vals);
-    uint32_t* rawn = at<uint32_t>(workspace, L.rawn);
-    uint8_t* sym = at<uint8_t>(workspace, L.sym);
-    uint8_t* raw = at<uint8_t>(workspace, L.raw);
-    uint8_t* cout = at<uint8_t>(workspace, L.cout);
-    int32_t* cbytes = at<int32_t>(workspace, L.cbytes);
-    uint32_t* freq = at<uint32_t>(workspace, L.freq);
     long long* sizes = at<long long>(workspace, L.sizes);
-    long long* coded = at<long long>(workspace, L.coded);
-    uint32_t* stmp = at<uint32_t>(workspace, L.stmp);
-    uint8_t* stage = at<uint8_t>(workspace, L.stage);
-    const size_t rans_ws = rans_layout(L.max_stream, chunk).total;
-    int64_t cbase[CS_N];
-    int64_t o = 0;
+    CCK(cudaEventRecord(SS->fork, st));
     for (int k = 0; k < CS_N; k++) {
-        cbase[k] = o;
+        const StreamRegions& R = L.st[k];
+        cudaStream_t sk = SS->s[k];
+        CCK(cudaStreamWaitEvent(sk, SS->fork, 0));
         const int64_t m = counts[k], nch = n_chunks(m, chunk);
-        o += (cont_max(m, chunk) + 15) / 16 * 16;
+        if (m > R.cap) return TPC_ERR_DATA;
         const uint32_t* v = vals + vbase[k];
-        if (m > 0) k_sym_count<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn);
-        scan_n(rawn, m, stmp, st);          // rawn[m] = escape bytes
-        if (m > 0) k_sym_write<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn, sym, raw);
+        uint32_t* rawn = at<uint32_t>(workspace, R.rawn);
+        uint8_t* sym = at<uint8_t>(workspace, R.sym);
+        uint8_t* raw = at<uint8_t>(workspace, R.raw);
+        if (m > 0) k_sym_count<<<grid_cap(m, 256), 256, 0, sk>>>(v, m, rawn);
+        scan_n(rawn, m, at<uint32_t>(workspace, R.stmp), sk);          // rawn[m] = escape bytes
+        if (m > 0) k_sym_write<<<grid_cap(m, 256), 256, 0, sk>>>(v, m, rawn, sym, raw);
         CCK(cudaGetLastError());
         int64_t maxb = 0;
         tpc_rans_max_bytes(m, chunk, &maxb);
-        rc = tpc_rans_encode(sym, m, chunk, at<void>(workspace, L.rans), rans_ws, freq, cbytes, cout,
-                             std::max<int64_t>(maxb, 1), nullptr, stream);
+        uint32_t* freq = at<uint32_t>(workspace, R.freq);
+        int32_t* cbytes = at<int32_t>(workspace, R.cbytes);
+        uint8_t* cout = at<uint8_t>(workspace, R.cout);
+        rc = tpc_rans_encode(sym, m, chunk, at<void>(workspace, R.rans), rans_layout(R.cap, chunk).total, freq,
+                             cbytes, cout, std::max<int64_t>(maxb, 1), nullptr, sk);
         if (rc) return rc;
-        k_pack_head<<<1, 256, 0, st>>>(stage + cbase[k], (uint32_t)m, chunk,
-                                       rawn + m, freq, cbytes, nch, coded);
-        k_pack_copy<<<grid_cap(2 * m + 4 * nch + 1, 256), 256, 0, st>>>(stage + cbase[k], nch, cout, coded, raw,
-                                                                        rawn + m, sizes + k);
+        long long* coded = at<long long>(workspace, R.coded);
+        uint8_t* cont = at<uint8_t>(workspace, R.cont);
+        k_pack_head<<<1, 256, 0, sk>>>(cont, (uint32_t)m, chunk, rawn + m, freq, cbytes, nch, coded);
+        k_pack_copy<<<grid_cap(2 * m + 4 * nch + 1, 256), 256, 0, sk>>>(cont, nch, cout, coded, raw, rawn + m,
+                                                                       sizes + k);
         CCK(cudaGetLastError());
+        CCK(cudaEventRecord(SS->join[k], sk));
+        CCK(cudaStreamWaitEvent(st, SS->join[k], 0));
     }
     long long sz[CS_N];
     CCK(cudaMemcpyAsync(sz, sizes, sizeof(sz), cudaMemcpyDeviceToHost, st));
     CCK(cudaStreamSynchronize(st));
     int64_t p = 0;
     for (int k = 0; k < CS_N; k++) {
-        CCK(cudaMemcpyAsync(out + p, stage + cbase[k], (size_t)sz[k], cudaMemcpyDeviceToDevice, st));
+        CCK(cudaMemcpyAsync(out + p, at<uint8_t>(workspace, L.st[k].cont), (size_t)sz[k], cudaMemcpyDeviceToDevice,
+                            st));
         bytes[k] = sz[k];
         p += sz[k];
     }
