@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--no-attach", action="store_true",
                     help="frame: skip the timing of the optional cluster attachment stage")
     ap.add_argument("--no-compress", action="store_true", help="frame: skip the cluster compression object")
+    ap.add_argument("--no-fit", action="store_true", help="calib: skip the closed-loop fit object")
     ap.add_argument("--no-batch", action="store_true",
                     help="frame workload: skip the bounded sub-time-frame batch object (graph vs per-frame loop)")
     ap.add_argument("--batch-stf", type=int, default=16, help="frame workload: sub-time-frames of the batch object")
@@ -1041,20 +1042,22 @@ def run_calib(args, ws, rank, local, pg):
     e2e_s = (time.perf_counter() - t0) / args.steps
     # the closed-loop fit from the nominal calibration (tpc_calib_fit)
     cal = ev.calib
+    fit = None
     torch.cuda.synchronize()
-    tf0 = time.perf_counter()
-    th_fit, rep = calib.fit(tpc.calib.nominal_theta(ev.v_drift, device=dev))
-    fit_s = time.perf_counter() - tf0
-    th_fit = th_fit.cpu().numpy().astype(np.float64)
-    spl_true = np.asarray(cal["spline"]).ravel()
-    fit = {"s": round(fit_s, 3), "evaluations": rep["evaluations"], "rounds": rep["rounds"],
-           "tracks": rep["tracks"], "dip_angles": rep["anchors"], "f_start": rep["f_start"],
-           "f_final": rep["f_final"], "v_fit": th_fit[0], "v_true": cal["v_drift"],
-           "v_rel_err": th_fit[0] / cal["v_drift"] - 1.0, "t0_fit_us": th_fit[1], "t0_true_us": cal["t0"],
-           "map_rms_err_cm": float(np.sqrt(((th_fit[2:] - spl_true) ** 2).mean())),
-           "map_rms_true_cm": float(np.sqrt((spl_true ** 2).mean())),
-           "how": "L-BFGS over theta on the GPU chi2 and gradient, prior sigma 0.3 cm on the map, "
-                  "dip angles of the matched inner tracks (generator truth smeared by 3e-4)"}
+    if not args.no_fit:
+        tf0 = time.perf_counter()
+        th_fit, rep = calib.fit(tpc.calib.nominal_theta(ev.v_drift, device=dev))
+        fit_s = time.perf_counter() - tf0
+        th_fit = th_fit.cpu().numpy().astype(np.float64)
+        spl_true = np.asarray(cal["spline"]).ravel()
+        fit = {"s": round(fit_s, 3), "evaluations": rep["evaluations"], "rounds": rep["rounds"],
+               "tracks": rep["tracks"], "dip_angles": rep["anchors"], "f_start": rep["f_start"],
+               "f_final": rep["f_final"], "v_fit": th_fit[0], "v_true": cal["v_drift"],
+               "v_rel_err": th_fit[0] / cal["v_drift"] - 1.0, "t0_fit_us": th_fit[1], "t0_true_us": cal["t0"],
+               "map_rms_err_cm": float(np.sqrt(((th_fit[2:] - spl_true) ** 2).mean())),
+               "map_rms_true_cm": float(np.sqrt((spl_true ** 2).mean())),
+               "how": "L-BFGS over theta on the GPU chi2 and gradient, prior sigma 0.3 cm on the map, "
+                      "dip angles of the matched inner tracks (generator truth smeared by 3e-4)"}
     pk = fma_peak(dev, 32)
     (ms, e2e_s), (steps_all,) = over_ranks(pg, dev, (ms, e2e_s), (float(n_steps),))
     if rank != 0:
@@ -1080,8 +1083,9 @@ def run_calib(args, ws, rank, local, pg):
                 "h2d_bytes_per_step": 4 * theta.numel(), "d2h_bytes_per_step": 4 + 4 * theta.numel()},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
-        "fit": fit,
     }
+    if fit is not None:
+        line["fit"] = fit
     if not args.no_cpu_baseline:
         import oracle
         rng = np.random.default_rng(0)
