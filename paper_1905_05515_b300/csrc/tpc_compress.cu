@@ -171,19 +171,20 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
                                                      const int* __restrict__ err)
 {
     // x / f by multiplication (Granlund and Montgomery, division by invariant
-    // integers): l = ceil(log2 f), m = ceil(2^(32 + l) / f); for x < 2^32,
-    // x / f = (x m) >> (32 + l) exactly; m <= 2^33 and x < 2^31 keep x m
-    // below 2^64
-    // per symbol, one 16-byte entry (frequency, cumulative frequency, shift,
-    // renormalisation bound) and its magic multiplier
+    // integers): l = ceil(log2 f), m = ceil(2^(32 + l) / f) <= 2^33; for x <
+    // 2^32, x / f = (x m) >> (32 + l) exactly.  With m = 2^32 m_hi + m_lo and
+    // x < 2^31: (x m) >> 32 = umulhi(x, m_lo) + x m_hi < 2^32, so q =
+    // (umulhi(x, m_lo) + x m_hi) >> l in 32-bit arithmetic.  Per symbol one
+    // 16-byte entry: f | l << 16 | m_hi << 24, the cumulative frequency, m_lo,
+    // the renormalisation bound.
     __shared__ uint4 tab[256];
-    __shared__ unsigned long long mag[256];
     for (int s = threadIdx.x; s < 256; s += blockDim.x) {
         const uint32_t f = freq_g[s];
         uint32_t l = 0;
         while (l < 12 && (1u << l) < f) l++;
-        tab[s] = make_uint4(f, cum_g[s], 32 + l, ((RANS_L >> RANS_BITS) << 8) * f);
-        mag[s] = f ? (((1ull << (32 + l)) - 1ull) / f + 1ull) : 0ull;
+        const unsigned long long m = f ? (((1ull << (32 + l)) - 1ull) / f + 1ull) : 0ull;
+        tab[s] = make_uint4(f | (l << 16) | ((uint32_t)(m >> 32) << 24), cum_g[s], (uint32_t)m,
+                            ((RANS_L >> RANS_BITS) << 8) * f);
     }
     __syncthreads();
     if (*err) return;
@@ -195,18 +196,19 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
         uint8_t* base = scratch + (size_t)c * cap;
         size_t p = cap;
         uint32_t x = RANS_L;
-        uint32_t sn = sym[a + m - 1];        // the next symbol, loaded a step ahead
+        // the entry of the next symbol is loaded a step ahead: the state chain
+        // does not wait for the table
+        uint4 en = tab[sym[a + m - 1]];
         for (int64_t i = a + m - 1; i >= a; i--) {
-            const uint32_t s = sn;
-            if (i > a) sn = sym[i - 1];
-            const uint4 e = tab[s];
-            const unsigned long long mg = mag[s];
+            const uint4 e = en;
+            if (i > a) en = tab[sym[i - 1]];
             while (x >= e.w) {
                 base[--p] = (uint8_t)(x & 0xFF);
                 x >>= 8;
             }
-            const uint32_t q = (uint32_t)(((unsigned long long)x * mg) >> e.z);
-            x = (q << RANS_BITS) + (x - q * e.x) + e.y;
+            const uint32_t f = e.x & 0xFFFFu, l = (e.x >> 16) & 0xFFu, mh = e.x >> 24;
+            const uint32_t q = (__umulhi(x, e.z) + x * mh) >> l;
+            x = (q << RANS_BITS) + (x - q * f) + e.y;
         }
         base[--p] = (uint8_t)(x & 0xFF);
         base[--p] = (uint8_t)((x >> 8) & 0xFF);
@@ -459,16 +461,26 @@ __device__ __forceinline__ long long predict(int nprev, long long v0, int r0, lo
     return v1 + ((v1 - v0) * (long long)(r - r1)) / (long long)(r1 - r0);
 }
 
-// one thread per track: its values in the track streams
+// One warp per track: lane j takes the clusters a + 32 i + j.  A cluster
+// starts a run when it is the track's first or its sector differs from the
+// previous cluster's; its residuals use the previous two clusters (a line
+// when neither the cluster nor the previous one starts a run).  Positions in
+// the head and residual streams are the counts of run starts and of the
+// other clusters before it (ballots), so each warp writes its track's values
+// contiguously.  The previous chunk's last two clusters carry over in
+// registers.
 __global__ void k_ct_fill(CmpArgs A)
 {
     if (*A.err) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int64_t T1 = (int64_t)A.T + 1;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.T; t += gridDim.x * blockDim.x) {
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < A.T; t += nw) {
         const int a = A.off[t], b = A.off[t + 1];
-        A.vals[A.vbase[CS_NT] + t] = (uint32_t)(b - a);
+        if (lane == 0) A.vals[A.vbase[CS_NT] + t] = (uint32_t)(b - a);
         if (b <= a) continue;
-        uint32_t* hs = A.vals + A.vbase[CS_HS] + A.tcnt[t];
         uint32_t* hr = A.vals + A.vbase[CS_HR] + A.tcnt[T1 + t];
         uint32_t* hy = A.vals + A.vbase[CS_HY] + A.tcnt[T1 + t];
         uint32_t* ht = A.vals + A.vbase[CS_HT] + A.tcnt[T1 + t];
@@ -476,30 +488,60 @@ __global__ void k_ct_fill(CmpArgs A)
         uint32_t* dr = A.vals + A.vbase[CS_DR] + A.tcnt[3 * T1 + t];
         uint32_t* ry = A.vals + A.vbase[CS_RY] + A.tcnt[3 * T1 + t];
         uint32_t* rt = A.vals + A.vbase[CS_RT] + A.tcnt[3 * T1 + t];
-        int run = 0, rp0 = 0, rp1 = 0, sec = -1, nh = 0, nr = 0;
-        long long y0 = 0, y1 = 0, t0 = 0, t1 = 0;
-        for (int k = a; k < b; k++) {
-            const int c = A.clus[k];
-            const int s = A.sector[c], r = A.row[c];
-            const long long qy = A.qy[c], qt = A.qt[c];
-            if (k > a) ds[k - a - 1] = zz32((long long)s - sec);
-            if (k == a || s != sec) {
-                if (k == a) hs[0] = (uint32_t)s;
-                hr[nh] = (uint32_t)r;
-                hy[nh] = zz32(qy);
-                ht[nh] = zz32(qt);
-                nh++;
-                run = 1;
-            } else {
-                dr[nr] = zz32((long long)r - rp1);
-                ry[nr] = zz32(qy - predict(run, y0, rp0, y1, rp1, r));
-                rt[nr] = zz32(qt - predict(run, t0, rp0, t1, rp1, r));
-                nr++;
-                run++;
+        if (lane == 0) A.vals[A.vbase[CS_HS] + A.tcnt[t]] = (uint32_t)A.sector[A.clus[a]];
+        // the cluster before the chunk (c1) and the one before that (c2)
+        int s1 = 0, r1 = 0, r2 = 0;
+        long long y1 = 0, t1 = 0, y2 = 0, t2 = 0;
+        bool st1 = false;
+        uint32_t nh = 0, nres = 0;
+        for (int k0 = a; k0 < b; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < b;
+            int sk = 0, rk = 0;
+            long long yk = 0, tk = 0;
+            if (valid) {
+                const int c = A.clus[k];
+                sk = A.sector[c];
+                rk = A.row[c];
+                yk = A.qy[c];
+                tk = A.qt[c];
             }
-            sec = s;
-            rp0 = rp1; y0 = y1; t0 = t1;
-            rp1 = r; y1 = qy; t1 = qt;
+            // previous and second previous cluster of each lane
+            int sp = __shfl_up_sync(FULL, sk, 1), rp = __shfl_up_sync(FULL, rk, 1);
+            long long yp = __shfl_up_sync(FULL, yk, 1), tp = __shfl_up_sync(FULL, tk, 1);
+            int rpp = __shfl_up_sync(FULL, rk, 2);
+            long long ypp = __shfl_up_sync(FULL, yk, 2), tpp = __shfl_up_sync(FULL, tk, 2);
+            if (lane == 0) { sp = s1; rp = r1; yp = y1; tp = t1; rpp = r2; ypp = y2; tpp = t2; }
+            if (lane == 1) { rpp = r1; ypp = y1; tpp = t1; }
+            const bool start = valid && (k == a || sk != sp);
+            bool stp = __shfl_up_sync(FULL, start, 1);
+            if (lane == 0) stp = st1;
+            const unsigned mh = __ballot_sync(FULL, start);
+            const unsigned mr = __ballot_sync(FULL, valid && !start);
+            if (valid && k > a) ds[k - a - 1] = zz32((long long)sk - sp);
+            if (start) {
+                const uint32_t o = nh + __popc(mh & lt);
+                hr[o] = (uint32_t)rk;
+                hy[o] = zz32(yk);
+                ht[o] = zz32(tk);
+            } else if (valid) {
+                const uint32_t o = nres + __popc(mr & lt);
+                const int nprev = stp ? 1 : 2;      // clusters of the run before this one (2: two or more)
+                dr[o] = zz32((long long)rk - rp);
+                ry[o] = zz32(yk - predict(nprev, ypp, rpp, yp, rp, rk));
+                rt[o] = zz32(tk - predict(nprev, tpp, rpp, tp, rp, rk));
+            }
+            nh += __popc(mh);
+            nres += __popc(mr);
+            // carry the chunk's last two clusters (the loop ends after a partial chunk)
+            s1 = __shfl_sync(FULL, sk, 31);
+            r1 = __shfl_sync(FULL, rk, 31);
+            y1 = __shfl_sync(FULL, yk, 31);
+            t1 = __shfl_sync(FULL, tk, 31);
+            st1 = __shfl_sync(FULL, start, 31);
+            r2 = __shfl_sync(FULL, rk, 30);
+            y2 = __shfl_sync(FULL, yk, 30);
+            t2 = __shfl_sync(FULL, tk, 30);
         }
     }
 }
@@ -844,7 +886,7 @@ int run_fields(const tpc_compress_in* in, int32_t ey, int32_t et, void* ws, cons
     if (A.T > 0) k_ct_count<<<grid_cap(A.T, 128), 128, 0, st>>>(A);
     for (int k = 0; k < 4; k++) scan_n(A.tcnt + k * T1, A.T, stmp, st);
     scan_n(A.pcnt, A.np, stmp, st);
-    k_ct_fill<<<grid_cap(std::max(A.T, 1), 128), 128, 0, st>>>(A);
+    k_ct_fill<<<grid_cap(32 * (int64_t)std::max(A.T, 1), 256), 256, 0, st>>>(A);
     if (A.n > 0) k_cu_scatter<<<grid_cap(A.n, 256), 256, 0, st>>>(A);
     k_cu_plane<<<(unsigned)std::min(A.np, 148 * 8), 256, 0, st>>>(A);
     CCK(cudaGetLastError());
