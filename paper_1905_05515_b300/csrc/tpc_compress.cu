@@ -3,19 +3,19 @@
 // "TPC Data Compression", step 4; the format is stated in tpc_compress.h).
 //
 // Kernels: k_rans_hist (block histograms in shared memory, one global add
-// per bin and block), k_rans_table (one thread: the largest-remainder
-// normalisation over 256 symbols), k_rans_chunks (one thread per chunk: the
+// per bin and block), k_rans_table (one block of 256 threads: the
+// largest-remainder normalisation), k_rans_chunks (one thread per chunk: the
 // chunk is coded last symbol first into its own scratch slot, bytes written
-// from the slot's end backward, so they come out in decode order), a scan of
-// the chunk sizes and k_rans_copy (one block per chunk) packing the chunks
-// back to back.
+// from the slot's end backward, so they come out in decode order; the
+// division by the symbol frequency by a magic multiplier), a scan of the
+// chunk sizes and k_rans_copy (one block per chunk) packing the chunks back
+// to back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "tpc_compress.h"
 #include "tpc_track.h"
@@ -163,12 +163,13 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_rans_table(const uint32_t* __
     if (s == 255) cum[256] = base + inc;
 }
 
-// one thread per chunk; slot c holds 4 + 2 chunk bytes, filled from its end
-__global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__ sym, int64_t n, int32_t chunk,
-                                                     const uint32_t* __restrict__ freq_g,
-                                                     const uint32_t* __restrict__ cum_g,
-                                                     uint8_t* __restrict__ scratch, int32_t* __restrict__ len,
-                                                     const int* __restrict__ err)
+// One thread per chunk; slot c holds 4 + 2 chunk bytes, filled from its end.
+// Codes the chunks of blocks bi, bi + nb, ... (blockDim.x chunks per block)
+// of one stream.
+__device__ void code_chunks(const uint8_t* __restrict__ sym, int64_t n, int32_t chunk,
+                            const uint32_t* __restrict__ freq_g, const uint32_t* __restrict__ cum_g,
+                            uint8_t* __restrict__ scratch, int32_t* __restrict__ len, const int* __restrict__ err,
+                            int64_t bi, int64_t nb)
 {
     // x / f by multiplication (Granlund and Montgomery, division by invariant
     // integers): l = ceil(log2 f), m = ceil(2^(32 + l) / f) <= 2^33; for x <
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
     if (*err) return;
     const int64_t nch = (n + chunk - 1) / chunk;
     const size_t cap = 4 + 2 * (size_t)chunk;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t c = bi * (int64_t)blockDim.x + threadIdx.x; c < nch; c += nb * blockDim.x) {
         const int64_t a = c * chunk;
         const int64_t m = min((int64_t)chunk, n - a);
         uint8_t* base = scratch + (size_t)c * cap;
@@ -216,6 +217,43 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
         base[--p] = (uint8_t)(x >> 24);
         len[c] = (int32_t)(cap - p);
     }
+}
+
+__global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__ sym, int64_t n, int32_t chunk,
+                                                     const uint32_t* __restrict__ freq_g,
+                                                     const uint32_t* __restrict__ cum_g,
+                                                     uint8_t* __restrict__ scratch, int32_t* __restrict__ len,
+                                                     const int* __restrict__ err)
+{
+    code_chunks(sym, n, chunk, freq_g, cum_g, scratch, len, err, blockIdx.x, gridDim.x);
+}
+
+// Several streams in one launch: the blocks [block0, block0 + blocks) of job
+// j code stream j's chunks (each block loads one stream's table).
+struct ChunkJob {
+    const uint8_t* sym;
+    int64_t n;
+    const uint32_t* freq;
+    const uint32_t* cum;
+    uint8_t* scratch;
+    int32_t* len;
+    const int* err;
+    int32_t block0, blocks;
+};
+constexpr int MAX_CHUNK_JOBS = 16;
+struct ChunkJobs {
+    ChunkJob j[MAX_CHUNK_JOBS];
+    int32_t njobs, chunk;
+};
+
+__global__ void __launch_bounds__(128) k_rans_chunks_multi(const ChunkJobs J)
+{
+    int k = 0;
+    while (k + 1 < J.njobs && (int)blockIdx.x >= J.j[k + 1].block0) k++;
+    const ChunkJob& q = J.j[k];
+    const int64_t bi = (int64_t)blockIdx.x - q.block0;
+    if (bi < 0 || bi >= q.blocks) return;
+    code_chunks(q.sym, q.n, J.chunk, q.freq, q.cum, q.scratch, q.len, q.err, bi, q.blocks);
 }
 
 // one block: exclusive scan of the chunk sizes (off[nch] = total)
@@ -340,12 +378,15 @@ extern "C" int tpc_rans_encode(const uint8_t* sym, int64_t n, int32_t chunk, voi
 // symbolised (escapes) and coded into its container.
 //
 // Kernels: k_cq (quantisation, plane counts of the other clusters, checks),
-// k_ct_count (per track: clusters, runs), k_scan1 (one-block exclusive scans
-// of the per-track and per-plane counts), k_ct_fill (one thread per track
-// writes its values at the scanned offsets), k_cu_scatter / k_cu_plane (the
-// other clusters by plane, then one block per plane ranks them by (qt, qy,
-// index) and writes the plane's values), k_sym_count / k_sym_write (escape
-// split), k_pack_head (container header and table).
+// k_ct_count (per track: clusters, runs), multi-block scans of the per-track
+// and per-plane counts (k_tile_sum, k_scan1, k_tile_apply), k_ct_fill (one
+// warp per track writes its values at the scanned offsets), k_cu_scatter /
+// k_cu_plane (the other clusters by plane, then one block per plane ranks
+// them by (qt, qy, index) and writes the plane's values), k_sym_count /
+// k_sym_write (escape split), the coder's histogram and table per stream,
+// k_rans_chunks_multi (the chunks of all streams in one launch: each chunk is
+// a serial chain, so the streams' chains run side by side), k_rans_scan /
+// k_rans_copy per stream, k_pack_head / k_pack_copy (the container).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -950,38 +991,6 @@ extern "C" int tpc_compress_fields(const tpc_compress_in* in, int32_t ey, int32_
     return TPC_OK;
 }
 
-namespace {
-
-// side streams for coding the 12 field streams concurrently: created once
-// per device (non-blocking), joined to the caller's stream with events
-struct SideStreams {
-    bool ready = false;
-    cudaStream_t s[CS_N];
-    cudaEvent_t fork, join[CS_N];
-};
-SideStreams g_side[64];
-std::mutex g_side_mu;
-
-int side_streams(SideStreams** out)
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TPC_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_side_mu);
-    SideStreams& S = g_side[dev];
-    if (!S.ready) {
-        if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess) return TPC_ERR_CUDA;
-        for (int k = 0; k < CS_N; k++)
-            if (cudaStreamCreateWithFlags(&S.s[k], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&S.join[k], cudaEventDisableTiming) != cudaSuccess)
-                return TPC_ERR_CUDA;
-        S.ready = true;
-    }
-    *out = &S;
-    return TPC_OK;
-}
-
-}  // namespace
-
 extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t et, int32_t chunk, void* workspace,
                                   size_t ws_bytes, uint8_t* out, int64_t out_cap, int64_t* bytes, void* stream)
 {
@@ -991,46 +1000,76 @@ extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t
     const CmpLayout L = cmp_layout(in, chunk);
     if (ws_bytes < L.total || out_cap < L.max_cont_total) return TPC_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SideStreams* SS = nullptr;
-    int rc = side_streams(&SS);
-    if (rc) return rc;
     int64_t counts[CS_N], vbase[CS_N];
-    rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
+    int rc = run_fields(in, ey, et, workspace, L, counts, vbase, st);
     if (rc) return rc;
     uint32_t* vals = at<uint32_t>(workspace, L.vals);
     long long* sizes = at<long long>(workspace, L.sizes);
-    CCK(cudaEventRecord(SS->fork, st));
+    // per stream: symbols and escape bytes, histogram and table
+    ChunkJobs J;
+    memset(&J, 0, sizeof(J));
+    J.chunk = chunk;
+    int32_t nblocks = 0;
+    int64_t nchs[CS_N];
     for (int k = 0; k < CS_N; k++) {
         const StreamRegions& R = L.st[k];
-        cudaStream_t sk = SS->s[k];
-        CCK(cudaStreamWaitEvent(sk, SS->fork, 0));
         const int64_t m = counts[k], nch = n_chunks(m, chunk);
+        nchs[k] = nch;
         if (m > R.cap) return TPC_ERR_DATA;
         const uint32_t* v = vals + vbase[k];
         uint32_t* rawn = at<uint32_t>(workspace, R.rawn);
         uint8_t* sym = at<uint8_t>(workspace, R.sym);
         uint8_t* raw = at<uint8_t>(workspace, R.raw);
-        if (m > 0) k_sym_count<<<grid_cap(m, 256), 256, 0, sk>>>(v, m, rawn);
-        scan_n(rawn, m, at<uint32_t>(workspace, R.stmp), sk);          // rawn[m] = escape bytes
-        if (m > 0) k_sym_write<<<grid_cap(m, 256), 256, 0, sk>>>(v, m, rawn, sym, raw);
-        CCK(cudaGetLastError());
-        int64_t maxb = 0;
-        tpc_rans_max_bytes(m, chunk, &maxb);
-        uint32_t* freq = at<uint32_t>(workspace, R.freq);
+        if (m > 0) k_sym_count<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn);
+        scan_n(rawn, m, at<uint32_t>(workspace, R.stmp), st);          // rawn[m] = escape bytes
+        if (m == 0) continue;
+        k_sym_write<<<grid_cap(m, 256), 256, 0, st>>>(v, m, rawn, sym, raw);
+        const RansLayout RL = rans_layout(R.cap, chunk);
+        void* rw = at<void>(workspace, R.rans);
+        CCK(cudaMemsetAsync(at<uint32_t>(rw, RL.hist), 0, 4 * 256, st));
+        CCK(cudaMemsetAsync(at<int>(rw, RL.err), 0, 4, st));
+        k_rans_hist<<<grid_cap(m, 256), 256, 0, st>>>(sym, m, at<uint32_t>(rw, RL.hist));
+        k_rans_table<<<1, TABLE_THREADS, 0, st>>>(at<uint32_t>(rw, RL.hist), at<uint32_t>(workspace, R.freq),
+                                                  at<uint32_t>(rw, RL.cum), at<int>(rw, RL.err));
+        ChunkJob& q = J.j[J.njobs++];
+        q.sym = sym;
+        q.n = m;
+        q.freq = at<uint32_t>(workspace, R.freq);
+        q.cum = at<uint32_t>(rw, RL.cum);
+        q.scratch = at<uint8_t>(rw, RL.scratch);
+        q.len = at<int32_t>(rw, RL.len);
+        q.err = at<int>(rw, RL.err);
+        q.block0 = nblocks;
+        q.blocks = (int32_t)std::min<int64_t>((nch + 127) / 128, 148 * 16);
+        nblocks += q.blocks;
+    }
+    CCK(cudaGetLastError());
+    // every stream's chunks in one launch: the serial chunk chains run side by side
+    if (J.njobs > 0) k_rans_chunks_multi<<<nblocks, 128, 0, st>>>(J);
+    // per stream: chunk offsets, the chunks back to back, the container
+    for (int k = 0; k < CS_N; k++) {
+        const StreamRegions& R = L.st[k];
+        const int64_t m = counts[k], nch = nchs[k];
+        uint32_t* rawn = at<uint32_t>(workspace, R.rawn);
+        const RansLayout RL = rans_layout(R.cap, chunk);
+        void* rw = at<void>(workspace, R.rans);
         int32_t* cbytes = at<int32_t>(workspace, R.cbytes);
         uint8_t* cout = at<uint8_t>(workspace, R.cout);
-        rc = tpc_rans_encode(sym, m, chunk, at<void>(workspace, R.rans), rans_layout(R.cap, chunk).total, freq,
-                             cbytes, cout, std::max<int64_t>(maxb, 1), nullptr, sk);
-        if (rc) return rc;
+        if (nch > 0) {
+            k_rans_scan<<<1, 1024, 0, st>>>(at<int32_t>(rw, RL.len), nch, at<long long>(rw, RL.off), at<int>(rw, RL.err));
+            k_rans_copy<<<(int)std::min<int64_t>(nch, 148 * 32), 128, 0, st>>>(
+                at<uint8_t>(rw, RL.scratch), chunk, nch, at<int32_t>(rw, RL.len), at<long long>(rw, RL.off), cout,
+                4 * nch + 2 * m, cbytes, at<int>(rw, RL.err));
+        }
         long long* coded = at<long long>(workspace, R.coded);
         uint8_t* cont = at<uint8_t>(workspace, R.cont);
-        k_pack_head<<<1, 256, 0, sk>>>(cont, (uint32_t)m, chunk, rawn + m, freq, cbytes, nch, coded);
-        k_pack_copy<<<grid_cap(2 * m + 4 * nch + 1, 256), 256, 0, sk>>>(cont, nch, cout, coded, raw, rawn + m,
+        k_pack_head<<<1, 256, 0, st>>>(cont, (uint32_t)m, chunk, rawn + m, at<uint32_t>(workspace, R.freq), cbytes,
+                                       nch, coded);
+        k_pack_copy<<<grid_cap(2 * m + 4 * nch + 1, 256), 256, 0, st>>>(cont, nch, cout, coded,
+                                                                       at<uint8_t>(workspace, R.raw), rawn + m,
                                                                        sizes + k);
-        CCK(cudaGetLastError());
-        CCK(cudaEventRecord(SS->join[k], sk));
-        CCK(cudaStreamWaitEvent(st, SS->join[k], 0));
     }
+    CCK(cudaGetLastError());
     long long sz[CS_N];
     CCK(cudaMemcpyAsync(sz, sizes, sizeof(sz), cudaMemcpyDeviceToHost, st));
     CCK(cudaStreamSynchronize(st));
