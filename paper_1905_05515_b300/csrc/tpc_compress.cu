@@ -411,8 +411,7 @@ struct CmpArgs {
     const int32_t* clus;
     const int32_t* assign;
     float sy, st;                 // 2^ey, 2^et
-    int32_t* qy;
-    int32_t* qt;
+    int4* rec;                    // [n] per cluster: qy, qt, sector | row << 8, 0 (one gather per cluster)
     uint32_t* tcnt;               // [4][T + 1]: has clusters, runs, clusters - 1, clusters - runs (then scanned)
     uint32_t* pcnt;               // [np + 1] other clusters per plane (then scanned)
     uint32_t* pfill;              // [np] fill cursors
@@ -431,8 +430,7 @@ __global__ void k_cq(CmpArgs A)
             atomicExch(A.err, 1);
             continue;
         }
-        A.qy[i] = __float2int_rn(A.y[i] * A.sy);
-        A.qt[i] = __float2int_rn(A.zt[i] * A.st);
+        A.rec[i] = make_int4(__float2int_rn(A.y[i] * A.sy), __float2int_rn(A.zt[i] * A.st), s | (r << 8), 0);
         if (A.assign[i] < 0) atomicAdd(&A.pcnt[s * A.nr + r], 1u);
     }
 }
@@ -541,11 +539,11 @@ __global__ void k_ct_fill(CmpArgs A)
             int sk = 0, rk = 0;
             long long yk = 0, tk = 0;
             if (valid) {
-                const int c = A.clus[k];
-                sk = A.sector[c];
-                rk = A.row[c];
-                yk = A.qy[c];
-                tk = A.qt[c];
+                const int4 e = A.rec[A.clus[k]];
+                sk = e.z & 0xFF;
+                rk = e.z >> 8;
+                yk = e.x;
+                tk = e.y;
             }
             // previous and second previous cluster of each lane
             int sp = __shfl_up_sync(FULL, sk, 1), rp = __shfl_up_sync(FULL, rk, 1);
@@ -621,8 +619,9 @@ __global__ void __launch_bounds__(256) k_cu_plane(CmpArgs A)
         if (sh)
             for (int k = threadIdx.x; k < m; k += blockDim.x) {
                 const int c = A.uord[ps + k];
-                kt[k] = A.qt[c];
-                ky[k] = A.qy[c];
+                const int4 e = A.rec[c];
+                kt[k] = e.y;
+                ky[k] = e.x;
                 ki[k] = c;
             }
         __syncthreads();
@@ -631,7 +630,10 @@ __global__ void __launch_bounds__(256) k_cu_plane(CmpArgs A)
             if (sh) {
                 t = kt[k]; yv = ky[k]; iv = ki[k];
             } else {
-                iv = A.uord[ps + k]; t = A.qt[iv]; yv = A.qy[iv];
+                iv = A.uord[ps + k];
+                const int4 e = A.rec[iv];
+                t = e.y;
+                yv = e.x;
             }
             int rank = 0;
             if (sh) {
@@ -639,7 +641,8 @@ __global__ void __launch_bounds__(256) k_cu_plane(CmpArgs A)
             } else {
                 for (int j = 0; j < m; j++) {
                     const int c = A.uord[ps + j];
-                    rank += cu_less(A.qt[c], A.qy[c], c, t, yv, iv);
+                    const int4 e = A.rec[c];
+                    rank += cu_less(e.y, e.x, c, t, yv, iv);
                 }
             }
             A.usort[ps + rank] = iv;
@@ -647,9 +650,10 @@ __global__ void __launch_bounds__(256) k_cu_plane(CmpArgs A)
         __syncthreads();                    // usort of the plane complete (global writes of this block)
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const int c = A.usort[ps + k];
-            const int32_t t = A.qt[c];
-            A.vals[A.vbase[CS_UT] + ps + k] = k == 0 ? zz32(t) : (uint32_t)(t - A.qt[A.usort[ps + k - 1]]);
-            A.vals[A.vbase[CS_UY] + ps + k] = zz32(A.qy[c]);
+            const int4 e = A.rec[c];
+            const int32_t t = e.y;
+            A.vals[A.vbase[CS_UT] + ps + k] = k == 0 ? zz32(t) : (uint32_t)(t - A.rec[A.usort[ps + k - 1]].y);
+            A.vals[A.vbase[CS_UY] + ps + k] = zz32(e.x);
         }
     }
 }
@@ -818,7 +822,7 @@ struct StreamRegions {
 };
 
 struct CmpLayout {
-    size_t err, qy, qt, tcnt, pcnt, pfill, uord, usort, stmp, sizes;   // fields
+    size_t err, rec, tcnt, pcnt, pfill, uord, usort, stmp, sizes;   // fields
     size_t vals;                                                        // the streams' values
     StreamRegions st[CS_N];                                             // coding (frame only)
     int64_t max_vals, max_stream, max_cont_total;
@@ -852,8 +856,7 @@ CmpLayout cmp_layout(const tpc_compress_in* in, int32_t chunk)
     size_t o = 0;
     auto take = [&](size_t b) { size_t r = o; o = al(o + std::max<size_t>(b, 1)); return r; };
     L.err = take(4);
-    L.qy = take(4 * (size_t)n);
-    L.qt = take(4 * (size_t)n);
+    L.rec = take(16 * (size_t)n);
     L.tcnt = take(4 * 4 * (size_t)(T + 1));
     L.pcnt = take(4 * (size_t)(np + 1));
     L.pfill = take(4 * (size_t)np);
@@ -904,8 +907,7 @@ int run_fields(const tpc_compress_in* in, int32_t ey, int32_t et, void* ws, cons
     A.off = in->clus_offset; A.clus = in->clus_index; A.assign = in->assign;
     A.sy = ldexpf(1.0f, ey);
     A.st = ldexpf(1.0f, et);
-    A.qy = at<int32_t>(ws, L.qy);
-    A.qt = at<int32_t>(ws, L.qt);
+    A.rec = at<int4>(ws, L.rec);
     A.tcnt = at<uint32_t>(ws, L.tcnt);
     A.pcnt = at<uint32_t>(ws, L.pcnt);
     A.pfill = at<uint32_t>(ws, L.pfill);
