@@ -154,3 +154,20 @@ def test_format_edge_cases(orc):
     _format_check(orc, sec, row, y, zt, off, clus, assign, 36, 152, ey=3, et=8)
     # no clusters at all
     _format_check(orc, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), [0], [], np.zeros(0), 36, 152)
+
+
+def test_format_full_frame(orc):
+    """The 50-collision frame (16 M clusters) with track lists made from the
+    generator's labels (each particle's clusters by row, noise unattached):
+    fields and containers byte-identical to the oracle's at full size."""
+    ev = tpcgen.time_frame(seed=3, n_collisions=50, with_truth=False)
+    lab = ev.label.astype(np.int64)
+    idx = np.nonzero(lab >= 0)[0]
+    o = np.lexsort((idx, ev.row[idx], lab[idx]))
+    clus = idx[o].astype(np.int32)
+    labs = lab[clus]
+    starts = np.concatenate([[0], np.nonzero(np.diff(labs))[0] + 1, [clus.size]]).astype(np.int32)
+    assign = np.full(ev.n, -1, np.int32)
+    assign[clus] = np.repeat(np.arange(starts.size - 1, dtype=np.int32), np.diff(starts))
+    nb = _format_check(orc, ev.sector, ev.row, ev.y, ev.zt, starts, clus, assign, 36, 152)
+    assert nb < 2.5 * ev.n
