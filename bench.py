@@ -46,7 +46,6 @@ FLOPS_MERGE = 520     # merge_chi2: rot32 (~90) + prop32 (181) + 5x5 Cholesky so
 # S, 1/det, chi2 24)
 FLOPS_REFIT64 = 376
 # nominal B300 binary64 rate (no measured FP64 peak is available)
-FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per cluster of the frame of one stage (both
 # tracklet passes), from the committed ncu capture of the same kernel build
 # (profiles/k_tracklets_frame20.md, 20-collision frame, scaled by clusters);
@@ -875,15 +874,16 @@ def run_batch(args, ws, rank, local, pg):
                "ns_per_cluster_largest_third": float(1e6 * nz[order[-third:], 1].sum() / nz[order[-third:], 0].sum())}
     # roofline of the dominant stage of the per-frame calls (stage events)
     dom = max(pf_stage_ms, key=pf_stage_ms.get)
+    fp32_peak, fp64_peak = fma_peak(dev, 32), fma_peak(dev, 64)
     if dom == "refit" and fp64_mode == 1:
         fl = pf_work["refit_prop"] / params.refit_passes * FLOPS_REFIT64
         ach = fl / (pf_stage_ms["refit"] / 1e3) / 1e12
-        roof = {"bound": "fp64", "stage": "refit", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "peak_note": "nominal B300 FP64 rate (no measured FP64 peak); the stage time includes the two "
-                             "binary32 passes"}
+        roof = {"bound": "fp64", "stage": "refit", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_note": "measured binary64 FMA rate (tpc_probe_fma, CUDA events); the stage time includes "
+                             "the two binary32 passes"}
     else:
-        roof = roofline(dom, pf_stage_ms, pf_work, n, peaks())
+        roof = roofline(dom, pf_stage_ms, pf_work, n, dict(peaks(), fp32_tflops_measured=fp32_peak))
     (ms_graph, e2e_s), (n_all,) = over_ranks(pg, dev, (ms_graph, e2e_s), (float(n),))
     if rank != 0:
         return

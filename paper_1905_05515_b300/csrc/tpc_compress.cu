@@ -166,10 +166,6 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_rans_table(const uint32_t* __
 // One thread per chunk; slot c holds 4 + 2 chunk bytes, filled from its end.
 // Codes the chunks of blocks bi, bi + nb, ... (blockDim.x chunks per block)
 // of one stream.
-// VEC: the symbols are read 16 at a time (the buffer 16-byte aligned, the
-// chunk a multiple of 16 symbols, and readable up to the next multiple of 16
-// past n), so that no global load sits on the state's dependent chain.
-template <bool VEC>
 __device__ void code_chunks(const uint8_t* __restrict__ sym, int64_t n, int32_t chunk,
                             const uint32_t* __restrict__ freq_g, const uint32_t* __restrict__ cum_g,
                             uint8_t* __restrict__ scratch, int32_t* __restrict__ len, const int* __restrict__ err,
@@ -203,19 +199,10 @@ __device__ void code_chunks(const uint8_t* __restrict__ sym, int64_t n, int32_t 
         uint32_t x = RANS_L;
         // the entry of the next symbol is loaded a step ahead: the state chain
         // does not wait for the table
-        uint4 wv = make_uint4(0u, 0u, 0u, 0u);
-        auto symbol = [&](int64_t i) -> uint32_t {
-            if (!VEC) return sym[i];
-            if ((i & 15) == 15 || i == a + m - 1)
-                wv = *reinterpret_cast<const uint4*>(sym + (i & ~(int64_t)15));
-            const int k = (int)(i & 15);
-            const uint32_t w = k < 4 ? wv.x : k < 8 ? wv.y : k < 12 ? wv.z : wv.w;
-            return (w >> (8 * (k & 3))) & 0xFFu;
-        };
-        uint4 en = tab[symbol(a + m - 1)];
+        uint4 en = tab[sym[a + m - 1]];
         for (int64_t i = a + m - 1; i >= a; i--) {
             const uint4 e = en;
-            if (i > a) en = tab[symbol(i - 1)];
+            if (i > a) en = tab[sym[i - 1]];
             while (x >= e.w) {
                 base[--p] = (uint8_t)(x & 0xFF);
                 x >>= 8;
@@ -238,7 +225,7 @@ __global__ void __launch_bounds__(128) k_rans_chunks(const uint8_t* __restrict__
                                                      uint8_t* __restrict__ scratch, int32_t* __restrict__ len,
                                                      const int* __restrict__ err)
 {
-    code_chunks<false>(sym, n, chunk, freq_g, cum_g, scratch, len, err, blockIdx.x, gridDim.x);
+    code_chunks(sym, n, chunk, freq_g, cum_g, scratch, len, err, blockIdx.x, gridDim.x);
 }
 
 // Several streams in one launch: the blocks [block0, block0 + blocks) of job
@@ -256,7 +243,7 @@ struct ChunkJob {
 constexpr int MAX_CHUNK_JOBS = 16;
 struct ChunkJobs {
     ChunkJob j[MAX_CHUNK_JOBS];
-    int32_t njobs, chunk, vec;
+    int32_t njobs, chunk;
 };
 
 __global__ void __launch_bounds__(128) k_rans_chunks_multi(const ChunkJobs J)
@@ -266,8 +253,7 @@ __global__ void __launch_bounds__(128) k_rans_chunks_multi(const ChunkJobs J)
     const ChunkJob& q = J.j[k];
     const int64_t bi = (int64_t)blockIdx.x - q.block0;
     if (bi < 0 || bi >= q.blocks) return;
-    if (J.vec) code_chunks<true>(q.sym, q.n, J.chunk, q.freq, q.cum, q.scratch, q.len, q.err, bi, q.blocks);
-    else code_chunks<false>(q.sym, q.n, J.chunk, q.freq, q.cum, q.scratch, q.len, q.err, bi, q.blocks);
+    code_chunks(q.sym, q.n, J.chunk, q.freq, q.cum, q.scratch, q.len, q.err, bi, q.blocks);
 }
 
 // one block: exclusive scan of the chunk sizes (off[nch] = total)
@@ -1025,7 +1011,6 @@ extern "C" int tpc_compress_frame(const tpc_compress_in* in, int32_t ey, int32_t
     ChunkJobs J;
     memset(&J, 0, sizeof(J));
     J.chunk = chunk;
-    J.vec = (chunk % 16) == 0;             // the symbol regions are 256-byte aligned and padded to 256
     int32_t nblocks = 0;
     int64_t nchs[CS_N];
     for (int k = 0; k < CS_N; k++) {
