@@ -139,3 +139,70 @@ def test_calib_select_rejects_bad_arguments_without_touching_the_gpu():
     assert L.tpc_calib_select(3, None, None, None, 5.0, None, None) == tpc.TPC_ERR_ARG
     assert L.tpc_calib_select(3, 8, 8, 8, float("nan"), 8, None) == tpc.TPC_ERR_ARG
     assert L.tpc_calib_select(0, None, None, None, 5.0, None, None) == tpc.TPC_OK
+
+
+def test_compress_entry_points_check_their_arguments():
+    """Sizes and argument checks of the compressed-format calls, host only."""
+    import paper_1905_05515_b300 as tpc
+    L = tpc.lib()
+    A = tpc.abi
+
+    def cin(n=1000, T=10, na=500, ns=36, nr=152, ptr=1):
+        p = C.c_void_p(ptr if ptr else None)
+        return A.TpcCompressIn(n, ns, nr, p, p, p, p, T, na, p, p, p)
+
+    ws, mv, mb = C.c_size_t(0), C.c_int64(0), C.c_int64(0)
+    assert L.tpc_compress_workspace_size(C.byref(cin()), 4096, C.byref(ws)) == 0
+    assert L.tpc_compress_max_size(C.byref(cin()), 4096, C.byref(mv), C.byref(mb)) == 0
+    # worst-case stream values: NT, HS (tracks), 7 streams of attached clusters, UN (planes), UT, UY
+    assert mv.value == 2 * 10 + 7 * 500 + 36 * 152 + 2 * 1000
+    assert mb.value >= 12 * 524 and ws.value > 16 * 1000
+    ws2 = C.c_size_t(0)
+    L.tpc_compress_workspace_size(C.byref(cin(n=2000)), 4096, C.byref(ws2))
+    assert ws2.value > ws.value
+    for bad in (cin(n=-1), cin(T=-1), cin(ns=0), cin(nr=256), cin(ptr=0)):
+        assert L.tpc_compress_workspace_size(C.byref(bad), 4096, C.byref(ws)) == A.TPC_ERR_ARG
+    assert L.tpc_compress_workspace_size(C.byref(cin()), 0, C.byref(ws)) == A.TPC_ERR_ARG
+    assert L.tpc_compress_workspace_size(C.byref(cin()), 65537, C.byref(ws)) == A.TPC_ERR_ARG
+    counts = (C.c_int64 * 12)()
+    # a null workspace, output or vals buffer is refused before any device work
+    assert L.tpc_compress_fields(C.byref(cin()), 5, 6, None, 0, None, 0, counts, None) == A.TPC_ERR_ARG
+    assert L.tpc_compress_frame(C.byref(cin()), 5, 6, 4096, None, 0, None, 0, counts, None) == A.TPC_ERR_ARG
+    assert L.tpc_compress_frame(C.byref(cin()), 5, 99, 4096, C.c_void_p(1), 1 << 40, C.c_void_p(1), 1 << 40,
+                                counts, None) == A.TPC_ERR_ARG
+
+
+def test_calib_fit_checks_its_arguments():
+    """Defaults, workspace size and argument checks of the closed-loop fit, host only."""
+    import paper_1905_05515_b300 as tpc
+    import tpcgen
+    L = tpc.lib()
+    A = tpc.abi
+    o = A.TpcCalibFitOpts()
+    assert L.tpc_calib_fit_defaults(C.byref(o)) == 0
+    assert o.prior_sigma == pytest.approx(0.3) and o.rounds == 2 and o.max_iter == 300
+    g = A.make_geometry(tpcgen.row_x_f32(), 36, 250.0, True)
+    s1, s2, s0 = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+    assert L.tpc_calib_fit_workspace_size(C.byref(g), 1000, 150_000, C.byref(s1)) == 0
+    assert L.tpc_calib_fit_workspace_size(C.byref(g), 2000, 300_000, C.byref(s2)) == 0
+    L.tpc_calib_workspace_size(C.byref(g), 1000, 150_000, C.byref(s0))
+    assert s0.value < s1.value < s2.value
+    p = tpc.tpc_params_default()
+    tr = A.TpcCalibTracks()
+    tr.n_tracks = 0
+    th = C.c_void_p(1)
+    rep = A.TpcCalibFitReport()
+    bad = A.TpcCalibFitOpts()
+    L.tpc_calib_fit_defaults(C.byref(bad))
+    bad.prior_sigma = 0.0
+    assert L.tpc_calib_fit(C.byref(p), C.byref(g), 0.5, 2.58, 0.01, C.byref(tr), C.byref(bad), th, None, 0, None,
+                           None, C.byref(rep), None) == A.TPC_ERR_ARG
+    # a dip-angle array needs a positive variance
+    tr.tgl_ext = C.c_void_p(1)
+    tr.tgl_var = 0.0
+    assert L.tpc_calib_fit(C.byref(p), C.byref(g), 0.5, 2.58, 0.01, C.byref(tr), C.byref(o), th, None, 0, None,
+                           None, C.byref(rep), None) == A.TPC_ERR_ARG
+    tr.tgl_var = 9e-8
+    # no workspace: capacity error, before any device work
+    assert L.tpc_calib_fit(C.byref(p), C.byref(g), 0.5, 2.58, 0.01, C.byref(tr), C.byref(o), th, None, 0, None,
+                           None, C.byref(rep), None) == A.TPC_ERR_CAPACITY
