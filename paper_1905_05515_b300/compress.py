@@ -88,6 +88,21 @@ def compress_fields(sector, row, y, zt, clus_offset, clus_index, assign, n_secto
     return out
 
 
+def compress_buffers(sector, row, y, zt, clus_offset, clus_index, assign, n_sectors=36, n_rows=152, chunk=4096):
+    """Workspace and output buffers (uint8 CUDA tensors) large enough for
+    compress_frame of these inputs."""
+    L = abi.lib()
+    cin = _compress_in(sector, row, y, zt, clus_offset, clus_index, assign, n_sectors, n_rows)
+    ws = C.c_size_t(0)
+    if L.tpc_compress_workspace_size(C.byref(cin), chunk, C.byref(ws)):
+        raise abi.TpcError(abi.TPC_ERR_ARG, "tpc_compress_workspace_size")
+    mb = C.c_int64(0)
+    L.tpc_compress_max_size(C.byref(cin), chunk, None, C.byref(mb))
+    d = y.device
+    return (torch.empty(int(ws.value), dtype=torch.uint8, device=d),
+            torch.empty(max(int(mb.value), 1), dtype=torch.uint8, device=d))
+
+
 def compress_frame(sector, row, y, zt, clus_offset, clus_index, assign, n_sectors=36, n_rows=152, ey=5, et=6,
                    chunk=4096, workspace=None, out=None):
     """The compressed frame (tpc_compress_frame): a CUDA uint8 tensor of the 12
