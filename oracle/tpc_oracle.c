@@ -535,10 +535,13 @@ static void iv_push(ivec *a, int32_t x)
     a->v[a->n++] = x;
 }
 
+/* merge partner sector of s: dir +1 / -1 the next / previous wedge of the
+ * same side, dir 0 the same wedge on the other side of the central membrane */
 static int neighbour_sector(int s, int dir, int n_sectors)
 {
     if (n_sectors != 36) return -1;
     int side = s / 18, w = s % 18;
+    if (dir == 0) return (1 - side) * 18 + w;
     return side * 18 + (w + (dir > 0 ? 1 : 17)) % 18;
 }
 
@@ -849,7 +852,11 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
         free(cand);
     }
 
-    /* ---- a8: cross-sector merger (adjacent sectors, same side) */
+    /* ---- a8: cross-sector merger: adjacent sectors of one side and, where
+     * the clusters carry z, the mirror sector across the central membrane.
+     * The two sides share the wedge's local frame (no rotation); with drift
+     * times the two halves of a crossing track are displaced in z by twice
+     * the drift over the unknown collision time, so that pair is not tried. */
     R->n_seg = ns;
     R->seg_trk = (int32_t *)malloc(sizeof(int32_t) * nz(ns));
     R->seg_next = (int32_t *)malloc(sizeof(int32_t) * nz(ns));
@@ -878,14 +885,21 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
         int ta = R->seg_trk[a];
         int sa = sector[R->trk_start[ta]];
         const float *top = R->trk_top + (size_t)ta * NST;
-        for (int dir = 1; dir >= -1; dir -= 2) {
+        for (int dir = 1; dir >= -1; dir--) {
+            if (dir == 0 && G->continuous) continue;
             int sb = neighbour_sector(sa, dir, NS);
             if (sb < 0) continue;
-            float sn = dir > 0 ? SIN20 : -SIN20;
+            float cs = dir == 0 ? 1.0f : COS20;
+            float sn = dir > 0 ? SIN20 : (dir < 0 ? -SIN20 : 0.0f);
             for (int q = sstart[sb]; q < sstart[sb + 1]; q++) {
                 int b = sidx[q];
                 int tb = R->seg_trk[b];
                 const float *bot = R->trk_bot + (size_t)tb * NST;
+                /* across the membrane B must continue A outward (one frame:
+                 * B's inner end not inside A's outer end); the pair taken
+                 * the other way round fits as well at small dip angles and
+                 * would close a two-segment cycle */
+                if (dir == 0 && !(bot[0] >= top[0])) continue;
                 if (!(fabsf(bot[2] - top[2]) <= P->merge_dz)) continue;
                 /* screen: tan(lambda) and q/pT (and their variances) are not
                  * changed by the rotation or the propagation, and each pull
@@ -896,7 +910,7 @@ int orc_track(const orc_params *P, const orc_geom *G, float bz, float v_drift, i
                 float lim = 2.0f * P->merge_chi2;
                 if (dtl * dtl > lim * (top[6 + 9] + bot[6 + 9]) || dqp * dqp > lim * (top[6 + 14] + bot[6 + 14]))
                     continue;
-                float c2 = orc_merge_chi2(top, bot, COS20, sn, kb);
+                float c2 = orc_merge_chi2(top, bot, cs, sn, kb);
                 if (!(c2 < P->merge_chi2)) continue;
                 int ida = R->trk_start[ta], idb = R->trk_start[tb];
                 if (best_next[a] < 0 || c2 < bchi_n[a] ||

@@ -14,6 +14,18 @@ do not come from the oracle:
   Kolmogorov-Smirnov test), which a dropped covariance term, a missed
   transport of A's covariance or a transposed index would break;
 * a piece paired with another track's piece is refused (chi2 above the cut).
+
+Across the central membrane (events with z given and a vertex spread along
+z), the two pieces of a track share the wedge's local frame:
+
+* a noise-free helix split at the membrane has zero chi2 with no rotation and
+  is refused with the +-20 degree rotation of the neighbouring wedges;
+* on an event, every merge across the membrane joins pieces of one generated
+  track, nearly every crossing track found as two pieces of one wedge is
+  merged, and the reversed pair (which also fits at small dip angles) is not
+  what joins them;
+* with drift times (z unknown up to the collision time) nothing is merged
+  across the membrane.
 """
 import math
 
@@ -163,3 +175,113 @@ def test_pieces_of_different_tracks_are_refused(orc, split_pairs):
         a2, b2, d2, ca2, cb2 = pairs[(i + 7) % len(pairs)]
         c2.append(orc.merge_chi2(*_ends(ev, a, b2, ca, cb2), COS20, SIN20 if d > 0 else -SIN20, kb))
     assert min(c2) > MERGE_CUT
+
+
+# ---- central membrane --------------------------------------------------------------
+def _fitcov(orc, ev, run, n_passes):
+    x = ev.row_x[ev.row[run]].astype(np.float64)
+    st0 = np.zeros(21)
+    st0[0] = x[-1]
+    st0[1:6] = track_truth_state(ev, run[-1])
+    st0[6], st0[8], st0[11], st0[15], st0[20] = 0.01, 0.0225, 0.25, 0.25, 100.0
+    ok, st, _ = orc.fit64(ev.sector[run].astype(np.int32), x, ev.true_y[run], ev.true_z[run], st0, KB64,
+                          n_passes=n_passes)
+    assert ok
+    return st[6:]
+
+
+@pytest.fixture(scope="module")
+def membrane_ev():
+    return tpcgen.central_event(seed=3, n_tracks=3000, vertex_z_sigma=20.0)
+
+
+@pytest.fixture(scope="module")
+def membrane_pairs(orc, membrane_ev):
+    """Tracks crossing the membrane once inside one wedge: (outermost cluster
+    on the vertex side, innermost on the other side, covariances as above)."""
+    ev = membrane_ev
+    out = []
+    for t in range(ev.trk_pt.size):
+        idx = np.where(ev.label == t)[0]
+        if idx.size < 40:
+            continue
+        idx = idx[np.argsort(ev.true_s[idx])]
+        s = ev.sector[idx].astype(int)
+        k = np.where(s[1:] != s[:-1])[0]
+        if k.size != 1 or s[0] % 18 != s[-1] % 18:
+            continue
+        a_run, b_run = idx[:k[0] + 1], idx[k[0] + 1:]
+        if a_run.size < 12 or b_run.size < 12:
+            continue
+        out.append((a_run[-1], b_run[0], _fitcov(orc, ev, a_run, 2), _fitcov(orc, ev, b_run, 3)))
+    assert len(out) >= 50
+    return out
+
+
+def test_membrane_split_helix_has_zero_chi2_without_rotation(orc, membrane_ev, membrane_pairs):
+    ev = membrane_ev
+    kb = _kb32(orc)
+    for a, b, ca, cb in membrane_pairs:
+        top, bot = _ends(ev, a, b, ca, cb)
+        assert ev.sector[a] // 18 != ev.sector[b] // 18
+        assert np.sign(top[2]) != np.sign(bot[2]) or min(abs(top[2]), abs(bot[2])) < 1.0
+        assert orc.merge_chi2(top, bot, np.float32(1.0), np.float32(0.0), kb) < 1e-4
+        # the rotation of a neighbouring wedge does not apply across the membrane
+        assert orc.merge_chi2(top, bot, COS20, SIN20, kb) > MERGE_CUT
+        assert orc.merge_chi2(top, bot, COS20, -SIN20, kb) > MERGE_CUT
+
+
+def _majority(ev, r, a):
+    tq = r.seg_trk[a]
+    h = r.trk_hits[r.trk_off[tq]:r.trk_off[tq + 1]]
+    v, c = np.unique(ev.label[h], return_counts=True)
+    return int(v[c.argmax()]), c.max() / h.size
+
+
+def test_membrane_merging_on_an_event(orc, membrane_ev):
+    ev = membrane_ev
+    r = orc.track_event(ev)
+    ns = r.seg_trk.size
+    sec = ev.sector[r.trk_start[r.seg_trk]].astype(int)
+    side = sec // 18
+    cross = [(a, int(r.seg_next[a])) for a in range(ns) if r.seg_next[a] >= 0 and side[a] != side[r.seg_next[a]]]
+    assert len(cross) >= 40
+    kb = _kb32(orc)
+    for a, b in cross:
+        la, fa = _majority(ev, r, a)
+        lb, fb = _majority(ev, r, b)
+        assert la == lb >= 0 and fa > 0.8 and fb > 0.8
+        assert sec[a] % 18 == sec[b] % 18
+        top, bot = r.trk_top[r.seg_trk[a]], r.trk_bot[r.seg_trk[b]]
+        assert bot[0] >= top[0]                      # B continues A outward
+        # the reversed pair (B's outer end to A's inner end) fits as well for
+        # most of them: the outward order, not the chi2, tells them apart
+    rev = [orc.merge_chi2(r.trk_top[r.seg_trk[b]], r.trk_bot[r.seg_trk[a]], np.float32(1.0), np.float32(0.0), kb)
+           for a, b in cross]
+    assert np.mean(np.array(rev) < MERGE_CUT) > 0.3
+    # crossing tracks found as one piece on each side of one wedge: merged
+    pieces = {}
+    for a in range(ns):
+        lab, frac = _majority(ev, r, a)
+        if lab >= 0 and frac > 0.9:
+            pieces.setdefault(lab, []).append(a)
+    found = merged = 0
+    for lab, segs in pieces.items():
+        if len(segs) != 2 or side[segs[0]] == side[segs[1]] or sec[segs[0]] % 18 != sec[segs[1]] % 18:
+            continue
+        found += 1
+        merged += r.seg_next[segs[0]] == segs[1] or r.seg_next[segs[1]] == segs[0]
+    assert found >= 40 and merged >= 0.9 * found, (found, merged)
+    # each merged track is still a valid track: ndf and sectors of one wedge
+    for t in range(r.n_tracks):
+        cl = r.track_clusters(t)
+        assert r.tr_ndf[t] == 2 * cl.size - 5
+
+
+def test_no_membrane_merging_with_drift_times(orc):
+    ev = tpcgen.time_frame(seed=4, n_collisions=2, vertex_z_sigma=10.0, with_truth=False)
+    r = orc.track_event(ev)
+    side = ev.sector[r.trk_start[r.seg_trk]].astype(int) // 18
+    nxt = r.seg_next
+    assert (nxt >= 0).sum() > 0
+    assert not any(side[a] != side[nxt[a]] for a in range(nxt.size) if nxt[a] >= 0)

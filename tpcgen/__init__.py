@@ -114,8 +114,9 @@ def _helix_lib():
     return _helix
 
 
-def _crossings(pt, phi0, eta, q, looper, bz, alphas, row_x64):
-    """All accepted plane crossings of helices from the origin.
+def _crossings(pt, phi0, eta, q, looper, bz, alphas, row_x64, z0=None):
+    """All accepted plane crossings of helices from the origin (shifted in z
+    by the vertex z0 of each track when given).
 
     Returns (track, wedge, row, y_local, z, snp_local, s).  The helix:
     direction phi(s) = phi0 + h s / R with h = -q sign(B), z = s tan(lambda);
@@ -130,8 +131,10 @@ def _crossings(pt, phi0, eta, q, looper, bz, alphas, row_x64):
     h = np.ascontiguousarray(-q * np.sign(bz))
     tgl = np.ascontiguousarray(np.sinh(eta))
     s_exit = np.where(2 * R > RHO_OUT, 2 * R * np.arcsin(np.minimum(RHO_OUT / (2 * R), 1.0)), np.inf)
-    with np.errstate(divide="ignore"):
-        s_z = np.where(np.abs(tgl) > 0, Z_MAX / np.abs(tgl), np.inf)
+    zv = np.zeros(n) if z0 is None else np.asarray(z0, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # the path to the end plate the track heads for
+        s_z = np.where(tgl > 0, (Z_MAX - zv) / tgl, np.where(tgl < 0, (Z_MAX + zv) / -tgl, np.inf))
     s_max = np.ascontiguousarray(np.minimum(np.minimum(s_exit, MAX_TURNS * 2.0 * np.pi * R), s_z))
     phi0 = np.ascontiguousarray(phi0, np.float64)
     lp = np.ascontiguousarray(looper, np.uint8)
@@ -151,7 +154,10 @@ def _crossings(pt, phi0, eta, q, looper, bz, alphas, row_x64):
     y, z, snp, sp = (np.empty(tot) for _ in range(4))
     L.helix_crossings(*args, trk.ctypes.data_as(P32), wedge.ctypes.data_as(P32), row.ctypes.data_as(P32),
                       y.ctypes.data_as(PD), z.ctypes.data_as(PD), snp.ctypes.data_as(PD), sp.ctypes.data_as(PD))
-    return trk.astype(np.int64), wedge, row, y, z, snp, sp
+    trk = trk.astype(np.int64)
+    if z0 is not None:
+        z = z + zv[trk]
+    return trk, wedge, row, y, z, snp, sp
 
 
 def _gen_tracks(rng, n, pt_lo, pt_hi, phi_lo, phi_hi):
@@ -165,7 +171,7 @@ def _gen_tracks(rng, n, pt_lo, pt_hi, phi_lo, phi_hi):
 def generate(n_sectors=36, n_tracks=None, n_collisions=0, mult_mean=2000.0,
              looper_frac=0.0, noise_frac=0.05, continuous=False, seed=1,
              bz=0.5, frame_us=FRAME_US, with_truth=True, v_drift_true=V_DRIFT,
-             t0_true=0.0, calib=None, shuffle=True) -> Event:
+             t0_true=0.0, calib=None, shuffle=True, vertex_z_sigma=0.0) -> Event:
     """Generate one event (triggered) or one continuous read-out frame.
 
     * triggered (``continuous=False``): ``n_tracks`` primaries at t = 0;
@@ -173,6 +179,9 @@ def generate(n_sectors=36, n_tracks=None, n_collisions=0, mult_mean=2000.0,
       [0, frame_us), each with ceil(Exp(mult_mean)) primaries and
       ``looper_frac`` extra loopers; clusters carry drift time.
     ``calib`` (optional) distorts the cluster positions (see :func:`distortion`).
+    ``vertex_z_sigma`` (cm, default 0: every vertex at the origin) spreads the
+    primary vertex along z (Gaussian), so that tracks at small dip angles
+    cross the central membrane between the A and C sides.
     """
     rng = np.random.Generator(np.random.Philox(seed))
     row_x = row_x_f32()
@@ -200,9 +209,10 @@ def generate(n_sectors=36, n_tracks=None, n_collisions=0, mult_mean=2000.0,
     pt, phi0, eta, q = _gen_tracks(rng, n_prim, 0.2, 5.0, phi_lo, phi_hi)
     lpt, lphi0, leta, lq = _gen_tracks(rng, n_loop_total, 0.05, 0.2, phi_lo, phi_hi)
 
+    zv = rng.normal(0.0, vertex_z_sigma, n_prim + n_loop_total) if vertex_z_sigma > 0 else None
     cp = _crossings(np.concatenate([pt, lpt]), np.concatenate([phi0, lphi0]), np.concatenate([eta, leta]),
                     np.concatenate([q, lq]), np.concatenate([np.zeros(n_prim, bool), np.ones(n_loop_total, bool)]),
-                    bz, alphas, row_x64)
+                    bz, alphas, row_x64, z0=zv)
     t_idx, wedge, row, y_true, z_true, snp_true, s_true = cp
 
     trk_pt = np.concatenate([pt, lpt])
