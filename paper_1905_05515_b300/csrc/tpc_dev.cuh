@@ -114,6 +114,38 @@ __device__ __forceinline__ bool prop32(float* st, float x2, float kb)
     return true;
 }
 
+// The parameter half of prop32: the same operations in the same order for x,
+// y, z and sin(phi) and the same refusals, without the Jacobian and the
+// covariance (for passes that only need the track's position).
+__device__ __forceinline__ bool prop32_pos(float* st, float x2, float kb)
+{
+    float* p = st + 1;
+    const float dx = x2 - st[0];
+    if (dx == 0.0f) return true;
+    const float k = kb * p[4];
+    const float s1 = p[2];
+    const float s2 = __fmaf_rn(k, dx, s1);
+    if (!(fabsf(s1) < SNP_MAX) || !(fabsf(s2) < SNP_MAX)) return false;
+    const float c1 = __fsqrt_rn((1.0f - s1) * (1.0f + s1));
+    const float c2 = __fsqrt_rn((1.0f - s2) * (1.0f + s2));
+    const float ss = s1 + s2, cc = c1 + c2;
+    const float tt = __fdiv_rn(ss, cc);
+    const float dy = dx * tt;
+    const float dl0 = __fsqrt_rn(__fmaf_rn(dx, dx, dy * dy));
+    const float dl = dx < 0.0f ? -dl0 : dl0;
+    const float u = (0.5f * k) * dl;
+    if (!(fabsf(u) <= U_MAX)) return false;
+    const float u2 = u * u;
+    const float A = __fmaf_rn(u2, __fmaf_rn(u2, __fmaf_rn(u2, AS3, AS2), AS1), 1.0f);
+    const float dS = dl * A;
+    const float dz = dS * p[3];
+    st[0] = x2;
+    p[0] = p[0] + dy;
+    p[1] = p[1] + dz;
+    p[2] = s2;
+    return true;
+}
+
 // Rotation of the local frame by +angle (cs = cos, sn = sin); the state is
 // then at x' = x cs + y sn.  First-order Jacobian at fixed x'.
 __device__ __forceinline__ bool rot32(float* st, float cs, float sn, float kb)
@@ -289,10 +321,13 @@ __host__ __device__ __forceinline__ uint64_t tracklet_weight(int nhits, int star
     return ((uint64_t)(uint32_t)nhits << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)start_id);
 }
 
+// merge partner sector of s: dir +1 / -1 the next / previous wedge of the same
+// side, dir 0 the same wedge across the central membrane
 __device__ __forceinline__ int neighbour_sector(int s, int dir, int n_sectors)
 {
     if (n_sectors != 36) return -1;
     const int side = s / 18, w = s - side * 18;
+    if (dir == 0) return (1 - side) * 18 + w;
     return side * 18 + (w + (dir > 0 ? 1 : 17)) % 18;
 }
 

@@ -126,7 +126,8 @@ Layout make_layout(const tpc_params* p, const tpc_geometry* g, int64_t n, int nf
         L.ncells = std::min<int64_t>(per * zcells, ((int64_t)UINT32_MAX - 1) / per * per);
     }
     int64_t cap = std::max<int64_t>(4096, (n * (int64_t)p->tracklets_per_1k) / 1000);
-    L.ntcap = (int32_t)std::min<int64_t>(cap, std::max<int64_t>(n, 4096));
+    // at most 2^30 slots: the merger's pair list keeps a record index in 30 bits
+    L.ntcap = (int32_t)std::min<int64_t>({cap, std::max<int64_t>(n, 4096), (int64_t)1 << 30});
     L.mnzmax = MAX_MERGE_CELLS;
     const int64_t N = std::max<int64_t>(n, 1);
     const int64_t T = L.ntcap;
@@ -1302,11 +1303,14 @@ __global__ void k_reject(Frame* f, int cap, int nr, int np, float kb, float ivy,
         for (int w = 0; w < REJ_WORDS; w++) rej[w] = 0u;
         int nc = 0;
         uint32_t m = 0u;
+        // the next hit's record is loaded a step ahead (two dependent loads per hit)
+        float4 cn = nh > 0 ? sc[trk_hit(slot, nr, nh, nup, 0)] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (int k = 0; k < nh; k++) {
             if ((k & 31) == 0) m = ownmask[(int64_t)(k >> 5) * cap + t];
-            const float4 c = sc[trk_hit(slot, nr, nh, nup, k)];
+            const float4 c = cn;
+            if (k + 1 < nh) cn = sc[trk_hit(slot, nr, nh, nup, k + 1)];
             const int r = (int)(sc_plane(c) % (uint32_t)np) % nr;
-            if (!prop32(st, rowtab[r * ROWTAB], kb)) break;
+            if (!prop32_pos(st, rowtab[r * ROWTAB], kb)) break;   // the position only: bit-identical to prop32's
             const float dy = c.x - st[1];
             const float dz = c.y - st[2];
             const float q2 = __fmaf_rn(dy * dy, ivy, (dz * dz) * ivz);
@@ -1324,7 +1328,12 @@ __global__ void k_reject(Frame* f, int cap, int nr, int np, float kb, float ivy,
 }
 
 // ---------------------------------------------------------------------------
-// a8: cross-sector merger (adjacent sectors of one side, inside one frame)
+// a8: cross-sector merger (adjacent sectors of one side, inside one frame,
+// and, where the clusters carry z, the same wedge across the central membrane:
+// one local frame on both sides, so no rotation; B must continue A outward
+// there, since at small dip angles the reversed pair fits as well and would
+// close a two-segment cycle.  With drift times the two halves are displaced in
+// z by twice the drift over the unknown collision time and are not tried.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int merge_cell(float zeta, const Frame* f)
 {
@@ -1370,17 +1379,18 @@ __global__ void k_seg_keys(const Frame* __restrict__ f, int ns, int nr, const in
 // Merge-candidate record of one segment end, stored in merge-grid order so
 // that a candidate scan reads 32 contiguous bytes per candidate: z, tan(lambda),
 // q/pT and the variances of the last two (the window test and the screen),
-// the start-hit id (tie-break) and the tracklet index.
+// the start-hit id (tie-break), the tracklet index and x (the outward order
+// across the membrane).
 struct MergeRec {
     float4 a;   // z, tan(lambda), q/pT, var(tan(lambda))
-    float4 b;   // var(q/pT), id (int bits), tracklet (int bits), 0
+    float4 b;   // var(q/pT), id (int bits), tracklet (int bits), x
 };
 
 __device__ __forceinline__ MergeRec merge_rec(const float* st, int id, int t)
 {
     MergeRec m;
     m.a = make_float4(st[2], st[4], st[5], st[6 + 9]);
-    m.b = make_float4(st[6 + 14], __int_as_float(id), __int_as_float(t), 0.0f);
+    m.b = make_float4(st[6 + 14], __int_as_float(id), __int_as_float(t), st[0]);
     return m;
 }
 
@@ -1421,9 +1431,11 @@ struct MergeArgs {
     int32_t* bprev;
     const MergeRec* recb;   // merge-grid order, as byb
     const MergeRec* rect;   // merge-grid order, as byt
+    int mirror;             // 1: also the same wedge across the membrane (z given, 36 sectors)
     int prof;
     Frame* fw;
-    int2* pairs;            // screened pairs: segment a, inner-end record q (bit 31: direction -1)
+    int2* pairs;            // screened pairs: segment a, inner-end record q (bit 31: direction -1,
+                            // bit 30: across the membrane)
     float* pc2;             // their chi2
     unsigned long long* bestA;   // per segment: min (chi2 bits, partner id) as outer piece
     unsigned long long* bestB;   // per segment: the same as inner piece
@@ -1473,6 +1485,21 @@ struct MergeBest {
 // and k_merge_resolve writes the winners.  If the list overflows its capacity,
 // k_merge_next / k_merge_prev (one warp per end, chi2 inline) do it instead.
 constexpr int MP_U = 4;
+constexpr int MP_QMASK = 0x3fffffff;
+constexpr int MP_DOWN = (int)0x80000000;
+constexpr int MP_MIRROR = 0x40000000;
+
+// the merge directions tried from a sector: the two neighbouring wedges, then
+// the mirror sector where enabled
+__device__ __forceinline__ int merge_ndir(const MergeArgs& M) { return M.mirror ? 3 : 2; }
+__device__ __forceinline__ int merge_dir(int k) { return k == 0 ? 1 : (k == 1 ? -1 : 0); }
+
+// rotation of A's frame into B's for B in direction dir from A
+__device__ __forceinline__ void merge_rotation(int dir, float& cs, float& sn)
+{
+    cs = dir == 0 ? 1.0f : COS20;
+    sn = dir > 0 ? SIN20 : (dir < 0 ? -SIN20 : 0.0f);
+}
 
 __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
 {
@@ -1485,13 +1512,14 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
         const float* tp = M.t_top + (int64_t)ta * NST;
         MergeRec ra;
         ra.a = make_float4(tp[2], tp[4], tp[5], tp[6 + 9]);
-        ra.b = make_float4(tp[6 + 14], 0.0f, 0.0f, 0.0f);
-        for (int dir = 1; dir >= -1; dir -= 2) {
+        ra.b = make_float4(tp[6 + 14], 0.0f, 0.0f, tp[0]);
+        for (int k = 0; k < merge_ndir(M); k++) {
+            const int dir = merge_dir(k);
             const int sb = neighbour_sector(sa, dir, M.ns);
             if (sb < 0) continue;
             const int gsb = fr * M.ns + sb;
             int lo, hi;
-            merge_window(ra.a.x, M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
+            merge_window(ra.a.x, M.dz, sb, M.ns, M.f, lo, hi);   // B's cells, folded by B's side
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
             // MP_U rounds of 32 records per iteration: their loads are in
             // flight together before any is tested (the pair list is order-free)
@@ -1505,7 +1533,8 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
 #pragma unroll
                 for (int u = 0; u < MP_U; u++) {
                     const int q = q0 + 32 * u + lane;
-                    const bool pass = q < qe && fabsf(rr[u].a.x - ra.a.x) <= M.dz &&
+                    const bool pass = q < qe && (dir != 0 || rr[u].b.w >= ra.b.w) &&
+                                      fabsf(rr[u].a.x - ra.a.x) <= M.dz &&
                                       !merge_screened(ra, rr[u], 2.0f * M.chi2cut);
                     m[u] = __ballot_sync(0xffffffffu, pass);
                     tot += __popc(m[u]);
@@ -1514,7 +1543,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs M)
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&M.fw->n_mpairs, tot);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                const int flag = dir < 0 ? (int)0x80000000 : 0;
+                const int flag = dir < 0 ? MP_DOWN : (dir == 0 ? MP_MIRROR : 0);
 #pragma unroll
                 for (int u = 0; u < MP_U; u++) {
                     if ((m[u] >> lane) & 1u) {
@@ -1540,11 +1569,12 @@ __global__ void k_merge_chi2(MergeArgs M)
     unsigned nchi = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np_; i += gridDim.x * blockDim.x) {
         const int2 pr = M.pairs[i];
-        const int a = pr.x, q = pr.y & 0x7fffffff;
+        const int a = pr.x, q = pr.y & MP_QMASK;
         const MergeRec rb = M.recb[q];
         const int ta = M.seg[a], tb = __float_as_int(rb.b.z);
-        const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, M.t_bot + (int64_t)tb * NST, COS20,
-                                    pr.y < 0 ? -SIN20 : SIN20, M.kb);
+        float cs, sn;
+        merge_rotation(pr.y < 0 ? -1 : ((pr.y & MP_MIRROR) ? 0 : 1), cs, sn);
+        const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, M.t_bot + (int64_t)tb * NST, cs, sn, M.kb);
         nchi++;
         M.pc2[i] = c2;
         if (c2 < M.chi2cut) {
@@ -1566,7 +1596,7 @@ __global__ void k_merge_resolve(MergeArgs M)
         const float c2 = M.pc2[i];
         if (!(c2 < M.chi2cut)) continue;
         const int2 pr = M.pairs[i];
-        const int a = pr.x, q = pr.y & 0x7fffffff;
+        const int a = pr.x, q = pr.y & MP_QMASK;
         const int b = M.byb[q];
         if (M.bestA[a] == merge_key(c2, __float_as_int(M.recb[q].b.y))) M.bnext[a] = b;
         if (M.bestB[b] == merge_key(c2, M.t_id[M.seg[a]])) M.bprev[b] = a;
@@ -1593,20 +1623,23 @@ __global__ void __launch_bounds__(128) k_merge_next(MergeArgs M)
         for (int i = 0; i < NST; i++) top[i] = M.t_top[(int64_t)ta * NST + i];
         const MergeRec ra = merge_rec(top, 0, ta);
         MergeBest b{-1, 0, 0.0f};
-        for (int dir = 1; dir >= -1; dir -= 2) {
+        for (int k = 0; k < merge_ndir(M); k++) {
+            const int dir = merge_dir(k);
             const int sb = neighbour_sector(sa, dir, M.ns);
             if (sb < 0) continue;
             const int gsb = fr * M.ns + sb;
-            const float sn = dir > 0 ? SIN20 : -SIN20;
+            float cs, sn;
+            merge_rotation(dir, cs, sn);
             int lo, hi;
-            merge_window(top[2], M.dz, sb, M.ns, M.f, lo, hi);   // B's cells: B's side folding (same side)
+            merge_window(top[2], M.dz, sb, M.ns, M.f, lo, hi);   // B's cells, folded by B's side
             const int qb = M.cntb[gsb * mnz + lo], qe = M.cntb[gsb * mnz + hi + 1];
             for (int q = qb + lane; q < qe; q += 32) {
                 const MergeRec rb = M.recb[q];
+                if (dir == 0 && !(rb.b.w >= top[0])) continue;
                 if (!(fabsf(rb.a.x - top[2]) <= M.dz)) continue;
                 if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
                 const int tb = __float_as_int(rb.b.z);
-                const float c2 = merge_chi2(top, M.t_bot + (int64_t)tb * NST, COS20, sn, M.kb);
+                const float c2 = merge_chi2(top, M.t_bot + (int64_t)tb * NST, cs, sn, M.kb);
                 nchi++;
                 if (c2 < M.chi2cut) b.offer(q, __float_as_int(rb.b.y), c2);
             }
@@ -1635,21 +1668,24 @@ __global__ void __launch_bounds__(128) k_merge_prev(MergeArgs M)
         for (int i = 0; i < NST; i++) bot[i] = M.t_bot[(int64_t)tb * NST + i];
         const MergeRec rb = merge_rec(bot, 0, tb);
         MergeBest best{-1, 0, 0.0f};
-        for (int d = 1; d >= -1; d -= 2) {
+        for (int k = 0; k < merge_ndir(M); k++) {
+            const int d = merge_dir(k);
             const int sa = neighbour_sector(sb, d, M.ns);
             if (sa < 0) continue;
             const int gsa = fr * M.ns + sa;
             // seen from A, B lies in direction -d
-            const float sn = (-d) > 0 ? SIN20 : -SIN20;
+            float cs, sn;
+            merge_rotation(-d, cs, sn);
             int lo, hi;
             merge_window(bot[2], M.dz, sa, M.ns, M.f, lo, hi);
             const int qb = M.cntt[gsa * mnz + lo], qe = M.cntt[gsa * mnz + hi + 1];
             for (int q = qb + lane; q < qe; q += 32) {
                 const MergeRec ra = M.rect[q];
+                if (d == 0 && !(bot[0] >= ra.b.w)) continue;
                 if (!(fabsf(bot[2] - ra.a.x) <= M.dz)) continue;
                 if (merge_screened(ra, rb, 2.0f * M.chi2cut)) continue;
                 const int ta = __float_as_int(ra.b.z);
-                const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, bot, COS20, sn, M.kb);
+                const float c2 = merge_chi2(M.t_top + (int64_t)ta * NST, bot, cs, sn, M.kb);
                 if (c2 < M.chi2cut) best.offer(q, __float_as_int(ra.b.y), c2);
             }
         }
@@ -2759,6 +2795,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     M.cntb = cntb; M.cntt = cntt; M.byb = at<int32_t>(ws, L.byb); M.byt = at<int32_t>(ws, L.byt);
     M.recb = at<MergeRec>(ws, L.recb); M.rect = at<MergeRec>(ws, L.rect);
     M.bnext = at<int32_t>(ws, L.bnext); M.bprev = at<int32_t>(ws, L.bprev); M.prof = prof ? 1 : 0; M.fw = f;
+    M.mirror = (g->n_sectors == 36 && !g->continuous) ? 1 : 0;
     M.pairs = at<int2>(ws, L.mpair); M.pc2 = at<float>(ws, L.mpc2);
     M.bestA = at<unsigned long long>(ws, L.bestA); M.bestB = at<unsigned long long>(ws, L.bestB);
     M.pcap = (int)std::min<int64_t>(L.mpcap, INT32_MAX);

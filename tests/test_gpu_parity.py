@@ -192,3 +192,18 @@ def test_golden_line_cases(orc):
         tracks = [g["clus_index"][off[t]:off[t + 1]] for t in range(int(g["n_tracks"]))]
         check_golden_case(case, y.size, tk["start"], tk["nhits"], tk["kept"], tracks)
     assert os.path.exists(GOLDEN)
+
+
+@pytest.mark.parametrize("cap", [None, 0])
+def test_membrane_crossing_merges(orc, cap):
+    """An event with z given and the vertex spread along z (sigma 20 cm):
+    tracks crossing the central membrane are merged across it, bit-exact with
+    the oracle, through the pair list and through the direct path."""
+    import paper_1905_05515_b300 as tpc
+    ev = tpcgen.central_event(seed=3, n_tracks=3000, vertex_z_sigma=20.0, with_truth=False)
+    params = None if cap is None else tpc.tpc_params_default(merge_pairs_per_1k=cap)
+    g, r = _check(ev, orc, params=params)
+    side = ev.sector[r.trk_start[r.seg_trk]].astype(int) // 18
+    nxt = np.asarray(r.seg_next)
+    cross = sum(1 for a in range(nxt.size) if nxt[a] >= 0 and side[a] != side[nxt[a]])
+    assert cross >= 100, cross
