@@ -335,7 +335,7 @@ int tpc_export_tracklets(const void *workspace, int32_t capacity, int32_t hits_s
  *     on two streams, or from two host threads -- race on it: serialise them.
  * Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY, TPC_ERR_DATA, TPC_ERR_CUDA. */
 #define TPC_LINKS_STATIC_MAX_CLUSTERS 262144
-#define TPC_LINKS_STATIC_SCRATCH_BYTES 14416896
+#define TPC_LINKS_STATIC_SCRATCH_BYTES 14417664
 int tpc_links_static(const tpc_params *p, const tpc_geometry *g, float v_drift, const tpc_clusters *cl,
                      int32_t *link_up, int32_t *link_dn, uint8_t *is_start, void *stream);
 

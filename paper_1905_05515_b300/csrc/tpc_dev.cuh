@@ -270,6 +270,11 @@ __device__ __forceinline__ float merge_chi2(const float* top, const float* bot, 
 // ---------------------------------------------------------------------------
 // shared layout of the per-call device state
 // ---------------------------------------------------------------------------
+// The counters that a stage bumps with many atomics (the tracklet queues, the
+// merger's pair count, the start-hit and segment counts) each sit on a
+// 128-byte line of their own: kernels read the grid fields and the error flag
+// of the first line all the time, and a line under a stream of atomics queues
+// those reads at its L2 slice.
 struct Frame {
     unsigned zmin_key, zmax_key;   // order-preserving keys of the folded-z extrema, all frames
     float mzmin, minv_cs;          // merger grid (all frames)
@@ -277,16 +282,19 @@ struct Frame {
     int ny;                        // grid y-bins per z-cell
     unsigned total_cells;          // grid cells of all frames
     int err;                       // TPC_ERR_* set by kernels (0 = ok)
-    int n_starts, n_seg, n_tracks, n_clus;
+    int n_tracks, n_clus;
     int n_bad;                     // clusters rejected by validation
-    int trk_next;                  // work queue heads of the tracklet constructor's two passes
-    int trk_next2;
-    int n_mpairs;                  // merger: candidate pairs that passed the screen
     int n_rejected;                // clusters rejected before the refit
     int n_loop_err;                // looper legs: a bounded union-find walk gave up (never expected)
+    alignas(128) int n_starts;
+    alignas(128) int n_seg;
+    alignas(128) int trk_next;     // work queue heads of the tracklet constructor's two passes
+    alignas(128) int trk_next2;
+    alignas(128) int n_mpairs;     // merger: candidate pairs that passed the screen
     // work counters (params.profile): tracklet propagations, updates, window
     // candidates examined; refit propagations; merger chi2 evaluations
-    unsigned long long w_prop, w_upd, w_cand, w_refit_prop, w_merge;
+    alignas(128) unsigned long long w_prop;
+    unsigned long long w_upd, w_cand, w_refit_prop, w_merge;
 };
 
 // per time frame: grid of that frame's clusters

@@ -925,9 +925,12 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
     unsigned nprop = 0, nupd = 0, ncand = 0;
 
     float st[NST];
+    // (pass 1 ends every tracklet in phase A, where the kept state is the state)
     auto save_keep = [&]() {
+        if (PASS != 1) {
 #pragma unroll
-        for (int i = 0; i < NST; i++) keep_sh[i][threadIdx.x] = st[i];
+            for (int i = 0; i < NST; i++) keep_sh[i][threadIdx.x] = st[i];
+        }
     };
     int t = -1, phase = PH_DONE;
     int h1 = 0, r1 = 0, s = 0, lbase = 0, pgbase = 0, rc = 0, r = 0, miss = 0, nu = 0, nd = 0, jump = BACK_JUMP;
@@ -937,6 +940,16 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
     int nx_h = -1, nx_row = 0;
     float2 nx_yz = make_float2(0.0f, 0.0f);
     int32_t* slot = nullptr;
+    // the frame, sector and start row of a tracklet from its start hit's plane
+    auto enter = [&](uint32_t pg1) {
+        const int fr = (int)(pg1 / (uint32_t)A.np);
+        const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
+        G = A.fg[fr];
+        s = pl1 / NR;
+        r1 = pl1 - s * NR;
+        lbase = s * NR;
+        pgbase = (int)pg1 - r1;
+    };
     for (;;) {
         // ---- bookkeeping transitions
         if (PASS == 1 && (phase == PH_B || phase == PH_CSTART)) {
@@ -972,16 +985,10 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
             if (t >= nt) break;
             if (PASS == 2) {
                 // continue from the state phase A left (the start hit's plane
-                // included: no load of the start hit itself)
+                // included: no load of the start hit itself); the step below
+                // runs in this same iteration
                 const float* sv = A.t_state + (int64_t)t * TSAVE;
-                const uint32_t pg1 = (uint32_t)__float_as_int(sv[NST + 3]);
-                const int fr = (int)(pg1 / (uint32_t)A.np);
-                const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
-                G = A.fg[fr];
-                s = pl1 / NR;
-                r1 = pl1 - s * NR;
-                lbase = s * NR;
-                pgbase = (int)pg1 - r1;
+                enter((uint32_t)__float_as_int(sv[NST + 3]));
 #pragma unroll
                 for (int i = 0; i < NST; i++) st[i] = sv[i];
                 phase = __float_as_int(sv[NST]);
@@ -991,19 +998,13 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
                 miss = 0;
                 slot = A.t_hits + (int64_t)t * NR;
                 save_keep();
-                continue;
             }
+        }
+        if (PASS != 2 && phase == PH_DONE) {     // a start hit just taken (passes 0 and 1)
             // initial state at the start hit: y, z measured, slopes from the first link
             h1 = A.starts[t];
             const float4 c1 = A.sc[h1];
-            const uint32_t pg1 = sc_plane(c1);
-            const int fr = (int)(pg1 / (uint32_t)A.np);
-            const int pl1 = (int)(pg1 - (uint32_t)fr * A.np);
-            G = A.fg[fr];
-            s = pl1 / NR;
-            r1 = pl1 - s * NR;
-            lbase = s * NR;
-            pgbase = (int)pg1 - r1;
+            enter(sc_plane(c1));
             if (PASS == 1) {
                 A.t_start[t] = h1;
                 A.t_id[t] = sc_id(c1);
@@ -1123,31 +1124,27 @@ __global__ void __launch_bounds__(TRK_BLOCK, 8) k_tracklets(TrkArgs A)
         }
         // ---- Kalman update (one call site)
         const bool took = upd && update32(st, my, mz, A.vy, A.vz, cmax);
-        if (phase == PH_A) {
-            slot[nu++] = hn;
+        // the hit is recorded and the state kept on one path for all phases
+        // (phase A keeps its chain hit whether or not the update was taken):
+        // hits above the start fill the slot from the front, those below it
+        // from the back
+        if (phase == PH_A || took) {
+            if (PROF && phase != PH_A) nupd++;
+            int k;
+            if (phase == PH_C) k = NR - (++nd);
+            else k = nu++;
+            slot[k] = phase == PH_A ? hn : c;
             save_keep();
-        } else if (phase == PH_B) {
-            if (took) {
-                if (PROF) nupd++;
-                slot[nu++] = c;
-                save_keep();
-                miss = 0;
-            } else if (++miss >= A.max_miss) {
+            miss = 0;
+        } else if (++miss >= A.max_miss) {
+            if (phase == PH_B) {
                 phase = PH_CSTART;
-            }
-        } else {
-            if (took) {
-                if (PROF) nupd++;
-                nd++;
-                slot[NR - nd] = c;
-                save_keep();
-                miss = 0;
-            } else if (++miss >= A.max_miss) {
+            } else {
                 phase = PH_DONE;
                 continue;
             }
-            r--;
         }
+        if (phase == PH_C) r--;
     }
     if (PROF) {
         // work counters: one atomic per warp (every lane of the warp gets here)
