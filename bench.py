@@ -59,7 +59,7 @@ ATTACH_B_PER_CLUSTER = 43
 # visit, flags) in an ncu capture of the 35-collision frame (26.5 + 78.8 + 15.9),
 # scaled to a launch by the cluster count
 NCU_ATTACH_TRAFFIC_B_PER_CLUSTER = 121.2
-NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 194.8}
+NCU_TRAFFIC_B_PER_CLUSTER = {"tracklets": 193.7}
 # Cluster compression, algorithmic bytes per input cluster (the coded output
 # is added per frame): one read of its sector, row, y, zt (10) and of its
 # assignment (4), one read of its entry in the track cluster lists (4).
