@@ -32,10 +32,11 @@ constexpr int MAX_MERGE_CELLS = 4096;
 constexpr int MAX_CHAIN = 36;
 constexpr int LEN_BUCKETS = 512;        // refit ordering: cluster counts above 511 share a bucket
 constexpr int MAX_FRAMES = 4096;
-// Binning: every plane's count is split over PSPLIT counters (by cluster
-// index), so that the thousands of clusters of one plane do not all meet at
-// one atomic; a plane's counters are consecutive, so its clusters stay one
-// range.  Planes x PSPLIT < 2^32 (36 x 255 x MAX_FRAMES x 16).
+// Per-plane bucket counters: PSPLIT consecutive counters per plane (the
+// cluster attachment spreads its reservations over them; the binning counts
+// each block's clusters per plane in shared memory and reserves them in the
+// plane's first counter), so a plane's entries stay one range.  Planes x
+// PSPLIT < 2^32 (36 x 255 x MAX_FRAMES x 16).
 constexpr int PSPLIT = 16;
 // grid cell budget of a batch beyond the first frame's max_z_cells: two
 // cells per cluster (a 50-collision frame occupies about 0.6 clusters per
@@ -330,19 +331,40 @@ __global__ void k_init_frame(Frame* f, FrameGrid* fg, int nframes)
 __device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36 && s >= 18) ? -z : z; }
 
 // blockIdx.y = frame; the blocks of one frame stride over its cluster range
-__device__ __forceinline__ uint32_t plane_bucket(uint32_t pg, int i) { return pg * PSPLIT + ((uint32_t)i & (PSPLIT - 1)); }
+// RANK: each block takes one contiguous chunk of its frame's clusters and
+// also ranks every cluster among the clusters of its plane (frame, sector,
+// row): first within the block, by counters of the frame's planes in shared
+// memory, then the block reserves each plane's count in the plane's first
+// global counter with one atomic and adds the reservation to its clusters'
+// ranks (the order of the atomics: any).  A block of a large frame touches
+// each plane once, so a frame of n clusters costs planes x blocks global
+// atomics instead of n.  Without RANK: a grid-stride pass with no ranks.
+constexpr int PREP_RANK_BLOCK = 1024;
 
-__global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
-                       const uint8_t* __restrict__ row, const float* __restrict__ y, const float* __restrict__ zt,
-                       int ns, int nr, int continuous, float zmax, float vdrift, float* __restrict__ zlin,
-                       uint16_t* __restrict__ cfr, Frame* f, FrameGrid* fg, int np, uint32_t* __restrict__ pcount,
-                       uint32_t* __restrict__ prank)
+template <bool RANK>
+__global__ void __launch_bounds__(RANK ? PREP_RANK_BLOCK : 256)
+k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
+       const uint8_t* __restrict__ row, const float* __restrict__ y, const float* __restrict__ zt,
+       int ns, int nr, int continuous, float zmax, float vdrift, float* __restrict__ zlin,
+       uint16_t* __restrict__ cfr, Frame* f, FrameGrid* fg, int np, uint32_t* __restrict__ pcount,
+       uint32_t* __restrict__ prank)
 {
+    extern __shared__ uint32_t pc_sh[];     // RANK: [np] the block's count, then its reservation, per plane
     const int fr = blockIdx.y;
     const int b = offsets[fr], e = offsets[fr + 1];
+    int i0 = b + blockIdx.x * blockDim.x + threadIdx.x, i1 = e, di = gridDim.x * blockDim.x;
+    if (RANK) {
+        const int chunk = (int)(((int64_t)(e - b) + gridDim.x - 1) / gridDim.x);
+        const int64_t c0 = (int64_t)b + (int64_t)blockIdx.x * chunk;
+        i0 = (int)(c0 < e ? c0 : e) + threadIdx.x;
+        i1 = (int)(c0 + chunk < e ? c0 + chunk : e);
+        di = blockDim.x;
+        for (int q = threadIdx.x; q < np; q += blockDim.x) pc_sh[q] = 0u;
+        __syncthreads();
+    }
     unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
     int bad = 0;
-    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+    for (int i = i0; i < i1; i += di) {
         const int s = sector[i], r = row[i];
         float z = zt[i];
         if (continuous) {
@@ -359,8 +381,7 @@ __global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __res
         const unsigned k = fkey(fold(z, s, ns));
         kmin = min(kmin, k);
         kmax = max(kmax, k);
-        // rank of the cluster in its share of its plane (order of the atomics: any)
-        if (pcount) prank[i] = atomicAdd(&pcount[plane_bucket((uint32_t)fr * (uint32_t)np + (uint32_t)(s * nr + r), i)], 1u);
+        if (RANK) prank[i] = atomicAdd(&pc_sh[s * nr + r], 1u);
     }
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -377,6 +398,19 @@ __global__ void k_prep(const int32_t* __restrict__ offsets, const uint8_t* __res
         if (bad) {
             atomicAdd(&f->n_bad, bad);
             atomicExch(&f->err, TPC_ERR_DATA);
+        }
+    }
+    if (RANK) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < np; q += blockDim.x) {
+            const uint32_t c = pc_sh[q];
+            if (c) pc_sh[q] = atomicAdd(&pcount[((uint32_t)fr * (uint32_t)np + (uint32_t)q) * PSPLIT], c);
+        }
+        __syncthreads();
+        // (a rejected cluster keeps an undefined rank: the call fails with TPC_ERR_DATA)
+        for (int i = i0; i < i1; i += di) {
+            const int s = sector[i], r = row[i];
+            if (s < ns && r < nr) prank[i] += pc_sh[s * nr + r];
         }
     }
 }
@@ -510,7 +544,7 @@ __global__ void k_pscatter(int n, const uint8_t* __restrict__ sector, const uint
     if (f->err) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pg = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
-        pbuf[pstart[plane_bucket(pg, i)] + prank[i]] = make_float4(y[i], zlin[i], __int_as_float(i), __uint_as_float(pg));
+        pbuf[pstart[(size_t)pg * PSPLIT] + prank[i]] = make_float4(y[i], zlin[i], __int_as_float(i), __uint_as_float(pg));
     }
 }
 
@@ -2688,9 +2722,12 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     CK(cudaMemsetAsync(pstart, 0, sizeof(uint32_t) * ((size_t)nplanes * PSPLIT + 1), st));
     k_init_frame<<<std::max(1, (NF + 255) / 256), 256, 0, st>>>(f, fg, NF);
     {
-        const int gx = std::max(1, std::min(grid_for(n, B), (148 * 16 + NF - 1) / NF));
-        k_prep<<<dim3(gx, NF), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
-                                          g->continuous, g->z_max, v_drift, zlin, cfr, f, fg, L.np, pstart, cell);
+        // chunks of about 32 k clusters (the average frame's), at most two blocks per SM per frame
+        const int64_t per_frame = ((int64_t)n + NF - 1) / NF;
+        const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((per_frame + 32767) / 32768, 2 * 148));
+        k_prep<true><<<dim3(gx, NF), PREP_RANK_BLOCK, sizeof(uint32_t) * L.np, st>>>(
+            offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows, g->continuous, g->z_max, v_drift,
+            zlin, cfr, f, fg, L.np, pstart, cell);
     }
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, NF, L.np, L.ny, p->z_cell, L.nzmax, (long long)L.ncells,
                                    0.25f * p->merge_dz, L.mnzmax, p->packed_links);
@@ -3275,8 +3312,8 @@ int tpc_links_static(const tpc_params* p, const tpc_geometry* g, float v_drift, 
     const int B = 256;
     const int gN = grid_for(n, B);
     k_init_frame<<<1, 32, 0, st>>>(f, fg, 1);
-    k_prep<<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
-                                      g->continuous, g->z_max, v_drift, zlin, cfr, f, fg, np, nullptr, nullptr);
+    k_prep<false><<<dim3(gN, 1), B, 0, st>>>(offsets, cl->sector, cl->row, cl->y, cl->zt, g->n_sectors, g->n_rows,
+                                             g->continuous, g->z_max, v_drift, zlin, cfr, f, fg, np, nullptr, nullptr);
     k_grid_setup<<<1, 32, 0, st>>>(f, fg, 1, np, 1, p->z_cell, STATIC_NZ, (long long)ncells, 0.25f * p->merge_dz,
                                    MAX_MERGE_CELLS, 0);
     // the histogram must start at zero: the scratch keeps the previous call's contents
