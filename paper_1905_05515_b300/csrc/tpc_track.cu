@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 using namespace tpc;
@@ -2684,6 +2686,47 @@ namespace {
 
 // Enqueue the whole chain on `st` (no host synchronisation, no pageable copy:
 // capturable in a CUDA graph once the tables are in the workspace).
+// Side stream of a caller's stream, with a fork and a join event: the cluster
+// rejection (it rewrites the owned-hit masks and counts) runs there beside the
+// merger (it reads the segment ends), which share no data.  One per (device,
+// caller stream), created on first use and kept for the life of the process;
+// the creation switches this thread to relaxed capture mode, so a first use
+// inside a stream capture is allowed.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+std::map<std::pair<int, cudaStream_t>, SideStream> g_side;
+
+cudaError_t side_stream(cudaStream_t st, SideStream& out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    const auto key = std::make_pair(dev, st);
+    const auto it = g_side.find(key);
+    if (it != g_side.end()) {
+        out = it->second;
+        return cudaSuccess;
+    }
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    e = cudaThreadExchangeStreamCaptureMode(&mode);
+    if (e != cudaSuccess) return e;
+    SideStream n;
+    e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming);
+    cudaStreamCaptureMode back = mode;
+    const cudaError_t e2 = cudaThreadExchangeStreamCaptureMode(&back);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e;
+    g_side[key] = n;
+    out = n;
+    return cudaSuccess;
+}
+
 int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift, const tpc_clusters* cl, void* ws,
             const Layout& L, tpc_tracks* out, int32_t* dev_counts, cudaStream_t st, bool prof)
 {
@@ -2799,14 +2842,21 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                                          at<int32_t>(ws, L.t_own), at<uint32_t>(ws, L.ownmask));
     }
     g_launches += 2;
-    if (p->outlier_chi2 > 0.0f) {
+    CK(mark(6));
+    // cluster rejection on the side stream, beside the merger below
+    SideStream side;
+    const bool reject = p->outlier_chi2 > 0.0f;
+    if (reject) {
+        CK(side_stream(st, side));
+        CK(cudaEventRecord(side.fork, st));
+        CK(cudaStreamWaitEvent(side.s, side.fork, 0));
         volatile float ivyv = 1.0f / vy, ivzv = 1.0f / vz;
-        k_reject<<<gt2, B, 0, st>>>(f, ntcap, g->n_rows, L.np, kb, ivyv, ivzv, p->outlier_chi2, seg, TA.t_nhits,
-                                    TA.t_nup, TA.t_hits, TA.t_bot, sc, rowtab, at<uint32_t>(ws, L.ownmask),
-                                    at<int32_t>(ws, L.t_own));
+        k_reject<<<gt2, B, 0, side.s>>>(f, ntcap, g->n_rows, L.np, kb, ivyv, ivzv, p->outlier_chi2, seg, TA.t_nhits,
+                                        TA.t_nup, TA.t_hits, TA.t_bot, sc, rowtab, at<uint32_t>(ws, L.ownmask),
+                                        at<int32_t>(ws, L.t_own));
+        CK(cudaEventRecord(side.join, side.s));
         g_launches++;
     }
-    CK(mark(6));
     // a8: merger
     const int64_t mcells = (int64_t)NF * g->n_sectors * L.mnzmax;
     uint32_t* cntb = at<uint32_t>(ws, L.cntb);
@@ -2853,6 +2903,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
                                    at<int32_t>(ws, L.next2), at<int32_t>(ws, L.prev2), seg, TA.t_id, headmark);
     g_launches += 9;
     scan_u32(headmark, n, aux, st);
+    if (reject) CK(cudaStreamWaitEvent(st, side.join, 0));
     CK(mark(7));
     // merged cluster lists and assignments
     uint32_t* tcount = at<uint32_t>(ws, L.tcount);
