@@ -2924,18 +2924,24 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     g_launches++;
     scan_u32(tcount, ntcap, aux, st);
     k_track_fill<<<gt2, B, 0, st>>>(AA);
-    k_seg_fill<<<gt2w, B, 0, st>>>(AA);
-    g_launches += 2;
-    CK(mark(8));
-    // a9: refit
-    // refit order: tracks by decreasing cluster count (counting sort over LEN_BUCKETS)
+    // the refit order (tracks by decreasing cluster count, a counting sort over
+    // LEN_BUCKETS) needs only the counts: on the side stream, beside the fill
+    // of the cluster lists
     uint32_t* lcnt = at<uint32_t>(ws, L.lencnt);
     int32_t* order = at<int32_t>(ws, L.order);
-    CK(cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * (LEN_BUCKETS + 1), st));
-    k_len_hist<<<gt2, B, 0, st>>>(f, out->nclus, out->capacity_tracks, lcnt);
-    scan_u32(lcnt, LEN_BUCKETS, aux, st);
-    k_len_scatter<<<gt2, B, 0, st>>>(f, out->nclus, out->capacity_tracks, lcnt, order);
-    g_launches += 2;
+    CK(side_stream(st, side));
+    CK(cudaEventRecord(side.fork, st));
+    CK(cudaStreamWaitEvent(side.s, side.fork, 0));
+    CK(cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * (LEN_BUCKETS + 1), side.s));
+    k_len_hist<<<gt2, B, 0, side.s>>>(f, out->nclus, out->capacity_tracks, lcnt);
+    scan_u32(lcnt, LEN_BUCKETS, aux, side.s);
+    k_len_scatter<<<gt2, B, 0, side.s>>>(f, out->nclus, out->capacity_tracks, lcnt, order);
+    CK(cudaEventRecord(side.join, side.s));
+    k_seg_fill<<<gt2w, B, 0, st>>>(AA);
+    g_launches += 4;
+    CK(mark(8));
+    // a9: refit
+    CK(cudaStreamWaitEvent(st, side.join, 0));
     int rr = tpc_launch_refit(p, g, bz, AA.tcl, order, f, AA.ttail, TA.t_top, out,
                               std::min(out->capacity_tracks, ntcap), st);
     if (rr) return rr;
