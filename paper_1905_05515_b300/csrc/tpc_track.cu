@@ -2800,6 +2800,34 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     k_clean_starts<<<gN, B, 0, st>>>(n, upr, dnr, up, dn, starts, ntcap, f);
     g_launches += 1;
     CK(mark(4));
+    // The initialisation of the later stages' buffers (the selector's hit
+    // weights, the merger's grids, lists and best keys, the assembly's counts,
+    // segment ranks and the assignment output) runs on the side stream while
+    // the tracklet constructor runs; nothing before the selector uses them.
+    const bool w32 = n <= (1 << 24);   // every start-hit id below 2^24: 32-bit weights
+    const int64_t mcells = (int64_t)NF * g->n_sectors * L.mnzmax;
+    uint32_t* cntb = at<uint32_t>(ws, L.cntb);
+    uint32_t* cntt = at<uint32_t>(ws, L.cntt);
+    uint32_t* headmark = at<uint32_t>(ws, L.headmark);
+    uint32_t* tcount = at<uint32_t>(ws, L.tcount);
+    SideStream side;
+    CK(side_stream(st, side));
+    CK(cudaEventRecord(side.fork, st));
+    CK(cudaStreamWaitEvent(side.s, side.fork, 0));
+    CK(cudaMemsetAsync(hitw, 0, (w32 ? 4 : 8) * (size_t)n, side.s));
+    CK(cudaMemsetAsync(cntb, 0, 4 * (size_t)(mcells + 1), side.s));
+    CK(cudaMemsetAsync(cntt, 0, 4 * (size_t)(mcells + 1), side.s));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), side.s));
+    CK(cudaMemsetAsync(at<unsigned long long>(ws, L.bestA), 0xFF, 8 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(at<unsigned long long>(ws, L.bestB), 0xFF, 8 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.bnext), 0xFF, 4 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.bprev), 0xFF, 4 * (size_t)ntcap, side.s));
+    CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), side.s));
+    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)n, side.s));
+    CK(cudaMemsetAsync(at<int32_t>(ws, L.segrank), 0xFF, sizeof(int32_t) * (size_t)ntcap, side.s));   // -1: in no track
+    CK(cudaEventRecord(side.join, side.s));
     // a6: tracklets
     TrkArgs TA;
     TA.rowtab = rowtab; TA.sc = sc; TA.cstart = cstart; TA.up = up;
@@ -2820,8 +2848,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     g_launches += 2;
     CK(mark(5));
     // a7: selector
-    const bool w32 = n <= (1 << 24);   // every start-hit id below 2^24: 32-bit weights
-    CK(cudaMemsetAsync(hitw, 0, (w32 ? 4 : 8) * (size_t)n, st));
+    CK(cudaStreamWaitEvent(st, side.join, 0));
     const int gt2 = grid_for(ntcap, B);
     uint8_t* kept = at<uint8_t>(ws, L.t_kept);
     int32_t* seg = at<int32_t>(ws, L.seg);
@@ -2844,10 +2871,8 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     g_launches += 2;
     CK(mark(6));
     // cluster rejection on the side stream, beside the merger below
-    SideStream side;
     const bool reject = p->outlier_chi2 > 0.0f;
     if (reject) {
-        CK(side_stream(st, side));
         CK(cudaEventRecord(side.fork, st));
         CK(cudaStreamWaitEvent(side.s, side.fork, 0));
         volatile float ivyv = 1.0f / vy, ivzv = 1.0f / vz;
@@ -2858,15 +2883,6 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
         g_launches++;
     }
     // a8: merger
-    const int64_t mcells = (int64_t)NF * g->n_sectors * L.mnzmax;
-    uint32_t* cntb = at<uint32_t>(ws, L.cntb);
-    uint32_t* cntt = at<uint32_t>(ws, L.cntt);
-    CK(cudaMemsetAsync(cntb, 0, 4 * (size_t)(mcells + 1), st));
-    CK(cudaMemsetAsync(cntt, 0, 4 * (size_t)(mcells + 1), st));
-    CK(cudaMemsetAsync(at<int32_t>(ws, L.snext), 0xFF, 4 * (size_t)ntcap, st));
-    CK(cudaMemsetAsync(at<int32_t>(ws, L.sprev), 0xFF, 4 * (size_t)ntcap, st));
-    uint32_t* headmark = at<uint32_t>(ws, L.headmark);
-    CK(cudaMemsetAsync(headmark, 0, 4 * (size_t)(n + 1), st));
     k_seg_keys<<<gt2, B, 0, st>>>(f, g->n_sectors, g->n_rows, seg, sc, TA.t_start, TA.t_top, TA.t_bot, cntb, cntt,
                                   at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt), at<uint32_t>(ws, L.slotb),
                                   at<uint32_t>(ws, L.slott));
@@ -2883,10 +2899,6 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     M.pairs = at<int2>(ws, L.mpair); M.pc2 = at<float>(ws, L.mpc2);
     M.bestA = at<unsigned long long>(ws, L.bestA); M.bestB = at<unsigned long long>(ws, L.bestB);
     M.pcap = (int)std::min<int64_t>(L.mpcap, INT32_MAX);
-    CK(cudaMemsetAsync(M.bestA, 0xFF, 8 * (size_t)ntcap, st));
-    CK(cudaMemsetAsync(M.bestB, 0xFF, 8 * (size_t)ntcap, st));
-    CK(cudaMemsetAsync(M.bnext, 0xFF, 4 * (size_t)ntcap, st));
-    CK(cudaMemsetAsync(M.bprev, 0xFF, 4 * (size_t)ntcap, st));
     k_seg_scatter<<<gt2, B, 0, st>>>(f, cntb, cntt, at<uint32_t>(ws, L.keyb), at<uint32_t>(ws, L.keyt),
                                      at<uint32_t>(ws, L.slotb), at<uint32_t>(ws, L.slott), at<int32_t>(ws, L.byb),
                                      at<int32_t>(ws, L.byt), seg, TA.t_id, TA.t_top, TA.t_bot,
@@ -2906,9 +2918,6 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     if (reject) CK(cudaStreamWaitEvent(st, side.join, 0));
     CK(mark(7));
     // merged cluster lists and assignments
-    uint32_t* tcount = at<uint32_t>(ws, L.tcount);
-    CK(cudaMemsetAsync(tcount, 0, 4 * (size_t)(ntcap + 1), st));
-    CK(cudaMemsetAsync(out->assign, 0xFF, 4 * (size_t)n, st));
     AsmArgs AA;
     AA.f = f; AA.nr = g->n_rows; AA.np = L.np; AA.n = n; AA.cap_tracks = out->capacity_tracks;
     AA.cap_clus = out->capacity_clusters; AA.ntcap = ntcap; AA.seg = seg; AA.next2 = at<int32_t>(ws, L.next2);
@@ -2919,7 +2928,6 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     AA.frame = out->frame;
     AA.rowtab = rowtab; AA.tcl = at<float4>(ws, L.tcl);
     AA.t_own = at<int32_t>(ws, L.t_own); AA.segoff = at<int32_t>(ws, L.segoff); AA.segrank = at<int32_t>(ws, L.segrank);
-    CK(cudaMemsetAsync(AA.segrank, 0xFF, sizeof(int32_t) * (size_t)ntcap, st));   // -1: in no track
     k_track_count<<<gt2, B, 0, st>>>(AA);
     g_launches++;
     scan_u32(tcount, ntcap, aux, st);
@@ -2929,7 +2937,6 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     // of the cluster lists
     uint32_t* lcnt = at<uint32_t>(ws, L.lencnt);
     int32_t* order = at<int32_t>(ws, L.order);
-    CK(side_stream(st, side));
     CK(cudaEventRecord(side.fork, st));
     CK(cudaStreamWaitEvent(side.s, side.fork, 0));
     CK(cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * (LEN_BUCKETS + 1), side.s));
