@@ -342,6 +342,7 @@ __device__ __forceinline__ float fold(float z, int s, int ns) { return (ns == 36
 // each plane once, so a frame of n clusters costs planes x blocks global
 // atomics instead of n.  Without RANK: a grid-stride pass with no ranks.
 constexpr int PREP_RANK_BLOCK = 1024;
+constexpr int PREP_U = 4;
 
 template <bool RANK>
 __global__ void __launch_bounds__(RANK ? PREP_RANK_BLOCK : 256)
@@ -366,24 +367,42 @@ k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
     }
     unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
     int bad = 0;
-    for (int i = i0; i < i1; i += di) {
-        const int s = sector[i], r = row[i];
-        float z = zt[i];
-        if (continuous) {
-            const float zl = zmax - vdrift * z;
-            z = (ns == 36 && s >= 18) ? -zl : zl;
+    // PREP_U clusters per thread and round, their loads in flight together
+    for (int ib = i0; ib < i1; ib += PREP_U * di) {
+        int sv[PREP_U], rv[PREP_U];
+        float zv[PREP_U], yv[PREP_U];
+#pragma unroll
+        for (int u = 0; u < PREP_U; u++) {
+            const int i = ib + u * di;
+            if (i < i1) {
+                sv[u] = sector[i];
+                rv[u] = row[i];
+                zv[u] = zt[i];
+                yv[u] = y[i];
+            }
         }
-        zlin[i] = z;
-        cfr[i] = (uint16_t)fr;
-        const bool ok = s < ns && r < nr && isfinite(z) && isfinite(y[i]);
-        if (!ok) {
-            bad++;
-            continue;
+#pragma unroll
+        for (int u = 0; u < PREP_U; u++) {
+            const int i = ib + u * di;
+            if (i >= i1) continue;
+            const int s = sv[u], r = rv[u];
+            float z = zv[u];
+            if (continuous) {
+                const float zl = zmax - vdrift * z;
+                z = (ns == 36 && s >= 18) ? -zl : zl;
+            }
+            zlin[i] = z;
+            cfr[i] = (uint16_t)fr;
+            const bool ok = s < ns && r < nr && isfinite(z) && isfinite(yv[u]);
+            if (!ok) {
+                bad++;
+                continue;
+            }
+            const unsigned k = fkey(fold(z, s, ns));
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+            if (RANK) prank[i] = atomicAdd(&pc_sh[s * nr + r], 1u);
         }
-        const unsigned k = fkey(fold(z, s, ns));
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-        if (RANK) prank[i] = atomicAdd(&pc_sh[s * nr + r], 1u);
     }
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -410,9 +429,23 @@ k_prep(const int32_t* __restrict__ offsets, const uint8_t* __restrict__ sector,
         }
         __syncthreads();
         // (a rejected cluster keeps an undefined rank: the call fails with TPC_ERR_DATA)
-        for (int i = i0; i < i1; i += di) {
-            const int s = sector[i], r = row[i];
-            if (s < ns && r < nr) prank[i] += pc_sh[s * nr + r];
+        for (int ib = i0; ib < i1; ib += PREP_U * di) {
+            int sv[PREP_U], rv[PREP_U];
+            uint32_t kv[PREP_U];
+#pragma unroll
+            for (int u = 0; u < PREP_U; u++) {
+                const int i = ib + u * di;
+                if (i < i1) {
+                    sv[u] = sector[i];
+                    rv[u] = row[i];
+                    kv[u] = prank[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PREP_U; u++) {
+                const int i = ib + u * di;
+                if (i < i1 && sv[u] < ns && rv[u] < nr) prank[i] = kv[u] + pc_sh[sv[u] * nr + rv[u]];
+            }
         }
     }
 }
@@ -544,9 +577,32 @@ __global__ void k_pscatter(int n, const uint8_t* __restrict__ sector, const uint
                            float4* __restrict__ pbuf, const Frame* __restrict__ f)
 {
     if (f->err) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t pg = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
-        pbuf[pstart[(size_t)pg * PSPLIT] + prank[i]] = make_float4(y[i], zlin[i], __int_as_float(i), __uint_as_float(pg));
+    // PSC_U clusters per thread and round: their loads, then their plane
+    // starts, are in flight together (the kernel is bound by the latency of
+    // the dependent plane-start gather)
+    constexpr int PSC_U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ib < n; ib += PSC_U * stride) {
+        uint32_t pg[PSC_U], rk[PSC_U], ps[PSC_U];
+        float yv[PSC_U], zv[PSC_U];
+#pragma unroll
+        for (int u = 0; u < PSC_U; u++) {
+            const int64_t i = ib + u * stride;
+            if (i < n) {
+                pg[u] = (uint32_t)cfr[i] * (uint32_t)np + (uint32_t)(sector[i] * nr + row[i]);
+                rk[u] = prank[i];
+                yv[u] = y[i];
+                zv[u] = zlin[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PSC_U; u++)
+            if (ib + u * stride < n) ps[u] = pstart[(size_t)pg[u] * PSPLIT];
+#pragma unroll
+        for (int u = 0; u < PSC_U; u++) {
+            const int64_t i = ib + u * stride;
+            if (i < n) pbuf[ps[u] + rk[u]] = make_float4(yv[u], zv[u], __int_as_float((int)i), __uint_as_float(pg[u]));
+        }
     }
 }
 
@@ -822,28 +878,54 @@ __global__ void k_clean_starts(int n, const int32_t* __restrict__ upr, const int
                                int cap, Frame* f)
 {
     if (f->err) return;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const int h = base + threadIdx.x;
-        bool is = false;
-        if (h < n) {
-            const int u = upr[h], d = dnr[h];
-            const int uc = (u >= 0 && dnr[u] == h) ? u : -1;
-            const int dc = (d >= 0 && upr[d] == h) ? d : -1;
-            up[h] = uc;
-            dn[h] = dc;
-            if (uc >= 0 && dc < 0) {
-                const int uu = upr[uc];
-                is = uu >= 0 && dnr[uu] == uc;      // the up neighbour keeps its up link
+    // CS_U hits per thread and round: each level of the dependent link reads
+    // (own links, the neighbours' back links, the up neighbour's up link and
+    // its back link) is in flight for all of them together
+    constexpr int CS_U = 4;
+    const int stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)CS_U * stride) {
+        int uv[CS_U], dv[CS_U], bu[CS_U], bd[CS_U];
+#pragma unroll
+        for (int k = 0; k < CS_U; k++) {
+            const int64_t h = base + (int64_t)k * stride + threadIdx.x;
+            uv[k] = -1;
+            dv[k] = -1;
+            if (h < n) {
+                uv[k] = upr[h];
+                dv[k] = dnr[h];
             }
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, is);
-        int pos0 = 0;
-        const int lane = threadIdx.x & 31;
-        if (lane == 0 && mask) pos0 = atomicAdd(&f->n_starts, __popc(mask));
-        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-        if (is) {
-            const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
-            if (pos < cap) starts[pos] = h;
+#pragma unroll
+        for (int k = 0; k < CS_U; k++) {
+            bu[k] = uv[k] >= 0 ? dnr[uv[k]] : -1;
+            bd[k] = dv[k] >= 0 ? upr[dv[k]] : -1;
+        }
+        int uc[CS_U], uu[CS_U];
+#pragma unroll
+        for (int k = 0; k < CS_U; k++) {
+            const int64_t h = base + (int64_t)k * stride + threadIdx.x;
+            uc[k] = (uv[k] >= 0 && bu[k] == h) ? uv[k] : -1;
+            const int dc = (dv[k] >= 0 && bd[k] == h) ? dv[k] : -1;
+            if (h < n) {
+                up[h] = uc[k];
+                dn[h] = dc;
+            }
+            // a start candidate: kept up link, no kept down link
+            uu[k] = (uc[k] >= 0 && dc < 0) ? upr[uc[k]] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < CS_U; k++) {
+            const int64_t h = base + (int64_t)k * stride + threadIdx.x;
+            const bool is = uu[k] >= 0 && dnr[uu[k]] == uc[k];      // the up neighbour keeps its up link
+            const unsigned mask = __ballot_sync(0xffffffffu, is);
+            int pos0 = 0;
+            if (lane == 0 && mask) pos0 = atomicAdd(&f->n_starts, __popc(mask));
+            pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+            if (is) {
+                const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
+                if (pos < cap) starts[pos] = (int)h;
+            }
         }
     }
 }
