@@ -1946,20 +1946,36 @@ __global__ void k_seg_fill(AsmArgs A)
         const int nh = A.t_nhits[t], nup = A.t_nup[t];
         const int32_t* slot = A.t_hits + (int64_t)t * A.nr;
         uint32_t o = A.tcount[r] + (uint32_t)A.segoff[b];
-        for (int k0 = 0; k0 < nh; k0 += 32) {
-            const unsigned m = A.ownmask[(int64_t)(k0 >> 5) * A.ntcap + t];   // bits past nh are 0
-            if ((m >> lane) & 1u) {
-                const int h = trk_hit(slot, A.nr, nh, nup, k0 + lane);
-                const uint32_t q = o + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                const float4 c = A.sc[h];
-                const int id = sc_id(c);
-                const int pl = (int)(sc_plane(c) % (uint32_t)A.np);
-                const int sec = pl / A.nr;
-                A.tcl[q] = make_float4(c.x, c.y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
-                A.clus_index[q] = id;
-                A.assign[id] = r;
+        // SF_U rounds of 32 hits at a time: their owned-hit words, slot reads
+        // and cluster records are each in flight together
+        constexpr int SF_U = 4;
+        for (int k0 = 0; k0 < nh; k0 += 32 * SF_U) {
+            unsigned m[SF_U];
+            int hh[SF_U];
+            float4 c[SF_U];
+#pragma unroll
+            for (int u = 0; u < SF_U; u++) {
+                const int kk = k0 + 32 * u;
+                m[u] = kk < nh ? A.ownmask[(int64_t)(kk >> 5) * A.ntcap + t] : 0u;   // bits past nh are 0
             }
-            o += (uint32_t)__popc(m);
+#pragma unroll
+            for (int u = 0; u < SF_U; u++) hh[u] = ((m[u] >> lane) & 1u) ? trk_hit(slot, A.nr, nh, nup, k0 + 32 * u + lane) : -1;
+#pragma unroll
+            for (int u = 0; u < SF_U; u++)
+                if (hh[u] >= 0) c[u] = A.sc[hh[u]];
+#pragma unroll
+            for (int u = 0; u < SF_U; u++) {
+                if (hh[u] >= 0) {
+                    const uint32_t q = o + (uint32_t)__popc(m[u] & ((1u << lane) - 1u));
+                    const int id = sc_id(c[u]);
+                    const int pl = (int)(sc_plane(c[u]) % (uint32_t)A.np);
+                    const int sec = pl / A.nr;
+                    A.tcl[q] = make_float4(c[u].x, c[u].y, A.rowtab[(pl - sec * A.nr) * ROWTAB], __int_as_float(sec));
+                    A.clus_index[q] = id;
+                    A.assign[id] = r;
+                }
+                o += (uint32_t)__popc(m[u]);
+            }
         }
     }
 }
