@@ -592,7 +592,8 @@ def run_ours(args, ws, rank, local, pg):
         "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_collisions": args.collisions, "clusters": n, "tracks_found": n_tracks,
+        "config": {"workload": WORKLOAD if args.collisions == 50 else WORKLOAD.replace("50-collision", f"{args.collisions}-collision"),
+                   "n_collisions": args.collisions, "clusters": n, "tracks_found": n_tracks,
                    "collisions_per_s": args.collisions * ws * args.steps / (ms_max / 1e3),
                    "ms_per_frame": ms_max / args.steps,
                    "l2": "inputs (10 B/cluster, 160 MB) and workspace exceed the 126 MB L2; no flush",
