@@ -19,11 +19,13 @@
  *   - Pointers named "device" are CUDA device memory owned by the caller;
  *     the library never frees them and never allocates device memory.
  *   - All work is enqueued on the caller's stream (a cudaStream_t passed as
- *     void*; NULL = legacy default stream).  The tracking calls fork one
- *     stage (the cluster rejection, beside the merger) onto a side stream of
- *     the library and join it back before the next stage, with events, so
- *     the work still completes in `stream`'s order and a stream capture of
- *     the call holds both branches.  The side stream and its two events are
+ *     void*; NULL = legacy default stream).  The tracking calls fork some
+ *     independent work (buffer initialisation beside the tracklet stage, the
+ *     cluster rejection beside the merger, the refit order beside the
+ *     cluster-list fill) onto a side stream of the library and join it back
+ *     before its results are used, with events, so the work still completes
+ *     in `stream`'s order and a stream capture of the call holds both
+ *     branches.  The side stream and its two events are
  *     created at the first call for each (device, caller stream) and kept
  *     until the process exits.
  *   - Return value: TPC_OK (0) or a negative TPC_ERR_* code; no exception

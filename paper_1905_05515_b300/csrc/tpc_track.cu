@@ -2784,12 +2784,17 @@ namespace {
 
 // Enqueue the whole chain on `st` (no host synchronisation, no pageable copy:
 // capturable in a CUDA graph once the tables are in the workspace).
-// Side stream of a caller's stream, with a fork and a join event: the cluster
-// rejection (it rewrites the owned-hit masks and counts) runs there beside the
-// merger (it reads the segment ends), which share no data.  One per (device,
-// caller stream), created on first use and kept for the life of the process;
-// the creation switches this thread to relaxed capture mode, so a first use
-// inside a stream capture is allowed.
+// Side stream of a caller's stream, with a fork and a join event, for work
+// that shares no data with the main stream's stage at the time: the
+// initialisation of the later stages' buffers (beside the tracklet
+// constructor), the cluster rejection (it rewrites the owned-hit masks and
+// counts; beside the merger, which reads the segment ends) and the refit
+// order (beside the fill of the cluster lists).  Each use forks from and
+// joins back into the caller's stream, so the work completes in that stream's
+// order and a stream capture holds both branches.  One per (device, caller
+// stream), created on first use and kept for the life of the process; the
+// creation switches this thread to relaxed capture mode, so a first use inside
+// a stream capture is allowed.
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
