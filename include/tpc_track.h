@@ -217,6 +217,14 @@ typedef struct {
                                     chi2 evaluations */
     int32_t n_rejected;          /* clusters the rejection before the refit took out of their tracks
                                     (tpc_track, tpc_track_batched) */
+    /* nullable input: a cudaEvent_t (passed as void*) that the tracking calls record on `stream`
+     * once every input of the track refit is complete, just before the refit (after it only the
+     * refit and the optional looper-leg and attachment stages run).  A caller streaming frames
+     * through separate workspaces and outputs may let the next frame's chain wait on this event
+     * instead of on the end of the call: the next frame's first stages then run beside this
+     * frame's refit, whose last long tracks keep few SMs busy.  Not recorded when the call fails
+     * before the refit. */
+    void *refit_event;
 } tpc_tracks;
 
 #define TPC_MAX_CLUSTERS 2145386495LL   /* INT32_MAX - 2^21 */

@@ -60,7 +60,7 @@ class TpcTracks(C.Structure):
                 ("n_tracks", C.c_int32), ("n_tracklets", C.c_int32), ("n_segments", C.c_int32),
                 ("tracklets_needed", C.c_int64), ("tracks_needed", C.c_int64), ("clusters_needed", C.c_int64),
                 ("n_launches", C.c_int32), ("stage_ms", C.c_float * 10), ("work", C.c_int64 * 5),
-                ("n_rejected", C.c_int32)]
+                ("n_rejected", C.c_int32), ("refit_event", C.c_void_p)]
 
 class TpcCalibTracks(C.Structure):
     _fields_ = [("n_tracks", C.c_int32), ("sector", C.c_void_p), ("x", C.c_void_p), ("param", C.c_void_p),

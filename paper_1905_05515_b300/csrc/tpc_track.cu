@@ -3052,6 +3052,7 @@ int enqueue(const tpc_params* p, const tpc_geometry* g, float bz, float v_drift,
     CK(mark(8));
     // a9: refit
     CK(cudaStreamWaitEvent(st, side.join, 0));
+    if (out->refit_event) CK(cudaEventRecord(static_cast<cudaEvent_t>(out->refit_event), st));
     int rr = tpc_launch_refit(p, g, bz, AA.tcl, order, f, AA.ttail, TA.t_top, out,
                               std::min(out->capacity_tracks, ntcap), st);
     if (rr) return rr;

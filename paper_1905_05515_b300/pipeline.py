@@ -6,8 +6,11 @@ each with its own CUDA stream, device input buffers, workspace and output
 buffers: while one slot's frame is being tracked, the next frame's clusters
 are copied in on another slot's stream and the previous frame's tracks are
 copied out, so the copies run beside the tracking instead of between frames.
-The tracking itself runs one frame at a time (each slot's chain waits for the
-previous frame's), so frames do not compete for the SMs and the L2.
+The tracking runs one frame at a time up to the refit: each slot's chain waits
+for the event the library records when the previous frame's refit starts
+(tpc_tracks.refit_event), so a frame's first stages run beside the previous
+frame's refit, whose last long tracks keep few SMs busy, while frames do not
+otherwise compete for the SMs and the L2.
 
 A push enqueues, on its slot's stream and without host synchronisation, the
 host-to-device copies, tpc_prepare_async and tpc_track_async, and a copy of
@@ -83,8 +86,12 @@ class _Slot:
         self.counts = torch.zeros(8, dtype=torch.int32, device=d)
         self.h_counts = torch.zeros(8, dtype=torch.int32).pin_memory()
         self.counts_ready = torch.cuda.Event()
-        self.tracked = torch.cuda.Event()
         self.done = torch.cuda.Event()
+        # recorded by the library when this slot's frame starts its refit; the
+        # first record on the slot's stream creates the CUDA event
+        self.refit_started = torch.cuda.Event()
+        self.refit_started.record(self.stream)
+        self.out.refit_event = self.refit_started.cuda_event
         sz = C.c_size_t(0)
         rc = pipe.lib.tpc_prepare_staging_size(1, C.byref(sz))
         if rc:
@@ -154,8 +161,10 @@ class FramePipeline:
         with torch.cuda.stream(st):
             for k, a in srcs.items():
                 s.ins[k][:n].copy_(a, non_blocking=True)
-            # one frame tracked at a time (frames tracked side by side share the
-            # SMs and the L2 and are slower together); the copies overlap
+            # one frame tracked at a time up to its refit (frames tracked side by
+            # side share the SMs and the L2 and are slower together); the copies
+            # overlap, and so do this frame's first stages and the previous
+            # frame's refit
             if self.last_tracked is not None:
                 st.wait_event(self.last_tracked)
             rc = self.lib.tpc_prepare_async(C.byref(self.params), C.byref(self.geometry), n, 1,
@@ -171,8 +180,7 @@ class FramePipeline:
                                           C.c_void_p(s.counts.data_ptr()), h)
             if rc:
                 raise abi.TpcError(rc, "tpc_track_async")
-            s.tracked.record(st)
-            self.last_tracked = s.tracked
+            self.last_tracked = s.refit_started
             s.h_counts.copy_(s.counts, non_blocking=True)
             s.counts_ready.record(st)
         self.n_launches += int(s.out.n_launches)
